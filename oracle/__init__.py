@@ -1,0 +1,281 @@
+"""ORACLE -- test infrastructure only.
+
+A plain, slow CPU implementation of the level-line Newton splitting of the
+hyperbolic polynomials p_n and the simplified Misiurewicz polynomials
+s_{l,n} = p_{l+n-1} + p_{l-1} (Mihalache & Vigneron, arXiv 2402.06083,
+Sec. 4 and Sec. 6.3), plus the closed-form counts the paper gives.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library under ``paper_2402_06083_gb300/`` and never imports it.
+
+The arithmetic lives in ``mt_oracle.c`` (binary128 by default, binary64 for
+the timed baseline); this module only loads it with ctypes and wraps the
+results in numpy arrays.  ``counts.py`` holds the closed-form counts
+(Thm countingHyp, eq. MisCount, eq. MisDeg).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+from . import counts  # noqa: F401  (re-export)
+from .counts import (deg_s, divisors, eps_dup_default, hyp_count, mis_count,  # noqa: F401
+                     mobius, period_histogram, phi, type_histogram_s)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mt_oracle.c")
+_LOCK = threading.Lock()
+_LIBS: dict[bool, ctypes.CDLL] = {}
+
+
+def lib_path(fp64: bool) -> str:
+    return os.path.join(_HERE, "_build", "liboracle_%s.so" % ("fp64" if fp64 else "q"))
+
+
+def build(force: bool = False) -> None:
+    """Compile both precisions of the oracle with gcc (no CUDA involved)."""
+    os.makedirs(os.path.join(_HERE, "_build"), exist_ok=True)
+    for fp64 in (False, True):
+        out = lib_path(fp64)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        cmd = ["gcc", "-O2", "-shared", "-fPIC", "-o", out + ".tmp", _SRC]
+        if fp64:
+            cmd.insert(1, "-DORACLE_FP64")
+        if os.uname().machine in ("x86_64", "i686") and not fp64:
+            cmd.append("-lquadmath")
+        cmd.append("-lm")
+        subprocess.check_call(cmd)
+        os.replace(out + ".tmp", out)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_long) for name in (
+        "degree", "n_roots", "n_real", "n_starts", "n_conv", "n_repeat", "n_diverge",
+        "n_timeout", "walk_newton", "desc_newton", "walk_fail")] + [
+        ("M", ctypes.c_int), ("cL", ctypes.c_int), ("retries", ctypes.c_int),
+        ("endpoint_ok", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def build_mutant(k: int, outdir: str) -> str:
+    """Build a copy of the oracle with planted mistake number k (1..5) into
+    outdir; used only by the test that shows the pins catch such mistakes."""
+    out = os.path.join(outdir, "liboracle_mutant%d.so" % k)
+    cmd = ["gcc", "-O2", "-shared", "-fPIC", "-DORACLE_MUTANT=%d" % k, "-o", out, _SRC]
+    if os.uname().machine in ("x86_64", "i686"):
+        cmd.append("-lquadmath")
+    cmd.append("-lm")
+    subprocess.check_call(cmd)
+    return out
+
+
+def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.or_degree.restype = ctypes.c_long
+    L.or_degree.argtypes = [ctypes.c_int] * 3
+    L.or_eval.restype = ctypes.c_int
+    L.or_eval.argtypes = [ctypes.c_int] * 3 + [dp, dp]
+    L.or_eval_pk.restype = ctypes.c_int
+    L.or_eval_pk.argtypes = [ctypes.c_int, dp, dp]
+    L.or_real_endpoint.restype = ctypes.c_int
+    L.or_real_endpoint.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, dp]
+    L.or_split.restype = ctypes.c_long
+    L.or_split.argtypes = ([ctypes.c_int] * 5 + [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.c_double]
+                           + [dp, ctypes.c_long, ip, ip, dp, ctypes.c_long, ctypes.POINTER(Stats)])
+    L.or_polish.restype = ctypes.c_int
+    L.or_polish.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_int, dp, dp]
+    L.or_classify.restype = ctypes.c_int
+    L.or_classify.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_double, ip, ip]
+    L.or_count_in_disk.restype = ctypes.c_long
+    L.or_count_in_disk.argtypes = [dp, ctypes.c_long, dp, ctypes.c_double]
+    L.or_precision_bits.restype = ctypes.c_int
+    return L
+
+
+_OVERRIDE: list = []
+
+
+class use_library:
+    """Context manager that routes every call of this module through another
+    build of the oracle (a planted-mistake copy in the mutant test)."""
+
+    def __init__(self, path: str):
+        self.L = _declare(ctypes.CDLL(path))
+
+    def __enter__(self):
+        _OVERRIDE.append(self.L)
+        return self
+
+    def __exit__(self, *exc):
+        _OVERRIDE.pop()
+
+
+def _lib(fp64: bool = False) -> ctypes.CDLL:
+    if _OVERRIDE:
+        return _OVERRIDE[-1]
+    with _LOCK:
+        if fp64 in _LIBS:
+            return _LIBS[fp64]
+        build()
+        L = ctypes.CDLL(lib_path(fp64))
+        _LIBS[fp64] = _declare(L)
+        return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _c4(c) -> np.ndarray:
+    """A point as (Re hi, Re lo, Im hi, Im lo); accepts complex or a 4-vector."""
+    if isinstance(c, (complex, float, int, np.complexfloating, np.floating)):
+        c = complex(c)
+        return np.array([c.real, 0.0, c.imag, 0.0], dtype=np.float64)
+    a = np.ascontiguousarray(c, dtype=np.float64)
+    assert a.shape == (4,)
+    return a
+
+
+def _kind_args(kind: str, l: int, n: int):
+    if kind == "hyp":
+        return 0, 0, n
+    if kind == "mis":
+        return 1, l, n
+    raise ValueError(kind)
+
+
+def degree(kind: str, n: int, l: int = 0) -> int:
+    k, ll, nn = _kind_args(kind, l, n)
+    return int(_lib().or_degree(k, ll, nn))
+
+
+def default_lambda0(kind: str) -> float:
+    """Outer level: 5 for p_n, 100 for the Misiurewicz family (Sec. 4.2)."""
+    return 5.0 if kind == "hyp" else 100.0
+
+
+def default_IN(kind: str) -> float:
+    """Newton cap factor I_N: 1 for p_n, 2.6 for the Misiurewicz family (Sec. 4.2)."""
+    return 1.0 if kind == "hyp" else 2.6
+
+
+def split(kind: str, n: int, l: int = 0, *, M: int = 8, cL: int = 4, lambda0: float | None = None,
+          I_N: float | None = None, eps_dup: float | None = None, max_retries: int = 2,
+          frac: float = 1.0, fp64: bool = False, want_starts: bool = False,
+          want_types: bool = True) -> dict:
+    """Split P (p_n for kind 'hyp', s_{l,n} for kind 'mis') with the oracle.
+
+    Returns a dict with 'roots' (complex128, the rounded values), 'roots4'
+    ([N, 4] Re hi, Re lo, Im hi, Im lo), 'type' ([N, 2] (preperiod, period)),
+    'stats' and optionally 'starts4' (upper-half level-line starts)."""
+    k, ll, nn = _kind_args(kind, l, n)
+    L = _lib(fp64)
+    d = int(L.or_degree(k, ll, nn))
+    if d <= 0:
+        raise ValueError("bad polynomial")
+    lam = default_lambda0(kind) if lambda0 is None else lambda0
+    IN = default_IN(kind) if I_N is None else I_N
+    eps = eps_dup_default(kind, n, l, bits=53 if fp64 else 113) if eps_dup is None else eps_dup
+    cap = d
+    roots4 = np.zeros((cap, 4), dtype=np.float64)
+    ta = np.zeros(cap, dtype=np.int32)
+    tb = np.zeros(cap, dtype=np.int32)
+    scap = (cL << max_retries) * d // 2 + 2 if want_starts else 0
+    starts4 = np.zeros((max(scap, 1), 4), dtype=np.float64)
+    st = Stats()
+    nr = L.or_split(k, ll, nn, M, cL, lam, IN, eps, max_retries, frac, _dp(roots4), cap,
+                    _ip(ta) if want_types else None, _ip(tb) if want_types else None,
+                    _dp(starts4) if want_starts else None, scap, ctypes.byref(st))
+    if nr < 0:
+        raise RuntimeError("oracle split failed (%d)" % nr)
+    m = min(nr, cap)
+    out = {
+        "roots4": roots4[:m].copy(),
+        "roots": roots4[:m, 0] + 1j * roots4[:m, 2],
+        "n_roots": int(nr),
+        "stats": st.as_dict(),
+        "eps_dup": eps,
+    }
+    if want_types:
+        out["type"] = np.stack([ta[:m], tb[:m]], axis=1)
+    if want_starts:
+        ns = min(int(st.n_starts), scap)
+        out["starts4"] = starts4[:ns].copy()
+        out["starts"] = starts4[:ns, 0] + 1j * starts4[:ns, 2]
+    return out
+
+
+def evaluate(kind: str, n: int, c, l: int = 0, fp64: bool = False):
+    """(P(c), P'(c)) as 4-vectors (hi/lo of Re and Im) each."""
+    k, ll, nn = _kind_args(kind, l, n)
+    out = np.zeros(8, dtype=np.float64)
+    if _lib(fp64).or_eval(k, ll, nn, _dp(_c4(c)), _dp(out)) != 0:
+        raise ValueError("bad polynomial")
+    return out[:4].copy(), out[4:].copy()
+
+
+def evaluate_pk(k: int, c, fp64: bool = False):
+    out = np.zeros(8, dtype=np.float64)
+    _lib(fp64).or_eval_pk(k, _dp(_c4(c)), _dp(out))
+    return out[:4].copy(), out[4:].copy()
+
+
+def real_endpoint(kind: str, n: int, l: int = 0, lambda0: float | None = None, fp64: bool = False):
+    k, ll, nn = _kind_args(kind, l, n)
+    out = np.zeros(2, dtype=np.float64)
+    lam = default_lambda0(kind) if lambda0 is None else lambda0
+    _lib(fp64).or_real_endpoint(k, ll, nn, lam, _dp(out))
+    return out
+
+
+def polish(kind: str, n: int, c, l: int = 0, steps: int = 3):
+    """Newton-polish one point in binary128; returns (4-vector, displacement)."""
+    k, ll, nn = _kind_args(kind, l, n)
+    out = np.zeros(4, dtype=np.float64)
+    disp = ctypes.c_double(0)
+    rc = _lib().or_polish(k, ll, nn, _dp(_c4(c)), steps, _dp(out), ctypes.byref(disp))
+    if rc != 0:
+        raise FloatingPointError("polish diverged")
+    return out, disp.value
+
+
+def classify(kind: str, n: int, c, l: int = 0, tau: float = 0.0, fp64: bool = False):
+    k, ll, nn = _kind_args(kind, l, n)
+    a = ctypes.c_int(0)
+    b = ctypes.c_int(0)
+    _lib(fp64).or_classify(k, ll, nn, _dp(_c4(c)), tau, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def count_in_disk(roots4: np.ndarray, c, r: float) -> int:
+    r4 = np.ascontiguousarray(roots4, dtype=np.float64)
+    return int(_lib().or_count_in_disk(_dp(r4), r4.shape[0], _dp(_c4(c)), r))
+
+
+def precision_bits(fp64: bool = False) -> int:
+    return int(_lib(fp64).or_precision_bits())
+
+
+def join4(a: np.ndarray):
+    """4-vectors -> (Re, Im) as pairs of float64 hi + lo (for mpmath use)."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1, 4)
+    return a[:, 0], a[:, 1], a[:, 2], a[:, 3]
+
+
+if __name__ == "__main__":  # pragma: no cover
+    build(force="--force" in sys.argv)
+    print("oracle built:", lib_path(False), lib_path(True))

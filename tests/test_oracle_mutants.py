@@ -1,0 +1,31 @@
+"""The pins are sensitive: each planted mistake in a copy of the oracle (built
+on the CPU with -DORACLE_MUTANT=k) fails at least one pin of
+test_oracle_pins.py.  Mutants: 1 derivative from the wrong orbit index,
+2 wrong sign in Re(z^2), 3 s_{l,n} built with p_l instead of p_{l-1},
+4 level line walked the wrong way, 5 missing conjugate fold."""
+from __future__ import annotations
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+# (mutant, pin function, its arguments)
+CASES = [
+    (1, pins.test_orbit_at_minus_two, (5,)),
+    (2, pins.test_period3_cardano, ()),
+    (2, pins.test_orbit_off_axis_against_integer_polynomial, ()),
+    (3, pins.test_tiny_misiurewicz, ()),
+    (3, pins.test_s_2_4_example, ()),
+    (4, pins.test_level_line_iso_angle_zero, (4,)),
+    (5, pins.test_counts_and_exact_periods, (8,)),
+]
+
+
+@pytest.mark.parametrize("k,pin,args", CASES, ids=[f"mutant{k}-{p.__name__}" for k, p, _ in CASES])
+def test_pin_catches_planted_mistake(tmp_path, k, pin, args):
+    path = oracle.build_mutant(k, str(tmp_path))
+    with oracle.use_library(path):
+        with pytest.raises(Exception):
+            pin(*args)
+    pin(*args)  # and the real oracle still passes
