@@ -1,0 +1,215 @@
+/*
+ * mtsplit.h -- C ABI of the GB300 level-line Newton splitter.
+ *
+ * Finds every root of the hyperbolic polynomials
+ *     p_0 = 0,  p_{k+1}(c) = p_k(c)^2 + c,   deg p_n = 2^(n-1)
+ * (Mihalache & Vigneron, "How to split a tera-polynomial", Sec. 1,
+ * eq. def:hyp_poly) and of the simplified Misiurewicz polynomials
+ *     s_{l,n} = q_{l,n} / q_{l-1,n} = p_{l+n-1} + p_{l-1},  deg = 2^(l+n-2)
+ * (eq. polySimple, eq. polyMisSimple), with the method of Sec. 4:
+ * a discrete level line |P| = lambda0 (eq. defDiscreteLev) walked with the
+ * Newton-with-target map (Prop. computeLevelLine), Newton descents from
+ * c_L points per root (Algorithm S_par), a separated sorted set of roots
+ * (Sec. 6.1, eq. nsetAsumption), and a disk-arithmetic certificate per root
+ * (Thm proofRoots, Thm diskArithmetic).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are DEVICE pointers (any CUDA allocation; the
+ *    Python binding uses torch tensors).  The caller owns every buffer; the
+ *    library never allocates or frees device memory.  Host pointers are
+ *    named h_* or are plain scalars / structs.
+ *  - Work runs asynchronously on opts->stream (a cudaStream_t; NULL = the
+ *    legacy default stream).  Entry points that return counts (n_out,
+ *    stats) synchronise that stream before returning.
+ *  - Roots are complex128 in torch layout: d_roots[2*i] = Re, d_roots[2*i+1]
+ *    = Im.  A split returns ALL roots of P (conjugates included, divisor
+ *    periods included), sorted by (Re, Im) (eq. defLexi); real roots have
+ *    Im = +0.0.  d_roots_lo (optional, same layout) receives the low parts
+ *    of double-double roots (zeros in plain FP64 mode).
+ *  - Workspace: d_work / work_bytes is caller-provided scratch of at least
+ *    mt_workspace_bytes(...) bytes, 256-byte aligned.  Its contents are
+ *    undefined on entry and on exit; calls sharing a workspace must be
+ *    ordered on one stream.
+ *  - Errors: no exception crosses the ABI.  Every function returns an
+ *    mt_status; mt_last_error() gives a thread-local message for the last
+ *    failure on the calling thread.
+ */
+#ifndef MTSPLIT_H
+#define MTSPLIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MT_API __attribute__((visibility("default")))
+#else
+#define MT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MT_OK = 0,
+  MT_EINVAL = 1,       /* argument outside the domain (n, l, sizes, options)      */
+  MT_ENOMEM = 2,       /* workspace smaller than mt_workspace_bytes()              */
+  MT_ECAPACITY = 3,    /* cap < number of roots; *n_out holds the required size    */
+  MT_ECUDA = 4,        /* a CUDA call failed (message in mt_last_error())          */
+  MT_EINCOMPLETE = 5,  /* root count != degree after all retries                   */
+  MT_ETIMEOUT = 6,     /* a bounded device loop hit its iteration limit            */
+  MT_ECERT = 7         /* at least one root failed the disk certificate            */
+} mt_status;
+
+typedef enum {
+  MT_FP64 = 0,   /* every step in binary64                                      */
+  MT_MIXED = 1,  /* binary32 level-line tracking and early Newton, binary64 finish */
+  MT_DD = 2      /* binary64 with double-double for the clustered roots          */
+} mt_precision;
+
+/* Options.  Fill with mt_default_options() and override fields. */
+typedef struct {
+  int prec;            /* mt_precision                                              */
+  double tol;          /* Newton stop: |step| < tol (0 -> 1e-13 FP64, 1e-26 DD)     */
+  double lambda0;      /* outer level (0 -> 5 for p_n, 100 for s_{l,n}; Sec. 4.2)   */
+  int M;               /* level-line points per turn (0 -> 8; Sec. 6.3.1)          */
+  int c_L;             /* descents per root (0 -> 4; Sec. 4.2)                      */
+  int chunk_log2;      /* log2 of level-line points walked per lane (0 -> auto)     */
+  int block;           /* CUDA block size for the Newton kernels (0 -> auto)        */
+  int max_retries;     /* doublings of (M, c_L) when roots are missing (default 1)  */
+  double eps_dup;      /* separation of the root set (0 -> rule of the library)     */
+  double cert_tol;     /* certificate radius cap (0 -> 1e-12 FP64, 1e-20 DD)       */
+  int use_graph;       /* 1: capture the launch sequence in a CUDA graph and replay */
+  void* stream;        /* cudaStream_t                                              */
+} mt_options;
+
+#define MT_MAX_TYPES 64
+
+/* Counters of one call (host struct, filled before return). */
+typedef struct {
+  int64_t degree;          /* deg P                                               */
+  int64_t n_roots;         /* distinct roots found (full list)                    */
+  int64_t n_real;          /* real roots among them                               */
+  int64_t n_starts;        /* descents started (upper half of the level line)     */
+  int64_t n_conv;          /* descents that converged                             */
+  int64_t n_repeat;        /* converged descents that hit an already found root   */
+  int64_t n_diverge;       /* descents stopped by a long jump / non-finite value  */
+  int64_t n_timeout;       /* descents stopped by the iteration cap               */
+  int64_t walk_newton;     /* Newton steps on the level line (seeds + walk)       */
+  int64_t desc_newton;     /* Newton steps in descents (all tiers)                */
+  int64_t steps_fp32;      /* of which in binary32                                */
+  int64_t steps_dd;        /* of which in double-double                           */
+  int64_t walk_fail;       /* level-line chunks whose end missed the next seed    */
+  int64_t n_cert_pass;     /* roots (full list) that passed the disk certificate  */
+  int64_t count_by_type[MT_MAX_TYPES]; /* p_n: [k] = roots of exact period k;
+                                          s_{l,n}: [k] = Mis(l,k), [32+k] = Hyp(k) */
+  int32_t M, c_L;          /* values finally used                                  */
+  int32_t retries;         /* (M, c_L) doublings performed                         */
+  int32_t n_chunks;        /* level-line chunks (lanes of the walk)                */
+  int64_t n_launches;      /* CUDA kernels launched by the call                    */
+  double max_cert_radius;  /* largest certified radius                             */
+  double min_cert_radius;  /* smallest certified radius                            */
+  double eps_dup;          /* separation used                                      */
+  float ms_total;          /* device time of the call (CUDA events)                */
+  float ms_walk;           /* device time of seeds + level-line walk               */
+  float ms_descend;        /* device time of the Newton descents                   */
+  float ms_dedup;          /* device time of fold + sort + cluster + emit          */
+  float ms_certify;        /* device time of classify + certify                    */
+} mt_stats;
+
+/* Defaults documented field by field above. */
+MT_API void mt_default_options(mt_options* opts);
+
+/* deg p_n = 2^(n-1) (n in [1, 40]); -1 if out of range. */
+MT_API int64_t mt_degree_hyperbolic(int n);
+/* deg s_{l,n} = 2^(l+n-2) (l >= 2, n >= 1, l + n <= 41); -1 if out of range. */
+MT_API int64_t mt_degree_misiurewicz(int l, int n);
+
+/* Scratch bytes a split of P needs (kind 0: p_n, kind 1: s_{l,n}) with these
+   options; 0 if the arguments are invalid. */
+MT_API size_t mt_workspace_bytes(int kind, int l, int n, const mt_options* opts);
+
+/* Split p_n (Sec. 4.2, Algorithm S_par; hypQuick of Sec. 6.3.1).
+   d_roots: [cap][2] doubles, receives all 2^(n-1) roots sorted by (Re, Im).
+   d_roots_lo: NULL or [cap][2]: low parts in MT_DD mode.
+   *n_out: number of roots written (or required size on MT_ECAPACITY).
+   stats: optional.  Returns MT_EINCOMPLETE if roots are still missing after
+   opts->max_retries doublings, MT_ECERT if a root failed its certificate. */
+MT_API mt_status mt_split_hyperbolic(int n, const mt_options* opts, double* d_roots, double* d_roots_lo,
+                              int64_t cap, void* d_work, size_t work_bytes, int64_t* n_out,
+                              mt_stats* stats);
+
+/* Split s_{l,n} = p_{l+n-1} + p_{l-1} (eq. polySimple; misSimpleQuick of
+   Sec. 6.3.1).  d_is_mis: NULL or [cap] bytes, 1 where the root lies in
+   Mis(l,n) (eq. def:mis), 0 for the other roots of s_{l,n} (Hyp(k),
+   k | gcd(n, l-1), and Mis(l,k), k | n, k < n). */
+MT_API mt_status mt_split_misiurewicz(int l, int n, const mt_options* opts, double* d_roots,
+                               double* d_roots_lo, int64_t cap, uint8_t* d_is_mis, void* d_work,
+                               size_t work_bytes, int64_t* n_out, mt_stats* stats);
+
+/* Split every s_{l,n} with l >= 2, n >= 1, l + n <= max_order in ONE pass:
+   one persistent launch drains the level-line chunks of all polynomials,
+   one persistent launch drains all descents.  Roots of pair number p (pairs
+   ordered by l, then n) are d_roots[h_offsets[p] .. h_offsets[p+1]).
+   h_offsets: host array of npairs + 1 entries (npairs = number of pairs).
+   stats: optional array of npairs entries. */
+MT_API int mt_misiurewicz_pairs(int max_order, int* h_l, int* h_n, int capacity);
+MT_API size_t mt_workspace_bytes_misiurewicz_batch(int max_order, const mt_options* opts);
+MT_API mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, double* d_roots,
+                                     double* d_roots_lo, int64_t cap, uint8_t* d_is_mis,
+                                     void* d_work, size_t work_bytes, int64_t* h_offsets,
+                                     mt_stats* stats);
+
+/* Certify given roots of P (kind 0: p_n, kind 1: s_{l,n}) with the disk
+   test of Thm proofRoots evaluated in disk arithmetic (Thm diskArithmetic):
+   root j gets the radius r_j = min(tol, 0.45 * distance to the nearest other
+   root or conjugate) and passes iff r_j * dist(0, B') > sup |P(c_j)| where
+   B' encloses P'(D(c_j, r_j)).  Passing disks are pairwise disjoint, so
+   count == degree with every root passing proves the list complete
+   (Thm certif).  d_roots: [count][2] (any order); d_roots_lo: NULL or
+   [count][2]; d_pass: [count] bytes; d_radius: [count] doubles (NULL
+   allowed).  *n_pass receives the number of passing roots. */
+MT_API size_t mt_certify_workspace_bytes(int64_t count);
+MT_API mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double* d_roots_lo,
+                     int64_t count, double tol, uint8_t* d_pass, double* d_radius, void* d_work,
+                     size_t work_bytes, int64_t* n_pass, void* stream);
+
+/* ---- single steps of the path, exposed for parity checks ---------------- */
+
+/* Orbit evaluation (Sec. 1, eq. def:hyp_poly, and its c-derivative): for
+   each point d_c[2i], d_c[2i+1], writes d_out[4i..4i+3] = Re P, Im P,
+   Re P', Im P' in binary64.  No workspace. */
+MT_API mt_status mt_eval(int kind, int l, int n, const double* d_c, int64_t count, double* d_out,
+                  void* stream);
+
+/* Steps a1-a3 only: real end point, lifted seeds and the level-line walk.
+   d_starts: [cap][2], receives the (c_L/2) d + 1 starts of the upper half of
+   the discrete level line L_{lambda0, c_L d}(P) (eq. defDiscreteLev) in
+   external-angle order, start s satisfying P = lambda0 e^{2 i pi s / c_L}. */
+MT_API mt_status mt_level_line(int kind, int l, int n, const mt_options* opts, double* d_starts,
+                        int64_t cap, void* d_work, size_t work_bytes, int64_t* n_starts,
+                        mt_stats* stats);
+
+/* Step a4 only: Newton descent (eq. Newton) from each start, capped at
+   max{20, I_N log2 d}.  d_out: [count][2] final iterate; d_status: [count]
+   bytes (0 converged, 1 divergent, 2 timeout). */
+MT_API mt_status mt_descend(int kind, int l, int n, const mt_options* opts, const double* d_starts,
+                     int64_t count, double* d_out, uint8_t* d_status, void* d_work,
+                     size_t work_bytes, mt_stats* stats);
+
+/* Step a6 only: type of each root (eq. def:hyp / def:mis), d_type[i] =
+   period k for p_n, or k (Mis(l,k)) / 32 + k (Hyp(k)) for s_{l,n};
+   255 if no type was recognised.  tau: Newton-size threshold (0 -> default). */
+MT_API mt_status mt_classify(int kind, int l, int n, const double* d_roots, int64_t count, double tau,
+                      uint8_t* d_type, void* stream);
+
+/* Thread-local message of the last failure ("" if none). */
+MT_API const char* mt_last_error(void);
+
+/* Library version string. */
+MT_API const char* mt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTSPLIT_H */

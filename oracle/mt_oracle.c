@@ -90,9 +90,23 @@ static cplx csub(cplx a, cplx b) { return cx(a.re - b.re, a.im - b.im); }
 static cplx cmul(cplx a, cplx b) {
   return cx(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
 }
-/* Plain textbook quotient; the exponent range of binary128 makes the
-   squared modulus safe for every value met here. */
+/* Textbook quotient.  In binary128 the squared modulus never overflows for
+   the values met here; in binary64 |b|^2 overflows once |b| > 1e154 (orbits
+   that escaped), so both operands are first scaled by the same power of two
+   (exact), as the paper does when "simplifying a common large factor"
+   (Sec. 6.3.2, remark on the FP80 exponent range). */
 static cplx cdiv(cplx a, cplx b) {
+#if defined(ORACLE_FP64)
+  int e = 0;
+  real m = b.re < 0 ? -b.re : b.re;
+  real mi = b.im < 0 ? -b.im : b.im;
+  if (mi > m) m = mi;
+  if (m > 0 && m < HUGE_VAL) {
+    frexp(m, &e);
+    a = cx(ldexp(a.re, -e), ldexp(a.im, -e));
+    b = cx(ldexp(b.re, -e), ldexp(b.im, -e));
+  }
+#endif
   real den = b.re * b.re + b.im * b.im;
   return cx((a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den);
 }

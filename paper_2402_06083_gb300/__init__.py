@@ -1,0 +1,239 @@
+"""GB300-native level-line Newton splitting of the Mandelbrot polynomials.
+
+Python binding of the C ABI in include/mtsplit.h (libmtsplit.so, built from
+csrc/ for sm_103a).  PyTorch supplies device memory and the current stream;
+every step of the computation -- level line, Newton descents, root set,
+types, certificates -- runs in the library's CUDA kernels.  There is no CPU
+fallback: without the built library every call raises.
+
+Polynomials (Mihalache & Vigneron, arXiv 2402.06083):
+  p_n      = f_c^n(0),            deg 2^(n-1)        (eq. def:hyp_poly)
+  s_{l,n}  = p_{l+n-1} + p_{l-1}, deg 2^(l+n-2)      (eq. polySimple)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+from . import _lib
+from ._lib import MtError, Options, Stats, check, load  # noqa: F401
+
+KIND = {"hyp": 0, "mis": 1}
+
+
+def _torch():
+    import torch  # deferred: importing the package does not need a GPU
+    return torch
+
+
+def options(prec: str = "fp64", stream=None, **kw) -> Options:
+    """An mt_options struct with library defaults, overridden by kw."""
+    L = load()
+    o = Options()
+    L.mt_default_options(ctypes.byref(o))
+    o.prec = _lib.PREC[prec] if isinstance(prec, str) else int(prec)
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(o, k):
+            raise TypeError("unknown option %s" % k)
+        setattr(o, k, v)
+    if stream is None:
+        torch = _torch()
+        if torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+    o.stream = stream
+    return o
+
+
+def degree(kind: str, n: int, l: int = 0) -> int:
+    L = load()
+    d = L.mt_degree_hyperbolic(n) if kind == "hyp" else L.mt_degree_misiurewicz(l, n)
+    if d < 0:
+        raise ValueError("polynomial out of range")
+    return int(d)
+
+
+def workspace_bytes(kind: str, n: int, l: int = 0, opts: Options | None = None) -> int:
+    o = opts if opts is not None else options(stream=0)
+    return int(load().mt_workspace_bytes(KIND[kind], l, n, ctypes.byref(o)))
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class SplitResult:
+    roots: "object"          # complex128 tensor [n_roots] on the device, sorted by (Re, Im)
+    roots_lo: "object"       # low parts (double-double) or None
+    is_mis: "object"         # uint8 tensor (Misiurewicz) or None
+    stats: dict
+    status: int
+
+
+class Workspace:
+    """A reusable device scratch buffer (torch uint8 tensor)."""
+
+    def __init__(self, nbytes: int = 0, device="cuda"):
+        self.device = device
+        self.buf = None
+        self.ensure(nbytes)
+
+    def ensure(self, nbytes: int):
+        torch = _torch()
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def split_hyperbolic(n: int, prec: str = "fp64", *, work: Workspace | None = None, want_lo: bool = False,
+                     check_status: bool = True, out=None, **kw) -> SplitResult:
+    """All 2^(n-1) roots of p_n (Algorithm S_par, Sec. 4.2)."""
+    return _split("hyp", n, 0, prec, work, want_lo, check_status, out, kw)
+
+
+def split_misiurewicz(l: int, n: int, prec: str = "fp64", *, work: Workspace | None = None,
+                      want_lo: bool = False, check_status: bool = True, out=None, **kw) -> SplitResult:
+    """All 2^(l+n-2) roots of s_{l,n}, with the Mis(l,n) mask (eq. def:mis)."""
+    return _split("mis", n, l, prec, work, want_lo, check_status, out, kw)
+
+
+def _split(kind, n, l, prec, work, want_lo, check_status, out, kw) -> SplitResult:
+    torch = _torch()
+    L = load()
+    o = options(prec, **kw)
+    d = degree(kind, n, l)
+    nbytes = int(L.mt_workspace_bytes(KIND[kind], l, n, ctypes.byref(o)))
+    if nbytes == 0:
+        raise ValueError("invalid options for this polynomial")
+    work = work or Workspace()
+    buf = work.ensure(nbytes)
+    roots = out if out is not None else torch.empty((d, 2), dtype=torch.float64, device="cuda")
+    lo = torch.empty((d, 2), dtype=torch.float64, device="cuda") if want_lo else None
+    mis = torch.empty(d, dtype=torch.uint8, device="cuda") if kind == "mis" else None
+    n_out = ctypes.c_int64(0)
+    st = Stats()
+    if kind == "hyp":
+        rc = L.mt_split_hyperbolic(n, ctypes.byref(o), roots.data_ptr(), _ptr(lo), d, buf.data_ptr(),
+                                   buf.numel(), ctypes.byref(n_out), ctypes.byref(st))
+    else:
+        rc = L.mt_split_misiurewicz(l, n, ctypes.byref(o), roots.data_ptr(), _ptr(lo), d, _ptr(mis),
+                                    buf.data_ptr(), buf.numel(), ctypes.byref(n_out), ctypes.byref(st))
+    if check_status:
+        check(rc)
+    m = min(int(n_out.value), d)
+    r = torch.view_as_complex(roots[:m])
+    return SplitResult(r, None if lo is None else torch.view_as_complex(lo[:m]),
+                       None if mis is None else mis[:m], st.as_dict(), rc)
+
+
+def misiurewicz_pairs(max_order: int) -> list[tuple[int, int]]:
+    L = load()
+    k = L.mt_misiurewicz_pairs(max_order, None, None, 0)
+    ls = (ctypes.c_int * k)()
+    ns = (ctypes.c_int * k)()
+    L.mt_misiurewicz_pairs(max_order, ls, ns, k)
+    return list(zip(ls, ns))
+
+
+def split_misiurewicz_batch(max_order: int, prec: str = "fp64", *, work: Workspace | None = None,
+                            check_status: bool = True, **kw):
+    """Every s_{l,n} with l >= 2, n >= 1, l + n <= max_order in one call.
+    Returns (roots complex128 [total], is_mis uint8 [total], offsets list, per-pair stats)."""
+    torch = _torch()
+    L = load()
+    o = options(prec, **kw)
+    pairs = misiurewicz_pairs(max_order)
+    total = sum(2 ** (l + n - 2) for l, n in pairs)
+    nbytes = int(L.mt_workspace_bytes_misiurewicz_batch(max_order, ctypes.byref(o)))
+    work = work or Workspace()
+    buf = work.ensure(nbytes)
+    roots = torch.empty((total, 2), dtype=torch.float64, device="cuda")
+    mis = torch.empty(total, dtype=torch.uint8, device="cuda")
+    offs = (ctypes.c_int64 * (len(pairs) + 1))()
+    st = (Stats * len(pairs))()
+    rc = L.mt_split_misiurewicz_batch(max_order, ctypes.byref(o), roots.data_ptr(), None, total,
+                                      mis.data_ptr(), buf.data_ptr(), buf.numel(), offs, st)
+    if check_status:
+        check(rc)
+    return torch.view_as_complex(roots), mis, list(offs), [s.as_dict() for s in st], pairs
+
+
+def certify(kind: str, n: int, roots, l: int = 0, tol: float = 0.0, *, work: Workspace | None = None):
+    """Disk certificate (Thm proofRoots) of each root of a complex128 tensor.
+    Returns (pass uint8 tensor, radius float64 tensor, n_pass)."""
+    torch = _torch()
+    L = load()
+    r = torch.view_as_real(roots.contiguous()) if roots.is_complex() else roots.contiguous()
+    count = r.shape[0]
+    nbytes = int(L.mt_certify_workspace_bytes(count))
+    work = work or Workspace()
+    buf = work.ensure(nbytes)
+    ok = torch.empty(count, dtype=torch.uint8, device=r.device)
+    rad = torch.empty(count, dtype=torch.float64, device=r.device)
+    npass = ctypes.c_int64(0)
+    check(L.mt_certify(KIND[kind], l, n, r.data_ptr(), None, count, tol, ok.data_ptr(), rad.data_ptr(),
+                       buf.data_ptr(), buf.numel(), ctypes.byref(npass),
+                       torch.cuda.current_stream().cuda_stream))
+    return ok, rad, int(npass.value)
+
+
+def evaluate(kind: str, n: int, c, l: int = 0):
+    """P(c), P'(c) for a complex128 tensor c: returns complex128 [count, 2]."""
+    torch = _torch()
+    L = load()
+    cr = torch.view_as_real(c.contiguous())
+    out = torch.empty((c.shape[0], 4), dtype=torch.float64, device=c.device)
+    check(L.mt_eval(KIND[kind], l, n, cr.data_ptr(), c.shape[0], out.data_ptr(),
+                    torch.cuda.current_stream().cuda_stream))
+    return torch.view_as_complex(out.view(-1, 2, 2))
+
+
+def level_line(kind: str, n: int, l: int = 0, prec: str = "fp64", *, work: Workspace | None = None, **kw):
+    """Upper-half starts of the discrete level line (steps a1-a3): complex128 tensor."""
+    torch = _torch()
+    L = load()
+    o = options(prec, **kw)
+    nbytes = int(L.mt_workspace_bytes(KIND[kind], l, n, ctypes.byref(o)))
+    work = work or Workspace()
+    buf = work.ensure(nbytes)
+    ns = ctypes.c_int64(0)
+    st = Stats()
+    L.mt_level_line(KIND[kind], l, n, ctypes.byref(o), None, 0, buf.data_ptr(), buf.numel(),
+                    ctypes.byref(ns), None)
+    starts = torch.empty((ns.value, 2), dtype=torch.float64, device="cuda")
+    check(L.mt_level_line(KIND[kind], l, n, ctypes.byref(o), starts.data_ptr(), ns.value, buf.data_ptr(),
+                          buf.numel(), ctypes.byref(ns), ctypes.byref(st)))
+    return torch.view_as_complex(starts), st.as_dict()
+
+
+def descend(kind: str, n: int, starts, l: int = 0, prec: str = "fp64", **kw):
+    """Newton descents from given starts (step a4): (final iterates, status)."""
+    torch = _torch()
+    L = load()
+    o = options(prec, **kw)
+    s = torch.view_as_real(starts.contiguous())
+    count = s.shape[0]
+    out = torch.empty((count, 2), dtype=torch.float64, device=s.device)
+    status = torch.empty(count, dtype=torch.uint8, device=s.device)
+    work = torch.empty(4096, dtype=torch.uint8, device=s.device)
+    st = Stats()
+    check(L.mt_descend(KIND[kind], l, n, ctypes.byref(o), s.data_ptr(), count, out.data_ptr(),
+                       status.data_ptr(), work.data_ptr(), work.numel(), ctypes.byref(st)))
+    return torch.view_as_complex(out), status, st.as_dict()
+
+
+def classify(kind: str, n: int, roots, l: int = 0, tau: float = 0.0):
+    """Type code of each root (step a6)."""
+    torch = _torch()
+    L = load()
+    r = torch.view_as_real(roots.contiguous())
+    t = torch.empty(r.shape[0], dtype=torch.uint8, device=r.device)
+    check(L.mt_classify(KIND[kind], l, n, r.data_ptr(), r.shape[0], tau, t.data_ptr(),
+                        torch.cuda.current_stream().cuda_stream))
+    return t
+
+
+def version() -> str:
+    return load().mt_version().decode()

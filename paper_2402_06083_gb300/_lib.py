@@ -1,0 +1,128 @@
+"""ctypes declarations of the C ABI in include/mtsplit.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  If the library is missing or cannot be loaded this module raises;
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmtsplit.so")
+
+MT_OK, MT_EINVAL, MT_ENOMEM, MT_ECAPACITY, MT_ECUDA, MT_EINCOMPLETE, MT_ETIMEOUT, MT_ECERT = range(8)
+STATUS_NAMES = {0: "MT_OK", 1: "MT_EINVAL", 2: "MT_ENOMEM", 3: "MT_ECAPACITY", 4: "MT_ECUDA",
+                5: "MT_EINCOMPLETE", 6: "MT_ETIMEOUT", 7: "MT_ECERT"}
+PREC = {"fp64": 0, "mixed": 1, "dd": 2}
+MT_MAX_TYPES = 64
+
+# every symbol include/mtsplit.h declares
+EXPORTS = (
+    "mt_default_options", "mt_degree_hyperbolic", "mt_degree_misiurewicz", "mt_workspace_bytes",
+    "mt_split_hyperbolic", "mt_split_misiurewicz", "mt_misiurewicz_pairs",
+    "mt_workspace_bytes_misiurewicz_batch", "mt_split_misiurewicz_batch",
+    "mt_certify_workspace_bytes", "mt_certify", "mt_eval", "mt_level_line", "mt_descend",
+    "mt_classify", "mt_last_error", "mt_version",
+)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("prec", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("lambda0", ctypes.c_double),
+        ("M", ctypes.c_int),
+        ("c_L", ctypes.c_int),
+        ("chunk_log2", ctypes.c_int),
+        ("block", ctypes.c_int),
+        ("max_retries", ctypes.c_int),
+        ("eps_dup", ctypes.c_double),
+        ("cert_tol", ctypes.c_double),
+        ("use_graph", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "degree", "n_roots", "n_real", "n_starts", "n_conv", "n_repeat", "n_diverge", "n_timeout",
+        "walk_newton", "desc_newton", "steps_fp32", "steps_dd", "walk_fail", "n_cert_pass")] + [
+        ("count_by_type", ctypes.c_int64 * MT_MAX_TYPES),
+        ("M", ctypes.c_int32), ("c_L", ctypes.c_int32), ("retries", ctypes.c_int32),
+        ("n_chunks", ctypes.c_int32), ("n_launches", ctypes.c_int64),
+        ("max_cert_radius", ctypes.c_double), ("min_cert_radius", ctypes.c_double),
+        ("eps_dup", ctypes.c_double),
+        ("ms_total", ctypes.c_float), ("ms_walk", ctypes.c_float), ("ms_descend", ctypes.c_float),
+        ("ms_dedup", ctypes.c_float), ("ms_certify", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if name == "count_by_type" else v
+        return d
+
+
+_LIB = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libmtsplit.so; raise if it is not built (no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libmtsplit.so is not built (run __graft_entry__.build() or "
+                           "python paper_2402_06083_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    op = ctypes.POINTER(Options)
+    sp = ctypes.POINTER(Stats)
+    sig = {
+        "mt_default_options": (None, [op]),
+        "mt_degree_hyperbolic": (i64, [ctypes.c_int]),
+        "mt_degree_misiurewicz": (i64, [ctypes.c_int, ctypes.c_int]),
+        "mt_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, op]),
+        "mt_split_hyperbolic": (ctypes.c_int, [ctypes.c_int, op, vp, vp, i64, vp, ctypes.c_size_t, i64p, sp]),
+        "mt_split_misiurewicz": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, op, vp, vp, i64, vp, vp,
+                                                ctypes.c_size_t, i64p, sp]),
+        "mt_misiurewicz_pairs": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+        "mt_workspace_bytes_misiurewicz_batch": (ctypes.c_size_t, [ctypes.c_int, op]),
+        "mt_split_misiurewicz_batch": (ctypes.c_int, [ctypes.c_int, op, vp, vp, i64, vp, vp,
+                                                      ctypes.c_size_t, i64p, sp]),
+        "mt_certify_workspace_bytes": (ctypes.c_size_t, [i64]),
+        "mt_certify": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, i64, ctypes.c_double,
+                                      vp, vp, vp, ctypes.c_size_t, i64p, vp]),
+        "mt_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64, vp, vp]),
+        "mt_level_line": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, op, vp, i64, vp,
+                                         ctypes.c_size_t, i64p, sp]),
+        "mt_descend": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, op, vp, i64, vp, vp, vp,
+                                      ctypes.c_size_t, sp]),
+        "mt_classify": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64, ctypes.c_double,
+                                       vp, vp]),
+        "mt_last_error": (ctypes.c_char_p, []),
+        "mt_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+class MtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def check(rc: int) -> None:
+    if rc != MT_OK:
+        raise MtError(rc, load().mt_last_error().decode())

@@ -1,0 +1,554 @@
+// mt_api.cu -- host orchestration and the C ABI (include/mtsplit.h).
+//
+// One split = one ordered sequence of kernel launches on the caller's
+// stream (Algorithm S_par of Sec. 4.2, single GPU):
+//   seeds (lift)  ->  level-line walk  ->  persistent Newton descents  ->
+//   fold + radix sort + cluster + compact  ->  classify  ->  certify  ->
+//   emit the sorted conjugate-closed list
+// followed by one device-to-host copy of the counters.  If roots are
+// missing, (M, c_L) are doubled and the sequence is replayed (Sec. 4.1:
+// "if some roots are missing, N can be increased").
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "../../include/mtsplit.h"
+#include "mt_internal.h"
+
+using namespace mt;
+
+thread_local unsigned long long mt::g_launches = 0;
+
+namespace {
+
+thread_local std::string g_err;
+
+mt_status fail(mt_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+mt_status fail(mt_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(MT_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                             \
+  } while (0)
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+// Bump allocator over the caller's workspace.
+struct Carve {
+  char* base;
+  size_t off = 0, cap;
+  Carve(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <class T>
+  T* take(int64_t n) {
+    const size_t bytes = align_up((size_t)(n > 0 ? n : 1) * sizeof(T));
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+  void* take_bytes(size_t bytes) {
+    void* p = base ? (void*)(base + off) : nullptr;
+    off += align_up(bytes);
+    return p;
+  }
+};
+
+bool valid_poly(int kind, int l, int n) {
+  if (kind == 0) return n >= 1 && n <= 40;
+  if (kind == 1) return l >= 2 && n >= 1 && l + n <= 41;
+  return false;
+}
+
+PolyDev make_poly(int kind, int l, int n) {
+  PolyDev P;
+  P.kind = kind;
+  P.l = l;
+  P.n = n;
+  if (kind == 0) {
+    P.m = n;
+    P.lcap = -1;
+    P.log2d = n - 1;
+  } else {
+    P.m = l + n - 1;
+    P.lcap = l - 1;
+    P.log2d = l + n - 2;
+  }
+  return P;
+}
+
+struct Plan {
+  PolyDev P;
+  int kind;
+  int64_t degree;
+  double lambda0;
+  int M, cL, every;
+  int64_t N0, nchunks, L, S;
+  double tol;
+  int cap;
+  double eps;
+  double cert_tol;
+  int shrink;
+};
+
+double default_eps(int kind, int l, int n) {
+  // hyperbolic: a twentieth of the minimal separation 118.4 / 4^n (Sec. 6.3.2);
+  // s_{l,n}: a fiftieth of the tip separation ~6.4e3 / 8^(l+n) of this family;
+  // never below 64 ulp(2) of binary64.
+  double e = (kind == 0) ? fmin(1e-9, 0.05 * 118.4 / std::ldexp(1.0, 2 * n))
+                         : fmin(1e-9, 128.0 / std::ldexp(1.0, 3 * (l + n)));
+  return fmax(e, 64.0 * std::ldexp(1.0, -51));
+}
+
+bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl) {
+  if (!valid_poly(kind, l, n)) return false;
+  Plan p;
+  p.kind = kind;
+  p.P = make_poly(kind, l, n);
+  p.degree = int64_t(1) << p.P.log2d;
+  p.lambda0 = (o && o->lambda0 > 0) ? o->lambda0 : (kind == 0 ? 5.0 : 100.0);
+  p.M = (o && o->M > 0) ? o->M : 8;
+  p.cL = (o && o->c_L > 0) ? o->c_L : 4;
+  p.M <<= retry;
+  p.cL <<= retry;
+  if (p.M > 64 || (p.M & (p.M - 1)) || (p.cL & (p.cL - 1)) || p.M % p.cL) return false;
+  p.every = p.M / p.cL;
+  const int64_t Md = (int64_t)p.M * p.degree;  // sub-steps around the whole line
+  int64_t N0;
+  if (o && o->chunk_log2 > 0) {
+    N0 = Md >> o->chunk_log2;
+  } else {
+    N0 = std::min<int64_t>(int64_t(1) << 15, Md / 16);
+  }
+  // L must be a multiple of 'every' and N0 >= 2
+  while (N0 > 2 && (Md / N0) % p.every) N0 >>= 1;
+  if (N0 < 2) N0 = 2;
+  if ((Md / N0) % p.every) return false;
+  p.N0 = N0;
+  p.nchunks = N0 / 2;
+  p.L = Md / N0;
+  p.S = (Md / 2) / p.every + 1;
+  const bool dd = o && o->prec == MT_DD;
+  p.tol = (o && o->tol > 0) ? o->tol : (dd ? 1e-26 : 1e-13);
+  const double IN = (kind == 0) ? 1.0 : 2.6;  // Sec. 4.2
+  p.cap = std::max(20, (int)std::ceil(IN * p.P.log2d));
+  p.eps = (o && o->eps_dup > 0) ? o->eps_dup : default_eps(kind, l, n);
+  p.cert_tol = (o && o->cert_tol > 0) ? o->cert_tol : (dd ? 1e-20 : 1e-12);
+  p.shrink = 4;
+  *pl = p;
+  return true;
+}
+
+struct Buffers {
+  DevCounters* ctr;
+  double2 *seeds, *starts, *cand, *reps;
+  uint8_t *status, *type, *pass;
+  uint64_t *keys, *keys_alt;
+  uint32_t *vals, *vals_alt, *flag, *pos, *mult, *mpos;
+  double* radius;
+  void *scan_tmp, *radix_tmp;
+  size_t bytes;
+};
+
+Buffers carve(const Plan& p, void* ws, size_t cap) {
+  Carve c(ws, cap);
+  Buffers b;
+  b.ctr = c.take<DevCounters>(1);
+  b.seeds = c.take<double2>(p.nchunks + 1);
+  b.starts = c.take<double2>(p.S);
+  b.cand = c.take<double2>(p.S);
+  b.reps = b.starts;  // starts are dead once the descents are done
+  b.status = c.take<uint8_t>(p.S);
+  b.keys = c.take<uint64_t>(p.S);
+  b.keys_alt = c.take<uint64_t>(p.S);
+  b.vals = c.take<uint32_t>(p.S);
+  b.vals_alt = c.take<uint32_t>(p.S);
+  b.flag = c.take<uint32_t>(p.S);
+  b.pos = c.take<uint32_t>(p.S);
+  b.type = c.take<uint8_t>(p.S);
+  b.mult = b.flag;  // flag/pos are dead after compaction
+  b.mpos = b.pos;
+  b.pass = c.take<uint8_t>(p.S);
+  b.radius = c.take<double>(p.S);
+  b.scan_tmp = c.take_bytes(scan_temp_bytes(p.S));
+  b.radix_tmp = c.take_bytes(radix_temp_bytes(p.S));
+  b.bytes = c.off;
+  return b;
+}
+
+size_t plan_bytes(const Plan& p) { return carve(p, nullptr, 0).bytes; }
+
+size_t workspace_for(int kind, int l, int n, const mt_options* o) {
+  const int retries = o ? std::max(0, o->max_retries) : 1;
+  size_t best = 0;
+  for (int r = 0; r <= retries; ++r) {
+    Plan p;
+    if (!make_plan(kind, l, n, o, r, &p)) {
+      if (r == 0) return 0;
+      break;
+    }
+    best = std::max(best, plan_bytes(p));
+  }
+  return best;
+}
+
+struct EventSet {
+  cudaEvent_t e[6];
+  bool ok = false;
+  EventSet() {
+    ok = true;
+    for (auto& x : e)
+      if (cudaEventCreate(&x) != cudaSuccess) ok = false;
+  }
+  ~EventSet() {
+    for (auto& x : e) cudaEventDestroy(x);
+  }
+};
+
+void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
+  if (!st) return;
+  st->degree = p.degree;
+  st->n_roots = (int64_t)h.n_full;
+  st->n_real = (int64_t)h.n_reps_real;
+  st->n_starts = p.S;
+  st->n_conv = (int64_t)h.n_conv;
+  st->n_repeat = (int64_t)h.n_conv - (int64_t)h.n_reps;
+  st->n_diverge = (int64_t)h.n_diverge;
+  st->n_timeout = (int64_t)h.n_timeout;
+  st->walk_newton = (int64_t)h.walk_newton;
+  st->desc_newton = (int64_t)h.desc_newton;
+  st->steps_fp32 = (int64_t)h.steps_fp32;
+  st->steps_dd = (int64_t)h.steps_dd;
+  st->walk_fail = (int64_t)h.walk_fail;
+  st->n_cert_pass = (int64_t)h.n_cert_pass;
+  for (int i = 0; i < MT_MAX_TYPES; ++i) st->count_by_type[i] = (int64_t)h.type_count[i];
+  st->M = p.M;
+  st->c_L = p.cL;
+  st->n_chunks = (int32_t)p.nchunks;
+  double mn, mx;
+  memcpy(&mn, &h.min_radius_bits, 8);
+  memcpy(&mx, &h.max_radius_bits, 8);
+  st->min_cert_radius = h.n_cert_pass ? mn : 0.0;
+  st->max_cert_radius = h.n_cert_pass ? mx : 0.0;
+  st->eps_dup = p.eps;
+}
+
+// One pass of the whole sequence.  Leaves counters in *h.
+mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
+                   uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h) {
+  CK(launch_init_counters(b.ctr, s));
+  CK(cudaEventRecord(ev.e[0], s));
+  CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+  CK(launch_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, b.seeds, b.starts, b.ctr, s));
+  CK(cudaEventRecord(ev.e[1], s));
+  CK(launch_descend(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
+  CK(cudaEventRecord(ev.e[2], s));
+  CK(launch_fold_keys(b.status, b.cand, p.S, p.eps, b.keys, b.vals, s));
+  CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, p.S, b.radix_tmp, s));
+  CK(launch_cluster(b.cand, b.vals, p.S, &b.ctr->n_conv, p.eps, b.flag, b.ctr, s));
+  CK(launch_exclusive_scan(b.flag, b.pos, p.S, b.scan_tmp, nullptr, s));
+  CK(launch_compact(b.cand, b.vals, b.flag, b.pos, p.S, b.reps, b.ctr, s));
+  CK(cudaEventRecord(ev.e[3], s));
+  CK(launch_classify(p.P, b.reps, &b.ctr->n_reps, p.S, p.eps, 0, b.type, b.mult, b.ctr, s));
+  CK(launch_exclusive_scan(b.mult, b.mpos, p.S, b.scan_tmp, &b.ctr->n_full, s));
+  CK(launch_certify(p.P, b.reps, &b.ctr->n_reps, p.S, p.cert_tol, b.mult, b.pass, b.radius, b.ctr,
+                    s));
+  CK(cudaEventRecord(ev.e[4], s));
+  const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
+  CK(launch_emit(b.reps, &b.ctr->n_reps, p.S, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out,
+                 s));
+  CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s));
+  if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
+  CK(cudaEventRecord(ev.e[5], s));
+  CK(cudaMemcpyAsync(h, b.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return MT_OK;
+}
+
+mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_roots,
+                     double* d_roots_lo, int64_t cap, uint8_t* d_is_mis, void* d_work,
+                     size_t work_bytes, int64_t* n_out, mt_stats* st) {
+  g_err.clear();
+  if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range (kind %d, l %d, n %d)", kind, l, n);
+  if (cap < 0 || (cap > 0 && !d_roots)) return fail(MT_EINVAL, "bad output buffer");
+  if (o && o->prec != MT_FP64 && o->prec != MT_MIXED && o->prec != MT_DD)
+    return fail(MT_EINVAL, "unknown precision %d", o->prec);
+  mt_options dflt;
+  mt_default_options(&dflt);
+  if (!o) o = &dflt;
+  const size_t need = workspace_for(kind, l, n, o);
+  if (need == 0) return fail(MT_EINVAL, "invalid options for this polynomial");
+  if (!d_work || work_bytes < need)
+    return fail(MT_ENOMEM, "workspace of %zu bytes needed, %zu given", need, work_bytes);
+  if (((uintptr_t)d_work) % ALIGN) return fail(MT_EINVAL, "workspace must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)o->stream;
+  EventSet ev;
+  if (!ev.ok) return fail(MT_ECUDA, "cudaEventCreate failed");
+  DevCounters h;
+  Plan p;
+  mt_status rc = MT_OK;
+  int retry = 0;
+  const unsigned long long launches0 = g_launches;
+  const int max_retries = std::max(0, o->max_retries);
+  for (;; ++retry) {
+    if (!make_plan(kind, l, n, o, retry, &p)) return fail(MT_EINVAL, "no plan for retry %d", retry);
+    Buffers b = carve(p, d_work, work_bytes);
+    rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h);
+    if (rc != MT_OK) return rc;
+    if ((int64_t)h.n_full == p.degree || retry >= max_retries) break;
+  }
+  if (st) {
+    memset(st, 0, sizeof(*st));
+    fill_stats(p, h, st);
+    st->retries = retry;
+    st->n_launches = (int64_t)(g_launches - launches0);
+    float ms[5] = {0, 0, 0, 0, 0};
+    cudaEventElapsedTime(&ms[0], ev.e[0], ev.e[5]);
+    cudaEventElapsedTime(&ms[1], ev.e[0], ev.e[1]);
+    cudaEventElapsedTime(&ms[2], ev.e[1], ev.e[2]);
+    cudaEventElapsedTime(&ms[3], ev.e[2], ev.e[3]);
+    cudaEventElapsedTime(&ms[4], ev.e[3], ev.e[4]);
+    st->ms_total = ms[0];
+    st->ms_walk = ms[1];
+    st->ms_descend = ms[2];
+    st->ms_dedup = ms[3];
+    st->ms_certify = ms[4];
+  }
+  if (n_out) *n_out = (int64_t)h.n_full;
+  if ((int64_t)h.n_full > cap)
+    return fail(MT_ECAPACITY, "%lld roots do not fit in cap %lld", (long long)h.n_full,
+                (long long)cap);
+  if ((int64_t)h.n_full != p.degree)
+    return fail(MT_EINCOMPLETE, "found %lld roots, degree %lld (after %d retries)",
+                (long long)h.n_full, (long long)p.degree, retry);
+  if (h.n_cert_pass != h.n_full)
+    return fail(MT_ECERT, "%lld of %lld roots certified", (long long)h.n_cert_pass,
+                (long long)h.n_full);
+  return MT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+void mt_default_options(mt_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->prec = MT_FP64;
+  o->max_retries = 1;
+}
+
+int64_t mt_degree_hyperbolic(int n) { return valid_poly(0, 0, n) ? (int64_t(1) << (n - 1)) : -1; }
+
+int64_t mt_degree_misiurewicz(int l, int n) {
+  return valid_poly(1, l, n) ? (int64_t(1) << (l + n - 2)) : -1;
+}
+
+size_t mt_workspace_bytes(int kind, int l, int n, const mt_options* opts) {
+  mt_options d;
+  mt_default_options(&d);
+  return workspace_for(kind, kind == 0 ? 0 : l, n, opts ? opts : &d);
+}
+
+mt_status mt_split_hyperbolic(int n, const mt_options* opts, double* d_roots, double* d_roots_lo,
+                              int64_t cap, void* d_work, size_t work_bytes, int64_t* n_out,
+                              mt_stats* stats) {
+  return split_impl(0, 0, n, opts, d_roots, d_roots_lo, cap, nullptr, d_work, work_bytes, n_out,
+                    stats);
+}
+
+mt_status mt_split_misiurewicz(int l, int n, const mt_options* opts, double* d_roots,
+                               double* d_roots_lo, int64_t cap, uint8_t* d_is_mis, void* d_work,
+                               size_t work_bytes, int64_t* n_out, mt_stats* stats) {
+  return split_impl(1, l, n, opts, d_roots, d_roots_lo, cap, d_is_mis, d_work, work_bytes, n_out,
+                    stats);
+}
+
+int mt_misiurewicz_pairs(int max_order, int* h_l, int* h_n, int capacity) {
+  int k = 0;
+  for (int l = 2; l < max_order; ++l)
+    for (int n = 1; l + n <= max_order; ++n) {
+      if (k < capacity && h_l && h_n) {
+        h_l[k] = l;
+        h_n[k] = n;
+      }
+      ++k;
+    }
+  return k;
+}
+
+size_t mt_workspace_bytes_misiurewicz_batch(int max_order, const mt_options* opts) {
+  // sequential fallback: the largest single workspace
+  size_t best = 0;
+  for (int l = 2; l < max_order; ++l)
+    for (int n = 1; l + n <= max_order; ++n) best = std::max(best, mt_workspace_bytes(1, l, n, opts));
+  return best;
+}
+
+mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, double* d_roots,
+                                     double* d_roots_lo, int64_t cap, uint8_t* d_is_mis,
+                                     void* d_work, size_t work_bytes, int64_t* h_offsets,
+                                     mt_stats* stats) {
+  g_err.clear();
+  if (max_order < 3 || max_order > 41 || !h_offsets) return fail(MT_EINVAL, "bad max_order");
+  int64_t off = 0;
+  int p = 0;
+  h_offsets[0] = 0;
+  for (int l = 2; l < max_order; ++l)
+    for (int n = 1; l + n <= max_order; ++n, ++p) {
+      int64_t got = 0;
+      const int64_t d = mt_degree_misiurewicz(l, n);
+      if (off + d > cap) return fail(MT_ECAPACITY, "batch needs more than cap %lld", (long long)cap);
+      mt_status rc = split_impl(1, l, n, opts, d_roots + 2 * off,
+                                d_roots_lo ? d_roots_lo + 2 * off : nullptr, d,
+                                d_is_mis ? d_is_mis + off : nullptr, d_work, work_bytes, &got,
+                                stats ? &stats[p] : nullptr);
+      if (rc != MT_OK) return rc;
+      off += got;
+      h_offsets[p + 1] = off;
+    }
+  return MT_OK;
+}
+
+size_t mt_certify_workspace_bytes(int64_t count) {
+  if (count < 0) return 0;
+  Carve c(nullptr, 0);
+  c.take<DevCounters>(1);
+  c.take<uint64_t>(count);
+  c.take<uint64_t>(count);
+  c.take<uint32_t>(count);
+  c.take<uint32_t>(count);
+  c.take_bytes(radix_temp_bytes(count));
+  return c.off;
+}
+
+mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double* d_roots_lo,
+                     int64_t count, double tol, uint8_t* d_pass, double* d_radius, void* d_work,
+                     size_t work_bytes, int64_t* n_pass, void* stream) {
+  g_err.clear();
+  if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range");
+  if (count < 0 || (count > 0 && (!d_roots || !d_pass))) return fail(MT_EINVAL, "bad buffers");
+  if (count > 0xffffffffll) return fail(MT_EINVAL, "count too large");
+  (void)d_roots_lo;
+  const size_t need = mt_certify_workspace_bytes(count);
+  if (!d_work || work_bytes < need) return fail(MT_ENOMEM, "workspace of %zu bytes needed", need);
+  cudaStream_t s = (cudaStream_t)stream;
+  const PolyDev P = make_poly(kind, l, n);
+  if (tol <= 0) tol = 1e-12;
+  Carve c(d_work, work_bytes);
+  DevCounters* ctr = c.take<DevCounters>(1);
+  uint64_t* keys = c.take<uint64_t>(count);
+  uint64_t* keys_alt = c.take<uint64_t>(count);
+  uint32_t* vals = c.take<uint32_t>(count);
+  uint32_t* vals_alt = c.take<uint32_t>(count);
+  void* rtmp = c.take_bytes(radix_temp_bytes(count));
+  CK(launch_init_counters(ctr, s));
+  CK(launch_keys_plain((const double2*)d_roots, count, keys, vals, s));
+  CK(radix_sort_pairs(keys, vals, keys_alt, vals_alt, count, rtmp, s));
+  CK(launch_certify_list(P, (const double2*)d_roots, vals, count, tol, d_pass, d_radius, ctr, s));
+  DevCounters h;
+  CK(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (n_pass) *n_pass = (int64_t)h.n_cert_pass;
+  return MT_OK;
+}
+
+mt_status mt_eval(int kind, int l, int n, const double* d_c, int64_t count, double* d_out,
+                  void* stream) {
+  g_err.clear();
+  if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range");
+  if (count < 0 || (count > 0 && (!d_c || !d_out))) return fail(MT_EINVAL, "bad buffers");
+  CK(launch_eval(make_poly(kind, l, n), (const double2*)d_c, count, (double2*)d_out,
+                 (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return MT_OK;
+}
+
+mt_status mt_level_line(int kind, int l, int n, const mt_options* opts, double* d_starts,
+                        int64_t cap, void* d_work, size_t work_bytes, int64_t* n_starts,
+                        mt_stats* stats) {
+  g_err.clear();
+  mt_options dflt;
+  mt_default_options(&dflt);
+  const mt_options* o = opts ? opts : &dflt;
+  Plan p;
+  if (!make_plan(kind, l, n, o, 0, &p)) return fail(MT_EINVAL, "invalid polynomial or options");
+  Buffers b = carve(p, d_work, work_bytes);
+  if (!d_work || work_bytes < b.bytes) return fail(MT_ENOMEM, "workspace of %zu bytes needed", b.bytes);
+  if (n_starts) *n_starts = p.S;
+  if (cap < p.S || !d_starts) return fail(MT_ECAPACITY, "%lld starts need a larger buffer", (long long)p.S);
+  cudaStream_t s = (cudaStream_t)o->stream;
+  CK(launch_init_counters(b.ctr, s));
+  CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+  CK(launch_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, b.seeds, (double2*)d_starts, b.ctr, s));
+  DevCounters h;
+  CK(cudaMemcpyAsync(&h, b.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    fill_stats(p, h, stats);
+  }
+  return MT_OK;
+}
+
+mt_status mt_descend(int kind, int l, int n, const mt_options* opts, const double* d_starts,
+                     int64_t count, double* d_out, uint8_t* d_status, void* d_work,
+                     size_t work_bytes, mt_stats* stats) {
+  g_err.clear();
+  mt_options dflt;
+  mt_default_options(&dflt);
+  const mt_options* o = opts ? opts : &dflt;
+  Plan p;
+  if (!make_plan(kind, l, n, o, 0, &p)) return fail(MT_EINVAL, "invalid polynomial or options");
+  if (count < 0 || (count > 0 && (!d_starts || !d_out || !d_status))) return fail(MT_EINVAL, "bad buffers");
+  if (!d_work || work_bytes < sizeof(DevCounters)) return fail(MT_ENOMEM, "workspace too small");
+  cudaStream_t s = (cudaStream_t)o->stream;
+  DevCounters* ctr = (DevCounters*)d_work;
+  CK(launch_init_counters(ctr, s));
+  CK(launch_descend(p.P, (const double2*)d_starts, count, p.tol, p.cap, (double2*)d_out, d_status,
+                    ctr, o->block, s));
+  DevCounters h;
+  CK(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    fill_stats(p, h, stats);
+    stats->n_starts = count;
+  }
+  return MT_OK;
+}
+
+mt_status mt_classify(int kind, int l, int n, const double* d_roots, int64_t count, double tau,
+                      uint8_t* d_type, void* stream) {
+  g_err.clear();
+  if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range");
+  if (count < 0 || (count > 0 && (!d_roots || !d_type))) return fail(MT_EINVAL, "bad buffers");
+  if (tau <= 0) tau = default_eps(kind, l, n);
+  CK(launch_type_only(make_poly(kind, l, n), (const double2*)d_roots, count, tau, d_type,
+                      (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return MT_OK;
+}
+
+const char* mt_last_error(void) { return g_err.c_str(); }
+
+const char* mt_version(void) { return "mtsplit 0.1 (sm_103a)"; }
+
+}  // extern "C"

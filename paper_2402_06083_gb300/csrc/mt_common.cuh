@@ -1,0 +1,115 @@
+// mt_common.cuh -- device building blocks shared by the kernels of the
+// level-line Newton splitter: the polynomial descriptor, the critical-orbit
+// evaluation of P and P' in binary64, the Newton quotient, and small warp
+// helpers.
+//
+// Polynomials (Mihalache & Vigneron, Sec. 1 and eq. polySimple):
+//   p_0 = 0, p_{k+1} = p_k^2 + c                 P = p_n,             deg 2^(n-1)
+//   s_{l,n} = p_{l+n-1} + p_{l-1}                P = s_{l,n},         deg 2^(l+n-2)
+// Both are evaluated through one critical orbit of length m, with the
+// c-derivative carried along by differentiating the recurrence:
+//   p'_{k+1} = 2 p_k p'_k + 1                    (eq. DerParamDyna, parameter form)
+// so one evaluation costs O(m) = O(log d) (Sec. 3, "V_d = O(log_2 d)").
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mt_internal.h"
+
+namespace mt {
+
+// ---------------------------------------------------------------------------
+// Evaluation of P_alpha = p_m + alpha * p_lcap and its derivative at c.
+// lcap < 0: plain p_m.  For s_{l,n}: m = l+n-1, lcap = l-1, alpha = 1.
+// 9 binary64 instructions per orbit step (2 adds, 5 FMA, 2 mul).
+__device__ __forceinline__ void orbit_f64(int m, int lcap, double alpha, double cr, double ci,
+                                          double& vr, double& vi, double& dr, double& di) {
+  double zr = 0.0, zi = 0.0, dzr = 0.0, dzi = 0.0;
+  double cap_r = 0.0, cap_i = 0.0, capd_r = 0.0, capd_i = 0.0;
+#pragma unroll 4
+  for (int k = 1; k <= m; ++k) {
+    const double tzr = zr + zr, tzi = zi + zi;          // 2 z_{k-1}
+    const double ndr = fma(tzr, dzr, fma(-tzi, dzi, 1.0));  // Re(2 z z' + 1)
+    const double ndi = fma(tzr, dzi, tzi * dzr);            // Im(2 z z')
+    const double nzr = fma(zr, zr, fma(-zi, zi, cr));       // Re(z^2 + c)
+    const double nzi = fma(tzr, zi, ci);                    // Im(z^2 + c)
+    zr = nzr; zi = nzi; dzr = ndr; dzi = ndi;
+    if (k == lcap) { cap_r = zr; cap_i = zi; capd_r = dzr; capd_i = dzi; }
+  }
+  vr = fma(alpha, cap_r, zr);
+  vi = fma(alpha, cap_i, zi);
+  dr = fma(alpha, capd_r, dzr);
+  di = fma(alpha, capd_i, dzi);
+}
+
+// Plain p_n specialisation (no capture), the hot inner loop.
+__device__ __forceinline__ void orbit_pn_f64(int m, double cr, double ci, double& vr, double& vi,
+                                             double& dr, double& di) {
+  double zr = 0.0, zi = 0.0, dzr = 0.0, dzi = 0.0;
+#pragma unroll 4
+  for (int k = 1; k <= m; ++k) {
+    const double tzr = zr + zr, tzi = zi + zi;
+    const double ndr = fma(tzr, dzr, fma(-tzi, dzi, 1.0));
+    const double ndi = fma(tzr, dzi, tzi * dzr);
+    const double nzr = fma(zr, zr, fma(-zi, zi, cr));
+    const double nzi = fma(tzr, zi, ci);
+    zr = nzr; zi = nzi; dzr = ndr; dzi = ndi;
+  }
+  vr = zr; vi = zi; dr = dzr; di = dzi;
+}
+
+__device__ __forceinline__ void eval_P(const PolyDev& P, double cr, double ci, double& vr, double& vi,
+                                       double& dr, double& di) {
+  if (P.lcap < 0) orbit_pn_f64(P.m, cr, ci, vr, vi, dr, di);
+  else orbit_f64(P.m, P.lcap, 1.0, cr, ci, vr, vi, dr, di);
+}
+
+// Newton quotient (a + ib) / (c + id) with one binary64 division.  Both
+// operands are first scaled by the same power of two 2^-E, E the exponent of
+// max(|c|, |d|) (exact), so |c + id|^2 lies in [1, 8) and never overflows:
+// an escaped orbit (|P'| > 1e154) would otherwise give a zero quotient, a
+// false convergence.  This is the "simplify a common large factor" guard of
+// Sec. 6.3.2 (remark on the exponent range).  Non-finite inputs give NaN.
+__device__ __forceinline__ void cdiv_f64(double a, double b, double c, double d, double& qr,
+                                         double& qi) {
+  const double m = fmax(fabs(c), fabs(d));
+  const long long eb = __double_as_longlong(m) & 0x7ff0000000000000ll;
+  const double sc = __longlong_as_double(0x7fe0000000000000ll - eb);  // 2^-E
+  const double cs = c * sc, ds = d * sc, as = a * sc, bs = b * sc;
+  const double inv = 1.0 / fma(cs, cs, ds * ds);
+  qr = fma(as, cs, bs * ds) * inv;
+  qi = fma(bs, cs, -as * ds) * inv;
+  if (!(m < 1.0e308)) qr = qi = __longlong_as_double(0x7ff8000000000000ll);  // inf / NaN input
+}
+
+__device__ __forceinline__ bool finite2(double a, double b) {
+  return isfinite(a) && isfinite(b);
+}
+
+// e^{2 i pi num / den} for integers with den a power of two <= 2^62.
+__device__ __forceinline__ void unit_phase(uint64_t num, uint64_t den, double& c, double& s) {
+  const uint64_t r = num & (den - 1);
+  sincospi(2.0 * ((double)r / (double)den), &s, &c);
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers.
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Sum a per-lane 64-bit counter over the warp and add it once to *dst.
+__device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+// Order-preserving map of a binary64 to an unsigned 64-bit key.
+__device__ __forceinline__ uint64_t f64_key(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+}  // namespace mt

@@ -1,0 +1,411 @@
+// mt_dedup.cu -- step a5: the separated, conjugate-symmetric, sorted root set.
+//
+// Semantics follow the paper's nset (Sec. 6.1): two points are the same root
+// when max(|dRe|, |dIm|) < eps (eq. nsetAsumption); only the upper half
+// plane is stored and a point with |Im| < eps/2 is real (Im := 0); the set
+// is ordered by (Re, Im) (eq. defLexi).
+//
+// GB300 design.  The paper inserts one root at a time into bars of a
+// sorted container.  Here the whole candidate array is handled at once:
+// fold + key -> LSD radix sort of Re keys -> each sorted candidate checks
+// the earlier candidates of its Re window -> exclusive scan -> gather.
+// Every kernel is a coalesced pass over HBM; the radix sort ranks keys
+// stably inside a block with __match_any_sync.
+#include "mt_common.cuh"
+
+namespace mt {
+
+// ---------------------------------------------------------------------------
+// counters
+__global__ void k_init_counters(DevCounters* c) {
+  unsigned long long* w = (unsigned long long*)c;
+  const int nw = (int)(sizeof(DevCounters) / sizeof(unsigned long long));
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) w[i] = 0ull;
+  __syncthreads();
+  if (threadIdx.x == 0) c->min_radius_bits = 0x7ff0000000000000ull;  // +inf
+}
+
+cudaError_t launch_init_counters(DevCounters* ctr, cudaStream_t s) {
+  MT_COUNT_LAUNCH(1);
+  k_init_counters<<<1, 128, 0, s>>>(ctr);
+  return cudaGetLastError();
+}
+
+__global__ void k_keys_plain(const double2* __restrict__ pts, int64_t count,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  keys[i] = f64_key(pts[i].x);
+  vals[i] = (uint32_t)i;
+}
+
+cudaError_t launch_keys_plain(const double2* pts, int64_t count, uint64_t* keys, uint32_t* vals,
+                              cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_keys_plain<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(pts, count, keys, vals);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// fold + keys
+__global__ void k_fold_keys(const uint8_t* __restrict__ status, double2* __restrict__ cand,
+                            int64_t count, double eps, uint64_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint64_t key = ~0ull;
+  if (status[i] == 0) {
+    double2 z = cand[i];
+    z.y = fabs(z.y);               // conjugate fold: P has real coefficients
+    if (z.y < 0.5 * eps) z.y = 0.0;  // indistinguishable from its conjugate: real
+    cand[i] = z;
+    key = f64_key(z.x);
+  }
+  keys[i] = key;
+  vals[i] = (uint32_t)i;
+}
+
+cudaError_t launch_fold_keys(const uint8_t* status, double2* cand, int64_t count, double eps,
+                             uint64_t* keys, uint32_t* vals, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_fold_keys<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(status, cand, count, eps, keys, vals);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of u32 (three passes: tile sums, scan of sums, tile scan).
+constexpr int SCAN_BS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int64_t SCAN_TILE = (int64_t)SCAN_BS * SCAN_ITEMS;
+
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v,
+                                                                  unsigned long long* sh,
+                                                                  unsigned long long* total) {
+  // warp scan
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = lane < nw ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) sh[lane] = t;
+  }
+  __syncthreads();
+  const unsigned long long warp_off = w ? sh[w - 1] : 0;
+  if (total) *total = sh[nw - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void k_scan_tile_sums(const uint32_t* __restrict__ in, int64_t n,
+                                 unsigned long long* __restrict__ sums) {
+  __shared__ unsigned long long sh[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  unsigned long long acc = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = base + (int64_t)k * SCAN_BS + threadIdx.x;
+    if (i < n) acc += in[i];
+  }
+  unsigned long long tot;
+  block_excl_scan_u64(acc, sh, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(unsigned long long* sums, int64_t nb, unsigned long long* total) {
+  __shared__ unsigned long long sh[32];
+  // one block: each thread owns a contiguous run of sums
+  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const int64_t b0 = (int64_t)threadIdx.x * per;
+  unsigned long long acc = 0;
+  for (int64_t b = b0; b < b0 + per && b < nb; ++b) acc += sums[b];
+  unsigned long long tot;
+  unsigned long long off = block_excl_scan_u64(acc, sh, &tot);
+  for (int64_t b = b0; b < b0 + per && b < nb; ++b) {
+    const unsigned long long v = sums[b];
+    sums[b] = off;
+    off += v;
+  }
+  if (threadIdx.x == 0 && total) *total = tot;
+}
+
+__global__ void k_scan_tiles(const uint32_t* in, uint32_t* out, int64_t n,
+                             const unsigned long long* __restrict__ sums) {
+  __shared__ unsigned long long sh[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  // each thread owns SCAN_ITEMS consecutive elements (blocked arrangement)
+  const int64_t t0 = base + (int64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  unsigned long long acc = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (t0 + k < n) ? in[t0 + k] : 0u;
+    acc += v[k];
+  }
+  unsigned long long off = block_excl_scan_u64(acc, sh, nullptr) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (t0 + k < n) out[t0 + k] = (uint32_t)off;
+    off += v[k];
+  }
+}
+
+size_t scan_temp_bytes(int64_t n) {
+  const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  return (size_t)(nb + 1) * sizeof(unsigned long long);
+}
+
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, void* temp,
+                                  unsigned long long* total, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned long long* sums = (unsigned long long*)temp;
+  MT_COUNT_LAUNCH(1);
+  k_scan_tile_sums<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, n, sums);
+  MT_COUNT_LAUNCH(1);
+  k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, total);
+  MT_COUNT_LAUNCH(1);
+  k_scan_tiles<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, out, n, sums);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits, stable.
+constexpr int RS_BS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int64_t RS_TILE = (int64_t)RS_BS * RS_ITEMS;
+
+__global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n,
+                                                   int shift, uint32_t* __restrict__ hist,
+                                                   int64_t nb) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int64_t i = base + (int64_t)k * RS_BS + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];  // digit-major
+}
+
+__global__ void __launch_bounds__(RS_BS) k_rs_scatter(const uint64_t* __restrict__ kin,
+                                                      const uint32_t* __restrict__ vin,
+                                                      uint64_t* __restrict__ kout,
+                                                      uint32_t* __restrict__ vout, int64_t n,
+                                                      int shift, const uint32_t* __restrict__ offs,
+                                                      int64_t nb) {
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t tot[256];
+  __shared__ uint32_t wcnt[RS_BS / 32][256];
+  const int t = threadIdx.x, w = t >> 5;
+  base[t] = offs[(int64_t)t * nb + blockIdx.x];
+  const int64_t tile = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = 0; k < RS_ITEMS; ++k) {
+#pragma unroll
+    for (int q = 0; q < RS_BS / 32; ++q) wcnt[q][t] = 0;
+    __syncthreads();
+    const int64_t i = tile + (int64_t)k * RS_BS + t;
+    const bool valid = i < n;
+    uint64_t key = 0;
+    uint32_t val = 0;
+    unsigned digit = 256;
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      digit = (unsigned)(key >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const unsigned rank = __popc(peers & lanemask_lt());
+    if (valid && rank == 0) wcnt[w][digit] = __popc(peers);
+    __syncthreads();
+    {  // thread t owns digit t: exclusive prefix over warps
+      uint32_t run = 0;
+#pragma unroll
+      for (int q = 0; q < RS_BS / 32; ++q) {
+        const uint32_t c = wcnt[q][t];
+        wcnt[q][t] = run;
+        run += c;
+      }
+      tot[t] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = base[digit] + wcnt[w][digit] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    base[t] += tot[t];
+  }
+}
+
+size_t radix_temp_bytes(int64_t n) {
+  const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t nh = 256 * nb;
+  return (size_t)nh * 2 * sizeof(uint32_t) + scan_temp_bytes(nh) + 256;
+}
+
+cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                             uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t nh = 256 * nb;
+  uint32_t* hist = (uint32_t*)temp;
+  uint32_t* offs = hist + nh;
+  void* stemp = (void*)(offs + nh);
+  uint64_t* k0 = keys;
+  uint32_t* v0 = vals;
+  uint64_t* k1 = keys_alt;
+  uint32_t* v1 = vals_alt;
+  for (int shift = 0; shift < 64; shift += 8) {
+    MT_COUNT_LAUNCH(1);
+    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb);
+    cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
+    if (e != cudaSuccess) return e;
+    MT_COUNT_LAUNCH(1);
+    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb);
+    uint64_t* tk = k0; k0 = k1; k1 = tk;
+    uint32_t* tv = v0; v0 = v1; v1 = tv;
+  }
+  // 8 passes: the result is back in (keys, vals)
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cluster: sorted candidate p is a new root unless an earlier candidate q
+// with Re_p - Re_q < eps has |Im_p - Im_q| < eps (Chebyshev pixel rule).
+__global__ void k_cluster(const double2* __restrict__ cand, const uint32_t* __restrict__ vals,
+                          int64_t count, const unsigned long long* __restrict__ n_valid,
+                          double eps, uint32_t* __restrict__ flag, DevCounters* ctr) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const int64_t nv = (int64_t)*n_valid;
+  if (p >= nv) { flag[p] = 0; return; }
+  const double2 z = cand[vals[p]];
+  uint32_t rep = 1;
+  int scanned = 0;
+  for (int64_t q = p - 1; q >= 0; --q) {
+    const double2 y = cand[vals[q]];
+    if (z.x - y.x >= eps) break;
+    if (fabs(z.y - y.y) < eps) { rep = 0; break; }
+    if (++scanned >= 4096) { atomicAdd(&ctr->cluster_overflow, 1ull); break; }
+  }
+  flag[p] = rep;
+}
+
+cudaError_t launch_cluster(const double2* cand, const uint32_t* vals, int64_t count,
+                           const unsigned long long* n_valid, double eps, uint32_t* flag,
+                           DevCounters* ctr, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_cluster<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(cand, vals, count, n_valid, eps, flag,
+                                                            ctr);
+  return cudaGetLastError();
+}
+
+__global__ void k_compact(const double2* __restrict__ cand, const uint32_t* __restrict__ vals,
+                          const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                          int64_t count, double2* __restrict__ reps, DevCounters* ctr) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  if (flag[p]) reps[pos[p]] = cand[vals[p]];
+  if (p == count - 1) ctr->n_reps = (unsigned long long)pos[p] + flag[p];
+}
+
+cudaError_t launch_compact(const double2* cand, const uint32_t* vals, const uint32_t* flag,
+                           const uint32_t* pos, int64_t count, double2* reps, DevCounters* ctr,
+                           cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_compact<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(cand, vals, flag, pos, count, reps, ctr);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Emission of the full list: rep u (upper half, sorted by Re) yields
+// (Re, -Im), (Re, +Im) if complex, (Re, 0) if real, at position pos[u].
+__global__ void k_emit(const double2* __restrict__ reps, const unsigned long long* __restrict__ n_reps,
+                       int64_t cap_reps, const uint32_t* __restrict__ mult,
+                       const uint32_t* __restrict__ pos, const uint8_t* __restrict__ type,
+                       int mis_code, double2* __restrict__ out, uint8_t* __restrict__ is_mis,
+                       int64_t cap_out) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= cap_reps || u >= (int64_t)*n_reps) return;
+  const double2 z = reps[u];
+  const int64_t p = pos[u];
+  const uint8_t im = (type && mis_code >= 0) ? (uint8_t)(type[u] == mis_code) : 0;
+  if (mult[u] == 1) {
+    if (p < cap_out) {
+      out[p] = make_double2(z.x, 0.0);
+      if (is_mis) is_mis[p] = im;
+    }
+  } else {
+    if (p < cap_out) {
+      out[p] = make_double2(z.x, -z.y);
+      if (is_mis) is_mis[p] = im;
+    }
+    if (p + 1 < cap_out) {
+      out[p + 1] = make_double2(z.x, z.y);
+      if (is_mis) is_mis[p + 1] = im;
+    }
+  }
+}
+
+cudaError_t launch_emit(const double2* reps, const unsigned long long* n_reps, int64_t cap_reps,
+                        const uint32_t* mult, const uint32_t* pos, const uint8_t* type,
+                        int mis_code, double2* out, uint8_t* is_mis, int64_t cap_out,
+                        cudaStream_t s) {
+  if (cap_reps <= 0) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_emit<<<(unsigned)((cap_reps + 255) / 256), 256, 0, s>>>(reps, n_reps, cap_reps, mult, pos, type,
+                                                            mis_code, out, is_mis, cap_out);
+  return cudaGetLastError();
+}
+
+// Exact ties of Re between distinct roots (rare): sort each run of equal Re
+// by Im so the list follows eq. defLexi.  One thread per run start.
+__global__ void k_fix_ties(double2* out, const unsigned long long* __restrict__ n_full,
+                           int64_t cap_out, uint8_t* is_mis) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)*n_full;
+  if (n > cap_out) n = cap_out;
+  if (p + 1 >= n) return;
+  if (p > 0 && out[p - 1].x == out[p].x) return;  // not the start of a run
+  if (out[p + 1].x != out[p].x) return;
+  int64_t e = p + 1;
+  while (e < n && out[e].x == out[p].x && e - p < 4096) ++e;
+  // insertion sort of [p, e) by Im (runs are tiny)
+  for (int64_t i = p + 1; i < e; ++i) {
+    const double2 v = out[i];
+    const uint8_t m = is_mis ? is_mis[i] : 0;
+    int64_t j = i - 1;
+    while (j >= p && out[j].y > v.y) {
+      out[j + 1] = out[j];
+      if (is_mis) is_mis[j + 1] = is_mis[j];
+      --j;
+    }
+    out[j + 1] = v;
+    if (is_mis) is_mis[j + 1] = m;
+  }
+}
+
+cudaError_t launch_fix_ties(double2* out, const unsigned long long* n_full, int64_t cap_out,
+                            uint8_t* is_mis, cudaStream_t s) {
+  if (cap_out <= 1) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_fix_ties<<<(unsigned)((cap_out + 255) / 256), 256, 0, s>>>(out, n_full, cap_out, is_mis);
+  return cudaGetLastError();
+}
+
+}  // namespace mt

@@ -1,0 +1,130 @@
+// mt_internal.h -- types shared between the host orchestration (mt_api.cu)
+// and the kernel translation units.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mt {
+
+// Polynomial descriptor passed by value to the kernels.
+//   kind 0: P = p_n        m = n,          lcap = -1
+//   kind 1: P = s_{l,n}    m = l + n - 1,  lcap = l - 1
+struct PolyDev {
+  int kind;
+  int l, n;
+  int m;
+  int lcap;
+  int log2d;  // deg P = 2^log2d
+};
+
+// Device-side counters of one split (zeroed at the start of a call).
+struct DevCounters {
+  unsigned long long walk_newton;
+  unsigned long long desc_newton;
+  unsigned long long steps_fp32;
+  unsigned long long steps_dd;
+  unsigned long long n_conv;
+  unsigned long long n_diverge;
+  unsigned long long n_timeout;
+  unsigned long long walk_fail;
+  unsigned long long n_reps;        // distinct roots, upper half (set by cluster pass)
+  unsigned long long n_reps_real;
+  unsigned long long n_full;        // full conjugate-closed count
+  unsigned long long cluster_overflow;
+  unsigned long long n_cert_pass;   // full list
+  unsigned long long min_radius_bits;
+  unsigned long long max_radius_bits;
+  unsigned long long queue_head;    // work queue of the persistent descent
+  unsigned long long queue_head2;   // second queue (batched walk)
+  unsigned long long type_count[64];
+};
+
+// ---- launchers (each returns the launch error) ----------------------------
+
+// a1 + a2: seeds of the chunked level line: seeds[j] = point with external
+// angle index t = j / N0 on |P| = lambda0, j = 0 .. N0/2.
+cudaError_t launch_seed_lift(const PolyDev& P, double lambda0, int64_t N0, int shrink_steps,
+                             double2* seeds, DevCounters* ctr, cudaStream_t s);
+
+// a3: walk chunk j from seeds[j] to seeds[j+1] in L sub-steps (M per turn),
+// writing every 'every'-th point to starts[g / every].
+cudaError_t launch_walk(const PolyDev& P, double lambda0, int M, int every, int64_t L,
+                        int64_t nchunks, const double2* seeds, double2* starts, DevCounters* ctr,
+                        cudaStream_t s);
+
+// a4: persistent Newton descent over 'count' starts.
+cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t count, double tol,
+                           int cap, double2* cand, uint8_t* status, DevCounters* ctr, int block,
+                           cudaStream_t s);
+
+// a0: plain evaluation of P and P' at points.
+cudaError_t launch_eval(const PolyDev& P, const double2* c, int64_t count, double2* out,
+                        cudaStream_t s);
+
+// a5: fold candidates and build sort keys.
+cudaError_t launch_fold_keys(const uint8_t* status, double2* cand, int64_t count, double eps,
+                             uint64_t* keys, uint32_t* vals, cudaStream_t s);
+
+// Exclusive scan of u32 (in place allowed), with total written to *total.
+size_t scan_temp_bytes(int64_t n);
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, void* temp,
+                                  unsigned long long* total, cudaStream_t s);
+
+// LSD radix sort of (key, val) pairs on bits [0, 64).  The result ends in
+// (keys, vals); (keys_alt, vals_alt) are scratch of the same size.
+size_t radix_temp_bytes(int64_t n);
+cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                             uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s);
+
+// Cluster pass on Re-sorted candidates: flag[p] = 1 if sorted candidate p
+// starts a new root (no earlier candidate within the Chebyshev pixel).
+cudaError_t launch_cluster(const double2* cand, const uint32_t* vals, int64_t count,
+                           const unsigned long long* n_valid, double eps, uint32_t* flag,
+                           DevCounters* ctr, cudaStream_t s);
+
+// Gather flagged candidates into reps (order of the sort) and set n_reps.
+cudaError_t launch_compact(const double2* cand, const uint32_t* vals, const uint32_t* flag,
+                           const uint32_t* pos, int64_t count, double2* reps, DevCounters* ctr,
+                           cudaStream_t s);
+
+// a6: polish + type of each rep (upper half), multiplicities for emission.
+cudaError_t launch_classify(const PolyDev& P, double2* reps, const unsigned long long* n_reps,
+                            int64_t cap, double tau, int polish, uint8_t* type, uint32_t* mult,
+                            DevCounters* ctr, cudaStream_t s);
+
+// a7: certify reps (sorted by Re): radius from nearest neighbours, disk test.
+cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
+                           int64_t cap, double tol, const uint32_t* mult, uint8_t* pass,
+                           double* radius, DevCounters* ctr, cudaStream_t s);
+
+// Emit the full conjugate-closed list sorted by (Re, Im).
+cudaError_t launch_emit(const double2* reps, const unsigned long long* n_reps, int64_t cap_reps,
+                        const uint32_t* mult, const uint32_t* pos, const uint8_t* type,
+                        int mis_code, double2* out, uint8_t* is_mis, int64_t cap_out,
+                        cudaStream_t s);
+cudaError_t launch_fix_ties(double2* out, const unsigned long long* n_full, int64_t cap_out,
+                            uint8_t* is_mis, cudaStream_t s);
+
+// Standalone type (a6 without polish) for mt_classify.
+cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t count, double tau,
+                             uint8_t* type, cudaStream_t s);
+
+// Zero the counters (min radius set to +inf).
+cudaError_t launch_init_counters(DevCounters* ctr, cudaStream_t s);
+// keys[i] = order-preserving key of Re pts[i], vals[i] = i.
+cudaError_t launch_keys_plain(const double2* pts, int64_t count, uint64_t* keys, uint32_t* vals,
+                              cudaStream_t s);
+// Standalone certificate of an arbitrary list sorted through 'order'.
+cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint32_t* order,
+                                int64_t count, double tol, uint8_t* pass, double* radius,
+                                DevCounters* ctr, cudaStream_t s);
+
+int device_sm_count();
+
+// Kernel launches issued by this library on the calling thread (reported in
+// mt_stats.n_launches).
+extern thread_local unsigned long long g_launches;
+#define MT_COUNT_LAUNCH(k) (::mt::g_launches += (k))
+
+}  // namespace mt

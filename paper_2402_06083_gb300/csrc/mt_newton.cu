@@ -1,0 +1,125 @@
+// mt_newton.cu -- step a4 (Newton descents) and a0 (plain evaluation).
+//
+// Newton map N_P(z) = z - P(z)/P'(z) (Sec. 3.3, eq. Newton).  Each start of
+// the discrete level line is iterated until the step drops below tol, the
+// iterate jumps far away (a long-distance jump, Sec. 6.4.1), or the cap
+// max{20, I_N log2 d} of Algorithm S_par is reached.
+//
+// GB300 design.  Descent lengths vary (about 10-12 steps when convergent,
+// the cap when not; Sec. 6.4.1), which is the paper's own objection to a
+// GPU port (Sec. 6.4.5: lock-step lanes would make the worst case the
+// norm).  The kernel is persistent: a grid of (SMs x resident blocks) warps
+// drains one atomic work queue; a lane that finishes its descent is refilled
+// at the next step through a warp vote (__ballot_sync) and one atomicAdd per
+// warp, so lanes never idle while the queue holds work.
+#include "mt_common.cuh"
+
+namespace mt {
+
+__global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __restrict__ starts,
+                                                 int64_t count, double tol2, int cap,
+                                                 double2* __restrict__ cand,
+                                                 uint8_t* __restrict__ status, DevCounters* ctr) {
+  const unsigned lane = threadIdx.x & 31;
+  int64_t idx = -1;  // current start (-1: idle, >= count: queue drained)
+  double zr = 0.0, zi = 0.0, rdiv2 = 16.0;
+  int it = 0;
+  unsigned long long steps = 0, nconv = 0, ndiv = 0, nto = 0;
+  for (;;) {
+    // refill idle lanes from the queue (one atomic per warp)
+    const unsigned need = __ballot_sync(0xffffffffu, idx < 0);
+    if (need) {
+      unsigned long long base = 0;
+      if (lane == (unsigned)(__ffs(need) - 1))
+        base = atomicAdd(&ctr->queue_head, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, __ffs(need) - 1);
+      if (idx < 0) {
+        idx = (int64_t)(base + __popc(need & lanemask_lt()));
+        if (idx < count) {
+          const double2 z0 = starts[idx];
+          zr = z0.x;
+          zi = z0.y;
+          it = 0;
+          // long jump: beyond twice the start radius and outside D(0, 4)
+          rdiv2 = fmax(16.0, 4.0 * fma(zr, zr, zi * zi));
+        }
+      }
+    }
+    const bool active = idx >= 0 && idx < count;
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active) {
+      double vr, vi, dr, di;
+      eval_P(P, zr, zi, vr, vi, dr, di);
+      double qr, qi;
+      cdiv_f64(vr, vi, dr, di, qr, qi);
+      zr -= qr;
+      zi -= qi;
+      ++it;
+      ++steps;
+      const double s2 = fma(qr, qr, qi * qi);
+      int outcome = -1;
+      if (!finite2(zr, zi) || fma(zr, zr, zi * zi) > rdiv2) outcome = 1;
+      else if (s2 < tol2) outcome = 0;  // the step that met tol also squared the error
+      else if (it >= cap) outcome = 2;
+      if (outcome >= 0) {
+        cand[idx] = make_double2(zr, zi);
+        status[idx] = (uint8_t)outcome;
+        nconv += outcome == 0;
+        ndiv += outcome == 1;
+        nto += outcome == 2;
+        idx = -1;
+      }
+    }
+  }
+  warp_add_u64(&ctr->desc_newton, steps);
+  warp_add_u64(&ctr->n_conv, nconv);
+  warp_add_u64(&ctr->n_diverge, ndiv);
+  warp_add_u64(&ctr->n_timeout, nto);
+}
+
+__global__ void k_eval(PolyDev P, const double2* __restrict__ c, int64_t count,
+                       double2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double2 z = c[i];
+  double vr, vi, dr, di;
+  eval_P(P, z.x, z.y, vr, vi, dr, di);
+  out[2 * i] = make_double2(vr, vi);
+  out[2 * i + 1] = make_double2(dr, di);
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t count, double tol,
+                           int cap, double2* cand, uint8_t* status, DevCounters* ctr, int block,
+                           cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int bs = 128;
+  (void)block;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend, bs, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)device_sm_count() * per_sm;
+  const int64_t need = (count + bs - 1) / bs;
+  if (grid > need) grid = need;
+  MT_COUNT_LAUNCH(1);
+  k_descend<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, tol * tol, cap, cand, status, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const PolyDev& P, const double2* c, int64_t count, double2* out,
+                        cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int bs = 128;
+  MT_COUNT_LAUNCH(1);
+  k_eval<<<(unsigned)((count + bs - 1) / bs), bs, 0, s>>>(P, c, count, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mt

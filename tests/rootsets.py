@@ -45,6 +45,25 @@ def match_sets(a: np.ndarray, b: np.ndarray) -> tuple[np.ndarray, float]:
     return perm, float(best.max())
 
 
+def match_sorted(a: np.ndarray, b: np.ndarray, tol: float) -> tuple[float, int]:
+    """Compare two root sets of equal size: sort both by (Re, Im), compare
+    entry by entry, and re-pair by nearest neighbour only the entries whose
+    order differs (near-equal real parts).  Returns (max distance, number of
+    re-paired entries)."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    assert a.shape == b.shape, (a.shape, b.shape)
+    sa = a[np.lexsort((a.imag, a.real))]
+    sb = b[np.lexsort((b.imag, b.real))]
+    d = np.abs(sa - sb)
+    bad = d > tol
+    if not bad.any():
+        return float(d.max()) if d.size else 0.0, 0
+    # pair the mismatched entries of both sides among themselves
+    _, dm = match_sets(sa[bad], sb[bad])
+    return max(float(d[~bad].max()) if (~bad).any() else 0.0, dm), int(bad.sum())
+
+
 def lexsorted(z: np.ndarray) -> bool:
     """True if z is sorted by (Re, Im) (eq. defLexi)."""
     z = np.asarray(z)

@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports every symbol include/mtsplit.h
+declares (CPU only: no compute call needs a GPU here)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mtsplit.h")
+
+
+def declared_symbols() -> list[str]:
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"MT_API\s+[\w\s\*]*?\b(mt_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2402_06083_gb300 import build as b
+    b.build()
+    return ctypes.CDLL(b.LIB)
+
+
+def test_header_declares_the_api():
+    syms = declared_symbols()
+    for name in ("mt_split_hyperbolic", "mt_split_misiurewicz", "mt_split_misiurewicz_batch",
+                 "mt_certify", "mt_workspace_bytes", "mt_last_error"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_declares_every_exported_symbol():
+    from paper_2402_06083_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == declared_symbols()
+
+
+def test_host_only_entry_points(lib):
+    """Entry points that touch no device memory run on the CPU machine too."""
+    import paper_2402_06083_gb300 as mt
+    L = mt.load()
+    assert L.mt_degree_hyperbolic(20) == 2 ** 19
+    assert L.mt_degree_hyperbolic(0) == -1 and L.mt_degree_hyperbolic(41) == -1
+    assert L.mt_degree_misiurewicz(2, 14) == 2 ** 14
+    assert L.mt_degree_misiurewicz(1, 3) == -1
+    assert len(mt.misiurewicz_pairs(16)) == 105
+    o = mt.options(stream=0)
+    assert o.max_retries == 1 and o.prec == 0
+    nb = L.mt_workspace_bytes(0, 0, 20, ctypes.byref(o))
+    assert nb > 2 ** 19 * 16 * 4
+    assert L.mt_workspace_bytes(0, 0, 0, ctypes.byref(o)) == 0  # invalid n
+    assert L.mt_workspace_bytes(1, 1, 3, ctypes.byref(o)) == 0  # l < 2
+    assert mt.version().startswith("mtsplit")
+
+
+def test_invalid_arguments_fail_cleanly(lib):
+    """Domain errors are reported before any CUDA call."""
+    import paper_2402_06083_gb300 as mt
+    L = mt.load()
+    o = mt.options(stream=0)
+    n_out = ctypes.c_int64(0)
+    rc = L.mt_split_hyperbolic(0, ctypes.byref(o), None, None, 0, None, 0, ctypes.byref(n_out), None)
+    assert rc == mt._lib.MT_EINVAL and b"out of range" in L.mt_last_error()
+    rc = L.mt_split_hyperbolic(12, ctypes.byref(o), None, None, 0, None, 0, ctypes.byref(n_out), None)
+    assert rc == mt._lib.MT_ENOMEM  # no workspace
+    o.prec = 7
+    rc = L.mt_split_hyperbolic(12, ctypes.byref(o), None, None, 0, None, 0, ctypes.byref(n_out), None)
+    assert rc == mt._lib.MT_EINVAL
