@@ -237,8 +237,11 @@ def test_errors_and_capacity(mt):
     rc = L.mt_split_hyperbolic(n, ctypes.byref(o), small.data_ptr(), None, 10, ws.buf.data_ptr(),
                                100, ctypes.byref(n_out), None)
     assert rc == mt._lib.MT_ENOMEM
-    with pytest.raises(mt.MtError):
+    with pytest.raises((ValueError, mt.MtError)):
         mt.split_hyperbolic(41)
+    rc = L.mt_split_hyperbolic(41, ctypes.byref(o), small.data_ptr(), None, 10, ws.buf.data_ptr(),
+                               ws.buf.numel(), ctypes.byref(n_out), None)
+    assert rc == mt._lib.MT_EINVAL
 
 
 def test_repeated_calls_are_identical(mt):
