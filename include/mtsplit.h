@@ -203,6 +203,33 @@ MT_API mt_status mt_descend(int kind, int l, int n, const mt_options* opts, cons
 MT_API mt_status mt_classify(int kind, int l, int n, const double* d_roots, int64_t count, double tau,
                       uint8_t* d_type, void* stream);
 
+/* ---- certificate without any device allocation --------------------------- */
+
+/* Largest list mt_certify_static accepts, and the size of the device array
+   that holds its scratch. */
+#define MT_CERTIFY_STATIC_MAX_ROOTS 131072
+#define MT_CERTIFY_STATIC_BYTES (4u << 20)
+
+/* The certificate of mt_certify for callers that cannot allocate device
+   memory -- code running in a host callback or an allocator hook, or a
+   plug-in inside a process whose device memory belongs to another
+   runtime's pool.  They pass only the roots and the output arrays; there
+   is no workspace argument and no allocation of any kind.  (The paper has
+   no counterpart: this is a deployment variant of mt_certify.)
+   Arguments and results are those of mt_certify (without d_roots_lo and
+   the workspace): d_roots [count][2] device, d_pass [count] device bytes,
+   d_radius [count] device doubles or NULL, *n_pass host.
+   The scratch is one static device array of MT_CERTIFY_STATIC_BYTES that
+   every GPU loading the library keeps until the process exits; count above
+   MT_CERTIFY_STATIC_MAX_ROOTS returns MT_ECAPACITY.  The first call on a
+   device looks up that array's device address (with the device current);
+   make that first call before any stream capture.  All calls share the
+   array, so calls that overlap on the GPU race: order them (one stream, or
+   synchronise between them).  Synchronises 'stream' before returning. */
+MT_API mt_status mt_certify_static(int kind, int l, int n, const double* d_roots, int64_t count,
+                                   double tol, uint8_t* d_pass, double* d_radius, int64_t* n_pass,
+                                   void* stream);
+
 /* Thread-local message of the last failure ("" if none). */
 MT_API const char* mt_last_error(void);
 

@@ -24,8 +24,9 @@ EXPORTS = (
     "mt_split_hyperbolic", "mt_split_misiurewicz", "mt_misiurewicz_pairs",
     "mt_workspace_bytes_misiurewicz_batch", "mt_split_misiurewicz_batch",
     "mt_certify_workspace_bytes", "mt_certify", "mt_eval", "mt_level_line", "mt_descend",
-    "mt_classify", "mt_last_error", "mt_version",
+    "mt_classify", "mt_certify_static", "mt_last_error", "mt_version",
 )
+MT_CERTIFY_STATIC_MAX_ROOTS = 131072
 
 
 class Options(ctypes.Structure):
@@ -106,6 +107,8 @@ def load() -> ctypes.CDLL:
                                       ctypes.c_size_t, sp]),
         "mt_classify": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64, ctypes.c_double,
                                        vp, vp]),
+        "mt_certify_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64, ctypes.c_double,
+                                             vp, vp, i64p, vp]),
         "mt_last_error": (ctypes.c_char_p, []),
         "mt_version": (ctypes.c_char_p, []),
     }

@@ -344,6 +344,8 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
 
 }  // namespace
 
+void mt::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
 // ===========================================================================
 // C ABI
 extern "C" {

@@ -122,6 +122,9 @@ cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint
 
 int device_sm_count();
 
+// Set the thread-local message returned by mt_last_error().
+void set_error_message(const char* msg);
+
 // Kernel launches issued by this library on the calling thread (reported in
 // mt_stats.n_launches).
 extern thread_local unsigned long long g_launches;
