@@ -32,7 +32,9 @@ CONFIGS = {
     # name: (kind, l, n, precision)
     "hyp12": ("hyp", 0, 12, "fp64"),
     "hyp20": ("hyp", 0, 20, "fp64"),
+    "hyp20mixed": ("hyp", 0, 20, "mixed"),
     "hyp24": ("hyp", 0, 24, "fp64"),
+    "hyp24mixed": ("hyp", 0, 24, "mixed"),
 }
 
 
@@ -180,6 +182,7 @@ def main():
     ap.add_argument("--config", default="hyp20", choices=sorted(CONFIGS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the mixed-tier comparison")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
@@ -202,10 +205,26 @@ def main():
     roots = torch.empty((d, 2), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
-    def step(out=None):
+    def step(out=None, p=None):
+        pp = prec if p is None else p
         if kind == "hyp":
-            return mt.split_hyperbolic(n, prec, work=work, out=roots)
-        return mt.split_misiurewicz(l, n, prec, work=work, out=roots)
+            return mt.split_hyperbolic(n, pp, work=work, out=roots)
+        return mt.split_misiurewicz(l, n, pp, work=work, out=roots)
+
+    def timed(p, steps):
+        for _ in range(3):
+            rr = step(p=p)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        st = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            rr = step(p=p)
+            ev[i][1].record(stream)
+            st.append(rr.stats)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev), st
 
     for _ in range(max(args.warmup, 3)):
         r = step()
@@ -296,6 +315,18 @@ def main():
                    "desc_newton": s0["desc_newton"], "n_chunks": s0["n_chunks"],
                    "wall_s": t_wall},
     }
+    # the same workload in the mixed tier (binary32 tracking, binary64 finish)
+    if prec == "fp64" and not args.no_compare:
+        ms_mix, st_mix = timed("mixed", args.steps)
+        sm = st_mix[-1]
+        line["compare"] = {
+            "mixed": {"value": min(x["n_cert_pass"] for x in st_mix) / (ms_mix / 1e3), "unit": "roots/s",
+                      "ms_per_step": ms_mix, "speedup_vs_fp64": ms / ms_mix,
+                      "prec_used": sm["prec_used"], "steps_fp32": sm["steps_fp32"],
+                      "desc_newton": sm["desc_newton"], "walk_newton": sm["walk_newton"],
+                      "ms_walk": sm["ms_walk"], "ms_descend": sm["ms_descend"],
+                      "ms_certify": sm["ms_certify"], "ms_dedup": sm["ms_dedup"],
+                      "all_certified": all(x["n_cert_pass"] == d for x in st_mix)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(kind, l, n)
     if rank == 0:

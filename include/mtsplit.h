@@ -115,6 +115,8 @@ typedef struct {
   float ms_descend;        /* device time of the Newton descents                   */
   float ms_dedup;          /* device time of fold + sort + cluster + emit          */
   float ms_certify;        /* device time of classify + certify                    */
+  int32_t prec_used;       /* tier of the attempt that produced the result         */
+  int32_t reserved;
 } mt_stats;
 
 /* Defaults documented field by field above. */

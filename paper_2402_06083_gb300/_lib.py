@@ -57,6 +57,7 @@ class Stats(ctypes.Structure):
         ("eps_dup", ctypes.c_double),
         ("ms_total", ctypes.c_float), ("ms_walk", ctypes.c_float), ("ms_descend", ctypes.c_float),
         ("ms_dedup", ctypes.c_float), ("ms_certify", ctypes.c_float),
+        ("prec_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -95,6 +95,7 @@ PolyDev make_poly(int kind, int l, int n) {
 struct Plan {
   PolyDev P;
   int kind;
+  int prec;  // tier of this attempt (MT_FP64 or MT_MIXED)
   int64_t degree;
   double lambda0;
   int M, cL, every;
@@ -119,6 +120,12 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   if (!valid_poly(kind, l, n)) return false;
   Plan p;
   p.kind = kind;
+  p.prec = MT_FP64;
+  if (o && o->prec == MT_MIXED) {
+    // attempt 0 in the mixed tier; a failed attempt repeats in binary64
+    if (retry == 0) p.prec = MT_MIXED;
+    else retry -= 1;
+  }
   p.P = make_poly(kind, l, n);
   p.degree = int64_t(1) << p.P.log2d;
   p.lambda0 = (o && o->lambda0 > 0) ? o->lambda0 : (kind == 0 ? 5.0 : 100.0);
@@ -148,8 +155,11 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   const double IN = (kind == 0) ? 1.0 : 2.6;  // Sec. 4.2
   p.cap = std::max(20, (int)std::ceil(IN * p.P.log2d));
   p.eps = (o && o->eps_dup > 0) ? o->eps_dup : default_eps(kind, l, n);
+  // the step that meets tol leaves an error ~ tol^2 / (root separation); keep
+  // it well inside the separation pixel so duplicates of a root always merge
+  p.tol = std::min(p.tol, 0.05 * p.eps);
   p.cert_tol = (o && o->cert_tol > 0) ? o->cert_tol : (dd ? 1e-20 : 1e-12);
-  p.shrink = 4;
+  p.shrink = 2 << retry;  // iso-angle shrink steps per lifted level
   *pl = p;
   return true;
 }
@@ -161,7 +171,7 @@ struct Buffers {
   uint64_t *keys, *keys_alt;
   uint32_t *vals, *vals_alt, *flag, *pos, *mult, *mpos;
   double* radius;
-  void *scan_tmp, *radix_tmp;
+  void *scan_tmp, *radix_tmp, *anchors;
   size_t bytes;
 };
 
@@ -187,14 +197,20 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
   b.radius = c.take<double>(p.S);
   b.scan_tmp = c.take_bytes(scan_temp_bytes(p.S));
   b.radix_tmp = c.take_bytes(radix_temp_bytes(p.S));
+  b.anchors = (p.prec == MT_MIXED) ? c.take_bytes(mixed_anchor_bytes(p.P, p.S)) : nullptr;
   b.bytes = c.off;
   return b;
 }
 
 size_t plan_bytes(const Plan& p) { return carve(p, nullptr, 0).bytes; }
 
+int max_attempts(const mt_options* o) {
+  const int r = o ? std::max(0, o->max_retries) : 1;
+  return (o && o->prec == MT_MIXED) ? r + 1 : r;
+}
+
 size_t workspace_for(int kind, int l, int n, const mt_options* o) {
-  const int retries = o ? std::max(0, o->max_retries) : 1;
+  const int retries = max_attempts(o);
   size_t best = 0;
   for (int r = 0; r <= retries; ++r) {
     Plan p;
@@ -246,6 +262,7 @@ void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
   st->min_cert_radius = h.n_cert_pass ? mn : 0.0;
   st->max_cert_radius = h.n_cert_pass ? mx : 0.0;
   st->eps_dup = p.eps;
+  st->prec_used = p.prec;
 }
 
 // One pass of the whole sequence.  Leaves counters in *h.
@@ -253,10 +270,25 @@ mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_l
                    uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h) {
   CK(launch_init_counters(b.ctr, s));
   CK(cudaEventRecord(ev.e[0], s));
-  CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
-  CK(launch_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, b.seeds, b.starts, b.ctr, s));
+  if (p.prec == MT_MIXED) {
+    CK(launch_seed_lift_mixed(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+  } else {
+    CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+  }
+  if (p.prec == MT_MIXED) {
+    CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts, b.ctr,
+                         s));
+  } else {
+    CK(launch_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, b.seeds, b.starts, b.ctr, s));
+  }
   CK(cudaEventRecord(ev.e[1], s));
-  CK(launch_descend(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
+  if (p.prec == MT_MIXED) {
+    // binary32 deltas and descent scales live in the (not yet used) sort buffers
+    CK(launch_descend_mixed(p.P, b.starts, p.S, p.tol, p.cap, b.cand, (float2*)b.keys,
+                            (float*)b.vals, b.status, b.anchors, b.ctr, s));
+  } else {
+    CK(launch_descend(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
+  }
   CK(cudaEventRecord(ev.e[2], s));
   CK(launch_fold_keys(b.status, b.cand, p.S, p.eps, b.keys, b.vals, s));
   CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, p.S, b.radix_tmp, s));
@@ -288,6 +320,7 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   if (cap < 0 || (cap > 0 && !d_roots)) return fail(MT_EINVAL, "bad output buffer");
   if (o && o->prec != MT_FP64 && o->prec != MT_MIXED && o->prec != MT_DD)
     return fail(MT_EINVAL, "unknown precision %d", o->prec);
+  if (o && o->prec == MT_DD) return fail(MT_EINVAL, "MT_DD is not available in this build");
   mt_options dflt;
   mt_default_options(&dflt);
   if (!o) o = &dflt;
@@ -304,13 +337,14 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   mt_status rc = MT_OK;
   int retry = 0;
   const unsigned long long launches0 = g_launches;
-  const int max_retries = std::max(0, o->max_retries);
+  const int max_retries = max_attempts(o);
   for (;; ++retry) {
     if (!make_plan(kind, l, n, o, retry, &p)) return fail(MT_EINVAL, "no plan for retry %d", retry);
     Buffers b = carve(p, d_work, work_bytes);
     rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h);
     if (rc != MT_OK) return rc;
-    if ((int64_t)h.n_full == p.degree || retry >= max_retries) break;
+    // retry on missing roots or on a level-line chunk that skipped a turn
+    if (((int64_t)h.n_full == p.degree && h.walk_fail == 0) || retry >= max_retries) break;
   }
   if (st) {
     memset(st, 0, sizeof(*st));
@@ -330,12 +364,12 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     st->ms_certify = ms[4];
   }
   if (n_out) *n_out = (int64_t)h.n_full;
-  if ((int64_t)h.n_full > cap)
-    return fail(MT_ECAPACITY, "%lld roots do not fit in cap %lld", (long long)h.n_full,
-                (long long)cap);
   if ((int64_t)h.n_full != p.degree)
     return fail(MT_EINCOMPLETE, "found %lld roots, degree %lld (after %d retries)",
                 (long long)h.n_full, (long long)p.degree, retry);
+  if ((int64_t)h.n_full > cap)
+    return fail(MT_ECAPACITY, "%lld roots do not fit in cap %lld", (long long)h.n_full,
+                (long long)cap);
   if (h.n_cert_pass != h.n_full)
     return fail(MT_ECERT, "%lld of %lld roots certified", (long long)h.n_cert_pass,
                 (long long)h.n_full);

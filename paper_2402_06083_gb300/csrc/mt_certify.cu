@@ -131,91 +131,86 @@ cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t cou
 }
 
 // ---------------------------------------------------------------------------
-// a7: disk arithmetic in binary64 (Thm diskArithmetic).
-struct Disk {
-  double x, y;  // centre, exact binary64 values
-  double r;     // radius, an upper bound
-};
+// a7: disk arithmetic (Thm diskArithmetic) with binary64 centres.
+//
+// The centres follow exactly the FMA sequence of the binary64 point orbit;
+// each rounding adds half an ulp of its rounded result to the radius (Prop.
+// rounding).  With FMA only the products that are rounded separately
+// contribute an ulp term -- a refinement of the theorem's R_*, whose four
+// product terms assume every product is rounded.  Radii are upper bounds
+// kept in binary32 with every operation rounded upward (__f*_ru): a radius
+// only needs a few correct bits, and this keeps the binary64 pipe for the
+// centres.  ulp terms are built from the binary64 exponent bits as binary32
+// powers of two rounded upward (2^-149 when the true ulp is smaller).
+// Modulus bounds |z| use upward-rounded binary32 conversions and square root.
 
-// the paper's ulp(x) = 2^(e(x) - 53) for normal x, 2^-1074 for subnormals and 0
-__device__ __forceinline__ double ulp64(double x) {
-  const double a = fabs(x);
-  if (!(a >= 2.2250738585072014e-308)) return 4.9406564584124654e-324;
-  const double p2 = __longlong_as_double(__double_as_longlong(a) & 0x7ff0000000000000ll);
-  return p2 * 2.220446049250313e-16;  // exact: product of powers of two above 2^-1074
+// upper bound, in binary32, of the paper's ulp(x) = 2^(e(x) - 53) for a
+// binary64 x (2^-1074 for subnormals and zero)
+__device__ __forceinline__ float ulp_ub(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  const int p = (e == 0) ? -1074 : e - 1075;
+  if (p < -149) return 1.40129846e-45f;  // 2^-149 >= 2^p
+  if (p > 127) return __int_as_float(0x7f800000);
+  if (p >= -126) return __int_as_float((p + 127) << 23);
+  return __int_as_float(1 << (p + 149));
 }
 
-__device__ __forceinline__ double abs_ru(double x, double y) {
-  return __dsqrt_ru(__fma_ru(x, x, __dmul_ru(y, y)));
+// upper bound of |x + iy| in binary32
+__device__ __forceinline__ float abs_ub(double x, double y) {
+  const float ax = __double2float_ru(fabs(x)), ay = __double2float_ru(fabs(y));
+  return __fsqrt_ru(__fmaf_ru(ax, ax, __fmul_ru(ay, ay)));
 }
-__device__ __forceinline__ double abs_rd(double x, double y) {
-  return __dsqrt_rd(__fma_rd(x, x, __dmul_rd(y, y)));
+// lower bound of |x + iy| in binary32
+__device__ __forceinline__ float abs_lb(double x, double y) {
+  return __double2float_rd(__dsqrt_rd(__fma_rd(x, x, __dmul_rd(y, y))));
 }
-
-// D(a) + D(b)
-__device__ __forceinline__ Disk d_add(const Disk& a, const Disk& b) {
-  Disk o;
-  o.x = a.x + b.x;
-  o.y = a.y + b.y;
-  const double half_ulp = __dmul_ru(0.5, __dadd_ru(ulp64(o.x), ulp64(o.y)));
-  o.r = __dadd_ru(__dadd_ru(a.r, b.r), half_ulp);
-  return o;
+__device__ __forceinline__ float hsum_ru(float a, float b) {
+  return __fmul_ru(0.5f, __fadd_ru(a, b));
 }
 
-// D(a) + exact point (cx, cy)
-__device__ __forceinline__ Disk d_add_pt(const Disk& a, double cx, double cy) {
-  Disk o;
-  o.x = a.x + cx;
-  o.y = a.y + cy;
-  o.r = __dadd_ru(a.r, __dmul_ru(0.5, __dadd_ru(ulp64(o.x), ulp64(o.y))));
-  return o;
-}
-
-// D(a) x D(b): centre by two FMAs, R* = 1/2 (ulp Re + ulp Im) + 1/2 sum of the
-// ulps of the four real products, radius ra rb + ra |b| + rb |a| + R*.
-__device__ __forceinline__ Disk d_mul(const Disk& a, const Disk& b) {
-  const double yy = a.y * b.y, yx = a.y * b.x, xx = a.x * b.x, xy = a.x * b.y;
-  Disk o;
-  o.x = fma(a.x, b.x, -yy);
-  o.y = fma(a.x, b.y, yx);
-  double rs = __dadd_ru(__dadd_ru(ulp64(o.x), ulp64(o.y)),
-                        __dadd_ru(__dadd_ru(ulp64(xx), ulp64(yy)), __dadd_ru(ulp64(xy), ulp64(yx))));
-  rs = __dmul_ru(0.5, rs);  // exact unless subnormal; rounded up then
-  const double ma = abs_ru(a.x, a.y), mb = abs_ru(b.x, b.y);
-  double r = __fma_ru(a.r, b.r, rs);
-  r = __fma_ru(a.r, mb, r);
-  r = __fma_ru(b.r, ma, r);
-  o.r = r;
-  return o;
-}
-
-// D(a)^2
-__device__ __forceinline__ Disk d_sqr(const Disk& a) { return d_mul(a, a); }
-
-// Disk orbit of P over D(c, rc): value disk V and derivative disk W.
-__device__ __forceinline__ void disk_orbit(const PolyDev& P, double cx, double cy, double rc,
-                                           Disk& V, Disk& W) {
-  Disk C;
-  C.x = cx;
-  C.y = cy;
-  C.r = rc;
-  Disk z = {0.0, 0.0, 0.0}, dz = {0.0, 0.0, 0.0};
-  Disk zc = {0.0, 0.0, 0.0}, dzc = {0.0, 0.0, 0.0};
+// One orbit over the disk D(c, rc) and over the point c at once (shared
+// centres): returns the value centre V with its point radius rv0, and the
+// derivative centre W with its disk radius rw (W encloses P'(D(c, rc))).
+__device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double cy, float rc,
+                                            double& Vx, double& Vy, float& rv0, double& Wx,
+                                            double& Wy, float& rw) {
+  double zx = 0.0, zy = 0.0, dx = 0.0, dy = 0.0;
+  float rz0 = 0.f, rz = 0.f, rd = 0.f;  // radii: z (point), z (disk), z' (disk)
+  double czx = 0.0, czy = 0.0, cdx = 0.0, cdy = 0.0;
+  float crz0 = 0.f, crd = 0.f;
   for (int k = 1; k <= P.m; ++k) {
-    Disk t = d_mul(z, dz);  // z_{k-1} z'_{k-1}
-    t.x *= 2.0;             // exact scaling by 2
-    t.y *= 2.0;
-    t.r = __dmul_ru(t.r, 2.0);
-    dz = d_add_pt(t, 1.0, 0.0);  // z'_k = 2 z_{k-1} z'_{k-1} + 1
-    z = d_add(d_sqr(z), C);      // z_k = z_{k-1}^2 + C
-    if (k == P.lcap) { zc = z; dzc = dz; }
+    const float mz = abs_ub(zx, zy), md = abs_ub(dx, dy);
+    // z' = 2 z z' + 1: re = fma(2zx, dx, fma(-2zy, dy, 1)), im = fma(2zx, dy, (2zy) dx)
+    const double tzx = zx + zx, tzy = zy + zy;
+    const double in_re = fma(-tzy, dy, 1.0);
+    const double nd_x = fma(tzx, dx, in_re);
+    const double p_im = tzy * dx;
+    const double nd_y = fma(tzx, dy, p_im);
+    const float Rd = hsum_ru(__fadd_ru(ulp_ub(in_re), ulp_ub(nd_x)), __fadd_ru(ulp_ub(p_im), ulp_ub(nd_y)));
+    // radius of 2 (z z'): 2 (rz rd + rz |z'| + rd |z|)
+    const float prod = __fmaf_ru(rz, rd, __fmaf_ru(rz, md, __fmul_ru(rd, mz)));
+    const float nrd = __fmaf_ru(2.f, prod, Rd);
+    // z = z^2 + c: re = fma(zx, zx, fma(-zy, zy, cx)), im = fma(2zx, zy, cy)
+    const double in_z = fma(-zy, zy, cx);
+    const double nz_x = fma(zx, zx, in_z);
+    const double nz_y = fma(tzx, zy, cy);
+    const float Rz = __fadd_ru(hsum_ru(ulp_ub(in_z), ulp_ub(nz_x)), __fmul_ru(0.5f, ulp_ub(nz_y)));
+    // radii of z^2 + C: 2 r |z| + r^2 (+ rc for the disk) + Rz
+    const float mz2 = __fmul_ru(2.f, mz);
+    const float nrz0 = __fmaf_ru(rz0, rz0, __fmaf_ru(mz2, rz0, Rz));
+    const float nrz = __fadd_ru(__fmaf_ru(rz, rz, __fmaf_ru(mz2, rz, Rz)), rc);
+    zx = nz_x; zy = nz_y; dx = nd_x; dy = nd_y;
+    rz0 = nrz0; rz = nrz; rd = nrd;
+    if (k == P.lcap) { czx = zx; czy = zy; cdx = dx; cdy = dy; crz0 = rz0; crd = rd; }
   }
-  if (P.lcap >= 0) {
-    z = d_add(z, zc);
-    dz = d_add(dz, dzc);
+  if (P.lcap >= 0) {  // s_{l,n} = p_m + p_{l-1}: one disk sum each
+    const double vx = zx + czx, vy = zy + czy, wx = dx + cdx, wy = dy + cdy;
+    rz0 = __fadd_ru(__fadd_ru(rz0, crz0), hsum_ru(ulp_ub(vx), ulp_ub(vy)));
+    rd = __fadd_ru(__fadd_ru(rd, crd), hsum_ru(ulp_ub(wx), ulp_ub(wy)));
+    zx = vx; zy = vy; dx = wx; dy = wy;
   }
-  V = z;
-  W = dz;
+  Vx = zx; Vy = zy; rv0 = rz0;
+  Wx = dx; Wy = dy; rw = rd;
 }
 
 // Certify the points of 'pts' (sorted by Re through 'order', or already
@@ -254,14 +249,23 @@ __global__ void k_certify(PolyDev P, const double2* __restrict__ pts,
       }
     }
     rad = fmin(tol, 0.45 * sqrt(nn2));
-    // |P(c)| bound: point disk orbit (radius = accumulated rounding)
-    Disk V0, W0, V, Wd;
-    disk_orbit(P, c.x, c.y, 0.0, V0, W0);
-    const double fz = __dadd_ru(abs_ru(V0.x, V0.y), V0.r);
-    // P'(D(c, rad)) inside B' = Wd
-    disk_orbit(P, c.x, c.y, rad, V, Wd);
-    const double dist = __dsub_rd(abs_rd(Wd.x, Wd.y), Wd.r);
-    ok = isfinite(fz) && isfinite(dist) && dist > 0.0 && rad > 0.0 && __dmul_rd(rad, dist) > fz;
+    // sup |P(c)| from the point orbit, B' = D(W, rw) encloses P'(D(c, rad)).
+    // Between two close roots the critical point sits about half-way, so a
+    // disk of 0.45 nn may bring 0 into B'; then retry with rad / 4, / 16, / 64
+    // (any passing radius proves the root; the disks stay disjoint).
+    for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
+      if (attempt) rad *= 0.25;  // exact
+      // the disk radius must be >= rad: round the binary32 copy upward
+      const float radu = __double2float_ru(rad), radd = __double2float_rd(rad);
+      double Vx, Vy, Wx, Wy;
+      float rv0, rw;
+      disk_orbit2(P, c.x, c.y, radu, Vx, Vy, rv0, Wx, Wy, rw);
+      const float fz = __fadd_ru(abs_ub(Vx, Vy), rv0);
+      const float dist = __fsub_rd(abs_lb(Wx, Wy), rw);
+      // any radius in [radd, radu] is proven: report the lower one
+      ok = isfinite(fz) && isfinite(dist) && dist > 0.f && radd > 0.f && __fmul_rd(radd, dist) > fz;
+      if (ok) rad = (double)radd;
+    }
     pass[ip] = ok ? 1 : 0;
     if (radius) radius[ip] = rad;
     npass = ok ? (mult ? mult[p] : 1u) : 0u;

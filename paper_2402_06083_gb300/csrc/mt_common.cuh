@@ -64,22 +64,29 @@ __device__ __forceinline__ void eval_P(const PolyDev& P, double cr, double ci, d
   else orbit_f64(P.m, P.lcap, 1.0, cr, ci, vr, vi, dr, di);
 }
 
-// Newton quotient (a + ib) / (c + id) with one binary64 division.  Both
-// operands are first scaled by the same power of two 2^-E, E the exponent of
-// max(|c|, |d|) (exact), so |c + id|^2 lies in [1, 8) and never overflows:
-// an escaped orbit (|P'| > 1e154) would otherwise give a zero quotient, a
-// false convergence.  This is the "simplify a common large factor" guard of
-// Sec. 6.3.2 (remark on the exponent range).  Non-finite inputs give NaN.
+// Newton quotient (a + ib) / (c + id) with one binary64 division.  When
+// |c + id|^2 leaves [1e-290, 1e290] (an escaped orbit has |P'| > 1e154 and
+// would give a zero quotient, a false convergence), both operands are first
+// scaled by the same power of two 2^-E, E the exponent of max(|c|, |d|)
+// (exact): the "simplify a common large factor" guard of Sec. 6.3.2 (remark
+// on the exponent range).  Non-finite inputs give NaN.
 __device__ __forceinline__ void cdiv_f64(double a, double b, double c, double d, double& qr,
                                          double& qi) {
-  const double m = fmax(fabs(c), fabs(d));
-  const long long eb = __double_as_longlong(m) & 0x7ff0000000000000ll;
-  const double sc = __longlong_as_double(0x7fe0000000000000ll - eb);  // 2^-E
-  const double cs = c * sc, ds = d * sc, as = a * sc, bs = b * sc;
-  const double inv = 1.0 / fma(cs, cs, ds * ds);
-  qr = fma(as, cs, bs * ds) * inv;
-  qi = fma(bs, cs, -as * ds) * inv;
-  if (!(m < 1.0e308)) qr = qi = __longlong_as_double(0x7ff8000000000000ll);  // inf / NaN input
+  double den = fma(c, c, d * d);
+  if (!(den <= 1e290 && den >= 1e-290)) {
+    const double m = fmax(fabs(c), fabs(d));
+    const long long eb = __double_as_longlong(m) & 0x7ff0000000000000ll;
+    const double sc = __longlong_as_double(0x7fe0000000000000ll - eb);  // 2^-E
+    c *= sc;
+    d *= sc;
+    a *= sc;
+    b *= sc;
+    den = fma(c, c, d * d);
+    if (!(m < 1.0e308)) den = __longlong_as_double(0x7ff8000000000000ll);  // inf / NaN input
+  }
+  const double inv = 1.0 / den;
+  qr = fma(a, c, b * d) * inv;
+  qi = fma(b, c, -a * d) * inv;
 }
 
 __device__ __forceinline__ bool finite2(double a, double b) {
@@ -90,6 +97,12 @@ __device__ __forceinline__ bool finite2(double a, double b) {
 __device__ __forceinline__ void unit_phase(uint64_t num, uint64_t den, double& c, double& s) {
   const uint64_t r = num & (den - 1);
   sincospi(2.0 * ((double)r / (double)den), &s, &c);
+}
+
+// Squared rounding floor of a binary64 Newton step at z: (16 ulp(1 + |z|))^2.
+__device__ __forceinline__ double floor2_f64(double zr, double zi) {
+  const double a = (1.0 + fabs(zr) + fabs(zi)) * 3.552713678800501e-15;  // 16 * 2^-52
+  return a * a;
 }
 
 // ---------------------------------------------------------------------------

@@ -58,6 +58,17 @@ cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t coun
                            int cap, double2* cand, uint8_t* status, DevCounters* ctr, int block,
                            cudaStream_t s);
 
+// a1-a4 in the mixed tier (binary32 perturbation around binary64 anchors).
+cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0, int shrink_steps,
+                                   double2* seeds, DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
+                              int64_t nchunks, int K, const double2* seeds, double2* starts,
+                              DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_t count, double tol,
+                                 int cap, double2* cand, float2* dlt, float* hscale, uint8_t* status,
+                                 void* anchors, DevCounters* ctr, cudaStream_t s);
+size_t mixed_anchor_bytes(const PolyDev& P, int64_t count);
+
 // a0: plain evaluation of P and P' at points.
 cudaError_t launch_eval(const PolyDev& P, const double2* c, int64_t count, double2* out,
                         cudaStream_t s);

@@ -21,33 +21,57 @@
 
 namespace mt {
 
-// Newton map with target (Sec. 4.1): iterate z <- z - (P_alpha(z) - T) / P_alpha'(z)
-// until the step falls below max(rel * first step, floor) or stagnates.
-// Returns the number of Newton steps.
+// Newton map with target (Sec. 4.1): iterate z <- z - (P_alpha(z) - T) / P_alpha'(z).
+//
+// Predictor.  When the previous target Tp and L = log(T / Tp) are known
+// (pred = true), the first step solves log P = log T instead of P = T:
+//   z <- z + P log(T / P) / P',   log(T / P) ~ L + (Tp - P) / P,
+// i.e. an Euler step of the level-line ODE lambda' = i P / P' (eq.
+// LevelLinesFlow; L = i 2 pi / M for a walk sub-step) or of the Newton flow
+// (real L for a radial shrink).  log P is d times less curved than P near
+// the line, so the predictor lands almost on the target and one Newton
+// correction usually meets the tolerance (a chord step P -> T leaves an
+// error of order |L|^2 / 2 that needs ~4 more steps).
+//
+// Stop once a step falls below rel * h (h = the predictor's length; errors
+// never accumulate along the walk because every target is an exact phase),
+// or when steps stop shrinking after the third (rounding floor).  Returns
+// the number of Newton steps; *first receives h.
 __device__ __forceinline__ int newton_target_f64(int m, int lcap, double alpha, double& zr,
                                                  double& zi, double tr, double ti, double rel,
-                                                 int cap, double* first_step) {
-  double h2 = 0.0, prev2 = 1e300;
+                                                 int cap, double* first, bool pred = false,
+                                                 double tpr = 0.0, double tpi = 0.0,
+                                                 double Lr = 0.0, double Li = 0.0) {
+  double thr2 = 0.0, prev2 = 0.0, h2 = 0.0;
   int it = 0;
-  for (; it < cap;) {
+  while (it < cap) {
     double vr, vi, dr, di;
     if (lcap < 0) orbit_pn_f64(m, zr, zi, vr, vi, dr, di);
     else orbit_f64(m, lcap, alpha, zr, zi, vr, vi, dr, di);
+    double nr, ni;
+    if (it == 0 && pred) {  // P - Tp - L P
+      nr = (vr - tpr) - fma(Lr, vr, -Li * vi);
+      ni = (vi - tpi) - fma(Lr, vi, Li * vr);
+    } else {
+      nr = vr - tr;
+      ni = vi - ti;
+    }
     double qr, qi;
-    cdiv_f64(vr - tr, vi - ti, dr, di, qr, qi);
+    cdiv_f64(nr, ni, dr, di, qr, qi);
     if (!finite2(qr, qi)) break;
     zr -= qr;
     zi -= qi;
     ++it;
     const double s2 = fma(qr, qr, qi * qi);
-    if (it == 1) h2 = s2;
-    const double mag = 1.0 + fabs(zr) + fabs(zi);
-    const double floor2 = (4e-16 * mag) * (4e-16 * mag);
-    if (s2 <= rel * rel * h2 || s2 <= floor2) break;
-    if (it >= 3 && s2 > 0.25 * prev2) break;  // rounding floor reached
+    if (it == 1) {
+      h2 = s2;
+      thr2 = rel * rel * s2;
+    } else if (s2 <= thr2 || (it >= 3 && s2 > 0.25 * prev2)) {
+      break;  // converged, or at the rounding floor
+    }
     prev2 = s2;
   }
-  if (first_step) *first_step = sqrt(h2);
+  if (first) *first = sqrt(h2);
   return it;
 }
 
@@ -71,13 +95,13 @@ __global__ void k_seed_lift(PolyDev P, double lambda0, int64_t N0, int log2N0, i
       // phase of level k+1: d_{k+1} t = 2^k j / N0 (exact in integers)
       const uint64_t num = (k >= log2N0) ? 0 : (((uint64_t)j << k) & (uint64_t)(N0 - 1));
       unit_phase(num, (uint64_t)N0, c, s);
-      const bool last_level = (k == P.m - 1) && P.kind == 0;
       steps += newton_target_f64(k + 1, -1, 0.0, zr, zi, lam2 * c, lam2 * s, 1e-3, 40, nullptr);
+      const double Lq = -log(lambda0) / shrink;  // log of the radius ratio per shrink step
       for (int q = 1; q <= shrink; ++q) {
+        const double rp = pow(lambda0, 2.0 - (double)(q - 1) / shrink);
         const double r = pow(lambda0, 2.0 - (double)q / shrink);
-        const bool tight = last_level && q == shrink;
-        steps += newton_target_f64(k + 1, -1, 0.0, zr, zi, r * c, r * s, tight ? 0.0 : 1e-3,
-                                   tight ? 60 : 40, nullptr);
+        steps += newton_target_f64(k + 1, -1, 0.0, zr, zi, r * c, r * s, 1e-3, 40, nullptr, true,
+                                   rp * c, rp * s, Lq, 0.0);
       }
     }
     if (P.kind == 1) {
@@ -88,8 +112,8 @@ __global__ void k_seed_lift(PolyDev P, double lambda0, int64_t N0, int log2N0, i
       const int A = 8;
       for (int a = 1; a <= A; ++a) {
         const double alpha = (double)a / A;
-        steps += newton_target_f64(P.m, P.lcap, alpha, zr, zi, lambda0 * c, lambda0 * s,
-                                   a == A ? 0.0 : 1e-3, a == A ? 60 : 40, nullptr);
+        steps += newton_target_f64(P.m, P.lcap, alpha, zr, zi, lambda0 * c, lambda0 * s, 1e-3, 40,
+                                   nullptr);
       }
     }
     if (j == 0 || j == N0 / 2) zi = 0.0;  // the two real end points of the line
@@ -118,10 +142,13 @@ __global__ void k_walk(PolyDev P, double lambda0, int M, int every, int64_t L, i
     double zr = z0.x, zi = z0.y;
     uint64_t g = (uint64_t)j * (uint64_t)L;
     double h = 0.0;
+    const double Li = 6.283185307179586 / M;  // L = log(T / Tp) = i 2 pi / M
     for (int64_t i = 0; i < L; ++i, ++g) {
       if ((g & (uint64_t)(every - 1)) == 0) starts[g / every] = make_double2(zr, zi);
+      const double2 Tp = ph[g & (uint64_t)(M - 1)];
       const double2 T = ph[(g + 1) & (uint64_t)(M - 1)];
-      steps += newton_target_f64(P.m, P.lcap, 1.0, zr, zi, T.x, T.y, 1e-6, 16, &h);
+      steps += newton_target_f64(P.m, P.lcap, 1.0, zr, zi, T.x, T.y, 1e-2, 16, &h, true, Tp.x, Tp.y,
+                                 0.0, Li);
     }
     if (j == nchunks - 1) starts[g / every] = make_double2(zr, 0.0);  // t = 1/2, real
     const double2 zn = seeds[j + 1];

@@ -1,0 +1,523 @@
+// mt_mixed.cu -- the mixed-precision tier (MT_MIXED): binary32 level-line
+// tracking and early Newton steps, binary64 anchors and binary64 finish.
+//
+// Why.  The paper runs everything in FP80 (Sec. 6.1) and notes that GPUs
+// offer little beyond FP64 (Sec. 6.4.5).  On a GB300 the binary64 pipe is
+// the bottleneck (about 1.2 TFLOP/s) while binary32 runs ~60x faster, so the
+// bulk of the Newton steps -- which only need to stay in the right basin --
+// move to binary32, and binary64 is spent where precision is decided.
+//
+// How.  Absolute binary32 coordinates cannot resolve the level line at the
+// periods of interest (sub-step spacings reach 1e-11 near c = -2 at n = 20),
+// so the binary32 work is done in perturbation form around a binary64
+// anchor c0 (the published perturbation technique of deep-zoom Mandelbrot
+// renderers): with Z_k = p_k(c0) in binary64 and c = c0 + delta,
+//   e_{k+1} = (2 Z_k + e_k) e_k + delta,   p_k(c) = Z_k + e_k,
+//   p'_{k+1}(c) = 2 (Z_k + e_k) p'_k(c) + 1            (binary32),
+// so binary32 carries only the difference from the anchor and its relative
+// precision applies to |delta|, not to |c|.  The residual P(c) - T is
+// (Z_m - T) + e_m with Z_m split into binary32 hi + lo.
+//   - Walk: the anchor is re-taken every K sub-steps (less than a turn of
+//     the phase) from the current point, so |delta| stays a few sub-steps.
+//   - Descent: the anchor is the start point; binary32 Newton steps run to
+//     the binary32 floor, then binary64 Newton steps (normally two) finish
+//     to the binary64 tolerance (eq. Newton).
+// Every anchor orbit and every finishing step is binary64; the chunk-end
+// check of the walk and the count check catch any tracking failure, and the
+// host then repeats the split in plain binary64.
+#include "mt_common.cuh"
+
+namespace mt {
+
+constexpr int MIX_MAXM = 41;
+constexpr int64_t MIX_BATCH = int64_t(1) << 23;  // starts per anchor batch
+
+// binary64 reference orbit at c0: zs[k * stride] = Z_k in binary32 for
+// k = 0 .. m-1, and v = P(c0) = Z_m (+ Z_lcap) as binary32 hi (x, y) + lo (z, w).
+__device__ __forceinline__ void ref_orbit(const PolyDev& P, double c0x, double c0y, float2* zs,
+                                          int stride, float4& v) {
+  double zx = 0.0, zy = 0.0, capx = 0.0, capy = 0.0;
+  zs[0] = make_float2(0.f, 0.f);
+  for (int k = 1; k <= P.m; ++k) {
+    const double nx = fma(zx, zx, fma(-zy, zy, c0x));
+    const double ny = fma(zx + zx, zy, c0y);
+    zx = nx;
+    zy = ny;
+    if (k < P.m) zs[k * stride] = make_float2((float)zx, (float)zy);
+    if (k == P.lcap) { capx = zx; capy = zy; }
+  }
+  const double vx = zx + capx, vy = zy + capy;
+  const float hx = (float)vx, hy = (float)vy;
+  v = make_float4(hx, hy, (float)(vx - (double)hx), (float)(vy - (double)hy));
+}
+
+// binary32 perturbation orbit: e = P(c0 + delta) - P(c0), D = P'(c0 + delta).
+__device__ __forceinline__ void pert_eval(const PolyDev& P, const float2* zs, int stride, float dx,
+                                          float dy, float& ex, float& ey, float& Dx, float& Dy) {
+  float e_x = 0.f, e_y = 0.f, d_x = 0.f, d_y = 0.f;
+  float ce_x = 0.f, ce_y = 0.f, cd_x = 0.f, cd_y = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < P.m; ++k) {
+    const float2 Z = zs[k * stride];
+    const float zx = Z.x + e_x, zy = Z.y + e_y;  // p_k(c)
+    const float tzx = zx + zx, tzy = zy + zy;
+    const float nd_x = fmaf(tzx, d_x, fmaf(-tzy, d_y, 1.f));
+    const float nd_y = fmaf(tzx, d_y, tzy * d_x);
+    const float sx = Z.x + zx, sy = Z.y + zy;  // 2 Z_k + e_k
+    const float ne_x = fmaf(sx, e_x, fmaf(-sy, e_y, dx));
+    const float ne_y = fmaf(sx, e_y, fmaf(sy, e_x, dy));
+    e_x = ne_x; e_y = ne_y; d_x = nd_x; d_y = nd_y;
+    if (k + 1 == P.lcap) { ce_x = e_x; ce_y = e_y; cd_x = d_x; cd_y = d_y; }
+  }
+  ex = e_x + ce_x;
+  ey = e_y + ce_y;
+  Dx = d_x + cd_x;
+  Dy = d_y + cd_y;
+}
+
+// binary32 quotient; false when |D|^2 leaves the safe binary32 range.
+__device__ __forceinline__ bool cdiv_f32(float a, float b, float c, float d, float& qr, float& qi) {
+  const float den = fmaf(c, c, d * d);
+  if (!(den < 1e36f && den > 1e-36f)) return false;
+  const float inv = __frcp_rn(den);
+  qr = fmaf(a, c, b * d) * inv;
+  qi = fmaf(b, c, -a * d) * inv;
+  return isfinite(qr) && isfinite(qi);
+}
+
+// Newton with target in perturbation form: the binary32 twin of the walk's
+// newton_target_f64, with the same predictor (pred: first step solves
+// log P = log T from the previous target Tp, L = log(T / Tp)) and stop rule.
+__device__ __forceinline__ int newton_target_pert(const PolyDev& P, const float2* zs, int stride,
+                                                  const float4& v, float& dx, float& dy, float tx,
+                                                  float ty, float rel, int cap, float* first,
+                                                  bool pred, float tpx, float tpy, float Lr,
+                                                  float Li, bool* bad) {
+  float thr2 = 0.f, prev2 = 0.f, h2 = 0.f;
+  int it = 0;
+  while (it < cap) {
+    float ex, ey, Dx, Dy;
+    pert_eval(P, zs, stride, dx, dy, ex, ey, Dx, Dy);
+    float nr, ni;
+    if (it == 0 && pred) {  // P - Tp - L P
+      const float Pr = v.x + (v.z + ex), Pi = v.y + (v.w + ey);
+      nr = (Pr - tpx) - fmaf(Lr, Pr, -Li * Pi);
+      ni = (Pi - tpy) - fmaf(Lr, Pi, Li * Pr);
+    } else {
+      nr = ((v.x - tx) + v.z) + ex;
+      ni = ((v.y - ty) + v.w) + ey;
+    }
+    float qr, qi;
+    if (!cdiv_f32(nr, ni, Dx, Dy, qr, qi)) { *bad = true; break; }
+    dx -= qr;
+    dy -= qi;
+    ++it;
+    const float s2 = fmaf(qr, qr, qi * qi);
+    if (it == 1) {
+      h2 = s2;
+      thr2 = rel * rel * s2;
+    } else if (s2 <= thr2 || (it >= 3 && s2 > 0.25f * prev2)) {
+      break;
+    }
+    prev2 = s2;
+  }
+  if (first) *first = sqrtf(h2);
+  return it;
+}
+
+// a1 + a2 in the mixed tier: the lift of k_seed_lift (Sec. 4.2) with each
+// level's solves in perturbation form around the point reached at the
+// previous level (one binary64 reference orbit of p_{k+1} per level instead
+// of ~(1 + shrink) x 3 binary64 Newton steps).  The s_{l,n} homotopy at the
+// last level stays binary64.
+__global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log2N0, int shrink,
+                                  double2* seeds, DevCounters* ctr) {
+  extern __shared__ float2 zsh[];
+  float2* zs = zsh + threadIdx.x;
+  const int stride = blockDim.x;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long steps = 0, s32 = 0, fails = 0;
+  if (j <= N0 / 2) {
+    double c, s;
+    unit_phase((uint64_t)j, (uint64_t)N0, c, s);
+    double zr = lambda0 * c, zi = lambda0 * s;
+    const float lam2 = (float)(lambda0 * lambda0);
+    const float Lq = (float)(-log(lambda0) / shrink);
+    bool bad = false;
+    for (int k = 1; k < P.m; ++k) {
+      const uint64_t num = (k >= log2N0) ? 0 : (((uint64_t)j << k) & (uint64_t)(N0 - 1));
+      unit_phase(num, (uint64_t)N0, c, s);
+      PolyDev Q;
+      Q.kind = 0; Q.l = 0; Q.n = k + 1; Q.m = k + 1; Q.lcap = -1; Q.log2d = k;
+      float4 v;
+      ref_orbit(Q, zr, zi, zs, stride, v);
+      float dx = 0.f, dy = 0.f;
+      const float ec = (float)c, es = (float)s;
+      int it = newton_target_pert(Q, zs, stride, v, dx, dy, lam2 * ec, lam2 * es, 1e-3f, 40, nullptr,
+                                  false, 0.f, 0.f, 0.f, 0.f, &bad);
+      for (int q = 1; q <= shrink; ++q) {
+        const float rp = (float)pow(lambda0, 2.0 - (double)(q - 1) / shrink);
+        const float r = (float)pow(lambda0, 2.0 - (double)q / shrink);
+        it += newton_target_pert(Q, zs, stride, v, dx, dy, r * ec, r * es, 1e-3f, 40, nullptr, true,
+                                 rp * ec, rp * es, Lq, 0.f, &bad);
+      }
+      steps += it;
+      s32 += it;
+      zr += (double)dx;
+      zi += (double)dy;
+    }
+    if (P.kind == 1) {
+      // binary64 homotopy p_m -> p_m + p_{l-1} (as in k_seed_lift)
+      const int k = P.m - 1;
+      const uint64_t num = (k >= log2N0) ? 0 : (((uint64_t)j << k) & (uint64_t)(N0 - 1));
+      unit_phase(num, (uint64_t)N0, c, s);
+      for (int a = 1; a <= 8; ++a) {
+        const double alpha = a / 8.0;
+        for (int t = 0; t < 40; ++t) {
+          double vr, vi, dr, di, qr, qi;
+          orbit_f64(P.m, P.lcap, alpha, zr, zi, vr, vi, dr, di);
+          cdiv_f64(vr - lambda0 * c, vi - lambda0 * s, dr, di, qr, qi);
+          if (!finite2(qr, qi)) break;
+          zr -= qr;
+          zi -= qi;
+          ++steps;
+          if (fma(qr, qr, qi * qi) <= 1e-24 * fma(zr, zr, zi * zi) + 1e-300) break;
+        }
+      }
+    }
+    if (j == 0 || j == N0 / 2) zi = 0.0;
+    seeds[j] = make_double2(zr, zi);
+    fails = bad ? 1 : 0;
+  }
+  warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->steps_fp32, s32);
+  warp_add_u64(&ctr->walk_fail, fails);
+}
+
+// a3 in the mixed tier.  Shared memory: m x blockDim binary32 pairs.
+__global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
+                             int K, const double2* __restrict__ seeds, double2* __restrict__ starts,
+                             DevCounters* ctr) {
+  extern __shared__ float2 zsh[];
+  __shared__ float2 ph[64];
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    double c, s;
+    unit_phase((uint64_t)q, (uint64_t)M, c, s);
+    ph[q] = make_float2((float)(lambda0 * c), (float)(lambda0 * s));
+  }
+  __syncthreads();
+  float2* zs = zsh + threadIdx.x;
+  const int stride = blockDim.x;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long steps = 0, anchors = 0, fails = 0;
+  if (j < nchunks) {
+    const double2 s0 = seeds[j];
+    double c0x = s0.x, c0y = s0.y;
+    float4 v;
+    ref_orbit(P, c0x, c0y, zs, stride, v);
+    ++anchors;
+    float dx = 0.f, dy = 0.f, h = 0.f;
+    bool bad = false;
+    const float Li = 6.2831853f / M;
+    uint64_t g = (uint64_t)j * (uint64_t)L;
+    for (int64_t i = 0; i < L; ++i, ++g) {
+      if ((g & (uint64_t)(every - 1)) == 0)
+        starts[g / every] = make_double2(c0x + (double)dx, c0y + (double)dy);
+      const float2 Tp = ph[g & (uint64_t)(M - 1)];
+      const float2 T = ph[(g + 1) & (uint64_t)(M - 1)];
+      steps += newton_target_pert(P, zs, stride, v, dx, dy, T.x, T.y, 1e-2f, 16, &h, true, Tp.x, Tp.y,
+                                  0.f, Li, &bad);
+      if (((i + 1) % K) == 0 && i + 1 < L) {  // re-anchor at the current point
+        c0x += (double)dx;
+        c0y += (double)dy;
+        dx = dy = 0.f;
+        ref_orbit(P, c0x, c0y, zs, stride, v);
+        ++anchors;
+      }
+    }
+    const double cx = c0x + (double)dx, cy = c0y + (double)dy;
+    if (j == nchunks - 1) starts[g / every] = make_double2(cx, 0.0);
+    const double2 zn = seeds[j + 1];
+    const double er = cx - zn.x, ei = cy - zn.y;
+    const double hh = (double)h;
+    if (bad || !(er * er + ei * ei <= 0.0625 * hh * hh + 1e-28)) fails = 1;
+  }
+  warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->steps_fp32, steps);
+  warp_add_u64(&ctr->walk_fail, fails);
+  (void)anchors;
+}
+
+// Float-float (binary32 pair) arithmetic from the published error-free
+// transforms: Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based TwoProd.
+// ~48-bit accurate; used where a binary64 result is not needed but binary32
+// is not enough (the descents' anchor orbits).
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff ff_from(double x) {
+  ff r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ ff ff_norm(float s, float e) {  // FastTwoSum, |s| >= |e|
+  ff r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.hi + b.hi;  // TwoSum
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+  return ff_norm(s, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;  // TwoProd
+  const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_twice(ff a) { return ff{a.hi + a.hi, a.lo + a.lo}; }
+
+// a4 in the mixed tier, anchors: for starts [base, base + cnt), the
+// reference orbit of each start in float-float, rounded to binary32 and
+// stored k-major (anch[(k - 1) * cnt + i] = Z_k, k = 1 .. m-1) so this write
+// and the descent's reads are coalesced, plus P(start) as binary32 hi + lo
+// and the long-jump bound on |delta|.  The anchor only steers the binary32
+// descent into the basin of its root (the binary64 finish sets the digits),
+// so float-float's ~1e-14 suffices and keeps this off the binary64 pipe.  A
+// uniform launch: computed inside the persistent descent, the orbit of one
+// refilling lane would be issued by its whole warp at nearly every step.
+__global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, int64_t base,
+                                int64_t cnt, float2* __restrict__ anch, float4* __restrict__ vv,
+                                float* __restrict__ rdel) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  const double2 c0 = starts[base + i];
+  const ff cx = ff_from(c0.x), cy = ff_from(c0.y);
+  ff zx{0.f, 0.f}, zy{0.f, 0.f}, capx{0.f, 0.f}, capy{0.f, 0.f};
+  for (int k = 1; k <= P.m; ++k) {
+    const ff nx = ff_add(ff_add(ff_mul(zx, zx), ff_neg(ff_mul(zy, zy))), cx);
+    const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
+    zx = nx;
+    zy = ny;
+    if (k < P.m) anch[(int64_t)(k - 1) * cnt + i] = make_float2(zx.hi, zy.hi);
+    if (k == P.lcap) { capx = zx; capy = zy; }
+  }
+  const ff vx = ff_add(zx, capx), vy = ff_add(zy, capy);
+  vv[i] = make_float4(vx.hi, vy.hi, vx.lo, vy.lo);
+  // long jump (as in k_descend: |c| > max(4, 2|c0|)); |delta| beyond rdel implies it
+  const float r0 = sqrtf(fmaf(cx.hi, cx.hi, cy.hi * cy.hi)) * 1.0001f;
+  rdel[i] = fmaxf(4.f, 2.f * r0) + r0;
+}
+
+// a4 in the mixed tier, binary32 phase (persistent, per-lane refill as in
+// k_descend) over starts [base, base + cnt).  A refilling lane copies its
+// anchor orbit to its shared-memory slot; the loop is binary32 only.  Each
+// descent runs binary32 Newton steps to the binary32 floor and leaves delta
+// with status 3 ("finish in binary64"), or stops as divergent (1) / timed
+// out (2).  The binary64 finish runs in k_finish_f64, a separate uniform
+// launch.
+__global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, int64_t cnt,
+                                                       const float2* __restrict__ anch,
+                                                       const float4* __restrict__ vv,
+                                                       const float* __restrict__ rdel, int cap,
+                                                       float2* __restrict__ dlt,
+                                                       float* __restrict__ hscale,
+                                                       uint8_t* __restrict__ status,
+                                                       unsigned long long* queue,
+                                                       DevCounters* ctr) {
+  extern __shared__ float2 zsh[];
+  float2* zs = zsh + threadIdx.x;
+  const int stride = blockDim.x;
+  const unsigned lane = threadIdx.x & 31;
+  int64_t idx = -1;
+  float dx = 0.f, dy = 0.f, h1 = 0.f, prev2 = 0.f, rdelta = 0.f;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  int it = 0;
+  unsigned long long s32 = 0, ndiv = 0, nto = 0;
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, idx < 0);
+    if (need) {
+      unsigned long long b0 = 0;
+      if (lane == (unsigned)(__ffs(need) - 1)) b0 = atomicAdd(queue, (unsigned long long)__popc(need));
+      b0 = __shfl_sync(0xffffffffu, b0, __ffs(need) - 1);
+      if (idx < 0) {
+        idx = (int64_t)(b0 + __popc(need & lanemask_lt()));
+        if (idx < cnt) {
+          zs[0] = make_float2(0.f, 0.f);
+          for (int k = 1; k < P.m; ++k) zs[k * stride] = anch[(int64_t)(k - 1) * cnt + idx];
+          v = vv[idx];
+          rdelta = rdel[idx];
+          dx = dy = 0.f;
+          it = 0;
+          prev2 = 0.f;
+          h1 = 0.f;
+        }
+      }
+    }
+    const bool active = idx >= 0 && idx < cnt;
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active) {
+      int outcome = -1;
+      float ex, ey, Dx, Dy, qr, qi;
+      pert_eval(P, zs, stride, dx, dy, ex, ey, Dx, Dy);
+      const float nr = (v.x + v.z) + ex, ni = (v.y + v.w) + ey;
+      if (!cdiv_f32(nr, ni, Dx, Dy, qr, qi)) {
+        outcome = 3;  // out of binary32 range: binary64 decides
+      } else {
+        dx -= qr;
+        dy -= qi;
+        ++it;
+        ++s32;
+        const float s2 = fmaf(qr, qr, qi * qi);
+        h1 = fmaxf(h1, s2);  // largest step so far
+        if (!(fmaf(dx, dx, dy * dy) <= rdelta * rdelta)) outcome = 1;
+        // binary32 floor: the step is 1e-5 of the descent's scale, or it
+        // stopped shrinking once already below 1e-3 of it
+        else if (s2 <= 1e-10f * h1 || (s2 <= 1e-6f * h1 && s2 > 0.25f * prev2)) outcome = 3;
+        else if (it >= cap) outcome = 2;
+        prev2 = s2;
+      }
+      if (outcome >= 0) {
+        dlt[base + idx] = make_float2(dx, dy);
+        hscale[base + idx] = h1;
+        status[base + idx] = (uint8_t)outcome;
+        ndiv += outcome == 1;
+        nto += outcome == 2;
+        idx = -1;
+      }
+    }
+  }
+  warp_add_u64(&ctr->desc_newton, s32);
+  warp_add_u64(&ctr->steps_fp32, s32);
+  warp_add_u64(&ctr->n_diverge, ndiv);
+  warp_add_u64(&ctr->n_timeout, nto);
+}
+
+// a4 in the mixed tier, binary64 finish: Newton steps (eq. Newton) from each
+// candidate left in status 3 until |step| < tol (normally two steps).
+__global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, int64_t count, double tol2, int cap,
+                                                    const double2* __restrict__ starts,
+                                                    const float2* __restrict__ dlt,
+                                                    const float* __restrict__ hscale,
+                                                    double2* __restrict__ cand,
+                                                    uint8_t* __restrict__ status,
+                                                    DevCounters* ctr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long s64 = 0, nconv = 0, ndiv = 0, nto = 0;
+  if (i < count && status[i] != 3) {
+    const double2 c0 = starts[i];
+    const float2 d = dlt[i];
+    cand[i] = make_double2(c0.x + (double)d.x, c0.y + (double)d.y);  // discarded descents
+  }
+  if (i < count && status[i] == 3) {
+    const double2 c0 = starts[i];
+    const float2 d = dlt[i];
+    double2 z = make_double2(c0.x + (double)d.x, c0.y + (double)d.y);
+    int outcome = 2;
+    double prev2 = 1e300;
+    for (int it = 0; it < cap; ++it) {
+      double vr, vi, dr, di, qr, qi;
+      eval_P(P, z.x, z.y, vr, vi, dr, di);
+      cdiv_f64(vr, vi, dr, di, qr, qi);
+      z.x -= qr;
+      z.y -= qi;
+      ++s64;
+      const double s2 = fma(qr, qr, qi * qi);
+      if (!finite2(z.x, z.y) || fma(z.x, z.x, z.y * z.y) > 1e4) { outcome = 1; break; }
+      if (s2 < tol2) { outcome = 0; break; }
+      if (s2 >= 0.25 * prev2 && s2 < floor2_f64(z.x, z.y)) { outcome = 0; break; }  // rounding floor
+
+      prev2 = s2;
+    }
+    cand[i] = z;
+    status[i] = (uint8_t)outcome;
+    nconv += outcome == 0;
+    ndiv += outcome == 1;
+    nto += outcome == 2;
+  }
+  warp_add_u64(&ctr->desc_newton, s64);
+  warp_add_u64(&ctr->n_conv, nconv);
+  warp_add_u64(&ctr->n_diverge, ndiv);
+  warp_add_u64(&ctr->n_timeout, nto);
+}
+
+cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0, int shrink_steps,
+                                   double2* seeds, DevCounters* ctr, cudaStream_t s) {
+  if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
+  int log2N0 = 0;
+  while ((int64_t(1) << log2N0) < N0) ++log2N0;
+  const int64_t n = N0 / 2 + 1;
+  const int bs = 128;
+  const size_t smem = (size_t)P.m * bs * sizeof(float2);
+  MT_COUNT_LAUNCH(1);
+  k_seed_lift_mixed<<<(unsigned)((n + bs - 1) / bs), bs, smem, s>>>(P, lambda0, N0, log2N0,
+                                                                    shrink_steps, seeds, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
+                              int64_t nchunks, int K, const double2* seeds, double2* starts,
+                              DevCounters* ctr, cudaStream_t s) {
+  if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
+  const int bs = 64;
+  const size_t smem = (size_t)P.m * bs * sizeof(float2);
+  const int64_t grid = (nchunks + bs - 1) / bs;
+  MT_COUNT_LAUNCH(1);
+  k_walk_mixed<<<(unsigned)grid, bs, smem, s>>>(P, lambda0, M, every, L, nchunks, K, seeds, starts,
+                                                ctr);
+  return cudaGetLastError();
+}
+
+// Anchors are processed in batches of at most MIX_BATCH starts so their
+// buffer stays bounded.
+size_t mixed_anchor_bytes(const PolyDev& P, int64_t count) {
+  const int64_t B = count < MIX_BATCH ? count : MIX_BATCH;
+  const int64_t b = B > 0 ? B : 1;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  return al((size_t)b * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2)) + al((size_t)b * sizeof(float4)) +
+         al((size_t)b * sizeof(float)) + 256;
+}
+
+cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_t count, double tol,
+                                 int cap, double2* cand, float2* dlt, float* hscale, uint8_t* status,
+                                 void* anchors, DevCounters* ctr, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
+  const int bs = 128;
+  const size_t smem = (size_t)P.m * bs * sizeof(float2);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_mixed, bs, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t B = count < MIX_BATCH ? count : MIX_BATCH;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  char* a = (char*)anchors;
+  float2* anch = (float2*)a;
+  float4* vv = (float4*)(a + al((size_t)B * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2)));
+  float* rdel = (float*)((char*)vv + al((size_t)B * sizeof(float4)));
+  for (int64_t base = 0; base < count; base += B) {
+    const int64_t cnt = (count - base < B) ? count - base : B;
+    MT_COUNT_LAUNCH(1);
+    k_anchor_orbits<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, s>>>(P, starts, base, cnt, anch, vv, rdel);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int64_t grid = (int64_t)device_sm_count() * per_sm;
+    const int64_t need = (cnt + bs - 1) / bs;
+    if (grid > need) grid = need;
+    // the work queue restarts at 0 for every batch
+    unsigned long long* q = &ctr->queue_head;
+    if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
+    MT_COUNT_LAUNCH(1);
+    k_descend_mixed<<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, dlt, hscale,
+                                                     status, q, ctr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  MT_COUNT_LAUNCH(1);
+  k_finish_f64<<<(unsigned)((count + bs - 1) / bs), bs, 0, s>>>(P, count, tol * tol, 6, starts, dlt,
+                                                                hscale, cand, status, ctr);
+  return cudaGetLastError();
+}
+
+}  // namespace mt

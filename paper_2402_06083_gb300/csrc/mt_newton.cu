@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __res
                                                  uint8_t* __restrict__ status, DevCounters* ctr) {
   const unsigned lane = threadIdx.x & 31;
   int64_t idx = -1;  // current start (-1: idle, >= count: queue drained)
-  double zr = 0.0, zi = 0.0, rdiv2 = 16.0;
+  double zr = 0.0, zi = 0.0, rdiv2 = 16.0, prev2 = 1e300;
   int it = 0;
   unsigned long long steps = 0, nconv = 0, ndiv = 0, nto = 0;
   for (;;) {
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __res
           zr = z0.x;
           zi = z0.y;
           it = 0;
+          prev2 = 1e300;
           // long jump: beyond twice the start radius and outside D(0, 4)
           rdiv2 = fmax(16.0, 4.0 * fma(zr, zr, zi * zi));
         }
@@ -60,7 +61,12 @@ __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __res
       int outcome = -1;
       if (!finite2(zr, zi) || fma(zr, zr, zi * zi) > rdiv2) outcome = 1;
       else if (s2 < tol2) outcome = 0;  // the step that met tol also squared the error
+      // binary64 rounding floor: steps stopped shrinking within a few ulp of z
+      // (between two close roots Newton also stalls, at |step| ~ their
+      // separation^2 / distance, far above this floor)
+      else if (s2 >= 0.25 * prev2 && s2 < floor2_f64(zr, zi)) outcome = 0;
       else if (it >= cap) outcome = 2;
+      prev2 = s2;
       if (outcome >= 0) {
         cand[idx] = make_double2(zr, zi);
         status[idx] = (uint8_t)outcome;
