@@ -35,6 +35,7 @@ CONFIGS = {
     "hyp20mixed": ("hyp", 0, 20, "mixed"),
     "hyp24": ("hyp", 0, 24, "fp64"),
     "hyp24mixed": ("hyp", 0, 24, "mixed"),
+    "mis16": ("misbatch", 0, 16, "fp64"),  # every s_{l,n}, l >= 2, n >= 1, l + n <= 16, one pass
 }
 
 
@@ -199,16 +200,30 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     kind, l, n, prec = cfg
-    d = mt.degree(kind, n, l)
+    if kind == "misbatch":
+        d = sum(2 ** (a + b - 2) for a, b in mt.misiurewicz_pairs(n))
+    else:
+        d = mt.degree(kind, n, l)
     stream = torch.cuda.current_stream()
     work = mt.Workspace()
     roots = torch.empty((d, 2), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
+    class _BatchResult:
+        def __init__(self, stats):
+            tot = dict(stats[0])
+            tot["n_roots"] = sum(x["n_roots"] for x in stats)
+            tot["n_cert_pass"] = sum(x["n_cert_pass"] for x in stats)
+            tot["steps_fp32"] = 0
+            self.stats = tot
+
     def step(out=None, p=None):
         pp = prec if p is None else p
         if kind == "hyp":
             return mt.split_hyperbolic(n, pp, work=work, out=roots)
+        if kind == "misbatch":
+            _, _, _, st, _ = mt.split_misiurewicz_batch(n, pp, work=work)
+            return _BatchResult(st)
         return mt.split_misiurewicz(l, n, pp, work=work, out=roots)
 
     def timed(p, steps):
@@ -277,7 +292,7 @@ def main():
     clocks = sampler.stop()
 
     s0 = stats[-1]
-    m = n if kind == "hyp" else l + n - 1
+    m = n if kind == "hyp" else (n - 1 if kind == "misbatch" else l + n - 1)
     fl_step = newton_flops(m)
     # dominant kernel by device time (library's CUDA events on the launch stream)
     parts = {"walk": s0["ms_walk"], "descend": s0["ms_descend"], "dedup": s0["ms_dedup"],
@@ -297,8 +312,12 @@ def main():
         "metric": METRIC, "value": value, "unit": "roots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (inputs fixed by n)",
-        "config": {"workload": "p_%d hyperbolic centres, %d roots, plain binary64, all certified" % (n, d)
-                   if kind == "hyp" else "s_{%d,%d}" % (l, n),
+        "config": {"workload": ("p_%d hyperbolic centres, %d roots, %s, all certified" % (
+                       n, d, "plain binary64" if prec == "fp64" else "mixed binary32/binary64")
+                       if kind == "hyp" else
+                       ("all s_{l,n} with l >= 2, n >= 1, l + n <= %d (%d polynomials, %d roots), one pass, "
+                        "binary64, all certified" % (n, len(mt.misiurewicz_pairs(n)), d))
+                       if kind == "misbatch" else "s_{%d,%d}" % (l, n)),
                    "precision": prec, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": world * d / e2e_s, "unit": "roots/s", "h2d_bytes_per_step": 0,
@@ -316,7 +335,7 @@ def main():
                    "wall_s": t_wall},
     }
     # the same workload in the mixed tier (binary32 tracking, binary64 finish)
-    if prec == "fp64" and not args.no_compare:
+    if prec == "fp64" and kind == "hyp" and not args.no_compare:
         ms_mix, st_mix = timed("mixed", args.steps)
         sm = st_mix[-1]
         line["compare"] = {
@@ -327,7 +346,7 @@ def main():
                       "ms_walk": sm["ms_walk"], "ms_descend": sm["ms_descend"],
                       "ms_certify": sm["ms_certify"], "ms_dedup": sm["ms_dedup"],
                       "all_certified": all(x["n_cert_pass"] == d for x in st_mix)}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and kind != "misbatch":
         line["cpu_baseline"] = cpu_baseline(kind, l, n)
     if rank == 0:
         print(json.dumps(line), flush=True)

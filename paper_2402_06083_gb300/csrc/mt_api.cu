@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "../../include/mtsplit.h"
 #include "mt_internal.h"
@@ -376,6 +377,185 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   return MT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched split of every s_{l,n} with l >= 2, n >= 1, l + n <= max_order.
+struct BatchPlan {
+  int np = 0;
+  std::vector<BatchEntry> E;
+  std::vector<PolyDev> polys;
+  std::vector<int64_t> seed_off, chunk_off, start_off, deg;
+  int64_t seeds_total = 0, chunks_total = 0, S = 0, deg_total = 0;
+  double lambda0 = 100.0, eps = 0.0, tol = 0.0, cert_tol = 0.0;
+  int M = 8, cL = 4, every = 2, shrink = 2;
+};
+
+bool make_batch_plan(int max_order, const mt_options* o, int retry, BatchPlan* bp) {
+  if (max_order < 3 || max_order > 41) return false;
+  BatchPlan b;
+  b.M = ((o && o->M > 0) ? o->M : 8) << retry;
+  b.cL = ((o && o->c_L > 0) ? o->c_L : 4) << retry;
+  if (b.M > 64 || (b.M & (b.M - 1)) || (b.cL & (b.cL - 1)) || b.M % b.cL) return false;
+  b.every = b.M / b.cL;
+  b.shrink = 2 << retry;
+  b.lambda0 = (o && o->lambda0 > 0) ? o->lambda0 : 100.0;
+  b.eps = 1.0;
+  for (int l = 2; l < max_order; ++l)
+    for (int n = 1; l + n <= max_order; ++n) b.eps = std::min(b.eps, default_eps(1, l, n));
+  if (o && o->eps_dup > 0) b.eps = o->eps_dup;
+  b.tol = std::min((o && o->tol > 0) ? o->tol : 1e-13, 0.05 * b.eps);
+  b.cert_tol = (o && o->cert_tol > 0) ? o->cert_tol : 1e-12;
+  for (int l = 2; l < max_order; ++l)
+    for (int n = 1; l + n <= max_order; ++n) {
+      BatchEntry e;
+      e.P = make_poly(1, l, n);
+      const int64_t d = int64_t(1) << e.P.log2d;
+      const int64_t Md = (int64_t)b.M * d;
+      int64_t N0 = std::max<int64_t>(2, Md / 32);  // chunks of ~32 sub-steps
+      while (N0 > 2 && (Md / N0) % b.every) N0 >>= 1;
+      if ((Md / N0) % b.every) return false;
+      e.N0 = N0;
+      e.log2N0 = 0;
+      while ((int64_t(1) << e.log2N0) < N0) ++e.log2N0;
+      e.L = Md / N0;
+      e.nchunks = N0 / 2;
+      e.cap = std::max(20, (int)std::ceil(2.6 * e.P.log2d));  // I_N = 2.6 (Sec. 4.2)
+      e.seed_off = b.seeds_total;
+      e.chunk_off = b.chunks_total;
+      e.start_off = b.S;
+      b.seed_off.push_back(b.seeds_total);
+      b.chunk_off.push_back(b.chunks_total);
+      b.start_off.push_back(b.S);
+      b.seeds_total += e.nchunks + 1;
+      b.chunks_total += e.nchunks;
+      b.S += (Md / 2) / b.every + 1;
+      b.deg.push_back(d);
+      b.deg_total += d;
+      b.E.push_back(e);
+      b.polys.push_back(e.P);
+    }
+  b.np = (int)b.E.size();
+  if (b.np > 0xfffe) return false;
+  b.seed_off.push_back(b.seeds_total);
+  b.chunk_off.push_back(b.chunks_total);
+  b.start_off.push_back(b.S);
+  *bp = b;
+  return true;
+}
+
+struct BatchBuffers {
+  DevCounters* ctr;
+  BatchEntry* E;
+  PolyDev* polys;
+  int64_t *seed_off, *chunk_off, *start_off;
+  unsigned long long* pstat;
+  double2 *seeds, *starts, *cand, *reps;
+  uint8_t *status, *type, *pass;
+  uint16_t *seg, *rep_seg, *out_seg;
+  uint64_t *keys, *keys_alt;
+  uint32_t *vals, *vals_alt, *flag, *pos, *mult, *mpos;
+  double* radius;
+  void *scan_tmp, *radix_tmp;
+  size_t bytes;
+};
+
+BatchBuffers carve_batch(const BatchPlan& b, void* ws, size_t cap) {
+  Carve c(ws, cap);
+  BatchBuffers r;
+  r.ctr = c.take<DevCounters>(1);
+  r.E = c.take<BatchEntry>(b.np);
+  r.polys = c.take<PolyDev>(b.np);
+  r.seed_off = c.take<int64_t>(b.np + 1);
+  r.chunk_off = c.take<int64_t>(b.np + 1);
+  r.start_off = c.take<int64_t>(b.np + 1);
+  r.pstat = c.take<unsigned long long>((int64_t)b.np * PSTAT_W);
+  r.seeds = c.take<double2>(b.seeds_total);
+  r.starts = c.take<double2>(b.S);
+  r.cand = c.take<double2>(b.S);
+  r.reps = r.starts;
+  r.status = c.take<uint8_t>(b.S);
+  r.seg = c.take<uint16_t>(b.S);
+  r.rep_seg = c.take<uint16_t>(b.S);
+  r.out_seg = c.take<uint16_t>(b.deg_total + 64);
+  r.keys = c.take<uint64_t>(b.S);
+  r.keys_alt = c.take<uint64_t>(b.S);
+  r.vals = c.take<uint32_t>(b.S);
+  r.vals_alt = c.take<uint32_t>(b.S);
+  r.flag = c.take<uint32_t>(b.S);
+  r.pos = c.take<uint32_t>(b.S);
+  r.type = c.take<uint8_t>(b.S);
+  r.mult = r.flag;
+  r.mpos = r.pos;
+  r.pass = c.take<uint8_t>(b.S);
+  r.radius = c.take<double>(b.S);
+  r.scan_tmp = c.take_bytes(scan_temp_bytes(b.S));
+  r.radix_tmp = c.take_bytes(radix_temp_bytes(b.S));
+  r.bytes = c.off;
+  return r;
+}
+
+size_t batch_workspace(int max_order, const mt_options* o) {
+  const int retries = o ? std::max(0, o->max_retries) : 1;
+  size_t best = 0;
+  for (int r = 0; r <= retries; ++r) {
+    BatchPlan b;
+    if (!make_batch_plan(max_order, o, r, &b)) {
+      if (r == 0) return 0;
+      break;
+    }
+    best = std::max(best, carve_batch(b, nullptr, 0).bytes);
+  }
+  return best;
+}
+
+mt_status run_batch_pass(const BatchPlan& b, const BatchBuffers& r, double2* out, int64_t cap_out,
+                         uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h,
+                         std::vector<unsigned long long>* ps) {
+  CK(launch_init_counters(r.ctr, s));
+  CK(cudaMemsetAsync(r.pstat, 0, sizeof(unsigned long long) * (size_t)b.np * PSTAT_W, s));
+  CK(cudaMemcpyAsync(r.E, b.E.data(), sizeof(BatchEntry) * b.np, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(r.polys, b.polys.data(), sizeof(PolyDev) * b.np, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(r.seed_off, b.seed_off.data(), sizeof(int64_t) * (b.np + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(r.chunk_off, b.chunk_off.data(), sizeof(int64_t) * (b.np + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(r.start_off, b.start_off.data(), sizeof(int64_t) * (b.np + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(ev.e[0], s));
+  CK(launch_seed_lift_batch(r.E, r.seed_off, b.np, b.seeds_total, b.lambda0, b.shrink, r.seeds, r.ctr, s));
+  CK(launch_walk_batch(r.E, r.chunk_off, b.np, b.chunks_total, b.lambda0, b.M, b.every, r.seeds,
+                       r.starts, r.ctr, s));
+  CK(cudaEventRecord(ev.e[1], s));
+  CK(launch_descend_batch(r.E, r.start_off, b.np, b.S, b.tol, r.starts, r.cand, r.status, r.seg,
+                          r.ctr, s));
+  CK(cudaEventRecord(ev.e[2], s));
+  SegView sv;
+  sv.tab = r.polys;
+  sv.seg = r.seg;
+  sv.rep_seg = r.rep_seg;
+  sv.out_seg = r.out_seg;
+  sv.pstat = r.pstat;
+  CK(launch_fold_keys(r.status, r.cand, b.S, b.eps, r.keys, r.vals, s));
+  CK(radix_sort_pairs(r.keys, r.vals, r.keys_alt, r.vals_alt, b.S, r.radix_tmp, s));
+  bool in_alt = false;
+  CK(launch_seg_keys(r.vals, r.seg, r.status, b.S, r.keys, s));
+  CK(radix_sort_bits(r.keys, r.vals, r.keys_alt, r.vals_alt, b.S, r.radix_tmp, 0, 16, &in_alt, s));
+  const uint32_t* vals = in_alt ? r.vals_alt : r.vals;
+  CK(launch_cluster(r.cand, vals, b.S, &r.ctr->n_conv, b.eps, r.flag, r.ctr, s, sv));
+  CK(launch_exclusive_scan(r.flag, r.pos, b.S, r.scan_tmp, nullptr, s));
+  CK(launch_compact(r.cand, vals, r.flag, r.pos, b.S, r.reps, r.ctr, s, sv));
+  CK(cudaEventRecord(ev.e[3], s));
+  PolyDev P0 = b.polys[0];
+  CK(launch_classify(P0, r.reps, &r.ctr->n_reps, b.S, b.eps, 0, r.type, r.mult, r.ctr, s, sv));
+  CK(launch_exclusive_scan(r.mult, r.mpos, b.S, r.scan_tmp, &r.ctr->n_full, s));
+  CK(launch_certify(P0, r.reps, &r.ctr->n_reps, b.S, b.cert_tol, r.mult, r.pass, r.radius, r.ctr, s, sv));
+  CK(cudaEventRecord(ev.e[4], s));
+  CK(launch_emit(r.reps, &r.ctr->n_reps, b.S, r.mult, r.mpos, r.type, -1, out, is_mis, cap_out, s, sv));
+  CK(launch_fix_ties(out, &r.ctr->n_full, cap_out, is_mis, s, sv));
+  CK(cudaEventRecord(ev.e[5], s));
+  ps->assign((size_t)b.np * PSTAT_W, 0ull);
+  CK(cudaMemcpyAsync(h, r.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ps->data(), r.pstat, sizeof(unsigned long long) * ps->size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return MT_OK;
+}
+
 }  // namespace
 
 void mt::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
@@ -431,11 +611,9 @@ int mt_misiurewicz_pairs(int max_order, int* h_l, int* h_n, int capacity) {
 }
 
 size_t mt_workspace_bytes_misiurewicz_batch(int max_order, const mt_options* opts) {
-  // sequential fallback: the largest single workspace
-  size_t best = 0;
-  for (int l = 2; l < max_order; ++l)
-    for (int n = 1; l + n <= max_order; ++n) best = std::max(best, mt_workspace_bytes(1, l, n, opts));
-  return best;
+  mt_options d;
+  mt_default_options(&d);
+  return batch_workspace(max_order, opts ? opts : &d);
 }
 
 mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, double* d_roots,
@@ -443,23 +621,81 @@ mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, doub
                                      void* d_work, size_t work_bytes, int64_t* h_offsets,
                                      mt_stats* stats) {
   g_err.clear();
-  if (max_order < 3 || max_order > 41 || !h_offsets) return fail(MT_EINVAL, "bad max_order");
-  int64_t off = 0;
-  int p = 0;
+  mt_options dflt;
+  mt_default_options(&dflt);
+  const mt_options* o = opts ? opts : &dflt;
+  if (max_order < 3 || max_order > 41 || !h_offsets) return fail(MT_EINVAL, "bad max_order or offsets");
+  if (o->prec != MT_FP64) return fail(MT_EINVAL, "the batched split runs in MT_FP64");
+  const size_t need = batch_workspace(max_order, o);
+  if (need == 0) return fail(MT_EINVAL, "invalid options for this batch");
+  if (!d_work || work_bytes < need)
+    return fail(MT_ENOMEM, "workspace of %zu bytes needed, %zu given", need, work_bytes);
+  if (((uintptr_t)d_work) % ALIGN) return fail(MT_EINVAL, "workspace must be 256-byte aligned");
+  if (cap < 0 || (cap > 0 && !d_roots)) return fail(MT_EINVAL, "bad output buffer");
+  cudaStream_t s = (cudaStream_t)o->stream;
+  EventSet ev;
+  if (!ev.ok) return fail(MT_ECUDA, "cudaEventCreate failed");
+  const unsigned long long launches0 = g_launches;
+  BatchPlan b;
+  DevCounters h;
+  std::vector<unsigned long long> ps;
+  int retry = 0;
+  bool good = false;
+  for (;; ++retry) {
+    if (!make_batch_plan(max_order, o, retry, &b)) return fail(MT_EINVAL, "no plan for retry %d", retry);
+    BatchBuffers r = carve_batch(b, d_work, work_bytes);
+    mt_status rc = run_batch_pass(b, r, (double2*)d_roots, cap, d_is_mis, s, ev, &h, &ps);
+    if (rc != MT_OK) return rc;
+    good = h.walk_fail == 0;
+    for (int p = 0; p < b.np; ++p) good = good && (int64_t)ps[(size_t)p * PSTAT_W + 2] == b.deg[p];
+    if (good || retry >= std::max(0, o->max_retries)) break;
+  }
   h_offsets[0] = 0;
-  for (int l = 2; l < max_order; ++l)
-    for (int n = 1; l + n <= max_order; ++n, ++p) {
-      int64_t got = 0;
-      const int64_t d = mt_degree_misiurewicz(l, n);
-      if (off + d > cap) return fail(MT_ECAPACITY, "batch needs more than cap %lld", (long long)cap);
-      mt_status rc = split_impl(1, l, n, opts, d_roots + 2 * off,
-                                d_roots_lo ? d_roots_lo + 2 * off : nullptr, d,
-                                d_is_mis ? d_is_mis + off : nullptr, d_work, work_bytes, &got,
-                                stats ? &stats[p] : nullptr);
-      if (rc != MT_OK) return rc;
-      off += got;
-      h_offsets[p + 1] = off;
-    }
+  for (int p = 0; p < b.np; ++p) h_offsets[p + 1] = h_offsets[p] + (int64_t)ps[(size_t)p * PSTAT_W + 2];
+  if (d_roots_lo && cap > 0) CK(cudaMemsetAsync(d_roots_lo, 0, (size_t)cap * sizeof(double2), s));
+  float ms[5] = {0, 0, 0, 0, 0};
+  cudaEventElapsedTime(&ms[0], ev.e[0], ev.e[5]);
+  cudaEventElapsedTime(&ms[1], ev.e[0], ev.e[1]);
+  cudaEventElapsedTime(&ms[2], ev.e[1], ev.e[2]);
+  cudaEventElapsedTime(&ms[3], ev.e[2], ev.e[3]);
+  cudaEventElapsedTime(&ms[4], ev.e[3], ev.e[4]);
+  int64_t bad_cert = 0;
+  for (int p = 0; p < b.np; ++p) {
+    const unsigned long long* q = &ps[(size_t)p * PSTAT_W];
+    bad_cert += (int64_t)(q[2] - q[3]);
+    if (!stats) continue;
+    mt_stats& st = stats[p];
+    memset(&st, 0, sizeof(st));
+    st.degree = b.deg[p];
+    st.n_roots = (int64_t)q[2];
+    st.n_real = (int64_t)q[1];
+    st.n_starts = b.start_off[p + 1] - b.start_off[p];
+    st.n_cert_pass = (int64_t)q[3];
+    for (int t = 0; t < MT_MAX_TYPES; ++t) st.count_by_type[t] = (int64_t)q[4 + t];
+    // batch-wide counters and timings are reported on every entry
+    st.n_conv = (int64_t)h.n_conv;
+    st.n_diverge = (int64_t)h.n_diverge;
+    st.n_timeout = (int64_t)h.n_timeout;
+    st.walk_newton = (int64_t)h.walk_newton;
+    st.desc_newton = (int64_t)h.desc_newton;
+    st.walk_fail = (int64_t)h.walk_fail;
+    st.M = b.M;
+    st.c_L = b.cL;
+    st.retries = retry;
+    st.n_chunks = (int32_t)(b.E[p].nchunks);
+    st.n_launches = (int64_t)(g_launches - launches0);
+    st.eps_dup = b.eps;
+    st.ms_total = ms[0];
+    st.ms_walk = ms[1];
+    st.ms_descend = ms[2];
+    st.ms_dedup = ms[3];
+    st.ms_certify = ms[4];
+    st.prec_used = MT_FP64;
+  }
+  if (!good) return fail(MT_EINCOMPLETE, "some polynomials of the batch miss roots (after %d retries)", retry);
+  if (h_offsets[b.np] > cap)
+    return fail(MT_ECAPACITY, "%lld roots do not fit in cap %lld", (long long)h_offsets[b.np], (long long)cap);
+  if (bad_cert) return fail(MT_ECERT, "%lld roots of the batch failed the certificate", (long long)bad_cert);
   return MT_OK;
 }
 

@@ -65,10 +65,10 @@ __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, d
   return 255;
 }
 
-__global__ void k_classify(PolyDev P, double2* __restrict__ reps,
+__global__ void k_classify(PolyDev P0, double2* __restrict__ reps,
                            const unsigned long long* __restrict__ n_reps, int64_t cap, double tau,
                            int polish, uint8_t* __restrict__ type, uint32_t* __restrict__ mult,
-                           DevCounters* ctr) {
+                           DevCounters* ctr, SegView sv) {
   __shared__ unsigned int hist[64];
   for (int q = threadIdx.x; q < 64; q += blockDim.x) hist[q] = 0;
   __syncthreads();
@@ -77,6 +77,8 @@ __global__ void k_classify(PolyDev P, double2* __restrict__ reps,
   unsigned long long nreal = 0;
   if (u < cap) {
     if (u < nr) {
+      const uint16_t sg = sv.rep_seg ? sv.rep_seg[u] : 0;
+      const PolyDev P = sv.tab ? sv.tab[sg] : P0;
       double2 z = reps[u];
       if (polish) {
         double vr, vi, dr, di, qr, qi;
@@ -94,6 +96,13 @@ __global__ void k_classify(PolyDev P, double2* __restrict__ reps,
       mult[u] = m;
       nreal += (m == 1);
       if (t < 64) atomicAdd(&hist[t], m);
+      if (sv.pstat) {
+        unsigned long long* ps = sv.pstat + (size_t)sg * PSTAT_W;
+        atomicAdd(&ps[0], 1ull);
+        if (m == 1) atomicAdd(&ps[1], 1ull);
+        atomicAdd(&ps[2], (unsigned long long)m);
+        if (t < 64) atomicAdd(&ps[4 + t], (unsigned long long)m);
+      }
     } else {
       mult[u] = 0;
     }
@@ -106,11 +115,11 @@ __global__ void k_classify(PolyDev P, double2* __restrict__ reps,
 
 cudaError_t launch_classify(const PolyDev& P, double2* reps, const unsigned long long* n_reps,
                             int64_t cap, double tau, int polish, uint8_t* type, uint32_t* mult,
-                            DevCounters* ctr, cudaStream_t s) {
+                            DevCounters* ctr, cudaStream_t s, SegView sv) {
   if (cap <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
   k_classify<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, n_reps, cap, tau, polish, type,
-                                                           mult, ctr);
+                                                           mult, ctr, sv);
   return cudaGetLastError();
 }
 
@@ -216,11 +225,11 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
 // Certify the points of 'pts' (sorted by Re through 'order', or already
 // sorted when order == nullptr).  upper: the list holds one representative
 // per conjugate pair, so conjugates count as neighbours too.
-__global__ void k_certify(PolyDev P, const double2* __restrict__ pts,
+__global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
                           const uint32_t* __restrict__ order, const unsigned long long* n_pts_dev,
                           int64_t n_pts_host, double tol, int upper, const uint32_t* __restrict__ mult,
                           uint8_t* __restrict__ pass, double* __restrict__ radius,
-                          DevCounters* ctr) {
+                          DevCounters* ctr, SegView sv) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = n_pts_dev ? (int64_t)*n_pts_dev : n_pts_host;
   unsigned long long npass = 0, overflow = 0;
@@ -229,6 +238,8 @@ __global__ void k_certify(PolyDev P, const double2* __restrict__ pts,
   if (valid) {
     const int64_t ip = order ? (int64_t)order[p] : p;
     const double2 c = pts[ip];
+    const uint16_t sg = sv.rep_seg ? sv.rep_seg[p] : 0;  // (batch mode: pts are reps, no order)
+    const PolyDev P = sv.tab ? sv.tab[sg] : P0;
     // nearest neighbour (and conjugates) within the window W = tol / 0.45
     const double W = tol / 0.45;
     double nn2 = W * W;
@@ -236,6 +247,7 @@ __global__ void k_certify(PolyDev P, const double2* __restrict__ pts,
     int scanned = 0;
     for (int dir = -1; dir <= 1; dir += 2) {
       for (int64_t q = p + dir; q >= 0 && q < n; q += dir) {
+        if (sv.rep_seg && sv.rep_seg[q] != sg) break;  // another polynomial of the batch
         const double2 v = pts[order ? (int64_t)order[q] : q];
         const double dx = v.x - c.x;
         if (fabs(dx) >= W) break;
@@ -269,6 +281,7 @@ __global__ void k_certify(PolyDev P, const double2* __restrict__ pts,
     pass[ip] = ok ? 1 : 0;
     if (radius) radius[ip] = rad;
     npass = ok ? (mult ? mult[p] : 1u) : 0u;
+    if (sv.pstat && npass) atomicAdd(&sv.pstat[(size_t)sg * PSTAT_W + 3], npass);
   }
   warp_add_u64(&ctr->n_cert_pass, npass);
   if (overflow) atomicAdd(&ctr->cluster_overflow, 1ull);
@@ -280,11 +293,11 @@ __global__ void k_certify(PolyDev P, const double2* __restrict__ pts,
 
 cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
                            int64_t cap, double tol, const uint32_t* mult, uint8_t* pass,
-                           double* radius, DevCounters* ctr, cudaStream_t s) {
+                           double* radius, DevCounters* ctr, cudaStream_t s, SegView sv) {
   if (cap <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
   k_certify<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, nullptr, n_reps, cap, tol, 1,
-                                                          mult, pass, radius, ctr);
+                                                          mult, pass, radius, ctr, sv);
   return cudaGetLastError();
 }
 
@@ -295,7 +308,7 @@ cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint
   if (count <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
   k_certify<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, pts, order, nullptr, count, tol, 0,
-                                                            nullptr, pass, radius, ctr);
+                                                            nullptr, pass, radius, ctr, SegView());
   return cudaGetLastError();
 }
 

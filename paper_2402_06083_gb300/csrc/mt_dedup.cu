@@ -256,6 +256,34 @@ size_t radix_temp_bytes(int64_t n) {
   return (size_t)nh * 2 * sizeof(uint32_t) + scan_temp_bytes(nh) + 256;
 }
 
+cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                            int64_t n, void* temp, int begin_bit, int end_bit, bool* in_alt,
+                            cudaStream_t s) {
+  *in_alt = false;
+  if (n <= 1) return cudaSuccess;
+  const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t nh = 256 * nb;
+  uint32_t* hist = (uint32_t*)temp;
+  uint32_t* offs = hist + nh;
+  void* stemp = (void*)(offs + nh);
+  uint64_t* k0 = keys;
+  uint32_t* v0 = vals;
+  uint64_t* k1 = keys_alt;
+  uint32_t* v1 = vals_alt;
+  for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    MT_COUNT_LAUNCH(1);
+    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb);
+    cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
+    if (e != cudaSuccess) return e;
+    MT_COUNT_LAUNCH(1);
+    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb);
+    uint64_t* tk = k0; k0 = k1; k1 = tk;
+    uint32_t* tv = v0; v0 = v1; v1 = tv;
+    *in_alt = !*in_alt;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s) {
   if (n <= 1) return cudaSuccess;
@@ -287,16 +315,19 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
 // with Re_p - Re_q < eps has |Im_p - Im_q| < eps (Chebyshev pixel rule).
 __global__ void k_cluster(const double2* __restrict__ cand, const uint32_t* __restrict__ vals,
                           int64_t count, const unsigned long long* __restrict__ n_valid,
-                          double eps, uint32_t* __restrict__ flag, DevCounters* ctr) {
+                          double eps, uint32_t* __restrict__ flag, DevCounters* ctr, SegView sv) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
   const int64_t nv = (int64_t)*n_valid;
   if (p >= nv) { flag[p] = 0; return; }
   const double2 z = cand[vals[p]];
+  const uint16_t sp = sv.seg ? sv.seg[vals[p]] : 0;
   uint32_t rep = 1;
   int scanned = 0;
   for (int64_t q = p - 1; q >= 0; --q) {
-    const double2 y = cand[vals[q]];
+    const uint32_t vq = vals[q];
+    if (sv.seg && sv.seg[vq] != sp) break;  // another polynomial of the batch
+    const double2 y = cand[vq];
     if (z.x - y.x >= eps) break;
     if (fabs(z.y - y.y) < eps) { rep = 0; break; }
     if (++scanned >= 4096) { atomicAdd(&ctr->cluster_overflow, 1ull); break; }
@@ -306,29 +337,34 @@ __global__ void k_cluster(const double2* __restrict__ cand, const uint32_t* __re
 
 cudaError_t launch_cluster(const double2* cand, const uint32_t* vals, int64_t count,
                            const unsigned long long* n_valid, double eps, uint32_t* flag,
-                           DevCounters* ctr, cudaStream_t s) {
+                           DevCounters* ctr, cudaStream_t s, SegView sv) {
   if (count <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
   k_cluster<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(cand, vals, count, n_valid, eps, flag,
-                                                            ctr);
+                                                            ctr, sv);
   return cudaGetLastError();
 }
 
 __global__ void k_compact(const double2* __restrict__ cand, const uint32_t* __restrict__ vals,
                           const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
-                          int64_t count, double2* __restrict__ reps, DevCounters* ctr) {
+                          int64_t count, double2* __restrict__ reps, DevCounters* ctr,
+                          SegView sv) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  if (flag[p]) reps[pos[p]] = cand[vals[p]];
+  if (flag[p]) {
+    reps[pos[p]] = cand[vals[p]];
+    if (sv.rep_seg) sv.rep_seg[pos[p]] = sv.seg[vals[p]];
+  }
   if (p == count - 1) ctr->n_reps = (unsigned long long)pos[p] + flag[p];
 }
 
 cudaError_t launch_compact(const double2* cand, const uint32_t* vals, const uint32_t* flag,
                            const uint32_t* pos, int64_t count, double2* reps, DevCounters* ctr,
-                           cudaStream_t s) {
+                           cudaStream_t s, SegView sv) {
   if (count <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_compact<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(cand, vals, flag, pos, count, reps, ctr);
+  k_compact<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(cand, vals, flag, pos, count, reps, ctr,
+                                                            sv);
   return cudaGetLastError();
 }
 
@@ -339,12 +375,18 @@ __global__ void k_emit(const double2* __restrict__ reps, const unsigned long lon
                        int64_t cap_reps, const uint32_t* __restrict__ mult,
                        const uint32_t* __restrict__ pos, const uint8_t* __restrict__ type,
                        int mis_code, double2* __restrict__ out, uint8_t* __restrict__ is_mis,
-                       int64_t cap_out) {
+                       int64_t cap_out, SegView sv) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= cap_reps || u >= (int64_t)*n_reps) return;
   const double2 z = reps[u];
   const int64_t p = pos[u];
+  const uint16_t sg = sv.rep_seg ? sv.rep_seg[u] : 0;
+  if (sv.tab) mis_code = (sv.tab[sg].kind == 1 && sv.tab[sg].n < 32) ? sv.tab[sg].n : -1;
   const uint8_t im = (type && mis_code >= 0) ? (uint8_t)(type[u] == mis_code) : 0;
+  if (sv.out_seg) {
+    if (p < cap_out) sv.out_seg[p] = sg;
+    if (mult[u] == 2 && p + 1 < cap_out) sv.out_seg[p + 1] = sg;
+  }
   if (mult[u] == 1) {
     if (p < cap_out) {
       out[p] = make_double2(z.x, 0.0);
@@ -365,26 +407,30 @@ __global__ void k_emit(const double2* __restrict__ reps, const unsigned long lon
 cudaError_t launch_emit(const double2* reps, const unsigned long long* n_reps, int64_t cap_reps,
                         const uint32_t* mult, const uint32_t* pos, const uint8_t* type,
                         int mis_code, double2* out, uint8_t* is_mis, int64_t cap_out,
-                        cudaStream_t s) {
+                        cudaStream_t s, SegView sv) {
   if (cap_reps <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
   k_emit<<<(unsigned)((cap_reps + 255) / 256), 256, 0, s>>>(reps, n_reps, cap_reps, mult, pos, type,
-                                                            mis_code, out, is_mis, cap_out);
+                                                            mis_code, out, is_mis, cap_out, sv);
   return cudaGetLastError();
 }
 
 // Exact ties of Re between distinct roots (rare): sort each run of equal Re
 // by Im so the list follows eq. defLexi.  One thread per run start.
 __global__ void k_fix_ties(double2* out, const unsigned long long* __restrict__ n_full,
-                           int64_t cap_out, uint8_t* is_mis) {
+                           int64_t cap_out, uint8_t* is_mis, SegView sv) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t n = (int64_t)*n_full;
   if (n > cap_out) n = cap_out;
   if (p + 1 >= n) return;
-  if (p > 0 && out[p - 1].x == out[p].x) return;  // not the start of a run
-  if (out[p + 1].x != out[p].x) return;
+  // a run: equal Re within one polynomial
+  auto same = [&](int64_t a, int64_t b) {
+    return out[a].x == out[b].x && (!sv.out_seg || sv.out_seg[a] == sv.out_seg[b]);
+  };
+  if (p > 0 && same(p - 1, p)) return;  // not the start of a run
+  if (!same(p + 1, p)) return;
   int64_t e = p + 1;
-  while (e < n && out[e].x == out[p].x && e - p < 4096) ++e;
+  while (e < n && same(e, p) && e - p < 4096) ++e;
   // insertion sort of [p, e) by Im (runs are tiny)
   for (int64_t i = p + 1; i < e; ++i) {
     const double2 v = out[i];
@@ -401,10 +447,10 @@ __global__ void k_fix_ties(double2* out, const unsigned long long* __restrict__ 
 }
 
 cudaError_t launch_fix_ties(double2* out, const unsigned long long* n_full, int64_t cap_out,
-                            uint8_t* is_mis, cudaStream_t s) {
+                            uint8_t* is_mis, cudaStream_t s, SegView sv) {
   if (cap_out <= 1) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_fix_ties<<<(unsigned)((cap_out + 255) / 256), 256, 0, s>>>(out, n_full, cap_out, is_mis);
+  k_fix_ties<<<(unsigned)((cap_out + 255) / 256), 256, 0, s>>>(out, n_full, cap_out, is_mis, sv);
   return cudaGetLastError();
 }
 

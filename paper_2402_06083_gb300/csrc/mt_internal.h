@@ -40,6 +40,30 @@ struct DevCounters {
   unsigned long long type_count[64];
 };
 
+// Several polynomials in one pass (the batched Misiurewicz split): the
+// polynomial of each candidate / representative / output root, and
+// per-polynomial counters.  All null for a single polynomial.
+constexpr int PSTAT_W = 68;  // per polynomial: n_reps, n_real, n_full, n_cert, 64 type counts
+struct SegView {
+  const PolyDev* tab = nullptr;         // [np] polynomials
+  const uint16_t* seg = nullptr;        // per candidate (original start index)
+  uint16_t* rep_seg = nullptr;          // per representative
+  uint16_t* out_seg = nullptr;          // per output root
+  unsigned long long* pstat = nullptr;  // [np][PSTAT_W]
+};
+
+// One polynomial of a batch: its level-line layout and where its seeds,
+// chunks and starts begin in the concatenated arrays.
+struct BatchEntry {
+  PolyDev P;
+  int log2N0;
+  int cap;          // Newton cap max{20, I_N log2 d}
+  int64_t N0;       // chunks around the whole line
+  int64_t L;        // sub-steps per chunk
+  int64_t nchunks;  // chunks of the upper half (N0 / 2)
+  int64_t seed_off, chunk_off, start_off;
+};
+
 // ---- launchers (each returns the launch error) ----------------------------
 
 // a1 + a2: seeds of the chunked level line: seeds[j] = point with external
@@ -69,6 +93,19 @@ cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_
                                  void* anchors, DevCounters* ctr, cudaStream_t s);
 size_t mixed_anchor_bytes(const PolyDev& P, int64_t count);
 
+// Batched (several polynomials) seeds, walk and descents.
+cudaError_t launch_seed_lift_batch(const BatchEntry* E, const int64_t* seed_off, int np,
+                                   int64_t total, double lambda0, int shrink, double2* seeds,
+                                   DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_walk_batch(const BatchEntry* E, const int64_t* chunk_off, int np, int64_t total,
+                              double lambda0, int M, int every, const double2* seeds,
+                              double2* starts, DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_descend_batch(const BatchEntry* E, const int64_t* start_off, int np,
+                                 int64_t count, double tol, const double2* starts, double2* cand,
+                                 uint8_t* status, uint16_t* seg, DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_seg_keys(const uint32_t* vals, const uint16_t* seg, const uint8_t* status,
+                            int64_t count, uint64_t* keys, cudaStream_t s);
+
 // a0: plain evaluation of P and P' at points.
 cudaError_t launch_eval(const PolyDev& P, const double2* c, int64_t count, double2* out,
                         cudaStream_t s);
@@ -87,35 +124,42 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 size_t radix_temp_bytes(int64_t n);
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s);
+// Stable passes on bits [begin_bit, end_bit) only (multiples of 8); the
+// result is in (keys, vals) after an even number of passes, else in the alt
+// buffers (*in_alt = true).
+cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                            int64_t n, void* temp, int begin_bit, int end_bit, bool* in_alt,
+                            cudaStream_t s);
 
 // Cluster pass on Re-sorted candidates: flag[p] = 1 if sorted candidate p
 // starts a new root (no earlier candidate within the Chebyshev pixel).
 cudaError_t launch_cluster(const double2* cand, const uint32_t* vals, int64_t count,
                            const unsigned long long* n_valid, double eps, uint32_t* flag,
-                           DevCounters* ctr, cudaStream_t s);
+                           DevCounters* ctr, cudaStream_t s, SegView sv = SegView());
 
 // Gather flagged candidates into reps (order of the sort) and set n_reps.
 cudaError_t launch_compact(const double2* cand, const uint32_t* vals, const uint32_t* flag,
                            const uint32_t* pos, int64_t count, double2* reps, DevCounters* ctr,
-                           cudaStream_t s);
+                           cudaStream_t s, SegView sv = SegView());
 
 // a6: polish + type of each rep (upper half), multiplicities for emission.
 cudaError_t launch_classify(const PolyDev& P, double2* reps, const unsigned long long* n_reps,
                             int64_t cap, double tau, int polish, uint8_t* type, uint32_t* mult,
-                            DevCounters* ctr, cudaStream_t s);
+                            DevCounters* ctr, cudaStream_t s, SegView sv = SegView());
 
 // a7: certify reps (sorted by Re): radius from nearest neighbours, disk test.
 cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
                            int64_t cap, double tol, const uint32_t* mult, uint8_t* pass,
-                           double* radius, DevCounters* ctr, cudaStream_t s);
+                           double* radius, DevCounters* ctr, cudaStream_t s,
+                           SegView sv = SegView());
 
 // Emit the full conjugate-closed list sorted by (Re, Im).
 cudaError_t launch_emit(const double2* reps, const unsigned long long* n_reps, int64_t cap_reps,
                         const uint32_t* mult, const uint32_t* pos, const uint8_t* type,
                         int mis_code, double2* out, uint8_t* is_mis, int64_t cap_out,
-                        cudaStream_t s);
+                        cudaStream_t s, SegView sv = SegView());
 cudaError_t launch_fix_ties(double2* out, const unsigned long long* n_full, int64_t cap_out,
-                            uint8_t* is_mis, cudaStream_t s);
+                            uint8_t* is_mis, cudaStream_t s, SegView sv = SegView());
 
 // Standalone type (a6 without polish) for mt_classify.
 cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t count, double tau,

@@ -282,3 +282,52 @@ def test_split_hyperbolic_n24_invariants(mt, prec):
     for i in idx:
         _, disp = oracle.polish("hyp", n, z[i], steps=3)
         assert disp < TOL_FP64
+
+
+# --- the batched Misiurewicz split (all s_{l,n}, l + n <= max_order, one pass) ----
+
+def _batch(mt, max_order):
+    roots, mis, offs, stats, pairs = mt.split_misiurewicz_batch(max_order)
+    return roots.cpu().numpy(), mis.cpu().numpy().astype(bool), offs, stats, pairs
+
+
+def test_batch_small_orders_match_oracle(mt):
+    """Every pair with l + n <= 9 against the binary128 oracle, root by root."""
+    roots, mis, offs, stats, pairs = _batch(mt, 9)
+    assert len(pairs) == len(counts.misiurewicz_pairs(9))
+    for p, (l, n) in enumerate(pairs):
+        z = roots[offs[p]:offs[p + 1]]
+        ref = oracle.split("mis", n, l=l)
+        assert z.size == ref["n_roots"] == counts.deg_s(l, n), (l, n)
+        dmax, _ = match_sorted(z, ref["roots"], TOL_FP64)
+        assert dmax < TOL_FP64, (l, n, dmax)
+        assert lexsorted(z)
+        perm, _ = match_sets(z, ref["roots"])
+        to = ref["type"][perm]
+        assert np.array_equal(mis[offs[p]:offs[p + 1]], (to[:, 0] == l) & (to[:, 1] == n)), (l, n)
+        assert stats[p]["n_cert_pass"] == z.size
+
+
+def test_batch_order16_full(mt):
+    """The whole l + n <= 16 batch (105 polynomials, 425,986 roots): per
+    polynomial exact count and type histogram (eq. MisCount /
+    eq. polyMisSimple), every root certified, conjugate symmetry; the largest
+    polynomials of each preperiod against the binary64 oracle."""
+    roots, mis, offs, stats, pairs = _batch(mt, 16)
+    assert len(pairs) == 105 and offs[-1] == 425986
+    assert int(mis.sum()) == 381108
+    for p, (l, n) in enumerate(pairs):
+        z = roots[offs[p]:offs[p + 1]]
+        st = stats[p]
+        assert z.size == counts.deg_s(l, n) and st["n_cert_pass"] == z.size, (l, n)
+        for (a, k), cnt in counts.type_histogram_s(l, n).items():
+            assert st["count_by_type"][k if a == l else 32 + k] == cnt, (l, n, a, k)
+        assert int(mis[offs[p]:offs[p + 1]].sum()) == counts.mis_count(l, n)
+        assert np.array_equal(np.sort_complex(np.conj(z)), np.sort_complex(z))
+    for (l, n) in [(2, 14), (3, 13), (5, 11), (8, 8), (12, 4), (15, 1)]:
+        p = pairs.index((l, n))
+        z = roots[offs[p]:offs[p + 1]]
+        ref = oracle.split("mis", n, l=l, fp64=True, want_types=False)
+        assert ref["n_roots"] == z.size
+        dmax, _ = match_sorted(z, ref["roots"], 1e-11)
+        assert dmax < 1e-11, (l, n, dmax)
