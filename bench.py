@@ -219,8 +219,8 @@ def main():
 
     def step(out=None, p=None):
         pp = prec if p is None else p
-        if kind == "hyp":
-            return mt.split_hyperbolic(n, pp, work=work, out=roots)
+        if kind == "hyp":  # the launch sequence is captured once and replayed as a CUDA graph
+            return mt.split_hyperbolic(n, pp, work=work, out=roots, use_graph=1)
         if kind == "misbatch":
             _, _, _, st, _ = mt.split_misiurewicz_batch(n, pp, work=work)
             return _BatchResult(st)

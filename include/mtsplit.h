@@ -176,6 +176,18 @@ MT_API mt_status mt_certify(int kind, int l, int n, const double* d_roots, const
                      int64_t count, double tol, uint8_t* d_pass, double* d_radius, void* d_work,
                      size_t work_bytes, int64_t* n_pass, void* stream);
 
+/* Autotuner (the paper tunes nothing; a GPU-layout choice).  Runs complete
+   splits of P for each candidate level-line chunk length 2^c (c = 3 .. 10
+   sub-steps per lane) and walk block size (32, 64, 128), three runs each,
+   and keeps the fastest in a process-wide table keyed by (kind, l, n,
+   tier).  Later calls whose options leave chunk_log2 / block at 0 use the
+   tuned values.  d_roots, cap, d_work, work_bytes are those of a split;
+   candidates whose workspace exceeds work_bytes are skipped.  Outputs:
+   best chunk_log2, block size and device milliseconds (any may be NULL). */
+MT_API mt_status mt_autotune(int kind, int l, int n, const mt_options* opts, double* d_roots,
+                             int64_t cap, void* d_work, size_t work_bytes, int* best_chunk_log2,
+                             int* best_block, float* best_ms);
+
 /* ---- single steps of the path, exposed for parity checks ---------------- */
 
 /* Orbit evaluation (Sec. 1, eq. def:hyp_poly, and its c-derivative): for

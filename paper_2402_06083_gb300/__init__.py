@@ -235,5 +235,29 @@ def classify(kind: str, n: int, roots, l: int = 0, tau: float = 0.0):
     return t
 
 
+def autotune(kind: str, n: int, l: int = 0, prec: str = "fp64", *, work: Workspace | None = None, **kw):
+    """Pick the level-line chunk length and walk block size for P by timing
+    complete splits (mt_autotune); later splits of P in this process use them.
+    Returns (chunk_log2, block, device ms of the best candidate)."""
+    torch = _torch()
+    L = load()
+    o = options(prec, **kw)
+    d = degree(kind, n, l)
+    # the largest workspace over the candidates (finer chunks need more seeds)
+    nbytes = int(L.mt_workspace_bytes(KIND[kind], l, n, ctypes.byref(o)))
+    for cl in range(3, 15):
+        oc = options(prec, chunk_log2=cl, **kw)
+        nbytes = max(nbytes, int(L.mt_workspace_bytes(KIND[kind], l, n, ctypes.byref(oc))))
+    work = work or Workspace()
+    buf = work.ensure(nbytes)
+    roots = torch.empty((d, 2), dtype=torch.float64, device="cuda")
+    c = ctypes.c_int(0)
+    b = ctypes.c_int(0)
+    ms = ctypes.c_float(0)
+    check(L.mt_autotune(KIND[kind], l, n, ctypes.byref(o), roots.data_ptr(), d, buf.data_ptr(), buf.numel(),
+                        ctypes.byref(c), ctypes.byref(b), ctypes.byref(ms)))
+    return c.value, b.value, ms.value
+
+
 def version() -> str:
     return load().mt_version().decode()

@@ -24,7 +24,7 @@ EXPORTS = (
     "mt_split_hyperbolic", "mt_split_misiurewicz", "mt_misiurewicz_pairs",
     "mt_workspace_bytes_misiurewicz_batch", "mt_split_misiurewicz_batch",
     "mt_certify_workspace_bytes", "mt_certify", "mt_eval", "mt_level_line", "mt_descend",
-    "mt_classify", "mt_certify_static", "mt_last_error", "mt_version",
+    "mt_classify", "mt_certify_static", "mt_autotune", "mt_last_error", "mt_version",
 )
 MT_CERTIFY_STATIC_MAX_ROOTS = 131072
 
@@ -110,6 +110,9 @@ def load() -> ctypes.CDLL:
                                        vp, vp]),
         "mt_certify_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64, ctypes.c_double,
                                              vp, vp, i64p, vp]),
+        "mt_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, op, vp, i64, vp, ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_float)]),
         "mt_last_error": (ctypes.c_char_p, []),
         "mt_version": (ctypes.c_char_p, []),
     }

@@ -96,7 +96,8 @@ PolyDev make_poly(int kind, int l, int n) {
 struct Plan {
   PolyDev P;
   int kind;
-  int prec;  // tier of this attempt (MT_FP64 or MT_MIXED)
+  int prec;        // tier of this attempt (MT_FP64 or MT_MIXED)
+  int walk_block;  // CUDA block size of the walk
   int64_t degree;
   double lambda0;
   int M, cL, every;
@@ -107,6 +108,34 @@ struct Plan {
   double cert_tol;
   int shrink;
 };
+
+// ---------------------------------------------------------------------------
+// Autotune table: (kind, l, n, tier) -> chunk length and walk block size
+// measured fastest by mt_autotune; used when the options leave them at 0.
+struct TuneKey {
+  int kind, l, n, prec;
+  bool operator==(const TuneKey& o) const {
+    return kind == o.kind && l == o.l && n == o.n && prec == o.prec;
+  }
+};
+struct TuneKeyHash {
+  size_t operator()(const TuneKey& k) const {
+    return ((size_t)k.kind * 131 + (size_t)k.l) * 131 * 131 + (size_t)k.n * 131 + (size_t)k.prec;
+  }
+};
+struct TuneVal {
+  int chunk_log2, walk_block;
+};
+std::mutex g_tune_mu;
+std::unordered_map<TuneKey, TuneVal, TuneKeyHash> g_tune;
+
+bool tuned(int kind, int l, int n, int prec, TuneVal* v) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey{kind, l, n, prec});
+  if (it == g_tune.end()) return false;
+  *v = it->second;
+  return true;
+}
 
 double default_eps(int kind, int l, int n) {
   // hyperbolic: a twentieth of the minimal separation 118.4 / 4^n (Sec. 6.3.2);
@@ -119,7 +148,7 @@ double default_eps(int kind, int l, int n) {
 
 bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl) {
   if (!valid_poly(kind, l, n)) return false;
-  Plan p;
+  Plan p{};  // value-initialised: padding is zero, so plans compare with memcmp
   p.kind = kind;
   p.prec = MT_FP64;
   if (o && o->prec == MT_MIXED) {
@@ -138,14 +167,20 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   p.every = p.M / p.cL;
   const int64_t Md = (int64_t)p.M * p.degree;  // sub-steps around the whole line
   int64_t N0;
+  TuneVal tv{0, 0};
+  const bool have_tune = tuned(kind, kind == 0 ? 0 : l, n, p.prec, &tv);
+  p.walk_block = (o && o->block > 0) ? o->block : (have_tune && tv.walk_block > 0 ? tv.walk_block : 64);
   if (o && o->chunk_log2 > 0) {
     N0 = Md >> o->chunk_log2;
+  } else if (have_tune && tv.chunk_log2 > 0) {
+    N0 = Md >> tv.chunk_log2;
   } else {
     N0 = std::min<int64_t>(int64_t(1) << 15, Md / 16);
   }
   // L must be a multiple of 'every' and N0 >= 2
   while (N0 > 2 && (Md / N0) % p.every) N0 >>= 1;
   if (N0 < 2) N0 = 2;
+  if (N0 > (int64_t(1) << 20)) return false;
   if ((Md / N0) % p.every) return false;
   p.N0 = N0;
   p.nchunks = N0 / 2;
@@ -266,11 +301,18 @@ void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
   st->prec_used = p.prec;
 }
 
-// One pass of the whole sequence.  Leaves counters in *h.
-mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
-                   uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h) {
+// Stage boundaries are marked with events; inside a stream capture they
+// are recorded as external event nodes so they still time the graph.
+cudaError_t mark(cudaEvent_t e, cudaStream_t s, bool capturing) {
+  return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
+// One pass of the whole sequence, enqueued on s (no host synchronisation).
+mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
+                       int64_t cap_out, uint8_t* is_mis, cudaStream_t s, EventSet& ev,
+                       bool capturing) {
   CK(launch_init_counters(b.ctr, s));
-  CK(cudaEventRecord(ev.e[0], s));
+  CK(mark(ev.e[0], s, capturing));
   if (p.prec == MT_MIXED) {
     CK(launch_seed_lift_mixed(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
   } else {
@@ -278,11 +320,12 @@ mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_l
   }
   if (p.prec == MT_MIXED) {
     CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts, b.ctr,
-                         s));
+                         s, p.walk_block));
   } else {
-    CK(launch_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, b.seeds, b.starts, b.ctr, s));
+    CK(launch_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, b.seeds, b.starts, b.ctr, s,
+                   p.walk_block));
   }
-  CK(cudaEventRecord(ev.e[1], s));
+  CK(mark(ev.e[1], s, capturing));
   if (p.prec == MT_MIXED) {
     // binary32 deltas and descent scales live in the (not yet used) sort buffers
     CK(launch_descend_mixed(p.P, b.starts, p.S, p.tol, p.cap, b.cand, (float2*)b.keys,
@@ -290,27 +333,120 @@ mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_l
   } else {
     CK(launch_descend(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
   }
-  CK(cudaEventRecord(ev.e[2], s));
+  CK(mark(ev.e[2], s, capturing));
   CK(launch_fold_keys(b.status, b.cand, p.S, p.eps, b.keys, b.vals, s));
   CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, p.S, b.radix_tmp, s));
   CK(launch_cluster(b.cand, b.vals, p.S, &b.ctr->n_conv, p.eps, b.flag, b.ctr, s));
   CK(launch_exclusive_scan(b.flag, b.pos, p.S, b.scan_tmp, nullptr, s));
   CK(launch_compact(b.cand, b.vals, b.flag, b.pos, p.S, b.reps, b.ctr, s));
-  CK(cudaEventRecord(ev.e[3], s));
+  CK(mark(ev.e[3], s, capturing));
   CK(launch_classify(p.P, b.reps, &b.ctr->n_reps, p.S, p.eps, 0, b.type, b.mult, b.ctr, s));
   CK(launch_exclusive_scan(b.mult, b.mpos, p.S, b.scan_tmp, &b.ctr->n_full, s));
   CK(launch_certify(p.P, b.reps, &b.ctr->n_reps, p.S, p.cert_tol, b.mult, b.pass, b.radius, b.ctr,
                     s));
-  CK(cudaEventRecord(ev.e[4], s));
+  CK(mark(ev.e[4], s, capturing));
   const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
   CK(launch_emit(b.reps, &b.ctr->n_reps, p.S, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out,
                  s));
   CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s));
   if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
-  CK(cudaEventRecord(ev.e[5], s));
+  CK(mark(ev.e[5], s, capturing));
+  return MT_OK;
+}
+
+mt_status read_counters(const Buffers& b, DevCounters* h, cudaStream_t s) {
   CK(cudaMemcpyAsync(h, b.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return MT_OK;
+}
+
+mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
+                   uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h) {
+  mt_status rc = enqueue_pass(p, b, out, out_lo, cap_out, is_mis, s, ev, false);
+  if (rc != MT_OK) return rc;
+  return read_counters(b, h, s);
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-graph cache (mt_options.use_graph): the launch sequence of a pass is
+// captured once per (plan, buffers) and replayed.  Capture runs on a stream
+// of the library (the legacy default stream cannot capture), joined to the
+// caller's stream with events.
+struct GraphEntry {
+  Plan p;
+  void *work, *out, *out_lo, *is_mis;
+  int64_t cap;
+  int device;
+  cudaGraphExec_t exec = nullptr;
+  EventSet* ev = nullptr;
+  unsigned long long launches = 0;  // kernels in the graph
+};
+thread_local std::vector<GraphEntry> t_graphs;
+thread_local cudaStream_t t_gstream = nullptr;
+thread_local EventSet* t_join = nullptr;
+
+bool same_plan(const Plan& a, const Plan& b) { return memcmp(&a, &b, sizeof(Plan)) == 0; }
+
+mt_status run_pass_graph(const Plan& p, const Buffers& b, void* work, double2* out, double2* out_lo,
+                         int64_t cap_out, uint8_t* is_mis, cudaStream_t s, DevCounters* h,
+                         EventSet** ev_out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (!t_gstream) CK(cudaStreamCreateWithFlags(&t_gstream, cudaStreamNonBlocking));
+  if (!t_join) t_join = new EventSet();
+  GraphEntry* g = nullptr;
+  for (auto& e : t_graphs)
+    if (e.device == dev && e.work == work && e.out == out && e.out_lo == out_lo &&
+        e.is_mis == is_mis && e.cap == cap_out && same_plan(e.p, p))
+      g = &e;
+  if (!g) {
+    if (t_graphs.size() >= 8) {  // bounded cache: drop the oldest
+      cudaGraphExecDestroy(t_graphs.front().exec);
+      delete t_graphs.front().ev;
+      t_graphs.erase(t_graphs.begin());
+    }
+    GraphEntry e;
+    e.p = p;
+    e.work = work;
+    e.out = out;
+    e.out_lo = out_lo;
+    e.is_mis = is_mis;
+    e.cap = cap_out;
+    e.device = dev;
+    e.ev = new EventSet();
+    CK(cudaStreamBeginCapture(t_gstream, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long l0 = g_launches;
+    mt_status rc = enqueue_pass(p, b, out, out_lo, cap_out, is_mis, t_gstream, *e.ev, true);
+    e.launches = g_launches - l0;
+    g_launches = l0;  // counted when the graph runs
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(t_gstream, &graph);
+    if (rc != MT_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      delete e.ev;
+      return rc;
+    }
+    if (ce != cudaSuccess) {
+      delete e.ev;
+      return fail(MT_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      delete e.ev;
+      return fail(MT_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    }
+    t_graphs.push_back(e);
+    g = &t_graphs.back();
+  }
+  CK(cudaEventRecord(t_join->e[0], s));  // the graph runs after the caller's prior work
+  CK(cudaStreamWaitEvent(t_gstream, t_join->e[0], 0));
+  CK(cudaGraphLaunch(g->exec, t_gstream));
+  g_launches += g->launches;
+  CK(cudaEventRecord(t_join->e[1], t_gstream));
+  CK(cudaStreamWaitEvent(s, t_join->e[1], 0));  // and the caller's later work after the graph
+  *ev_out = g->ev;
+  return read_counters(b, h, s);
 }
 
 mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_roots,
@@ -339,10 +475,16 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   int retry = 0;
   const unsigned long long launches0 = g_launches;
   const int max_retries = max_attempts(o);
+  EventSet* evp = &ev;
   for (;; ++retry) {
     if (!make_plan(kind, l, n, o, retry, &p)) return fail(MT_EINVAL, "no plan for retry %d", retry);
     Buffers b = carve(p, d_work, work_bytes);
-    rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h);
+    evp = &ev;
+    if (o->use_graph && retry == 0)
+      rc = run_pass_graph(p, b, d_work, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, &h,
+                          &evp);
+    else
+      rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h);
     if (rc != MT_OK) return rc;
     // retry on missing roots or on a level-line chunk that skipped a turn
     if (((int64_t)h.n_full == p.degree && h.walk_fail == 0) || retry >= max_retries) break;
@@ -353,11 +495,11 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     st->retries = retry;
     st->n_launches = (int64_t)(g_launches - launches0);
     float ms[5] = {0, 0, 0, 0, 0};
-    cudaEventElapsedTime(&ms[0], ev.e[0], ev.e[5]);
-    cudaEventElapsedTime(&ms[1], ev.e[0], ev.e[1]);
-    cudaEventElapsedTime(&ms[2], ev.e[1], ev.e[2]);
-    cudaEventElapsedTime(&ms[3], ev.e[2], ev.e[3]);
-    cudaEventElapsedTime(&ms[4], ev.e[3], ev.e[4]);
+    cudaEventElapsedTime(&ms[0], evp->e[0], evp->e[5]);
+    cudaEventElapsedTime(&ms[1], evp->e[0], evp->e[1]);
+    cudaEventElapsedTime(&ms[2], evp->e[1], evp->e[2]);
+    cudaEventElapsedTime(&ms[3], evp->e[2], evp->e[3]);
+    cudaEventElapsedTime(&ms[4], evp->e[3], evp->e[4]);
     st->ms_total = ms[0];
     st->ms_walk = ms[1];
     st->ms_descend = ms[2];
@@ -696,6 +838,65 @@ mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, doub
   if (h_offsets[b.np] > cap)
     return fail(MT_ECAPACITY, "%lld roots do not fit in cap %lld", (long long)h_offsets[b.np], (long long)cap);
   if (bad_cert) return fail(MT_ECERT, "%lld roots of the batch failed the certificate", (long long)bad_cert);
+  return MT_OK;
+}
+
+mt_status mt_autotune(int kind, int l, int n, const mt_options* opts, double* d_roots, int64_t cap,
+                      void* d_work, size_t work_bytes, int* best_chunk_log2, int* best_block,
+                      float* best_ms) {
+  g_err.clear();
+  mt_options base;
+  if (opts) base = *opts; else mt_default_options(&base);
+  if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range");
+  if (base.prec != MT_FP64 && base.prec != MT_MIXED) return fail(MT_EINVAL, "tier cannot be tuned");
+  base.max_retries = 0;
+  base.use_graph = 0;
+  const int ll = kind == 0 ? 0 : l;
+  {  // forget a previous result so the default plan is among the candidates
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.erase(TuneKey{kind, ll, n, base.prec});
+  }
+  float best = 1e30f;
+  int bc = 0, bb = 0;
+  const int blocks[3] = {32, 64, 128};
+  for (int cl = 3; cl <= 14; ++cl) {
+    for (int bi = 0; bi < 3; ++bi) {
+      mt_options o = base;
+      o.chunk_log2 = cl;
+      o.block = blocks[bi];
+      Plan p;
+      if (!make_plan(kind, ll, n, &o, 0, &p)) continue;
+      if (p.L != (int64_t(1) << cl)) continue;  // the plan adjusted the chunk: not this candidate
+      if (p.nchunks < 64 && cl > 3) continue;     // too few lanes to be a sensible layout
+      if (workspace_for(kind, ll, n, &o) > work_bytes) continue;
+      float tsum = 0.f;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        int64_t got = 0;
+        mt_stats st;
+        mt_status rc = split_impl(kind, ll, n, &o, d_roots, nullptr, cap, nullptr, d_work, work_bytes,
+                                  &got, &st);
+        ok = (rc == MT_OK);
+        if (rep > 0) tsum += st.ms_total;  // first run warms up
+      }
+      if (!ok) continue;
+      const float t = tsum / 2.f;
+      if (t < best) {
+        best = t;
+        bc = cl;
+        bb = blocks[bi];
+      }
+    }
+  }
+  g_err.clear();
+  if (bc == 0) return fail(MT_EINVAL, "no candidate layout succeeded");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[TuneKey{kind, ll, n, base.prec}] = TuneVal{bc, bb};
+  }
+  if (best_chunk_log2) *best_chunk_log2 = bc;
+  if (best_block) *best_block = bb;
+  if (best_ms) *best_ms = best;
   return MT_OK;
 }
 

@@ -75,7 +75,7 @@ cudaError_t launch_seed_lift(const PolyDev& P, double lambda0, int64_t N0, int s
 // writing every 'every'-th point to starts[g / every].
 cudaError_t launch_walk(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                         int64_t nchunks, const double2* seeds, double2* starts, DevCounters* ctr,
-                        cudaStream_t s);
+                        cudaStream_t s, int block = 64);
 
 // a4: persistent Newton descent over 'count' starts.
 cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t count, double tol,
@@ -87,7 +87,7 @@ cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0,
                                    double2* seeds, DevCounters* ctr, cudaStream_t s);
 cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                               int64_t nchunks, int K, const double2* seeds, double2* starts,
-                              DevCounters* ctr, cudaStream_t s);
+                              DevCounters* ctr, cudaStream_t s, int block = 64);
 cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_t count, double tol,
                                  int cap, double2* cand, float2* dlt, float* hscale, uint8_t* status,
                                  void* anchors, DevCounters* ctr, cudaStream_t s);

@@ -60,8 +60,8 @@ cudaError_t launch_seed_lift(const PolyDev& P, double lambda0, int64_t N0, int s
 
 cudaError_t launch_walk(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                         int64_t nchunks, const double2* seeds, double2* starts, DevCounters* ctr,
-                        cudaStream_t s) {
-  const int bs = 64;
+                        cudaStream_t s, int block) {
+  const int bs = (block >= 32 && block <= 1024 && block % 32 == 0) ? block : 64;
   const int64_t grid = (nchunks + bs - 1) / bs;
   MT_COUNT_LAUNCH(1);
   k_walk<<<(unsigned)grid, bs, 0, s>>>(P, lambda0, M, every, L, nchunks, seeds, starts, ctr);

@@ -460,9 +460,9 @@ cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0,
 
 cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                               int64_t nchunks, int K, const double2* seeds, double2* starts,
-                              DevCounters* ctr, cudaStream_t s) {
+                              DevCounters* ctr, cudaStream_t s, int block) {
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
-  const int bs = 64;
+  const int bs = (block >= 32 && block <= 256 && block % 32 == 0) ? block : 64;
   const size_t smem = (size_t)P.m * bs * sizeof(float2);
   const int64_t grid = (nchunks + bs - 1) / bs;
   MT_COUNT_LAUNCH(1);

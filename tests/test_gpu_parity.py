@@ -331,3 +331,24 @@ def test_batch_order16_full(mt):
         assert ref["n_roots"] == z.size
         dmax, _ = match_sorted(z, ref["roots"], 1e-11)
         assert dmax < 1e-11, (l, n, dmax)
+
+
+# --- CUDA-graph replay and the autotuner ---------------------------------------------
+
+@pytest.mark.parametrize("n,prec", [(12, "fp64"), (20, "mixed")])
+def test_graph_replay_is_identical(mt, n, prec):
+    """Captured once, replayed twice: the same roots as the plain launch sequence."""
+    a = mt.split_hyperbolic(n, prec).roots.cpu().numpy()
+    w = mt.Workspace()
+    b = mt.split_hyperbolic(n, prec, use_graph=1, work=w)
+    c = mt.split_hyperbolic(n, prec, use_graph=1, work=w)
+    assert np.array_equal(a, b.roots.cpu().numpy()) and np.array_equal(a, c.roots.cpu().numpy())
+    assert c.stats["n_cert_pass"] == a.size and c.stats["ms_total"] > 0
+
+
+def test_autotune_picks_a_valid_layout(mt):
+    cl, blk, ms = mt.autotune("hyp", 14)
+    assert 3 <= cl <= 10 and blk in (32, 64, 128) and ms > 0
+    res = mt.split_hyperbolic(14)
+    assert res.stats["n_roots"] == 2 ** 13 and res.stats["n_cert_pass"] == 2 ** 13
+    assert res.stats["n_chunks"] == (8 * 2 ** 13 >> cl) // 2
