@@ -81,6 +81,12 @@ typedef struct {
   double cert_tol;     /* certificate radius cap (0 -> 1e-12 FP64, 1e-20 DD)       */
   int use_graph;       /* 1: capture the launch sequence in a CUDA graph and replay */
   void* stream;        /* cudaStream_t                                              */
+  /* MT_DD only.  A binary64 pass runs first; around each root whose
+     certificate failed or needed a shrunken radius, the disk of radius
+     dd_radius is redone in double-double (level-line chunks, descents,
+     root set, types, certificates).  dd_all = 1 redoes every root. */
+  double dd_radius;    /* zone radius (0 -> 1e-9)                                   */
+  int dd_all;          /* 1: the whole split in double-double                       */
 } mt_options;
 
 #define MT_MAX_TYPES 64
@@ -115,8 +121,12 @@ typedef struct {
   float ms_descend;        /* device time of the Newton descents                   */
   float ms_dedup;          /* device time of fold + sort + cluster + emit          */
   float ms_certify;        /* device time of classify + certify                    */
-  int32_t prec_used;       /* tier of the attempt that produced the result         */
-  int32_t reserved;
+  int32_t prec_used;       /* tier of the attempt that produced the result
+                              (MT_DD when a double-double pass ran)              */
+  float ms_dd;             /* device time of the double-double pass                */
+  int64_t n_zones;         /* double-double zone centres (0 in dd_all mode)        */
+  int64_t n_zone_roots;    /* roots (upper half) produced by the dd pass           */
+  int64_t n_dd_pieces;     /* 64-sub-step pieces of the level line redone in dd    */
 } mt_stats;
 
 /* Defaults documented field by field above. */
@@ -169,8 +179,10 @@ MT_API mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opt
    B' encloses P'(D(c_j, r_j)).  Passing disks are pairwise disjoint, so
    count == degree with every root passing proves the list complete
    (Thm certif).  d_roots: [count][2] (any order); d_roots_lo: NULL or
-   [count][2]; d_pass: [count] bytes; d_radius: [count] doubles (NULL
-   allowed).  *n_pass receives the number of passing roots. */
+   [count][2], the low parts of double-double roots (then the orbit runs in
+   double-double and tol = 0 means 1e-20); d_pass: [count] bytes; d_radius:
+   [count] doubles (NULL allowed).  *n_pass receives the number of passing
+   roots. */
 MT_API size_t mt_certify_workspace_bytes(int64_t count);
 MT_API mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double* d_roots_lo,
                      int64_t count, double tol, uint8_t* d_pass, double* d_radius, void* d_work,

@@ -160,12 +160,17 @@ def split_misiurewicz_batch(max_order: int, prec: str = "fp64", *, work: Workspa
     return torch.view_as_complex(roots), mis, list(offs), [s.as_dict() for s in st], pairs
 
 
-def certify(kind: str, n: int, roots, l: int = 0, tol: float = 0.0, *, work: Workspace | None = None):
-    """Disk certificate (Thm proofRoots) of each root of a complex128 tensor.
+def certify(kind: str, n: int, roots, l: int = 0, tol: float = 0.0, *, work: Workspace | None = None,
+            roots_lo=None):
+    """Disk certificate (Thm proofRoots) of each root of a complex128 tensor
+    (roots_lo: low parts of double-double roots, certified in double-double).
     Returns (pass uint8 tensor, radius float64 tensor, n_pass)."""
     torch = _torch()
     L = load()
     r = torch.view_as_real(roots.contiguous()) if roots.is_complex() else roots.contiguous()
+    rl = None
+    if roots_lo is not None:
+        rl = torch.view_as_real(roots_lo.contiguous()) if roots_lo.is_complex() else roots_lo.contiguous()
     count = r.shape[0]
     nbytes = int(L.mt_certify_workspace_bytes(count))
     work = work or Workspace()
@@ -173,7 +178,7 @@ def certify(kind: str, n: int, roots, l: int = 0, tol: float = 0.0, *, work: Wor
     ok = torch.empty(count, dtype=torch.uint8, device=r.device)
     rad = torch.empty(count, dtype=torch.float64, device=r.device)
     npass = ctypes.c_int64(0)
-    check(L.mt_certify(KIND[kind], l, n, r.data_ptr(), None, count, tol, ok.data_ptr(), rad.data_ptr(),
+    check(L.mt_certify(KIND[kind], l, n, r.data_ptr(), _ptr(rl), count, tol, ok.data_ptr(), rad.data_ptr(),
                        buf.data_ptr(), buf.numel(), ctypes.byref(npass),
                        torch.cuda.current_stream().cuda_stream))
     return ok, rad, int(npass.value)

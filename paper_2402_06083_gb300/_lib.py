@@ -43,6 +43,8 @@ class Options(ctypes.Structure):
         ("cert_tol", ctypes.c_double),
         ("use_graph", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("dd_radius", ctypes.c_double),
+        ("dd_all", ctypes.c_int),
     ]
 
 
@@ -57,7 +59,8 @@ class Stats(ctypes.Structure):
         ("eps_dup", ctypes.c_double),
         ("ms_total", ctypes.c_float), ("ms_walk", ctypes.c_float), ("ms_descend", ctypes.c_float),
         ("ms_dedup", ctypes.c_float), ("ms_certify", ctypes.c_float),
-        ("prec_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("prec_used", ctypes.c_int32), ("ms_dd", ctypes.c_float),
+        ("n_zones", ctypes.c_int64), ("n_zone_roots", ctypes.c_int64), ("n_dd_pieces", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

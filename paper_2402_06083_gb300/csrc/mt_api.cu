@@ -107,7 +107,20 @@ struct Plan {
   double eps;
   double cert_tol;
   int shrink;
+  // MT_DD: the double-double pass
+  int dd;             // 1: run it when the base pass is not certified complete
+  int dd_all;         // 1: every root is redone
+  double dd_R;        // zone radius
+  double dd_margin;   // chunks / main reps within dd_R + dd_margin are revisited
+  double eps_dd, tol_dd, cert_tol_dd;
+  int64_t dd_Ls;      // sub-steps per redone piece of the level line
+  int64_t dd_npieces; // pieces of the upper half
+  int64_t dd_nb;      // pieces per dd batch
+  int64_t dd_zcap;    // zone candidate capacity
+  int64_t dd_near_cap;
 };
+
+constexpr int DD_MAX_BAD = 16384;  // zone centres the dd pass accepts
 
 // ---------------------------------------------------------------------------
 // Autotune table: (kind, l, n, tier) -> chunk length and walk block size
@@ -137,13 +150,16 @@ bool tuned(int kind, int l, int n, int prec, TuneVal* v) {
   return true;
 }
 
+// hyperbolic: a twentieth of the minimal separation 118.4 / 4^n (Sec. 6.3.2);
+// s_{l,n}: a fiftieth of the tip separation ~6.4e3 / 8^(l+n) of this family.
+double raw_eps(int kind, int l, int n) {
+  return (kind == 0) ? fmin(1e-9, 0.05 * 118.4 / std::ldexp(1.0, 2 * n))
+                     : fmin(1e-9, 128.0 / std::ldexp(1.0, 3 * (l + n)));
+}
+
+// the binary64 pixel: never below 64 ulp(2)
 double default_eps(int kind, int l, int n) {
-  // hyperbolic: a twentieth of the minimal separation 118.4 / 4^n (Sec. 6.3.2);
-  // s_{l,n}: a fiftieth of the tip separation ~6.4e3 / 8^(l+n) of this family;
-  // never below 64 ulp(2) of binary64.
-  double e = (kind == 0) ? fmin(1e-9, 0.05 * 118.4 / std::ldexp(1.0, 2 * n))
-                         : fmin(1e-9, 128.0 / std::ldexp(1.0, 3 * (l + n)));
-  return fmax(e, 64.0 * std::ldexp(1.0, -51));
+  return fmax(raw_eps(kind, l, n), 64.0 * std::ldexp(1.0, -51));
 }
 
 bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl) {
@@ -151,7 +167,7 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   Plan p{};  // value-initialised: padding is zero, so plans compare with memcmp
   p.kind = kind;
   p.prec = MT_FP64;
-  if (o && o->prec == MT_MIXED) {
+  if (o && (o->prec == MT_MIXED || o->prec == MT_DD)) {
     // attempt 0 in the mixed tier; a failed attempt repeats in binary64
     if (retry == 0) p.prec = MT_MIXED;
     else retry -= 1;
@@ -187,18 +203,52 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   p.L = Md / N0;
   p.S = (Md / 2) / p.every + 1;
   const bool dd = o && o->prec == MT_DD;
-  p.tol = (o && o->tol > 0) ? o->tol : (dd ? 1e-26 : 1e-13);
+  // the base pass of MT_DD runs with the binary64 settings; the user's tol
+  // and cert_tol then apply to the double-double pass
+  p.tol = (o && o->tol > 0 && !dd) ? o->tol : 1e-13;
   const double IN = (kind == 0) ? 1.0 : 2.6;  // Sec. 4.2
   p.cap = std::max(20, (int)std::ceil(IN * p.P.log2d));
   p.eps = (o && o->eps_dup > 0) ? o->eps_dup : default_eps(kind, l, n);
   // the step that meets tol leaves an error ~ tol^2 / (root separation); keep
   // it well inside the separation pixel so duplicates of a root always merge
   p.tol = std::min(p.tol, 0.05 * p.eps);
-  p.cert_tol = (o && o->cert_tol > 0) ? o->cert_tol : (dd ? 1e-20 : 1e-12);
+  p.cert_tol = (o && o->cert_tol > 0 && !dd) ? o->cert_tol : 1e-12;
   p.shrink = 2 << retry;  // iso-angle shrink steps per lifted level
+  if (dd) {
+    p.dd = 1;
+    p.dd_all = o->dd_all ? 1 : 0;
+    p.dd_R = o->dd_radius > 0 ? o->dd_radius : 1e-9;
+    p.dd_margin = std::max(1e-11, 100.0 * p.eps);
+    p.eps_dd = std::max(1e-28, raw_eps(kind, l, n));
+    p.tol_dd = std::min(o->tol > 0 ? o->tol : 1e-26, 0.05 * p.eps_dd);
+    p.cert_tol_dd = o->cert_tol > 0 ? o->cert_tol : 1e-20;
+    p.dd_Ls = std::min<int64_t>(p.L, 64);
+    p.dd_npieces = (Md / 2) / p.dd_Ls;
+    if (p.dd_npieces > (int64_t(1) << 31)) return false;
+    p.dd_nb = std::min<int64_t>(p.dd_npieces, (int64_t(1) << 20) / (p.dd_Ls / p.every));
+    p.dd_zcap = 2 * p.S + 64;
+    if (!p.dd_all) p.dd_zcap = std::min<int64_t>(p.dd_zcap, int64_t(1) << 21);
+    p.dd_near_cap = p.dd_all ? p.S : std::min<int64_t>(p.S, int64_t(1) << 21);
+  }
   *pl = p;
   return true;
 }
+
+// Scratch of the double-double pass (dd arrays are pairs of doubles).
+struct DdBuffers {
+  unsigned long long* cnt;  // [0] centres [1] polish list [2] zone points [3] zone reps
+                            // [4] kept main multiplicity [5] zone multiplicity [6] main reps
+  double2* bad;
+  uint32_t *pflag, *ppos;  // per piece of the level line: redo flag, its scan
+  int64_t* pids;           // redone pieces
+  void* pscan;
+  dd *sx, *sy, *stx, *sty, *zcx, *zcy, *zrx, *zry;
+  uint8_t *st_ok, *ztype, *zpass;
+  uint32_t* near;
+  uint64_t *zkeys, *zkeys_alt;
+  uint32_t *zvals, *zvals_alt, *zflag, *zpos, *zmult, *zmpos;
+  void *zradix, *zscan;
+};
 
 struct Buffers {
   DevCounters* ctr;
@@ -208,8 +258,11 @@ struct Buffers {
   uint32_t *vals, *vals_alt, *flag, *pos, *mult, *mpos;
   double* radius;
   void *scan_tmp, *radix_tmp, *anchors;
+  DdBuffers d;
   size_t bytes;
 };
+
+dd* take_dd(Carve& c, int64_t n) { return reinterpret_cast<dd*>(c.take<double2>(n)); }
 
 Buffers carve(const Plan& p, void* ws, size_t cap) {
   Carve c(ws, cap);
@@ -234,6 +287,39 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
   b.scan_tmp = c.take_bytes(scan_temp_bytes(p.S));
   b.radix_tmp = c.take_bytes(radix_temp_bytes(p.S));
   b.anchors = (p.prec == MT_MIXED) ? c.take_bytes(mixed_anchor_bytes(p.P, p.S)) : nullptr;
+  b.d = DdBuffers{};
+  if (p.dd) {
+    DdBuffers& d = b.d;
+    const int64_t nst = p.dd_nb * (p.dd_Ls / p.every) + 1;
+    d.cnt = c.take<unsigned long long>(8);
+    d.bad = c.take<double2>(DD_MAX_BAD);
+    d.pflag = c.take<uint32_t>(p.dd_npieces);
+    d.ppos = c.take<uint32_t>(p.dd_npieces);
+    d.pids = c.take<int64_t>(p.dd_npieces);
+    d.pscan = c.take_bytes(scan_temp_bytes(p.dd_npieces));
+    d.sx = take_dd(c, 2 * p.dd_nb);
+    d.sy = take_dd(c, 2 * p.dd_nb);
+    d.stx = take_dd(c, nst);
+    d.sty = take_dd(c, nst);
+    d.st_ok = c.take<uint8_t>(nst);
+    d.near = c.take<uint32_t>(p.dd_near_cap);
+    d.zcx = take_dd(c, p.dd_zcap);
+    d.zcy = take_dd(c, p.dd_zcap);
+    d.zrx = take_dd(c, p.dd_zcap);
+    d.zry = take_dd(c, p.dd_zcap);
+    d.zkeys = c.take<uint64_t>(p.dd_zcap);
+    d.zkeys_alt = c.take<uint64_t>(p.dd_zcap);
+    d.zvals = c.take<uint32_t>(p.dd_zcap);
+    d.zvals_alt = c.take<uint32_t>(p.dd_zcap);
+    d.zflag = c.take<uint32_t>(p.dd_zcap);
+    d.zpos = c.take<uint32_t>(p.dd_zcap);
+    d.zmult = c.take<uint32_t>(p.dd_zcap);
+    d.zmpos = c.take<uint32_t>(p.dd_zcap);
+    d.ztype = c.take<uint8_t>(p.dd_zcap);
+    d.zpass = c.take<uint8_t>(p.dd_zcap);
+    d.zradix = c.take_bytes(radix_temp_bytes(p.dd_zcap));
+    d.zscan = c.take_bytes(scan_temp_bytes(p.dd_zcap));
+  }
   b.bytes = c.off;
   return b;
 }
@@ -242,7 +328,7 @@ size_t plan_bytes(const Plan& p) { return carve(p, nullptr, 0).bytes; }
 
 int max_attempts(const mt_options* o) {
   const int r = o ? std::max(0, o->max_retries) : 1;
-  return (o && o->prec == MT_MIXED) ? r + 1 : r;
+  return (o && (o->prec == MT_MIXED || o->prec == MT_DD)) ? r + 1 : r;
 }
 
 size_t workspace_for(int kind, int l, int n, const mt_options* o) {
@@ -449,6 +535,113 @@ mt_status run_pass_graph(const Plan& p, const Buffers& b, void* work, double2* o
   return read_counters(b, h, s);
 }
 
+// ---------------------------------------------------------------------------
+// The double-double pass (MT_DD) after a base pass whose result is not
+// certified complete; see mt_ddtier.cu for the method.  Host decisions
+// (zone centres sorted by Re, the list of chunks to redo) need a few small
+// synchronous copies; the bulk stays on the device.
+struct DdReport {
+  int64_t zones = 0, zone_roots = 0, pieces = 0;
+  float ms = 0.f;
+};
+
+mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
+                 uint8_t* is_mis, cudaStream_t s, DevCounters* h, DdReport* rep) {
+  const DdBuffers& d = b.d;
+  EventSet ev;
+  if (!ev.ok) return fail(MT_ECUDA, "cudaEventCreate failed");
+  CK(cudaEventRecord(ev.e[0], s));
+  CK(cudaMemsetAsync(d.cnt, 0, 8 * sizeof(unsigned long long), s));
+  CK(cudaMemcpyAsync(&d.cnt[6], &b.ctr->n_reps, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+  const unsigned long long* n_main = &d.cnt[6];
+  int nbad = -1;  // "all" mode
+  if (!p.dd_all) {
+    CK(dd_collect_bad(b.reps, n_main, p.S, b.pass, b.radius, 2.0 * p.eps, d.bad, &d.cnt[0], DD_MAX_BAD,
+                      s));
+    unsigned long long nb_h = 0;
+    CK(cudaMemcpyAsync(&nb_h, &d.cnt[0], sizeof(nb_h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nb_h > (unsigned long long)DD_MAX_BAD)
+      return fail(MT_ECERT, "%llu roots need the double-double pass, more than its %d zones",
+                  nb_h, DD_MAX_BAD);
+    nbad = (int)nb_h;
+    rep->zones = nbad;
+    if (nbad == 0) return MT_OK;  // nothing the dd pass can improve
+    std::vector<double2> hb((size_t)nbad);
+    CK(cudaMemcpyAsync(hb.data(), d.bad, sizeof(double2) * nbad, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::sort(hb.begin(), hb.end(), [](const double2& a, const double2& c) { return a.x < c.x; });
+    CK(cudaMemcpyAsync(d.bad, hb.data(), sizeof(double2) * nbad, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  const double Rm = p.dd_R + p.dd_margin;
+  // pieces of the level line to redo
+  int64_t npieces = p.dd_npieces;
+  if (p.dd_all) {
+    CK(dd_piece_ids(nullptr, nullptr, p.dd_npieces, d.pids, s));
+  } else {
+    CK(cudaMemsetAsync(d.pflag, 0, sizeof(uint32_t) * (size_t)p.dd_npieces, s));
+    CK(dd_mark_pieces(b.cand, b.status, p.S, p.every, p.dd_Ls, p.dd_npieces, d.bad, nbad, Rm, d.pflag, s));
+    CK(launch_exclusive_scan(d.pflag, d.ppos, p.dd_npieces, d.pscan, &d.cnt[7], s));
+    CK(dd_piece_ids(d.pflag, d.ppos, p.dd_npieces, d.pids, s));
+    unsigned long long np_h = 0;
+    CK(cudaMemcpyAsync(&np_h, &d.cnt[7], sizeof(np_h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    npieces = (int64_t)np_h;
+  }
+  rep->pieces = npieces;
+  // b.status is dead from here on: it becomes the drop flag of the main reps
+  uint8_t* drop = b.status;
+  CK(cudaMemsetAsync(drop, 0, (size_t)p.S, s));
+  CK(dd_near_reps(b.reps, n_main, p.S, d.bad, nbad, Rm, d.near, &d.cnt[1], p.dd_near_cap, s));
+  // dd level line and descents, dd_nb pieces at a time
+  const int64_t per_piece = p.dd_Ls / p.every;
+  for (int64_t k0 = 0; k0 < npieces; k0 += p.dd_nb) {
+    const int64_t nb = std::min<int64_t>(p.dd_nb, npieces - k0);
+    const int64_t nst = nb * per_piece + 1;
+    CK(cudaMemsetAsync(d.st_ok, 0, (size_t)nst, s));
+    CK(dd_seeds(p.P, p.lambda0, 2 * p.dd_npieces, p.shrink, d.pids + k0, nb, d.sx, d.sy, b.ctr, s));
+    CK(dd_walk(p.P, p.lambda0, p.M, p.every, p.dd_Ls, p.dd_npieces, d.pids + k0, nb, d.sx, d.sy, d.stx,
+               d.sty, d.st_ok, b.ctr, s));
+    CK(dd_descend(p.P, nst, d.stx, d.sty, d.st_ok, p.tol_dd, p.cap + 4, d.bad, nbad, p.dd_R, d.zcx,
+                  d.zcy, &d.cnt[2], p.dd_zcap, b.ctr, s));
+  }
+  CK(dd_polish(p.P, b.reps, d.near, &d.cnt[1], p.dd_near_cap, p.dd_near_cap, p.tol_dd, d.bad, nbad,
+               p.dd_R, p.dd_margin, drop, d.zcx, d.zcy, &d.cnt[2], p.dd_zcap, b.ctr, s));
+  unsigned long long c_h[8];
+  CK(cudaMemcpyAsync(c_h, d.cnt, sizeof(c_h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c_h[1] > (unsigned long long)p.dd_near_cap || c_h[2] > (unsigned long long)p.dd_zcap)
+    return fail(MT_EINCOMPLETE, "double-double zones too large (%llu polished, %llu zone points)",
+                c_h[1], c_h[2]);
+  // the zone's root set
+  CK(dd_keys(d.zcx, d.zcy, &d.cnt[2], p.dd_zcap, p.eps_dd, d.zkeys, d.zvals, s));
+  CK(radix_sort_pairs(d.zkeys, d.zvals, d.zkeys_alt, d.zvals_alt, p.dd_zcap, d.zradix, s));
+  CK(dd_cluster(d.zcx, d.zcy, d.zvals, &d.cnt[2], p.dd_zcap, p.eps_dd, d.zflag, s));
+  CK(launch_exclusive_scan(d.zflag, d.zpos, p.dd_zcap, d.zscan, &d.cnt[3], s));
+  CK(dd_compact(d.zcx, d.zcy, d.zvals, d.zflag, d.zpos, p.dd_zcap, d.zrx, d.zry, s));
+  CK(dd_type_cert(p.P, d.zrx, d.zry, &d.cnt[3], p.eps_dd, p.cert_tol_dd, b.reps, n_main, drop,
+                  b.radius, p.cert_tol, d.ztype, d.zpass, d.zmult, p.dd_zcap, b.ctr, s));
+  // merge with the kept main representatives and emit
+  uint32_t* kmult = b.vals;  // dead after the base pass
+  uint32_t* mpos = b.pos;
+  CK(dd_keep(n_main, p.S, b.mult, drop, b.type, b.pass, kmult, b.ctr, s));
+  CK(launch_exclusive_scan(kmult, mpos, p.S, b.scan_tmp, &d.cnt[4], s));
+  CK(launch_exclusive_scan(d.zmult, d.zmpos, p.dd_zcap, d.zscan, &d.cnt[5], s));
+  if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
+  const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
+  CK(dd_emit(b.reps, n_main, p.S, kmult, mpos, &d.cnt[4], b.type, mis_code, d.zrx, d.zry, &d.cnt[3],
+             p.dd_zcap, d.zmult, d.zmpos, &d.cnt[5], d.ztype, out, out_lo, is_mis, cap_out, b.ctr, s));
+  CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s, SegView(), out_lo));
+  CK(cudaEventRecord(ev.e[1], s));
+  CK(cudaMemcpyAsync(c_h, d.cnt, sizeof(c_h), cudaMemcpyDeviceToHost, s));
+  mt_status rc = read_counters(b, h, s);
+  if (rc != MT_OK) return rc;
+  rep->zone_roots = (int64_t)c_h[3];
+  cudaEventElapsedTime(&rep->ms, ev.e[0], ev.e[1]);
+  return MT_OK;
+}
+
 mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_roots,
                      double* d_roots_lo, int64_t cap, uint8_t* d_is_mis, void* d_work,
                      size_t work_bytes, int64_t* n_out, mt_stats* st) {
@@ -457,7 +650,6 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   if (cap < 0 || (cap > 0 && !d_roots)) return fail(MT_EINVAL, "bad output buffer");
   if (o && o->prec != MT_FP64 && o->prec != MT_MIXED && o->prec != MT_DD)
     return fail(MT_EINVAL, "unknown precision %d", o->prec);
-  if (o && o->prec == MT_DD) return fail(MT_EINVAL, "MT_DD is not available in this build");
   mt_options dflt;
   mt_default_options(&dflt);
   if (!o) o = &dflt;
@@ -476,6 +668,8 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   const unsigned long long launches0 = g_launches;
   const int max_retries = max_attempts(o);
   EventSet* evp = &ev;
+  DdReport ddr;
+  bool dd_ran = false;
   for (;; ++retry) {
     if (!make_plan(kind, l, n, o, retry, &p)) return fail(MT_EINVAL, "no plan for retry %d", retry);
     Buffers b = carve(p, d_work, work_bytes);
@@ -487,7 +681,20 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
       rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h);
     if (rc != MT_OK) return rc;
     // retry on missing roots or on a level-line chunk that skipped a turn
-    if (((int64_t)h.n_full == p.degree && h.walk_fail == 0) || retry >= max_retries) break;
+    bool done = (int64_t)h.n_full == p.degree && h.walk_fail == 0;
+    const bool certified = (int64_t)h.n_full == p.degree && h.n_cert_pass == h.n_full;
+    dd_ran = false;
+    if (p.dd && (p.dd_all || !certified)) {
+      // MT_DD: a certified complete list is the goal (it proves itself)
+      ddr = DdReport();
+      rc = run_dd(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, &h, &ddr);
+      if (rc != MT_OK) return rc;
+      dd_ran = true;
+      done = (int64_t)h.n_full == p.degree && h.n_cert_pass == h.n_full;
+    } else if (p.dd) {
+      done = certified;
+    }
+    if (done || retry >= max_retries) break;
   }
   if (st) {
     memset(st, 0, sizeof(*st));
@@ -505,6 +712,14 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     st->ms_descend = ms[2];
     st->ms_dedup = ms[3];
     st->ms_certify = ms[4];
+    if (dd_ran) {
+      st->prec_used = MT_DD;
+      st->ms_dd = ddr.ms;
+      st->ms_total += ddr.ms;
+      st->n_zones = ddr.zones;
+      st->n_zone_roots = ddr.zone_roots;
+      st->n_dd_pieces = ddr.pieces;
+    }
   }
   if (n_out) *n_out = (int64_t)h.n_full;
   if ((int64_t)h.n_full != p.degree)
@@ -919,12 +1134,11 @@ mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double
   if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range");
   if (count < 0 || (count > 0 && (!d_roots || !d_pass))) return fail(MT_EINVAL, "bad buffers");
   if (count > 0xffffffffll) return fail(MT_EINVAL, "count too large");
-  (void)d_roots_lo;
   const size_t need = mt_certify_workspace_bytes(count);
   if (!d_work || work_bytes < need) return fail(MT_ENOMEM, "workspace of %zu bytes needed", need);
   cudaStream_t s = (cudaStream_t)stream;
   const PolyDev P = make_poly(kind, l, n);
-  if (tol <= 0) tol = 1e-12;
+  if (tol <= 0) tol = d_roots_lo ? 1e-20 : 1e-12;
   Carve c(d_work, work_bytes);
   DevCounters* ctr = c.take<DevCounters>(1);
   uint64_t* keys = c.take<uint64_t>(count);
@@ -935,7 +1149,11 @@ mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double
   CK(launch_init_counters(ctr, s));
   CK(launch_keys_plain((const double2*)d_roots, count, keys, vals, s));
   CK(radix_sort_pairs(keys, vals, keys_alt, vals_alt, count, rtmp, s));
-  CK(launch_certify_list(P, (const double2*)d_roots, vals, count, tol, d_pass, d_radius, ctr, s));
+  if (d_roots_lo)
+    CK(dd_certify_list(P, (const double2*)d_roots, (const double2*)d_roots_lo, vals, count, tol, d_pass,
+                       d_radius, ctr, s));
+  else
+    CK(launch_certify_list(P, (const double2*)d_roots, vals, count, tol, d_pass, d_radius, ctr, s));
   DevCounters h;
   CK(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

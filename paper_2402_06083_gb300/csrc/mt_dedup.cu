@@ -418,7 +418,7 @@ cudaError_t launch_emit(const double2* reps, const unsigned long long* n_reps, i
 // Exact ties of Re between distinct roots (rare): sort each run of equal Re
 // by Im so the list follows eq. defLexi.  One thread per run start.
 __global__ void k_fix_ties(double2* out, const unsigned long long* __restrict__ n_full,
-                           int64_t cap_out, uint8_t* is_mis, SegView sv) {
+                           int64_t cap_out, uint8_t* is_mis, SegView sv, double2* out_lo) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t n = (int64_t)*n_full;
   if (n > cap_out) n = cap_out;
@@ -434,23 +434,27 @@ __global__ void k_fix_ties(double2* out, const unsigned long long* __restrict__ 
   // insertion sort of [p, e) by Im (runs are tiny)
   for (int64_t i = p + 1; i < e; ++i) {
     const double2 v = out[i];
+    const double2 vl = out_lo ? out_lo[i] : make_double2(0.0, 0.0);
     const uint8_t m = is_mis ? is_mis[i] : 0;
     int64_t j = i - 1;
     while (j >= p && out[j].y > v.y) {
       out[j + 1] = out[j];
+      if (out_lo) out_lo[j + 1] = out_lo[j];
       if (is_mis) is_mis[j + 1] = is_mis[j];
       --j;
     }
     out[j + 1] = v;
+    if (out_lo) out_lo[j + 1] = vl;
     if (is_mis) is_mis[j + 1] = m;
   }
 }
 
 cudaError_t launch_fix_ties(double2* out, const unsigned long long* n_full, int64_t cap_out,
-                            uint8_t* is_mis, cudaStream_t s, SegView sv) {
+                            uint8_t* is_mis, cudaStream_t s, SegView sv, double2* out_lo) {
   if (cap_out <= 1) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_fix_ties<<<(unsigned)((cap_out + 255) / 256), 256, 0, s>>>(out, n_full, cap_out, is_mis, sv);
+  k_fix_ties<<<(unsigned)((cap_out + 255) / 256), 256, 0, s>>>(out, n_full, cap_out, is_mis, sv,
+                                                               out_lo);
   return cudaGetLastError();
 }
 

@@ -159,7 +159,8 @@ cudaError_t launch_emit(const double2* reps, const unsigned long long* n_reps, i
                         int mis_code, double2* out, uint8_t* is_mis, int64_t cap_out,
                         cudaStream_t s, SegView sv = SegView());
 cudaError_t launch_fix_ties(double2* out, const unsigned long long* n_full, int64_t cap_out,
-                            uint8_t* is_mis, cudaStream_t s, SegView sv = SegView());
+                            uint8_t* is_mis, cudaStream_t s, SegView sv = SegView(),
+                            double2* out_lo = nullptr);
 
 // Standalone type (a6 without polish) for mt_classify.
 cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t count, double tau,
@@ -174,6 +175,59 @@ cudaError_t launch_keys_plain(const double2* pts, int64_t count, uint64_t* keys,
 cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint32_t* order,
                                 int64_t count, double tol, uint8_t* pass, double* radius,
                                 DevCounters* ctr, cudaStream_t s);
+
+// ---- the double-double tier (mt_ddtier.cu) ----------------------------------
+// dd values are pairs of binary64 (hi, lo), 16 bytes like a double2.
+struct dd;
+cudaError_t dd_collect_bad(const double2* reps, const unsigned long long* n_reps, int64_t cap,
+                           const uint8_t* pass, const double* radius, double thr, double2* bad,
+                           unsigned long long* nbad, int max_bad, cudaStream_t s);
+cudaError_t dd_mark_pieces(const double2* cand, const uint8_t* status, int64_t S, int every,
+                           int64_t Ls, int64_t npieces, const double2* bad, int nbad, double R,
+                           uint32_t* flag, cudaStream_t s);
+cudaError_t dd_piece_ids(const uint32_t* flag, const uint32_t* pos, int64_t npieces, int64_t* ids,
+                         cudaStream_t s);
+cudaError_t dd_near_reps(const double2* reps, const unsigned long long* n_reps, int64_t cap,
+                         const double2* bad, int nbad, double R, uint32_t* near,
+                         unsigned long long* nnear, int64_t near_cap, cudaStream_t s);
+cudaError_t dd_seeds(const PolyDev& P, double lambda0, int64_t NQ, int shrink, const int64_t* ids,
+                     int64_t nb, dd* sx, dd* sy, DevCounters* ctr, cudaStream_t s);
+cudaError_t dd_walk(const PolyDev& P, double lambda0, int M, int every, int64_t Ls, int64_t npieces,
+                    const int64_t* ids, int64_t nb, const dd* sx, const dd* sy, dd* stx, dd* sty,
+                    uint8_t* st_ok, DevCounters* ctr, cudaStream_t s);
+cudaError_t dd_descend(const PolyDev& P, int64_t count, const dd* zx0, const dd* zy0,
+                       const uint8_t* ok0, double tol, int cap, const double2* bad, int nbad,
+                       double R, dd* ox, dd* oy, unsigned long long* nout, int64_t out_cap,
+                       DevCounters* ctr, cudaStream_t s);
+cudaError_t dd_polish(const PolyDev& P, const double2* reps, const uint32_t* near,
+                      const unsigned long long* nnear, int64_t near_cap, int64_t launch_n, double tol,
+                      const double2* bad, int nbad, double R, double margin, uint8_t* drop, dd* ox,
+                      dd* oy, unsigned long long* nout, int64_t out_cap, DevCounters* ctr,
+                      cudaStream_t s);
+cudaError_t dd_keys(const dd* zx, dd* zy, const unsigned long long* nz, int64_t zcap, double eps,
+                    uint64_t* keys, uint32_t* vals, cudaStream_t s);
+cudaError_t dd_cluster(const dd* zx, const dd* zy, const uint32_t* vals, const unsigned long long* nz,
+                       int64_t zcap, double eps, uint32_t* flag, cudaStream_t s);
+cudaError_t dd_compact(const dd* zx, const dd* zy, const uint32_t* vals, const uint32_t* flag,
+                       const uint32_t* pos, int64_t zcap, dd* rx, dd* ry, cudaStream_t s);
+cudaError_t dd_type_cert(const PolyDev& P, const dd* rx, const dd* ry, const unsigned long long* nz,
+                         double tau, double tol, const double2* reps, const unsigned long long* n_main,
+                         const uint8_t* drop, const double* radius, double wmax, uint8_t* type,
+                         uint8_t* pass, uint32_t* mult, int64_t zcap, DevCounters* ctr,
+                         cudaStream_t s);
+cudaError_t dd_keep(const unsigned long long* n_reps, int64_t cap, const uint32_t* mult,
+                    const uint8_t* drop, const uint8_t* type, const uint8_t* pass, uint32_t* kmult,
+                    DevCounters* ctr, cudaStream_t s);
+cudaError_t dd_emit(const double2* reps, const unsigned long long* n_reps, int64_t cap,
+                    const uint32_t* kmult, const uint32_t* mpos, const unsigned long long* mt,
+                    const uint8_t* type, int mis_code, const dd* zrx, const dd* zry,
+                    const unsigned long long* nz, int64_t zcap, const uint32_t* zmult,
+                    const uint32_t* zmpos, const unsigned long long* zt, const uint8_t* ztype,
+                    double2* out, double2* out_lo, uint8_t* is_mis, int64_t cap_out,
+                    DevCounters* ctr, cudaStream_t s);
+cudaError_t dd_certify_list(const PolyDev& P, const double2* hi, const double2* lo,
+                            const uint32_t* order, int64_t n, double tol, uint8_t* pass,
+                            double* radius, DevCounters* ctr, cudaStream_t s);
 
 int device_sm_count();
 
