@@ -9,9 +9,10 @@ walk, Newton descents, root set, types, certificates, sorted output.
     python bench.py --impl reference ...   # the CPU oracle on the same metric
 
 For N > 1 (torchrun) every rank splits its own copy of the workload
-(replicas: the path needs a cross-rank exchange to shard one polynomial,
-see the design doc), timing is the max over ranks, value = all ranks' roots /
-that time.  Prints one JSON line on rank 0.
+(replicas: one polynomial is split on one GPU; sharding it would need a
+cross-rank exchange of the level-line seeds and of the root set), timing
+is the max over ranks, value = all ranks' roots / that time.  Prints one
+JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -35,6 +36,8 @@ CONFIGS = {
     "hyp20mixed": ("hyp", 0, 20, "mixed"),
     "hyp24": ("hyp", 0, 24, "fp64"),
     "hyp24mixed": ("hyp", 0, 24, "mixed"),
+    "hyp26dd": ("hyp", 0, 26, "dd"),
+    "hyp28dd": ("hyp", 0, 28, "dd"),  # binary64 cannot separate its tip roots: dd zones
     "mis16": ("misbatch", 0, 16, "fp64"),  # every s_{l,n}, l >= 2, n >= 1, l + n <= 16, one pass
 }
 
@@ -207,6 +210,7 @@ def main():
     stream = torch.cuda.current_stream()
     work = mt.Workspace()
     roots = torch.empty((d, 2), dtype=torch.float64, device="cuda")
+    roots_lo = torch.empty((d, 2), dtype=torch.float64, device="cuda") if prec == "dd" else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
     class _BatchResult:
@@ -220,7 +224,8 @@ def main():
     def step(out=None, p=None):
         pp = prec if p is None else p
         if kind == "hyp":  # the launch sequence is captured once and replayed as a CUDA graph
-            return mt.split_hyperbolic(n, pp, work=work, out=roots, use_graph=1)
+            return mt.split_hyperbolic(n, pp, work=work, out=roots, use_graph=1,
+                                       out_lo=roots_lo if pp == "dd" else None)
         if kind == "misbatch":
             _, _, _, st, _ = mt.split_misiurewicz_batch(n, pp, work=work)
             return _BatchResult(st)
@@ -280,9 +285,12 @@ def main():
     host = torch.empty((d, 2), dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    host_lo = torch.empty((d, 2), dtype=torch.float64, pin_memory=True) if roots_lo is not None else None
     for i in range(args.steps):
         r = step()
         host.copy_(roots, non_blocking=True)
+        if host_lo is not None:
+            host_lo.copy_(roots_lo, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
     if dist:
@@ -313,7 +321,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (inputs fixed by n)",
         "config": {"workload": ("p_%d hyperbolic centres, %d roots, %s, all certified" % (
-                       n, d, "plain binary64" if prec == "fp64" else "mixed binary32/binary64")
+                       n, d, {"fp64": "plain binary64", "mixed": "mixed binary32/binary64",
+                              "dd": "mixed binary32/binary64 + double-double zones"}[prec])
                        if kind == "hyp" else
                        ("all s_{l,n} with l >= 2, n >= 1, l + n <= %d (%d polynomials, %d roots), one pass, "
                         "binary64, all certified" % (n, len(mt.misiurewicz_pairs(n)), d))
@@ -321,7 +330,7 @@ def main():
                    "precision": prec, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": world * d / e2e_s, "unit": "roots/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": d * 16 + 1024,
+                "d2h_bytes_per_step": d * 16 * (2 if roots_lo is not None else 1) + 1024,
                 "note": "input is the integer n (no device input); result roots copied to pinned host memory"},
         "roofline": {"bound": "alu", "kernel": "k_" + ("descend" if dom == "descend" else "walk"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -332,7 +341,9 @@ def main():
         "detail": {"ms_walk": s0["ms_walk"], "ms_descend": s0["ms_descend"], "ms_dedup": s0["ms_dedup"],
                    "ms_certify": s0["ms_certify"], "walk_newton": s0["walk_newton"],
                    "desc_newton": s0["desc_newton"], "n_chunks": s0["n_chunks"],
-                   "wall_s": t_wall},
+                   "ms_dd": s0.get("ms_dd", 0.0), "n_zones": s0.get("n_zones", 0),
+                   "n_zone_roots": s0.get("n_zone_roots", 0), "steps_dd": s0["steps_dd"],
+                   "prec_used": s0["prec_used"], "wall_s": t_wall},
     }
     # the same workload in the mixed tier (binary32 tracking, binary64 finish)
     if prec == "fp64" and kind == "hyp" and not args.no_compare:

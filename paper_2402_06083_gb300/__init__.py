@@ -88,18 +88,20 @@ class Workspace:
 
 
 def split_hyperbolic(n: int, prec: str = "fp64", *, work: Workspace | None = None, want_lo: bool = False,
-                     check_status: bool = True, out=None, **kw) -> SplitResult:
-    """All 2^(n-1) roots of p_n (Algorithm S_par, Sec. 4.2)."""
-    return _split("hyp", n, 0, prec, work, want_lo, check_status, out, kw)
+                     check_status: bool = True, out=None, out_lo=None, **kw) -> SplitResult:
+    """All 2^(n-1) roots of p_n (Algorithm S_par, Sec. 4.2).  out / out_lo:
+    optional float64 [deg, 2] device buffers for the roots and low parts."""
+    return _split("hyp", n, 0, prec, work, want_lo, check_status, out, out_lo, kw)
 
 
 def split_misiurewicz(l: int, n: int, prec: str = "fp64", *, work: Workspace | None = None,
-                      want_lo: bool = False, check_status: bool = True, out=None, **kw) -> SplitResult:
+                      want_lo: bool = False, check_status: bool = True, out=None, out_lo=None,
+                      **kw) -> SplitResult:
     """All 2^(l+n-2) roots of s_{l,n}, with the Mis(l,n) mask (eq. def:mis)."""
-    return _split("mis", n, l, prec, work, want_lo, check_status, out, kw)
+    return _split("mis", n, l, prec, work, want_lo, check_status, out, out_lo, kw)
 
 
-def _split(kind, n, l, prec, work, want_lo, check_status, out, kw) -> SplitResult:
+def _split(kind, n, l, prec, work, want_lo, check_status, out, out_lo, kw) -> SplitResult:
     torch = _torch()
     L = load()
     o = options(prec, **kw)
@@ -110,7 +112,8 @@ def _split(kind, n, l, prec, work, want_lo, check_status, out, kw) -> SplitResul
     work = work or Workspace()
     buf = work.ensure(nbytes)
     roots = out if out is not None else torch.empty((d, 2), dtype=torch.float64, device="cuda")
-    lo = torch.empty((d, 2), dtype=torch.float64, device="cuda") if want_lo else None
+    lo = out_lo if out_lo is not None else (
+        torch.empty((d, 2), dtype=torch.float64, device="cuda") if want_lo else None)
     mis = torch.empty(d, dtype=torch.uint8, device="cuda") if kind == "mis" else None
     n_out = ctypes.c_int64(0)
     st = Stats()
