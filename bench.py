@@ -50,17 +50,49 @@ def peaks() -> dict:
         return {}
 
 
-# FP64 work of one Newton step on an orbit of length m (binary64 flops, FMA = 2):
-# orbit step: 2 add + 5 FMA + 2 mul = 14 flops; quotient with power-of-two
-# scaling, target subtraction and update: 24 flops.
+# Work of one Newton step on an orbit of length m, in flops (FMA = 2): the
+# orbit step is 2 add + 5 FMA + 1 mul = 13 flops; the quotient with its
+# power-of-two guard, the target subtraction and the update about 24.
 def newton_flops(m: int) -> int:
-    return 14 * m + 24
+    return 13 * m + 24
 
 
-# Nominal binary64 rate of a GB300 (profiling recipe table): 1.25 TFLOP/s
-# at the 2070 MHz maximum SM clock.
+# Nominal rates of a GB300 at the 2070 MHz maximum SM clock: binary64
+# 1.25 TFLOP/s (profiling recipe table; 2 DFMA lanes per SM), binary32
+# 152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SM_MAX_MHZ = 2070.0
+
+
+def roofline(prec: str, m: int, stats: list) -> dict:
+    """ALU roofline of the dominant kernel (walk or descent) from the
+    library's own CUDA events (on the launch stream, inside the graph) and
+    its own step counters.  Binary32 steps of the mixed tier count at the
+    binary64/binary32 peak ratio, so frac is the share of the binary64 pipe
+    the same work would need.  Walk time excludes the seed lifts."""
+    fl = newton_flops(m)
+    ratio = FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS
+    s0 = stats[-1]
+    walk_ms = statistics.mean(s["ms_walk"] - s["ms_seeds"] for s in stats)
+    desc_ms = statistics.mean(s["ms_descend"] for s in stats)
+    walk_steps = s0["walk_newton"] - s0["seed_newton"]
+    if prec == "fp64":
+        walk_eq = walk_steps * fl
+        desc_eq = s0["desc_newton"] * fl
+    else:  # mixed walk: binary32 sub-steps; descents: binary32 then binary64 finish
+        walk_eq = walk_steps * fl * ratio
+        desc_eq = (s0["desc_newton"] - s0["desc_fp32"]) * fl + s0["desc_fp32"] * fl * ratio
+    kern, eq, ms = ("k_descend", desc_eq, desc_ms) if desc_ms >= walk_ms else ("k_walk", walk_eq, walk_ms)
+    if prec != "fp64":
+        kern += "_mixed"
+    achieved = eq / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "ms_per_launch": ms, "flops_per_launch": eq,
+            "peak_source": "nominal binary64 1.25 TFLOP/s at 2070 MHz (profiling recipe table)"
+                           + ("" if prec == "fp64" else "; binary32 steps weighted by 1.25/80.5"),
+            "work": "Newton steps x (13 m + 24) flops, m = %d, steps counted by the kernel" % m}
 
 
 class ClockSampler:
@@ -125,6 +157,21 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The slowest rank's value (the job's time): all-reduce MAX, or x alone."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, seconds: float) -> float:
+    """Weak scaling: every rank processes its own copy; all units / job time."""
+    return world * units_per_rank / seconds
 
 
 def cpu_baseline(kind: str, l: int, n: int, target_s: float = 15.0) -> dict:
@@ -273,13 +320,9 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = statistics.mean(step_ms)
-    # max over ranks
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     certified = min(s["n_cert_pass"] for s in stats)
-    value = world * certified / (ms / 1e3)
+    value = whole_job_rate(world, certified, ms / 1e3)
 
     # end to end through the public API with a pinned host result buffer
     host = torch.empty((d, 2), dtype=torch.float64, pin_memory=True)
@@ -293,29 +336,11 @@ def main():
             host_lo.copy_(roots_lo, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     clocks = sampler.stop()
 
     s0 = stats[-1]
     m = n if kind == "hyp" else (n - 1 if kind == "misbatch" else l + n - 1)
-    fl_step = newton_flops(m)
-    # dominant kernel by device time (library's CUDA events on the launch stream)
-    parts = {"walk": s0["ms_walk"], "descend": s0["ms_descend"], "dedup": s0["ms_dedup"],
-             "certify": s0["ms_certify"]}
-    dom = max(parts, key=parts.get)
-    if dom == "descend":
-        flops = s0["desc_newton"] * fl_step
-        dom_ms = statistics.mean(s["ms_descend"] for s in stats)
-    else:
-        flops = s0["walk_newton"] * fl_step
-        dom_ms = statistics.mean(s["ms_walk"] for s in stats)
-    achieved = flops / (dom_ms / 1e3) / 1e12
-    peak = FP64_PEAK_TFLOPS
-    if clocks.get("sm_mhz"):
-        pass
     line = {
         "metric": METRIC, "value": value, "unit": "roots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -329,17 +354,16 @@ def main():
                        if kind == "misbatch" else "s_{%d,%d}" % (l, n)),
                    "precision": prec, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "e2e": {"value": world * d / e2e_s, "unit": "roots/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": whole_job_rate(world, d, e2e_s), "unit": "roots/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d * 16 * (2 if roots_lo is not None else 1) + 1024,
                 "note": "input is the integer n (no device input); result roots copied to pinned host memory"},
-        "roofline": {"bound": "alu", "kernel": "k_" + ("descend" if dom == "descend" else "walk"),
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None,
-                     "peak_source": "nominal binary64 1.25 TFLOP/s at 2070 MHz (profiling recipe table)"},
+        "roofline": roofline(prec, m, stats),
         "gpu_launches": int(sum(s["n_launches"] for s in stats)),
         "clocks": clocks,
         "detail": {"ms_walk": s0["ms_walk"], "ms_descend": s0["ms_descend"], "ms_dedup": s0["ms_dedup"],
-                   "ms_certify": s0["ms_certify"], "walk_newton": s0["walk_newton"],
+                   "ms_certify": s0["ms_certify"], "ms_seeds": s0["ms_seeds"],
+                   "walk_newton": s0["walk_newton"], "seed_newton": s0["seed_newton"],
+                   "desc_fp32": s0["desc_fp32"], "n_finish": s0["n_finish"],
                    "desc_newton": s0["desc_newton"], "n_chunks": s0["n_chunks"],
                    "ms_dd": s0.get("ms_dd", 0.0), "n_zones": s0.get("n_zones", 0),
                    "n_zone_roots": s0.get("n_zone_roots", 0), "steps_dd": s0["steps_dd"],
@@ -354,6 +378,7 @@ def main():
                       "ms_per_step": ms_mix, "speedup_vs_fp64": ms / ms_mix,
                       "prec_used": sm["prec_used"], "steps_fp32": sm["steps_fp32"],
                       "desc_newton": sm["desc_newton"], "walk_newton": sm["walk_newton"],
+                      "desc_fp32": sm["desc_fp32"], "n_finish": sm["n_finish"],
                       "ms_walk": sm["ms_walk"], "ms_descend": sm["ms_descend"],
                       "ms_certify": sm["ms_certify"], "ms_dedup": sm["ms_dedup"],
                       "all_certified": all(x["n_cert_pass"] == d for x in st_mix)}}

@@ -127,6 +127,12 @@ typedef struct {
   int64_t n_zones;         /* double-double zone centres (0 in dd_all mode)        */
   int64_t n_zone_roots;    /* roots (upper half) produced by the dd pass           */
   int64_t n_dd_pieces;     /* 64-sub-step pieces of the level line redone in dd    */
+  int64_t seed_newton;     /* Newton steps of the seed lifts (part of walk_newton) */
+  int64_t desc_fp32;       /* binary32 Newton steps of the descents                */
+  float ms_seeds;          /* device time of the seed lifts (part of ms_walk)      */
+  int32_t reserved;
+  int64_t n_finish;        /* binary64 finishes in the mixed tier (one per run of
+                              descents that reached the same root in binary32)   */
 } mt_stats;
 
 /* Defaults documented field by field above. */

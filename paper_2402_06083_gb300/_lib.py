@@ -61,6 +61,8 @@ class Stats(ctypes.Structure):
         ("ms_dedup", ctypes.c_float), ("ms_certify", ctypes.c_float),
         ("prec_used", ctypes.c_int32), ("ms_dd", ctypes.c_float),
         ("n_zones", ctypes.c_int64), ("n_zone_roots", ctypes.c_int64), ("n_dd_pieces", ctypes.c_int64),
+        ("seed_newton", ctypes.c_int64), ("desc_fp32", ctypes.c_int64), ("ms_seeds", ctypes.c_float),
+        ("reserved", ctypes.c_int32), ("n_finish", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -346,7 +346,7 @@ size_t workspace_for(int kind, int l, int n, const mt_options* o) {
 }
 
 struct EventSet {
-  cudaEvent_t e[6];
+  cudaEvent_t e[8];
   bool ok = false;
   EventSet() {
     ok = true;
@@ -372,6 +372,9 @@ void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
   st->desc_newton = (int64_t)h.desc_newton;
   st->steps_fp32 = (int64_t)h.steps_fp32;
   st->steps_dd = (int64_t)h.steps_dd;
+  st->seed_newton = (int64_t)h.seed_newton;
+  st->desc_fp32 = (int64_t)h.desc_fp32;
+  st->n_finish = (int64_t)h.n_finish;
   st->walk_fail = (int64_t)h.walk_fail;
   st->n_cert_pass = (int64_t)h.n_cert_pass;
   for (int i = 0; i < MT_MAX_TYPES; ++i) st->count_by_type[i] = (int64_t)h.type_count[i];
@@ -404,6 +407,7 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
   } else {
     CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
   }
+  CK(mark(ev.e[6], s, capturing));
   if (p.prec == MT_MIXED) {
     CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts, b.ctr,
                          s, p.walk_block));
@@ -414,8 +418,11 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
   CK(mark(ev.e[1], s, capturing));
   if (p.prec == MT_MIXED) {
     // binary32 deltas and descent scales live in the (not yet used) sort buffers
+    // the root-set buffers are free until the fold: binary32 deltas and scales
+    // in keys / vals, the finish lists in flag / pos / vals_alt / type
+    FinishScratch fin{b.flag, b.pos, b.vals_alt, b.type, b.scan_tmp, &b.ctr->n_finish};
     CK(launch_descend_mixed(p.P, b.starts, p.S, p.tol, p.cap, b.cand, (float2*)b.keys,
-                            (float*)b.vals, b.status, b.anchors, b.ctr, s));
+                            (float*)b.vals, b.status, b.anchors, fin, b.ctr, s));
   } else {
     CK(launch_descend(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
   }
@@ -712,6 +719,7 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     st->ms_descend = ms[2];
     st->ms_dedup = ms[3];
     st->ms_certify = ms[4];
+    cudaEventElapsedTime(&st->ms_seeds, evp->e[0], evp->e[6]);
     if (dd_ran) {
       st->prec_used = MT_DD;
       st->ms_dd = ddr.ms;
@@ -876,6 +884,7 @@ mt_status run_batch_pass(const BatchPlan& b, const BatchBuffers& r, double2* out
   CK(cudaMemcpyAsync(r.start_off, b.start_off.data(), sizeof(int64_t) * (b.np + 1), cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(ev.e[0], s));
   CK(launch_seed_lift_batch(r.E, r.seed_off, b.np, b.seeds_total, b.lambda0, b.shrink, r.seeds, r.ctr, s));
+  CK(cudaEventRecord(ev.e[6], s));
   CK(launch_walk_batch(r.E, r.chunk_off, b.np, b.chunks_total, b.lambda0, b.M, b.every, r.seeds,
                        r.starts, r.ctr, s));
   CK(cudaEventRecord(ev.e[1], s));
@@ -1016,6 +1025,8 @@ mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, doub
   cudaEventElapsedTime(&ms[2], ev.e[1], ev.e[2]);
   cudaEventElapsedTime(&ms[3], ev.e[2], ev.e[3]);
   cudaEventElapsedTime(&ms[4], ev.e[3], ev.e[4]);
+  float ms_seeds = 0.f;
+  cudaEventElapsedTime(&ms_seeds, ev.e[0], ev.e[6]);
   int64_t bad_cert = 0;
   for (int p = 0; p < b.np; ++p) {
     const unsigned long long* q = &ps[(size_t)p * PSTAT_W];
@@ -1036,6 +1047,8 @@ mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, doub
     st.walk_newton = (int64_t)h.walk_newton;
     st.desc_newton = (int64_t)h.desc_newton;
     st.walk_fail = (int64_t)h.walk_fail;
+    st.seed_newton = (int64_t)h.seed_newton;
+    st.ms_seeds = ms_seeds;
     st.M = b.M;
     st.c_L = b.cL;
     st.retries = retry;

@@ -36,6 +36,7 @@ __global__ void k_seed_lift_batch(const BatchEntry* __restrict__ E, const int64_
     seeds[g] = lift_seed(e.P, lambda0, e.N0, e.log2N0, shrink, g - seed_off[p], steps);
   }
   warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->seed_newton, steps);
 }
 
 // persistent: lanes pop level-line chunks of any polynomial from one queue

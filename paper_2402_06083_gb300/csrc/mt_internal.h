@@ -37,6 +37,9 @@ struct DevCounters {
   unsigned long long max_radius_bits;
   unsigned long long queue_head;    // work queue of the persistent descent
   unsigned long long queue_head2;   // second queue (batched walk)
+  unsigned long long seed_newton;   // Newton steps of the seed lifts (part of walk_newton)
+  unsigned long long desc_fp32;     // binary32 Newton steps of the descents (part of desc_newton)
+  unsigned long long n_finish;      // binary64 finishes of the mixed tier (run heads)
   unsigned long long type_count[64];
 };
 
@@ -88,9 +91,17 @@ cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0,
 cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                               int64_t nchunks, int K, const double2* seeds, double2* starts,
                               DevCounters* ctr, cudaStream_t s, int block = 64);
+// Scratch of the binary64 finish of the mixed tier (count entries each).
+struct FinishScratch {
+  uint32_t *head, *pos, *list;
+  uint8_t* link;
+  void* scan_tmp;                 // scan_temp_bytes(count)
+  unsigned long long* nheads;     // device counter
+};
 cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_t count, double tol,
                                  int cap, double2* cand, float2* dlt, float* hscale, uint8_t* status,
-                                 void* anchors, DevCounters* ctr, cudaStream_t s);
+                                 void* anchors, const FinishScratch& fin, DevCounters* ctr,
+                                 cudaStream_t s);
 size_t mixed_anchor_bytes(const PolyDev& P, int64_t count);
 
 // Batched (several polynomials) seeds, walk and descents.

@@ -27,6 +27,7 @@ __global__ void k_seed_lift(PolyDev P, double lambda0, int64_t N0, int log2N0, i
   unsigned long long steps = 0;
   if (j <= N0 / 2) seeds[j] = lift_seed(P, lambda0, N0, log2N0, shrink, j, steps);
   warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->seed_newton, steps);
 }
 
 __global__ void k_walk(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,

@@ -190,6 +190,7 @@ __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log
     fails = bad ? 1 : 0;
   }
   warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->seed_newton, steps);
   warp_add_u64(&ctr->steps_fp32, s32);
   warp_add_u64(&ctr->walk_fail, fails);
 }
@@ -391,31 +392,88 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
     }
   }
   warp_add_u64(&ctr->desc_newton, s32);
+  warp_add_u64(&ctr->desc_fp32, s32);
   warp_add_u64(&ctr->steps_fp32, s32);
   warp_add_u64(&ctr->n_diverge, ndiv);
   warp_add_u64(&ctr->n_timeout, nto);
 }
 
-// a4 in the mixed tier, binary64 finish: Newton steps (eq. Newton) from each
-// candidate left in status 3 until |step| < tol (normally two steps).
-__global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, int64_t count, double tol2, int cap,
+// a4 in the mixed tier, binary64 finish.
+//
+// Nearby starts of the level line mostly descend to the same root (the c_L
+// starts of one turn; about three in four descents are repeats, Table
+// newtonSteps).  Their binary32 end points then agree to the binary32 floor
+// (~1e-5 of the descent's largest step), while distinct roots sit at a
+// distance comparable to that step.  So a candidate whose binary32 end
+// point lies within FINISH_SAME (1e-4) of the descent scale from one of the
+// FINISH_BACK previous candidates' is a follower of that candidate: only
+// the head of each group gets the binary64 Newton steps, and followers take
+// the head's result (the root set merges them anyway).  Links never cross a
+// 64-candidate boundary, so a follower's head is at most 63 back.  A wrong
+// merge can only drop a duplicate or, at worst, one of the c_L descents of a
+// root; the count check then reports it and the tier falls back to binary64
+// (measured: 3e-3 instead of 1e-4 already merges distinct roots at p_24).
+constexpr float FINISH_SAME2 = 1e-8f;  // (1e-4)^2 of the squared scale h1
+constexpr int FINISH_BACK = 3;
+
+__device__ __forceinline__ double2 mixed_point(const double2* starts, const float2* dlt, int64_t i) {
+  const double2 c0 = starts[i];
+  const float2 d = dlt[i];
+  return make_double2(c0.x + (double)d.x, c0.y + (double)d.y);
+}
+
+// head[i] = 1 for a candidate in status 3 that starts a group; link[i] =
+// offset back to the candidate a follower matched (0 for heads and others)
+__global__ void k_finish_heads(int64_t count, const double2* __restrict__ starts,
+                               const float2* __restrict__ dlt, const float* __restrict__ hscale,
+                               const uint8_t* __restrict__ status, uint32_t* __restrict__ head,
+                               uint8_t* __restrict__ link) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint32_t h = 0;
+  uint8_t lk = 0;
+  if (status[i] == 3) {
+    h = 1;
+    const double2 a = mixed_point(starts, dlt, i);
+    const float ha = hscale[i];
+    for (int k = 1; k <= FINISH_BACK && k <= (int)(i & 63); ++k) {
+      if (status[i - k] != 3) continue;
+      const double2 b = mixed_point(starts, dlt, i - k);
+      const double ex = a.x - b.x, ey = a.y - b.y;
+      const double sc = (double)fminf(ha, hscale[i - k]);
+      if (fma(ex, ex, ey * ey) <= (double)FINISH_SAME2 * sc) {
+        h = 0;
+        lk = (uint8_t)k;
+        break;
+      }
+    }
+  }
+  head[i] = h;
+  link[i] = lk;
+}
+
+// list[pos[i]] = i for the heads
+__global__ void k_finish_list(int64_t count, const uint32_t* __restrict__ head,
+                              const uint32_t* __restrict__ pos, uint32_t* __restrict__ list) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count && head[i]) list[pos[i]] = (uint32_t)i;
+}
+
+// Binary64 Newton steps (eq. Newton) from each head's binary32 end point
+// until |step| < tol (normally two steps) or the rounding floor.
+__global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* __restrict__ list,
+                                                    const unsigned long long* __restrict__ nlist,
+                                                    int64_t cap_list, double tol2, int cap,
                                                     const double2* __restrict__ starts,
                                                     const float2* __restrict__ dlt,
-                                                    const float* __restrict__ hscale,
                                                     double2* __restrict__ cand,
                                                     uint8_t* __restrict__ status,
                                                     DevCounters* ctr) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long s64 = 0, nconv = 0, ndiv = 0, nto = 0;
-  if (i < count && status[i] != 3) {
-    const double2 c0 = starts[i];
-    const float2 d = dlt[i];
-    cand[i] = make_double2(c0.x + (double)d.x, c0.y + (double)d.y);  // discarded descents
-  }
-  if (i < count && status[i] == 3) {
-    const double2 c0 = starts[i];
-    const float2 d = dlt[i];
-    double2 z = make_double2(c0.x + (double)d.x, c0.y + (double)d.y);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long s64 = 0;
+  if (t < cap_list && t < (int64_t)*nlist) {
+    const int64_t i = list[t];
+    double2 z = mixed_point(starts, dlt, i);
     int outcome = 2;
     double prev2 = 1e300;
     for (int it = 0; it < cap; ++it) {
@@ -429,16 +487,43 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, int64_t count, do
       if (!finite2(z.x, z.y) || fma(z.x, z.x, z.y * z.y) > 1e4) { outcome = 1; break; }
       if (s2 < tol2) { outcome = 0; break; }
       if (s2 >= 0.25 * prev2 && s2 < floor2_f64(z.x, z.y)) { outcome = 0; break; }  // rounding floor
-
       prev2 = s2;
     }
     cand[i] = z;
     status[i] = (uint8_t)outcome;
-    nconv += outcome == 0;
-    ndiv += outcome == 1;
-    nto += outcome == 2;
   }
   warp_add_u64(&ctr->desc_newton, s64);
+}
+
+// Followers take their head's result (following the links back, at most
+// 63 steps within the 64-candidate block); descents discarded by the
+// binary32 phase (status 1, 2, already counted there) keep their binary32
+// end point.  The outcomes of the finished groups are counted here.
+__global__ void k_finish_followers(int64_t count, const double2* __restrict__ starts,
+                                   const float2* __restrict__ dlt, const uint32_t* __restrict__ head,
+                                   const uint8_t* __restrict__ link, double2* __restrict__ cand,
+                                   uint8_t* __restrict__ status, DevCounters* ctr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long nconv = 0, ndiv = 0, nto = 0;
+  if (i < count) {
+    uint8_t st = status[i];
+    bool finished = head[i] != 0;
+    if (st == 3 && !finished) {
+      int64_t j = i - link[i];
+      for (int g = 0; g < 64 && !head[j]; ++g) j -= link[j];
+      cand[i] = cand[j];
+      st = status[j];
+      status[i] = st;
+      finished = true;
+    } else if (!finished) {
+      cand[i] = mixed_point(starts, dlt, i);
+    }
+    if (finished) {
+      nconv = st == 0;
+      ndiv = st == 1;
+      nto = st == 2;
+    }
+  }
   warp_add_u64(&ctr->n_conv, nconv);
   warp_add_u64(&ctr->n_diverge, ndiv);
   warp_add_u64(&ctr->n_timeout, nto);
@@ -483,7 +568,8 @@ size_t mixed_anchor_bytes(const PolyDev& P, int64_t count) {
 
 cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_t count, double tol,
                                  int cap, double2* cand, float2* dlt, float* hscale, uint8_t* status,
-                                 void* anchors, DevCounters* ctr, cudaStream_t s) {
+                                 void* anchors, const FinishScratch& fin, DevCounters* ctr,
+                                 cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
   const int bs = 128;
@@ -514,9 +600,22 @@ cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_
                                                      status, q, ctr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  // binary64 finish, once per run of candidates on the same root
+  const unsigned nb = (unsigned)((count + bs - 1) / bs);
   MT_COUNT_LAUNCH(1);
-  k_finish_f64<<<(unsigned)((count + bs - 1) / bs), bs, 0, s>>>(P, count, tol * tol, 6, starts, dlt,
-                                                                hscale, cand, status, ctr);
+  k_finish_heads<<<nb, bs, 0, s>>>(count, starts, dlt, hscale, status, fin.head, fin.link);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_exclusive_scan(fin.head, fin.pos, count, fin.scan_tmp, fin.nheads, s)) != cudaSuccess)
+    return e;
+  MT_COUNT_LAUNCH(1);
+  k_finish_list<<<nb, bs, 0, s>>>(count, fin.head, fin.pos, fin.list);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  MT_COUNT_LAUNCH(1);
+  k_finish_f64<<<nb, bs, 0, s>>>(P, fin.list, fin.nheads, count, tol * tol, 6, starts, dlt, cand, status,
+                                 ctr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  MT_COUNT_LAUNCH(1);
+  k_finish_followers<<<nb, bs, 0, s>>>(count, starts, dlt, fin.head, fin.link, cand, status, ctr);
   return cudaGetLastError();
 }
 
