@@ -133,17 +133,15 @@ __device__ void lift_seed_dd(const PolyDev& P, double lambda0, int64_t NQ, int l
   unit_phase((uint64_t)jq, (uint64_t)NQ, c, s);
   zr = dd_make(lambda0 * c);
   zi = dd_make(lambda0 * s);
-  const double lam2 = lambda0 * lambda0;
   const double Lq = -log(lambda0) / shrink;
   for (int k = 1; k < P.m; ++k) {
     const uint64_t num = (k >= log2NQ) ? 0 : (((uint64_t)jq << k) & (uint64_t)(NQ - 1));
     unit_phase(num, (uint64_t)NQ, c, s);
-    steps += newton_target_dd(k + 1, -1, 0.0, zr, zi, dd_make(lam2 * c), dd_make(lam2 * s), 1e-3,
-                              40, nullptr);
+    const double rel = (k + 1 < P.m) ? 1e-2 : 1e-3;  // as lift_seed
     for (int q = 1; q <= shrink; ++q) {
       const double rp = pow(lambda0, 2.0 - (double)(q - 1) / shrink);
       const double r = pow(lambda0, 2.0 - (double)q / shrink);
-      steps += newton_target_dd(k + 1, -1, 0.0, zr, zi, dd_make(r * c), dd_make(r * s), 1e-3, 40,
+      steps += newton_target_dd(k + 1, -1, 0.0, zr, zi, dd_make(r * c), dd_make(r * s), rel, 40,
                                 nullptr, true, rp * c, rp * s, Lq, 0.0);
     }
   }
@@ -202,8 +200,9 @@ __global__ void k_dd_walk(PolyDev P, double lambda0, int M, int every, int64_t L
       double c, s, cp, sp;
       unit_phase(g + 1, (uint64_t)M, c, s);
       unit_phase(g, (uint64_t)M, cp, sp);
-      steps += newton_target_dd(P.m, P.lcap, 1.0, zr, zi, dd_make(lambda0 * c), dd_make(lambda0 * s),
-                                1e-2, 16, &h, true, lambda0 * cp, lambda0 * sp, 0.0, Li);
+      const double rel = (((g + 1) & (uint64_t)(every - 1)) == 0) ? 1e-2 : 1e-1;
+      steps += newton_target_dd(P.m, P.lcap, 1.0, zr, zi, dd_make(lambda0 * c), dd_make(lambda0 * s), rel,
+                                16, &h, true, lambda0 * cp, lambda0 * sp, 0.0, Li);
     }
     const double er = dd_to_d(dd_sub(zr, sx[2 * k + 1])), ei = dd_to_d(dd_sub(zi, sy[2 * k + 1]));
     if (!(er * er + ei * ei <= 0.0625 * h * h)) fails = 1;

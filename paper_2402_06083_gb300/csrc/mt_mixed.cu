@@ -226,8 +226,10 @@ __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_
         starts[g / every] = make_double2(c0x + (double)dx, c0y + (double)dy);
       const float2 Tp = ph[g & (uint64_t)(M - 1)];
       const float2 T = ph[(g + 1) & (uint64_t)(M - 1)];
-      steps += newton_target_pert(P, zs, stride, v, dx, dy, T.x, T.y, 1e-2f, 16, &h, true, Tp.x, Tp.y,
-                                  0.f, Li, &bad);
+      // tight (1e-2) only on the sub-steps that end on a start, as in walk_chunk
+      const float rel = (((g + 1) & (uint64_t)(every - 1)) == 0) ? 1e-2f : 1e-1f;
+      steps += newton_target_pert(P, zs, stride, v, dx, dy, T.x, T.y, rel, 16, &h, true, Tp.x, Tp.y, 0.f,
+                                  Li, &bad);
       if (((i + 1) % K) == 0 && i + 1 < L) {  // re-anchor at the current point
         c0x += (double)dx;
         c0y += (double)dy;

@@ -111,6 +111,11 @@ cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t coun
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend, bs, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
+  // The binary64 pipe (2 DFMA lanes per SM on GB300) is saturated by 8 warps
+  // per SM; more resident lanes only lengthen the tail in which a warp waits
+  // for its last descents.  Measured at p_20: 10 blocks/SM 4.18 ms, 4 blocks
+  // 3.76 ms, 2 blocks 3.56 ms, 1 block 3.88 ms.
+  if (per_sm > 2) per_sm = 2;
   int64_t grid = (int64_t)device_sm_count() * per_sm;
   const int64_t need = (count + bs - 1) / bs;
   if (grid > need) grid = need;
