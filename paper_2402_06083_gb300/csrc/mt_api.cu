@@ -775,7 +775,9 @@ bool make_batch_plan(int max_order, const mt_options* o, int retry, BatchPlan* b
       e.P = make_poly(1, l, n);
       const int64_t d = int64_t(1) << e.P.log2d;
       const int64_t Md = (int64_t)b.M * d;
-      int64_t N0 = std::max<int64_t>(2, Md / 32);  // chunks of ~32 sub-steps
+      // chunks of 32 sub-steps, 64 from degree 4096 up (fewer seed lifts where
+      // lanes are plentiful; measured on l + n <= 16: 8.8 -> 7.4 ms)
+      int64_t N0 = std::max<int64_t>(2, Md / (d >= 4096 ? 64 : 32));
       while (N0 > 2 && (Md / N0) % b.every) N0 >>= 1;
       if ((Md / N0) % b.every) return false;
       e.N0 = N0;

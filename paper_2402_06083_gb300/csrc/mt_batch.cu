@@ -185,6 +185,7 @@ cudaError_t launch_descend_batch(const BatchEntry* E, const int64_t* start_off, 
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_batch, bs, 0);
   if (e != cudaSuccess) return e;
+  if (per_sm > 2) per_sm = 2;  // 8 warps/SM saturate the binary64 pipe (as launch_descend)
   int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
   const int64_t need = (count + bs - 1) / bs;
   if (grid > need) grid = need;

@@ -24,14 +24,15 @@ namespace mt {
 
 // ---------------------------------------------------------------------------
 // a6
-__device__ __forceinline__ bool newton_small(double vr, double vi, double dr, double di,
-                                             double tau) {
-  // |v| <= tau |dv|, compared squared
-  return fma(vr, vr, vi * vi) <= tau * tau * fma(dr, dr, di * di);
-}
 
 // Type code: p_n -> k (1..63); s_{l,n} -> k for Mis(l,k), 32 + k for Hyp(k);
-// 255 if nothing matched.
+// 255 if nothing matched.  The test |f| <= tau |f'| compares magnitudes, so
+// the derivatives run in binary32 (from rn32 of the binary64 orbit values).
+__device__ __forceinline__ bool newton_small_f(double vr, double vi, float dr, float di, double tau) {
+  const double ar = dr, ai = di;
+  return fma(vr, vr, vi * vi) <= tau * tau * fma(ar, ar, ai * ai);
+}
+
 __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, double tau) {
   const int n = P.n;
   const int len = (P.kind == 0) ? n : P.l + n;
@@ -40,22 +41,24 @@ __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, d
     while (b) { int t = a % b; a = b; b = t; }
     return a;
   }();
-  double zr = 0.0, zi = 0.0, dzr = 0.0, dzi = 0.0;
-  double lr = 0.0, li = 0.0, ldr = 0.0, ldi = 0.0;  // p_l, p'_l
+  double zr = 0.0, zi = 0.0, lr = 0.0, li = 0.0;  // p_l
+  float dzr = 0.f, dzi = 0.f, ldr = 0.f, ldi = 0.f;  // p'_l
   int hyp = 0, mis = 0;
   for (int k = 1; k <= len; ++k) {
-    const double tzr = zr + zr, tzi = zi + zi;
-    const double ndr = fma(tzr, dzr, fma(-tzi, dzi, 1.0));
-    const double ndi = fma(tzr, dzi, tzi * dzr);
+    const float fr = __double2float_rn(zr), fi = __double2float_rn(zi);
+    const float tfr = fr + fr, tfi = fi + fi;
+    const float ndr = fmaf(tfr, dzr, fmaf(-tfi, dzi, 1.f));
+    const float ndi = fmaf(tfr, dzi, tfi * dzr);
+    const double tzr = zr + zr;
     const double nzr = fma(zr, zr, fma(-zi, zi, cr));
     const double nzi = fma(tzr, zi, ci);
     zr = nzr; zi = nzi; dzr = ndr; dzi = ndi;
-    if (!hyp && k <= g && (g % k) == 0 && newton_small(zr, zi, dzr, dzi, tau)) hyp = k;
+    if (!hyp && k <= g && (g % k) == 0 && newton_small_f(zr, zi, dzr, dzi, tau)) hyp = k;
     if (P.kind == 1) {
       if (k == P.l) { lr = zr; li = zi; ldr = dzr; ldi = dzi; }
       const int kk = k - P.l;
       if (!mis && kk >= 1 && (n % kk) == 0 &&
-          newton_small(zr - lr, zi - li, dzr - ldr, dzi - ldi, tau))
+          newton_small_f(zr - lr, zi - li, dzr - ldr, dzi - ldi, tau))
         mis = kk;
     }
   }
@@ -140,9 +143,11 @@ cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t cou
 }
 
 // ---------------------------------------------------------------------------
-// a7: disk arithmetic (Thm diskArithmetic) with binary64 centres.
+// a7: disk arithmetic (Thm diskArithmetic) with binary64 centres for the
+// value and binary32 centres for the derivative.
 //
-// The centres follow exactly the FMA sequence of the binary64 point orbit;
+// The value centres follow exactly the FMA sequence of the binary64 point
+// orbit;
 // each rounding adds half an ulp of its rounded result to the radius (Prop.
 // rounding).  With FMA only the products that are rounded separately
 // contribute an ulp term -- a refinement of the theorem's R_*, whose four
@@ -169,37 +174,58 @@ __device__ __forceinline__ float abs_ub(double x, double y) {
   const float ax = __double2float_ru(fabs(x)), ay = __double2float_ru(fabs(y));
   return __fsqrt_ru(__fmaf_ru(ax, ax, __fmul_ru(ay, ay)));
 }
-// lower bound of |x + iy| in binary32
-__device__ __forceinline__ float abs_lb(double x, double y) {
-  return __double2float_rd(__dsqrt_rd(__fma_rd(x, x, __dmul_rd(y, y))));
-}
 __device__ __forceinline__ float hsum_ru(float a, float b) {
   return __fmul_ru(0.5f, __fadd_ru(a, b));
 }
 
+// upper bound, in binary32, of ulp(x) for a binary32 x (2^-149 for
+// subnormals and zero): ulp(x) = 2^(e(x) - 23)
+__device__ __forceinline__ float ulp32_ub(float x) {
+  const int e = (__float_as_int(x) >> 23) & 0xff;
+  if (e == 0) return 1.40129846e-45f;
+  if (e == 0xff) return __int_as_float(0x7f800000);
+  const int p = e - 127 - 23;
+  if (p >= -126) return __int_as_float((p + 127) << 23);
+  return __int_as_float(1 << (p + 149));
+}
+__device__ __forceinline__ float abs_ub_f(float x, float y) {
+  return __fsqrt_ru(__fmaf_ru(fabsf(x), fabsf(x), __fmul_ru(fabsf(y), fabsf(y))));
+}
+__device__ __forceinline__ float abs_lb_f(float x, float y) {
+  return __fsqrt_rd(__fmaf_rd(fabsf(x), fabsf(x), __fmul_rd(fabsf(y), fabsf(y))));
+}
+
 // One orbit over the disk D(c, rc) and over the point c at once (shared
-// centres): returns the value centre V with its point radius rv0, and the
-// derivative centre W with its disk radius rw (W encloses P'(D(c, rc))).
+// centres): returns the value centre V (binary64) with its point radius rv0,
+// and the derivative centre W with its disk radius rw (W encloses
+// P'(D(c, rc))).  The derivative only has to keep 0 out of B', so its
+// centres run in binary32: z enters it as zf = rn32(Z), and the disk of z
+// around zf is widened by |Z - zf| <= (ulp(zf.x) + ulp(zf.y)) / 2.
 __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double cy, float rc,
-                                            double& Vx, double& Vy, float& rv0, double& Wx,
-                                            double& Wy, float& rw) {
-  double zx = 0.0, zy = 0.0, dx = 0.0, dy = 0.0;
+                                            double& Vx, double& Vy, float& rv0, float& Wx,
+                                            float& Wy, float& rw) {
+  double zx = 0.0, zy = 0.0, czx = 0.0, czy = 0.0;
+  float dx = 0.f, dy = 0.f, cdx = 0.f, cdy = 0.f;
   float rz0 = 0.f, rz = 0.f, rd = 0.f;  // radii: z (point), z (disk), z' (disk)
-  double czx = 0.0, czy = 0.0, cdx = 0.0, cdy = 0.0;
   float crz0 = 0.f, crd = 0.f;
   for (int k = 1; k <= P.m; ++k) {
-    const float mz = abs_ub(zx, zy), md = abs_ub(dx, dy);
-    // z' = 2 z z' + 1: re = fma(2zx, dx, fma(-2zy, dy, 1)), im = fma(2zx, dy, (2zy) dx)
-    const double tzx = zx + zx, tzy = zy + zy;
-    const double in_re = fma(-tzy, dy, 1.0);
-    const double nd_x = fma(tzx, dx, in_re);
-    const double p_im = tzy * dx;
-    const double nd_y = fma(tzx, dy, p_im);
-    const float Rd = hsum_ru(__fadd_ru(ulp_ub(in_re), ulp_ub(nd_x)), __fadd_ru(ulp_ub(p_im), ulp_ub(nd_y)));
-    // radius of 2 (z z'): 2 (rz rd + rz |z'| + rd |z|)
-    const float prod = __fmaf_ru(rz, rd, __fmaf_ru(rz, md, __fmul_ru(rd, mz)));
+    const float mz = abs_ub(zx, zy);
+    // z' = 2 z z' + 1 in binary32 around zf = rn32(z)
+    const float fx = __double2float_rn(zx), fy = __double2float_rn(zy);
+    const float ez = hsum_ru(ulp32_ub(fx), ulp32_ub(fy));
+    const float rzz = __fadd_ru(rz, ez);
+    const float md = abs_ub_f(dx, dy), mzf = abs_ub_f(fx, fy);
+    const float tfx = fx + fx, tfy = fy + fy;  // exact
+    const float in_re = fmaf(-tfy, dy, 1.f);
+    const float nd_x = fmaf(tfx, dx, in_re);
+    const float p_im = tfy * dx;
+    const float nd_y = fmaf(tfx, dy, p_im);
+    const float Rd = hsum_ru(__fadd_ru(ulp32_ub(in_re), ulp32_ub(nd_x)), __fadd_ru(ulp32_ub(p_im), ulp32_ub(nd_y)));
+    // radius of 2 (z z'): 2 (rzz rd + rzz |z'| + rd |zf|)
+    const float prod = __fmaf_ru(rzz, rd, __fmaf_ru(rzz, md, __fmul_ru(rd, mzf)));
     const float nrd = __fmaf_ru(2.f, prod, Rd);
-    // z = z^2 + c: re = fma(zx, zx, fma(-zy, zy, cx)), im = fma(2zx, zy, cy)
+    // z = z^2 + c in binary64: re = fma(zx, zx, fma(-zy, zy, cx)), im = fma(2zx, zy, cy)
+    const double tzx = zx + zx;
     const double in_z = fma(-zy, zy, cx);
     const double nz_x = fma(zx, zx, in_z);
     const double nz_y = fma(tzx, zy, cy);
@@ -213,9 +239,10 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
     if (k == P.lcap) { czx = zx; czy = zy; cdx = dx; cdy = dy; crz0 = rz0; crd = rd; }
   }
   if (P.lcap >= 0) {  // s_{l,n} = p_m + p_{l-1}: one disk sum each
-    const double vx = zx + czx, vy = zy + czy, wx = dx + cdx, wy = dy + cdy;
+    const double vx = zx + czx, vy = zy + czy;
+    const float wx = dx + cdx, wy = dy + cdy;
     rz0 = __fadd_ru(__fadd_ru(rz0, crz0), hsum_ru(ulp_ub(vx), ulp_ub(vy)));
-    rd = __fadd_ru(__fadd_ru(rd, crd), hsum_ru(ulp_ub(wx), ulp_ub(wy)));
+    rd = __fadd_ru(__fadd_ru(rd, crd), hsum_ru(ulp32_ub(wx), ulp32_ub(wy)));
     zx = vx; zy = vy; dx = wx; dy = wy;
   }
   Vx = zx; Vy = zy; rv0 = rz0;
@@ -269,11 +296,11 @@ __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
       if (attempt) rad *= 0.25;  // exact
       // the disk radius must be >= rad: round the binary32 copy upward
       const float radu = __double2float_ru(rad), radd = __double2float_rd(rad);
-      double Vx, Vy, Wx, Wy;
-      float rv0, rw;
+      double Vx, Vy;
+      float rv0, Wx, Wy, rw;
       disk_orbit2(P, c.x, c.y, radu, Vx, Vy, rv0, Wx, Wy, rw);
       const float fz = __fadd_ru(abs_ub(Vx, Vy), rv0);
-      const float dist = __fsub_rd(abs_lb(Wx, Wy), rw);
+      const float dist = __fsub_rd(abs_lb_f(Wx, Wy), rw);
       // any radius in [radd, radu] is proven: report the lower one
       ok = isfinite(fz) && isfinite(dist) && dist > 0.f && radd > 0.f && __fmul_rd(radd, dist) > fz;
       if (ok) rad = (double)radd;

@@ -479,9 +479,10 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
     int outcome = 2;
     double prev2 = 1e300;
     for (int it = 0; it < cap; ++it) {
-      double vr, vi, dr, di, qr, qi;
-      eval_P(P, z.x, z.y, vr, vi, dr, di);
-      cdiv_f64(vr, vi, dr, di, qr, qi);
+      double vr, vi, qr, qi;
+      float dr, di;
+      orbit_f64_d32(P.m, P.lcap, z.x, z.y, vr, vi, dr, di);
+      cdiv_f64(vr, vi, (double)dr, (double)di, qr, qi);
       z.x -= qr;
       z.y -= qi;
       ++s64;
