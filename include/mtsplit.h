@@ -126,7 +126,7 @@ typedef struct {
   float ms_dd;             /* device time of the double-double pass                */
   int64_t n_zones;         /* double-double zone centres (0 in dd_all mode)        */
   int64_t n_zone_roots;    /* roots (upper half) produced by the dd pass           */
-  int64_t n_dd_pieces;     /* 64-sub-step pieces of the level line redone in dd    */
+  int64_t n_dd_pieces;     /* 32-sub-step pieces of the level line redone in dd    */
   int64_t seed_newton;     /* Newton steps of the seed lifts (part of walk_newton) */
   int64_t desc_fp32;       /* binary32 Newton steps of the descents                */
   float ms_seeds;          /* device time of the seed lifts (part of ms_walk)      */

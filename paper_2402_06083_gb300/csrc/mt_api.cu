@@ -190,7 +190,15 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
     N0 = Md >> o->chunk_log2;
   } else if (have_tune && tv.chunk_log2 > 0) {
     N0 = Md >> tv.chunk_log2;
+  } else if (p.prec == MT_MIXED) {
+    // the binary32 walk is latency-bound with one lane per chunk: 2^16 lanes
+    // instead of 2^14 pay for the extra seed lifts from p_22 up (measured:
+    // p_24 36.2 -> 33.8 ms, p_26 with dd zones 185 -> 172 ms)
+    N0 = std::min<int64_t>(int64_t(1) << 17,
+                           std::max<int64_t>(Md / 128, std::min<int64_t>(int64_t(1) << 15, Md / 16)));
   } else {
+    // binary64: the walk already keeps the binary64 pipe busy; more chunks
+    // would only add seed lifts
     N0 = std::min<int64_t>(int64_t(1) << 15, Md / 16);
   }
   // L must be a multiple of 'every' and N0 >= 2
@@ -222,7 +230,7 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
     p.eps_dd = std::max(1e-28, raw_eps(kind, l, n));
     p.tol_dd = std::min(o->tol > 0 ? o->tol : 1e-26, 0.05 * p.eps_dd);
     p.cert_tol_dd = o->cert_tol > 0 ? o->cert_tol : 1e-20;
-    p.dd_Ls = std::min<int64_t>(p.L, 64);
+    p.dd_Ls = std::min<int64_t>(p.L, 32);
     p.dd_npieces = (Md / 2) / p.dd_Ls;
     if (p.dd_npieces > (int64_t(1) << 31)) return false;
     p.dd_nb = std::min<int64_t>(p.dd_npieces, (int64_t(1) << 20) / (p.dd_Ls / p.every));
@@ -242,6 +250,8 @@ struct DdBuffers {
   uint32_t *pflag, *ppos;  // per piece of the level line: redo flag, its scan
   int64_t* pids;           // redone pieces
   void* pscan;
+  uint32_t *scnt, *soff;   // seeds per piece of a batch and their scan
+  void* sscan;
   dd *sx, *sy, *stx, *sty, *zcx, *zcy, *zrx, *zry;
   uint8_t *st_ok, *ztype, *zpass;
   uint32_t* near;
@@ -299,6 +309,9 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
     d.pscan = c.take_bytes(scan_temp_bytes(p.dd_npieces));
     d.sx = take_dd(c, 2 * p.dd_nb);
     d.sy = take_dd(c, 2 * p.dd_nb);
+    d.scnt = c.take<uint32_t>(p.dd_nb);
+    d.soff = c.take<uint32_t>(p.dd_nb);
+    d.sscan = c.take_bytes(scan_temp_bytes(p.dd_nb));
     d.stx = take_dd(c, nst);
     d.sty = take_dd(c, nst);
     d.st_ok = c.take<uint8_t>(nst);
@@ -607,9 +620,10 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
     const int64_t nb = std::min<int64_t>(p.dd_nb, npieces - k0);
     const int64_t nst = nb * per_piece + 1;
     CK(cudaMemsetAsync(d.st_ok, 0, (size_t)nst, s));
-    CK(dd_seeds(p.P, p.lambda0, 2 * p.dd_npieces, p.shrink, d.pids + k0, nb, d.sx, d.sy, b.ctr, s));
-    CK(dd_walk(p.P, p.lambda0, p.M, p.every, p.dd_Ls, p.dd_npieces, d.pids + k0, nb, d.sx, d.sy, d.stx,
-               d.sty, d.st_ok, b.ctr, s));
+    CK(dd_seeds(p.P, p.lambda0, 2 * p.dd_npieces, p.shrink, d.pids + k0, nb, d.scnt, d.soff, d.sscan,
+                d.sx, d.sy, b.ctr, s));
+    CK(dd_walk(p.P, p.lambda0, p.M, p.every, p.dd_Ls, p.dd_npieces, d.pids + k0, d.soff, nb, d.sx, d.sy,
+               d.stx, d.sty, d.st_ok, b.ctr, s));
     CK(dd_descend(p.P, nst, d.stx, d.sty, d.st_ok, p.tol_dd, p.cap + 4, d.bad, nbad, p.dd_R, d.zcx,
                   d.zcy, &d.cnt[2], p.dd_zcap, b.ctr, s));
   }

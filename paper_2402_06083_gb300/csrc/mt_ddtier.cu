@@ -12,7 +12,7 @@
 // radius retries of the certificate).  Every representative that failed,
 // or whose proven radius is below 2 eps, becomes a zone centre f, and the
 // disk D(f, R) is redone in double-double:
-//   1. the pieces of the level line (Ls = 64 sub-steps each) whose descents
+//   1. the pieces of the level line (Ls = 32 sub-steps each) whose descents
 //      ended within R + margin of a zone centre are walked again in dd,
 //      each from its own dd-lifted seed;
 //   2. their starts descend in dd; main representatives within R + margin
@@ -156,19 +156,34 @@ __device__ void lift_seed_dd(const PolyDev& P, double lambda0, int64_t NQ, int l
   if (jq == 0 || jq == NQ / 2) zi = dd_make(0.0);
 }
 
-// Seeds of the redone pieces: for piece k of the batch (line piece ids[k])
-// the points at t = ids[k] / NQ and (ids[k] + 1) / NQ (NQ = pieces around
-// the whole line), in sx[2k], sx[2k + 1].
+// Seeds of the redone pieces.  Piece k of the batch (line piece ids[k])
+// needs the points at t = ids[k] / NQ and (ids[k] + 1) / NQ (NQ = pieces
+// around the whole line).  Adjacent redone pieces share their boundary, so
+// piece k contributes its start seed and, unless piece k + 1 starts where
+// it ends, its end seed: cnt[k] = 1 or 2, off = exclusive scan of cnt, and
+// the start seed of piece k is seed off[k], its end seed seed off[k] + 1
+// in both cases.
+__global__ void k_dd_seed_count(const int64_t* __restrict__ ids, int64_t nb,
+                                uint32_t* __restrict__ cnt) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  cnt[k] = (k + 1 < nb && ids[k + 1] == ids[k] + 1) ? 1u : 2u;
+}
+
+// thread (k, e): e = 0 the start seed of piece k, e = 1 its own end seed
 __global__ void k_dd_seeds(PolyDev P, double lambda0, int64_t NQ, int log2NQ, int shrink,
-                           const int64_t* __restrict__ ids, int64_t nb, dd* __restrict__ sx,
+                           const int64_t* __restrict__ ids, const uint32_t* __restrict__ cnt,
+                           const uint32_t* __restrict__ off, int64_t nb, dd* __restrict__ sx,
                            dd* __restrict__ sy, DevCounters* ctr) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long steps = 0;
-  if (g < 2 * nb) {
+  const int64_t k = g >> 1;
+  const int e = (int)(g & 1);
+  if (k < nb && (e == 0 || cnt[k] == 2)) {
     dd zr, zi;
-    lift_seed_dd(P, lambda0, NQ, log2NQ, shrink, ids[g >> 1] + (g & 1), zr, zi, steps);
-    sx[g] = zr;
-    sy[g] = zi;
+    lift_seed_dd(P, lambda0, NQ, log2NQ, shrink, ids[k] + e, zr, zi, steps);
+    sx[off[k] + e] = zr;
+    sy[off[k] + e] = zi;
   }
   warp_add_u64(&ctr->steps_dd, steps);
 }
@@ -179,14 +194,15 @@ __global__ void k_dd_seeds(PolyDev P, double lambda0, int64_t NQ, int log2NQ, in
 // piece) goes to slot nb Ls / every.  A piece that does not end on its end
 // seed (a skipped turn) counts in walk_fail.
 __global__ void k_dd_walk(PolyDev P, double lambda0, int M, int every, int64_t Ls, int64_t npieces,
-                          const int64_t* __restrict__ ids, int64_t nb, const dd* __restrict__ sx,
-                          const dd* __restrict__ sy, dd* __restrict__ stx, dd* __restrict__ sty,
-                          uint8_t* __restrict__ st_ok, DevCounters* ctr) {
+                          const int64_t* __restrict__ ids, const uint32_t* __restrict__ off, int64_t nb,
+                          const dd* __restrict__ sx, const dd* __restrict__ sy, dd* __restrict__ stx,
+                          dd* __restrict__ sty, uint8_t* __restrict__ st_ok, DevCounters* ctr) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long steps = 0, fails = 0;
   if (k < nb) {
     const int64_t G = ids[k];
-    dd zr = sx[2 * k], zi = sy[2 * k];
+    const int64_t s0 = off[k];
+    dd zr = sx[s0], zi = sy[s0];
     uint64_t g = (uint64_t)G * (uint64_t)Ls;
     double h = 0.0;
     const double Li = 6.283185307179586 / M;
@@ -204,7 +220,7 @@ __global__ void k_dd_walk(PolyDev P, double lambda0, int M, int every, int64_t L
       steps += newton_target_dd(P.m, P.lcap, 1.0, zr, zi, dd_make(lambda0 * c), dd_make(lambda0 * s), rel,
                                 16, &h, true, lambda0 * cp, lambda0 * sp, 0.0, Li);
     }
-    const double er = dd_to_d(dd_sub(zr, sx[2 * k + 1])), ei = dd_to_d(dd_sub(zi, sy[2 * k + 1]));
+    const double er = dd_to_d(dd_sub(zr, sx[s0 + 1])), ei = dd_to_d(dd_sub(zi, sy[s0 + 1]));
     if (!(er * er + ei * ei <= 0.0625 * h * h)) fails = 1;
     if (G == npieces - 1) {
       const int64_t slot = (nb * Ls) / every;
@@ -774,17 +790,21 @@ cudaError_t dd_near_reps(const double2* reps, const unsigned long long* n_reps, 
 }
 
 cudaError_t dd_seeds(const PolyDev& P, double lambda0, int64_t NQ, int shrink, const int64_t* ids,
-                     int64_t nb, dd* sx, dd* sy, DevCounters* ctr, cudaStream_t s) {
+                     int64_t nb, uint32_t* cnt, uint32_t* off, void* scan_tmp, dd* sx, dd* sy,
+                     DevCounters* ctr, cudaStream_t s) {
   int log2NQ = 0;
   while ((int64_t(1) << log2NQ) < NQ) ++log2NQ;
-  MT_DD_LAUNCH(k_dd_seeds, 2 * nb, 64, P, lambda0, NQ, log2NQ, shrink, ids, nb, sx, sy, ctr);
+  MT_DD_LAUNCH(k_dd_seed_count, nb, 256, ids, nb, cnt);
+  cudaError_t e = launch_exclusive_scan(cnt, off, nb, scan_tmp, nullptr, s);
+  if (e != cudaSuccess) return e;
+  MT_DD_LAUNCH(k_dd_seeds, 2 * nb, 64, P, lambda0, NQ, log2NQ, shrink, ids, cnt, off, nb, sx, sy, ctr);
   return cudaGetLastError();
 }
 
 cudaError_t dd_walk(const PolyDev& P, double lambda0, int M, int every, int64_t Ls, int64_t npieces,
-                    const int64_t* ids, int64_t nb, const dd* sx, const dd* sy, dd* stx, dd* sty,
-                    uint8_t* st_ok, DevCounters* ctr, cudaStream_t s) {
-  MT_DD_LAUNCH(k_dd_walk, nb, 64, P, lambda0, M, every, Ls, npieces, ids, nb, sx, sy, stx, sty, st_ok,
+                    const int64_t* ids, const uint32_t* off, int64_t nb, const dd* sx, const dd* sy,
+                    dd* stx, dd* sty, uint8_t* st_ok, DevCounters* ctr, cudaStream_t s) {
+  MT_DD_LAUNCH(k_dd_walk, nb, 64, P, lambda0, M, every, Ls, npieces, ids, off, nb, sx, sy, stx, sty, st_ok,
                ctr);
   return cudaGetLastError();
 }

@@ -202,10 +202,11 @@ cudaError_t dd_near_reps(const double2* reps, const unsigned long long* n_reps, 
                          const double2* bad, int nbad, double R, uint32_t* near,
                          unsigned long long* nnear, int64_t near_cap, cudaStream_t s);
 cudaError_t dd_seeds(const PolyDev& P, double lambda0, int64_t NQ, int shrink, const int64_t* ids,
-                     int64_t nb, dd* sx, dd* sy, DevCounters* ctr, cudaStream_t s);
+                     int64_t nb, uint32_t* cnt, uint32_t* off, void* scan_tmp, dd* sx, dd* sy,
+                     DevCounters* ctr, cudaStream_t s);
 cudaError_t dd_walk(const PolyDev& P, double lambda0, int M, int every, int64_t Ls, int64_t npieces,
-                    const int64_t* ids, int64_t nb, const dd* sx, const dd* sy, dd* stx, dd* sty,
-                    uint8_t* st_ok, DevCounters* ctr, cudaStream_t s);
+                    const int64_t* ids, const uint32_t* off, int64_t nb, const dd* sx, const dd* sy,
+                    dd* stx, dd* sty, uint8_t* st_ok, DevCounters* ctr, cudaStream_t s);
 cudaError_t dd_descend(const PolyDev& P, int64_t count, const dd* zx0, const dd* zy0,
                        const uint8_t* ok0, double tol, int cap, const double2* bad, int nbad,
                        double R, dd* ox, dd* oy, unsigned long long* nout, int64_t out_cap,
