@@ -65,7 +65,15 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SM_MAX_MHZ = 2070.0
 
 
-def roofline(prec: str, m: int, stats: list) -> dict:
+# DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
+# capture of the same kernel and workload (profiles/kernels_hyp20_fp64.md:
+# dram__bytes_read.sum 16.8 MB, dram__bytes_write.sum 0; the candidates it
+# writes stay in the 129 MB L2).  Only for kernels unchanged since that
+# capture; everything else reports null.
+TRAFFIC = {("hyp20", "k_descend"): 16.8e6}
+
+
+def roofline(prec: str, m: int, stats: list, config: str = "") -> dict:
     """ALU roofline of the dominant kernel (walk or descent) from the
     library's own CUDA events (on the launch stream, inside the graph) and
     its own step counters.  Binary32 steps of the mixed tier count at the
@@ -88,7 +96,8 @@ def roofline(prec: str, m: int, stats: list) -> dict:
         kern += "_mixed"
     achieved = eq / (ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": TRAFFIC.get((config, kern)),
             "ms_per_launch": ms, "flops_per_launch": eq,
             "peak_source": "nominal binary64 1.25 TFLOP/s at 2070 MHz (profiling recipe table)"
                            + ("" if prec == "fp64" else "; binary32 steps weighted by 1.25/80.5"),
@@ -357,7 +366,7 @@ def main():
         "e2e": {"value": whole_job_rate(world, d, e2e_s), "unit": "roots/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d * 16 * (2 if roots_lo is not None else 1) + 1024,
                 "note": "input is the integer n (no device input); result roots copied to pinned host memory"},
-        "roofline": roofline(prec, m, stats),
+        "roofline": roofline(prec, m, stats, args.config),
         "gpu_launches": int(sum(s["n_launches"] for s in stats)),
         "clocks": clocks,
         "detail": {"ms_walk": s0["ms_walk"], "ms_descend": s0["ms_descend"], "ms_dedup": s0["ms_dedup"],
