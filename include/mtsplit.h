@@ -194,6 +194,21 @@ MT_API mt_status mt_certify(int kind, int l, int n, const double* d_roots, const
                      int64_t count, double tol, uint8_t* d_pass, double* d_radius, void* d_work,
                      size_t work_bytes, int64_t* n_pass, void* stream);
 
+/* Newton-basin certificate (Thm proofContract; Thm certif, the radius
+   eps_N of Fig. rootCertif): root j, proven by mt_certify to lie in
+   D(c_j, r_j) (d_radius), gets the largest eps_j = min(eps_max, 0.25 nn_j)
+   / 4^k with eps_j > 3 eta_j (eta_j <= r_j the localisation radius the
+   disk test itself yields) such that P'(D(c_j, eps_j)) lies in a disk B'
+   with dist(0, B') > 2 diam(B').  Then D(c_j, eps_j) lies in the basin of
+   attraction of the root for the Newton map: Newton from any point of it
+   converges to that root.  d_basin[j] = eps_j, or 0 where no radius passes
+   (r_j = 0, or no eps above 3 eta_j).  d_roots_lo: NULL or the low parts
+   (double-double centres).  eps_max: 0 -> 1e-6.  *n_pass: roots with a
+   basin radius.  Workspace: mt_certify_workspace_bytes(count). */
+MT_API mt_status mt_certify_basin(int kind, int l, int n, const double* d_roots, const double* d_roots_lo,
+                                  int64_t count, const double* d_radius, double eps_max, double* d_basin,
+                                  void* d_work, size_t work_bytes, int64_t* n_pass, void* stream);
+
 /* Autotuner (the paper tunes nothing; a GPU-layout choice).  Runs complete
    splits of P for each candidate level-line chunk length 2^c (c = 3 .. 10
    sub-steps per lane) and walk block size (32, 64, 128), three runs each,

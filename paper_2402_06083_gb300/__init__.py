@@ -187,6 +187,28 @@ def certify(kind: str, n: int, roots, l: int = 0, tol: float = 0.0, *, work: Wor
     return ok, rad, int(npass.value)
 
 
+def certify_basin(kind: str, n: int, roots, radius, l: int = 0, eps_max: float = 0.0, *,
+                  work: Workspace | None = None, roots_lo=None):
+    """Newton-basin radius of each root (Thm proofContract), given the proven
+    radii of certify().  Returns (basin float64 tensor, n_pass)."""
+    torch = _torch()
+    L = load()
+    r = torch.view_as_real(roots.contiguous()) if roots.is_complex() else roots.contiguous()
+    rl = None
+    if roots_lo is not None:
+        rl = torch.view_as_real(roots_lo.contiguous()) if roots_lo.is_complex() else roots_lo.contiguous()
+    count = r.shape[0]
+    rad = radius.contiguous().to(torch.float64)
+    work = work or Workspace()
+    buf = work.ensure(int(L.mt_certify_workspace_bytes(count)))
+    out = torch.empty(count, dtype=torch.float64, device=r.device)
+    npass = ctypes.c_int64(0)
+    check(L.mt_certify_basin(KIND[kind], l, n, r.data_ptr(), _ptr(rl), count, rad.data_ptr(), eps_max,
+                             out.data_ptr(), buf.data_ptr(), buf.numel(), ctypes.byref(npass),
+                             torch.cuda.current_stream().cuda_stream))
+    return out, int(npass.value)
+
+
 def evaluate(kind: str, n: int, c, l: int = 0):
     """P(c), P'(c) for a complex128 tensor c: returns complex128 [count, 2]."""
     torch = _torch()

@@ -1190,6 +1190,41 @@ mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double
   return MT_OK;
 }
 
+mt_status mt_certify_basin(int kind, int l, int n, const double* d_roots, const double* d_roots_lo,
+                           int64_t count, const double* d_radius, double eps_max, double* d_basin,
+                           void* d_work, size_t work_bytes, int64_t* n_pass, void* stream) {
+  g_err.clear();
+  if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range");
+  if (count < 0 || (count > 0 && (!d_roots || !d_radius || !d_basin))) return fail(MT_EINVAL, "bad buffers");
+  if (count > 0xffffffffll) return fail(MT_EINVAL, "count too large");
+  if (!(eps_max >= 0.0)) return fail(MT_EINVAL, "eps_max must be >= 0");
+  const size_t need = mt_certify_workspace_bytes(count);
+  if (!d_work || work_bytes < need) return fail(MT_ENOMEM, "workspace of %zu bytes needed", need);
+  cudaStream_t s = (cudaStream_t)stream;
+  const PolyDev P = make_poly(kind, l, n);
+  if (eps_max == 0.0) eps_max = 1e-6;
+  Carve c(d_work, work_bytes);
+  DevCounters* ctr = c.take<DevCounters>(1);
+  uint64_t* keys = c.take<uint64_t>(count);
+  uint64_t* keys_alt = c.take<uint64_t>(count);
+  uint32_t* vals = c.take<uint32_t>(count);
+  uint32_t* vals_alt = c.take<uint32_t>(count);
+  void* rtmp = c.take_bytes(radix_temp_bytes(count));
+  CK(launch_init_counters(ctr, s));
+  CK(launch_keys_plain((const double2*)d_roots, count, keys, vals, s));
+  CK(radix_sort_pairs(keys, vals, keys_alt, vals_alt, count, rtmp, s));
+  if (d_roots_lo)
+    CK(dd_basin(P, (const double2*)d_roots, (const double2*)d_roots_lo, vals, count, d_radius, eps_max,
+                d_basin, ctr, s));
+  else
+    CK(launch_basin(P, (const double2*)d_roots, vals, count, d_radius, eps_max, d_basin, ctr, s));
+  DevCounters h;
+  CK(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (n_pass) *n_pass = (int64_t)h.n_cert_pass;
+  return MT_OK;
+}
+
 mt_status mt_eval(int kind, int l, int n, const double* d_c, int64_t count, double* d_out,
                   void* stream) {
   g_err.clear();

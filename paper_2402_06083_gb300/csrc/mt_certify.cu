@@ -318,6 +318,75 @@ __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Newton-basin certificate (Thm proofContract): z* a simple root with
+// |z0 - z*| < eta; if eps > 3 eta and P'(D(z0, eps)) lies in a disk B' with
+// dist(0, B') > 2 diam(B'), then D(z0, eps) lies in the basin of attraction
+// of z* for the Newton map.  eta comes from the localisation test itself:
+// with B'_r enclosing P'(D(z0, r)) and r dist(0, B'_r) > |P(z0)|, the proof
+// of Thm proofRoots places the root in D(z0, |P(z0)| / dist(0, B'_r)), so
+// eta = |P(z0)|_ub / dist_lb (<= r).  eps runs over 0.25 nn, / 4, / 16, ...
+// while eps > 3 eta; the first that passes is reported (0 if none).
+__global__ void k_basin(PolyDev P, const double2* __restrict__ pts, const uint32_t* __restrict__ order,
+                        int64_t n, const double* __restrict__ rin, double eps_max,
+                        double* __restrict__ basin, DevCounters* ctr) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long npass = 0;
+  if (p < n) {
+    const int64_t ip = order[p];
+    const double2 c = pts[ip];
+    // nearest other root within 4 eps_max (the window of eps <= 0.25 nn)
+    const double Wn = 4.0 * eps_max;
+    double nn2 = Wn * Wn;
+    for (int dir = -1; dir <= 1; dir += 2) {
+      for (int64_t q = p + dir; q >= 0 && q < n && (q - p) * dir < 4096; q += dir) {
+        const double2 v = pts[order[q]];
+        const double dx = v.x - c.x;
+        if (fabs(dx) >= Wn) break;
+        const double dy = v.y - c.y;
+        nn2 = fmin(nn2, fma(dx, dx, dy * dy));
+      }
+    }
+    double out = 0.0;
+    const double r = rin[ip];
+    if (r > 0.0) {
+      const float ru = __double2float_ru(r);
+      double Vx, Vy;
+      float rv0, Wx, Wy, rw;
+      disk_orbit2(P, c.x, c.y, ru, Vx, Vy, rv0, Wx, Wy, rw);
+      const float fz = __fadd_ru(abs_ub(Vx, Vy), rv0);
+      const float dist = __fsub_rd(abs_lb_f(Wx, Wy), rw);
+      if (isfinite(fz) && isfinite(dist) && dist > 0.f) {
+        const float eta = fminf(__fdiv_ru(fz, dist), ru);
+        double eps = fmin(eps_max, 0.25 * sqrt(nn2));
+        for (int k = 0; k < 24 && eps > 3.0 * (double)eta; ++k, eps *= 0.25) {
+          const float eu = __double2float_ru(eps);
+          disk_orbit2(P, c.x, c.y, eu, Vx, Vy, rv0, Wx, Wy, rw);
+          const float wl = abs_lb_f(Wx, Wy);
+          // dist(0, B') = |W| - rw > 2 diam(B') = 4 rw
+          if (isfinite(wl) && isfinite(rw) && __fsub_rd(wl, rw) > __fmul_ru(4.f, rw)) {
+            out = (double)__double2float_rd(eps);
+            break;
+          }
+        }
+      }
+    }
+    basin[ip] = out;
+    npass = out > 0.0;
+  }
+  warp_add_u64(&ctr->n_cert_pass, npass);
+}
+
+cudaError_t launch_basin(const PolyDev& P, const double2* pts, const uint32_t* order, int64_t count,
+                         const double* radius, double eps_max, double* basin, DevCounters* ctr,
+                         cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_basin<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, pts, order, count, radius, eps_max, basin,
+                                                          ctr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
                            int64_t cap, double tol, const uint32_t* mult, uint8_t* pass,
                            double* radius, DevCounters* ctr, cudaStream_t s, SegView sv) {

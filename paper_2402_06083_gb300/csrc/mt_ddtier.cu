@@ -456,7 +456,11 @@ __device__ __forceinline__ double dd_abs_ub(const dd& x, const dd& y) {
   return __dadd_ru(abs_ub64(x.hi, y.hi), __dadd_ru(fabs(x.lo), fabs(y.lo)));
 }
 
-__device__ bool certify_dd(const PolyDev& P, dd cr, dd ci, double rad) {
+// Disk evaluation of P over D(c, rad) with dd centres: fz >= sup |P(c)|
+// over the point orbit, the derivative disk B' = D(W, rw) encloses
+// P'(D(c, rad)); returns fz, |W|_lb and rw.
+__device__ void dd_disk_eval(const PolyDev& P, dd cr, dd ci, double rad, double& fz_out,
+                             double& wabs_lb, double& rw_out) {
   const double E = DD_REL_ERR * 1.0001;
   dd zr = dd_make(0.0), zi = dd_make(0.0), czr = dd_make(0.0), czi = dd_make(0.0);
   double dx = 0.0, dy = 0.0, cdx = 0.0, cdy = 0.0;
@@ -512,8 +516,16 @@ __device__ bool certify_dd(const PolyDev& P, dd cr, dd ci, double rad) {
     dx = wx;
     dy = wy;
   }
-  const double fz = __dadd_ru(dd_abs_ub(zr, zi), rz0);
-  const double dist = __dsub_rd(abs_lb64(dx, dy), rd);
+  fz_out = __dadd_ru(dd_abs_ub(zr, zi), rz0);
+  wabs_lb = abs_lb64(dx, dy);
+  rw_out = rd;
+}
+
+// Thm proofRoots with dd centres: one root in D(c, rad)
+__device__ bool certify_dd(const PolyDev& P, dd cr, dd ci, double rad) {
+  double fz, wl, rw;
+  dd_disk_eval(P, cr, ci, rad, fz, wl, rw);
+  const double dist = __dsub_rd(wl, rw);
   return isfinite(fz) && isfinite(dist) && dist > 0.0 && __dmul_rd(rad, dist) > fz;
 }
 
@@ -748,6 +760,52 @@ __global__ void k_dd_certify_list(PolyDev P, const double2* __restrict__ hi,
   warp_add_u64(&ctr->n_cert_pass, npass);
 }
 
+// Newton-basin certificate (Thm proofContract) of a list with low parts, as
+// k_basin with dd centres (sorted by hi Re through 'order').
+__global__ void k_dd_basin(PolyDev P, const double2* __restrict__ hi, const double2* __restrict__ lo,
+                           const uint32_t* __restrict__ order, int64_t n,
+                           const double* __restrict__ rin, double eps_max,
+                           double* __restrict__ basin, DevCounters* ctr) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long npass = 0;
+  if (p < n) {
+    const int64_t ip = order[p];
+    const dd cr = dd{hi[ip].x, lo[ip].x}, ci = dd{hi[ip].y, lo[ip].y};
+    const double Wn = 4.0 * eps_max;
+    double nn2 = Wn * Wn;
+    for (int dir = -1; dir <= 1; dir += 2) {
+      for (int64_t q = p + dir; q >= 0 && q < n && (q - p) * dir < 4096; q += dir) {
+        const int64_t iq = order[q];
+        if (hi_beyond(hi[iq].x, cr.hi, Wn)) break;
+        const double ex = dd_to_d(dd_sub(dd{hi[iq].x, lo[iq].x}, cr));
+        const double ey = dd_to_d(dd_sub(dd{hi[iq].y, lo[iq].y}, ci));
+        nn2 = fmin(nn2, fma(ex, ex, ey * ey));
+      }
+    }
+    double out = 0.0;
+    const double r = rin[ip];
+    if (r > 0.0) {
+      double fz, wl, rw;
+      dd_disk_eval(P, cr, ci, r, fz, wl, rw);
+      const double dist = __dsub_rd(wl, rw);
+      if (isfinite(fz) && isfinite(dist) && dist > 0.0) {
+        const double eta = fmin(__ddiv_ru(fz, dist), r);
+        double eps = fmin(eps_max, 0.25 * sqrt(nn2));
+        for (int k = 0; k < 24 && eps > 3.0 * eta; ++k, eps *= 0.25) {
+          dd_disk_eval(P, cr, ci, eps, fz, wl, rw);
+          if (isfinite(wl) && isfinite(rw) && __dsub_rd(wl, rw) > __dmul_ru(4.0, rw)) {
+            out = eps;
+            break;
+          }
+        }
+      }
+    }
+    basin[ip] = out;
+    npass = out > 0.0;
+  }
+  warp_add_u64(&ctr->n_cert_pass, npass);
+}
+
 // ---- launchers ---------------------------------------------------------------------
 
 namespace {
@@ -883,6 +941,13 @@ cudaError_t dd_certify_list(const PolyDev& P, const double2* hi, const double2* 
                             const uint32_t* order, int64_t n, double tol, uint8_t* pass,
                             double* radius, DevCounters* ctr, cudaStream_t s) {
   MT_DD_LAUNCH(k_dd_certify_list, n, 64, P, hi, lo, order, n, tol, pass, radius, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t dd_basin(const PolyDev& P, const double2* hi, const double2* lo, const uint32_t* order,
+                     int64_t n, const double* radius, double eps_max, double* basin, DevCounters* ctr,
+                     cudaStream_t s) {
+  MT_DD_LAUNCH(k_dd_basin, n, 64, P, hi, lo, order, n, radius, eps_max, basin, ctr);
   return cudaGetLastError();
 }
 

@@ -177,6 +177,12 @@ cudaError_t launch_fix_ties(double2* out, const unsigned long long* n_full, int6
 cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t count, double tau,
                              uint8_t* type, cudaStream_t s);
 
+// Newton-basin certificate (Thm proofContract) of a list sorted through
+// 'order', with the proven radii of the localisation test.
+cudaError_t launch_basin(const PolyDev& P, const double2* pts, const uint32_t* order, int64_t count,
+                         const double* radius, double eps_max, double* basin, DevCounters* ctr,
+                         cudaStream_t s);
+
 // Zero the counters (min radius set to +inf).
 cudaError_t launch_init_counters(DevCounters* ctr, cudaStream_t s);
 // keys[i] = order-preserving key of Re pts[i], vals[i] = i.
@@ -237,6 +243,9 @@ cudaError_t dd_emit(const double2* reps, const unsigned long long* n_reps, int64
                     const uint32_t* zmpos, const unsigned long long* zt, const uint8_t* ztype,
                     double2* out, double2* out_lo, uint8_t* is_mis, int64_t cap_out,
                     DevCounters* ctr, cudaStream_t s);
+cudaError_t dd_basin(const PolyDev& P, const double2* hi, const double2* lo, const uint32_t* order,
+                     int64_t n, const double* radius, double eps_max, double* basin, DevCounters* ctr,
+                     cudaStream_t s);
 cudaError_t dd_certify_list(const PolyDev& P, const double2* hi, const double2* lo,
                             const uint32_t* order, int64_t n, double tol, uint8_t* pass,
                             double* radius, DevCounters* ctr, cudaStream_t s);
