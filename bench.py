@@ -38,6 +38,8 @@ CONFIGS = {
     "hyp24mixed": ("hyp", 0, 24, "mixed"),
     "hyp26dd": ("hyp", 0, 26, "dd"),
     "hyp28dd": ("hyp", 0, 28, "dd"),  # binary64 cannot separate its tip roots: dd zones
+    "hyp29dd": ("hyp", 0, 29, "dd"),
+    "hyp31dd": ("hyp", 0, 31, "dd"),  # 2^30 roots, ~230 GB of device memory
     "mis16": ("misbatch", 0, 16, "fp64"),  # every s_{l,n}, l >= 2, n >= 1, l + n <= 16, one pass
 }
 
@@ -280,8 +282,11 @@ def main():
     def step(out=None, p=None):
         pp = prec if p is None else p
         if kind == "hyp":  # the launch sequence is captured once and replayed as a CUDA graph
+            # from p_30 up the workspace of a retry with doubled (M, c_L) would
+            # not fit in HBM next to the roots: one attempt per tier
+            extra = {"max_retries": 0} if n >= 30 else {}
             return mt.split_hyperbolic(n, pp, work=work, out=roots, use_graph=1,
-                                       out_lo=roots_lo if pp == "dd" else None)
+                                       out_lo=roots_lo if pp == "dd" else None, **extra)
         if kind == "misbatch":
             _, _, _, st, _ = mt.split_misiurewicz_batch(n, pp, work=work)
             return _BatchResult(st)

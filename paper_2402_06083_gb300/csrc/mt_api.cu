@@ -120,7 +120,7 @@ struct Plan {
   int64_t dd_near_cap;
 };
 
-constexpr int DD_MAX_BAD = 16384;  // zone centres the dd pass accepts
+constexpr int DD_MAX_BAD = 1 << 22;  // zone centres the dd pass accepts
 
 // ---------------------------------------------------------------------------
 // Autotune table: (kind, l, n, tier) -> chunk length and walk block size
@@ -234,9 +234,11 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
     p.dd_npieces = (Md / 2) / p.dd_Ls;
     if (p.dd_npieces > (int64_t(1) << 31)) return false;
     p.dd_nb = std::min<int64_t>(p.dd_npieces, (int64_t(1) << 20) / (p.dd_Ls / p.every));
+    // zone capacities: every point in dd_all mode; otherwise 2^21 points, or
+    // S / 16 from p_29 up, where the zones grow to 10^5 - 10^6 centres
     p.dd_zcap = 2 * p.S + 64;
-    if (!p.dd_all) p.dd_zcap = std::min<int64_t>(p.dd_zcap, int64_t(1) << 21);
-    p.dd_near_cap = p.dd_all ? p.S : std::min<int64_t>(p.S, int64_t(1) << 21);
+    if (!p.dd_all) p.dd_zcap = std::min<int64_t>(p.dd_zcap, std::max<int64_t>(int64_t(1) << 21, p.S / 16));
+    p.dd_near_cap = p.dd_all ? p.S : std::min<int64_t>(p.S, std::max<int64_t>(int64_t(1) << 21, p.S / 64));
   }
   *pl = p;
   return true;
@@ -268,6 +270,7 @@ struct Buffers {
   uint32_t *vals, *vals_alt, *flag, *pos, *mult, *mpos;
   double* radius;
   void *scan_tmp, *radix_tmp, *anchors;
+  uint8_t *seed_bad, *chunk_fail;  // mixed tier: items the binary64 repairs redo
   DdBuffers d;
   size_t bytes;
 };
@@ -297,6 +300,8 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
   b.scan_tmp = c.take_bytes(scan_temp_bytes(p.S));
   b.radix_tmp = c.take_bytes(radix_temp_bytes(p.S));
   b.anchors = (p.prec == MT_MIXED) ? c.take_bytes(mixed_anchor_bytes(p.P, p.S)) : nullptr;
+  b.seed_bad = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks + 1) : nullptr;
+  b.chunk_fail = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks) : nullptr;
   b.d = DdBuffers{};
   if (p.dd) {
     DdBuffers& d = b.d;
@@ -416,14 +421,17 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
   CK(launch_init_counters(b.ctr, s));
   CK(mark(ev.e[0], s, capturing));
   if (p.prec == MT_MIXED) {
-    CK(launch_seed_lift_mixed(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+    CK(launch_seed_lift_mixed(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.seed_bad, b.ctr, s));
+    CK(launch_mixed_repair_seeds(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.seed_bad, b.ctr, s));
   } else {
     CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
   }
   CK(mark(ev.e[6], s, capturing));
   if (p.prec == MT_MIXED) {
-    CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts, b.ctr,
-                         s, p.walk_block));
+    CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts,
+                         b.chunk_fail, b.ctr, s, p.walk_block));
+    CK(launch_mixed_repair_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.shrink, b.seeds,
+                                b.starts, b.chunk_fail, b.ctr, s));
   } else {
     CK(launch_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, b.seeds, b.starts, b.ctr, s,
                    p.walk_block));

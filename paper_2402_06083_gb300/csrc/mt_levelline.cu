@@ -69,4 +69,80 @@ cudaError_t launch_walk(const PolyDev& P, double lambda0, int M, int every, int6
   return cudaGetLastError();
 }
 
+// Repairs of the mixed tier in binary64, inside the same launch sequence
+// (no host round trip).  Seeds whose binary32 lift failed are lifted again;
+// chunks whose binary32 walk missed the next seed (a skipped turn, or a
+// binary32 end seed farther off than the end check allows near a cluster)
+// are walked again from both end seeds lifted again in binary64 (kept
+// local: the other chunks met the array's seeds already).  A repaired item
+// takes its failure off walk_fail; one that fails again stays counted and
+// the host then repeats the split in binary64.  Lanes without a flag exit
+// at once.
+__global__ void k_seed_repair(PolyDev P, double lambda0, int64_t N0, int log2N0, int shrink,
+                              double2* __restrict__ seeds, uint8_t* __restrict__ seed_bad,
+                              DevCounters* ctr) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long steps = 0, fixed = 0;
+  if (j <= N0 / 2 && seed_bad[j]) {
+    seeds[j] = lift_seed(P, lambda0, N0, log2N0, shrink, j, steps);
+    seed_bad[j] = 0;
+    fixed = 1;
+  }
+  warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->seed_newton, steps);
+  warp_add_u64(&ctr->walk_fail, 0ull - fixed);
+}
+
+__global__ void k_walk_repair(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
+                              int64_t N0, int log2N0, int shrink, const double2* __restrict__ seeds,
+                              double2* __restrict__ starts, uint8_t* __restrict__ chunk_fail,
+                              DevCounters* ctr) {
+  __shared__ double2 ph[64];
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    double c, s;
+    unit_phase((uint64_t)q, (uint64_t)M, c, s);
+    ph[q] = make_double2(lambda0 * c, lambda0 * s);
+  }
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long steps = 0, fixed = 0;
+  if (j < nchunks && chunk_fail[j]) {
+    const double2 a = lift_seed(P, lambda0, N0, log2N0, shrink, j, steps);
+    const double2 b = lift_seed(P, lambda0, N0, log2N0, shrink, j + 1, steps);
+    if (!walk_chunk_from(P, ph, M, every, L, nchunks, j, a, b, starts, steps)) {
+      chunk_fail[j] = 0;
+      fixed = 1;
+    }
+  }
+  warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->walk_fail, 0ull - fixed);
+}
+
+cudaError_t launch_mixed_repair_seeds(const PolyDev& P, double lambda0, int64_t N0, int shrink,
+                                      double2* seeds, uint8_t* seed_bad, DevCounters* ctr,
+                                      cudaStream_t s) {
+  int log2N0 = 0;
+  while ((int64_t(1) << log2N0) < N0) ++log2N0;
+  const int64_t n = N0 / 2 + 1;
+  MT_COUNT_LAUNCH(1);
+  k_seed_repair<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(P, lambda0, N0, log2N0, shrink, seeds,
+                                                            seed_bad, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_repair_walk(const PolyDev& P, double lambda0, int M, int every, int64_t L,
+                                     int64_t nchunks, int shrink, const double2* seeds,
+                                     double2* starts, uint8_t* chunk_fail, DevCounters* ctr,
+                                     cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  const int64_t N0 = 2 * nchunks;
+  int log2N0 = 0;
+  while ((int64_t(1) << log2N0) < N0) ++log2N0;
+  MT_COUNT_LAUNCH(1);
+  k_walk_repair<<<(unsigned)((nchunks + 127) / 128), 128, 0, s>>>(P, lambda0, M, every, L, nchunks, N0,
+                                                                  log2N0, shrink, seeds, starts,
+                                                                  chunk_fail, ctr);
+  return cudaGetLastError();
+}
+
 }  // namespace mt

@@ -166,12 +166,10 @@ __device__ __forceinline__ int walk_substep_f64(int m, int lcap, double& zr, dou
 // g has P = lambda0 e^{2 i pi g / M}, ph[q] = lambda0 e^{2 i pi q / M});
 // every 'every'-th point is a descent start with index g / every.  Returns
 // true if the chunk did not end on the next seed (a skipped turn).
-__device__ __forceinline__ bool walk_chunk(const PolyDev& P, const double2* ph, int M, int every,
-                                           int64_t L, int64_t nchunks, int64_t j,
-                                           const double2* __restrict__ seeds,
-                                           double2* __restrict__ starts,
-                                           unsigned long long& steps) {
-  const double2 z0 = seeds[j];
+__device__ __forceinline__ bool walk_chunk_from(const PolyDev& P, const double2* ph, int M, int every,
+                                                int64_t L, int64_t nchunks, int64_t j, double2 z0,
+                                                double2 zn, double2* __restrict__ starts,
+                                                unsigned long long& steps) {
   double zr = z0.x, zi = z0.y;
   uint64_t g = (uint64_t)j * (uint64_t)L;
   double h = 0.0, zpr = 0.0, zpi = 0.0;
@@ -187,10 +185,17 @@ __device__ __forceinline__ bool walk_chunk(const PolyDev& P, const double2* ph, 
     steps += walk_substep_f64(P.m, P.lcap, zr, zi, T.x, T.y, Tp.x, Tp.y, Li, i > 0, zpr, zpi, rel, 16, h);
   }
   if (j == nchunks - 1) starts[g / every] = make_double2(zr, 0.0);  // t = 1/2, real
-  const double2 zn = seeds[j + 1];
   const double er = zr - zn.x, ei = zi - zn.y;
   // the end of the chunk must be the next seed, not a neighbour one turn away
   return !(er * er + ei * ei <= 0.0625 * h * h + 1e-28);
+}
+
+__device__ __forceinline__ bool walk_chunk(const PolyDev& P, const double2* ph, int M, int every,
+                                           int64_t L, int64_t nchunks, int64_t j,
+                                           const double2* __restrict__ seeds,
+                                           double2* __restrict__ starts,
+                                           unsigned long long& steps) {
+  return walk_chunk_from(P, ph, M, every, L, nchunks, j, seeds[j], seeds[j + 1], starts, steps);
 }
 
 }  // namespace mt

@@ -131,7 +131,7 @@ __device__ __forceinline__ int newton_target_pert(const PolyDev& P, const float2
 // of ~(1 + shrink) x 3 binary64 Newton steps).  The s_{l,n} homotopy at the
 // last level stays binary64.
 __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log2N0, int shrink,
-                                  double2* seeds, DevCounters* ctr) {
+                                  double2* seeds, uint8_t* __restrict__ seed_bad, DevCounters* ctr) {
   extern __shared__ float2 zsh[];
   float2* zs = zsh + threadIdx.x;
   const int stride = blockDim.x;
@@ -188,6 +188,7 @@ __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log
     if (j == 0 || j == N0 / 2) zi = 0.0;
     seeds[j] = make_double2(zr, zi);
     fails = bad ? 1 : 0;
+    seed_bad[j] = bad ? 1 : 0;  // lifted again in binary64 by k_seed_repair
   }
   warp_add_u64(&ctr->walk_newton, steps);
   warp_add_u64(&ctr->seed_newton, steps);
@@ -198,7 +199,7 @@ __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log
 // a3 in the mixed tier.  Shared memory: m x blockDim binary32 pairs.
 __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
                              int K, const double2* __restrict__ seeds, double2* __restrict__ starts,
-                             DevCounters* ctr) {
+                             uint8_t* __restrict__ chunk_fail, DevCounters* ctr) {
   extern __shared__ float2 zsh[];
   __shared__ float2 ph[64];
   for (int q = threadIdx.x; q < M; q += blockDim.x) {
@@ -244,6 +245,7 @@ __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_
     const double er = cx - zn.x, ei = cy - zn.y;
     const double hh = (double)h;
     if (bad || !(er * er + ei * ei <= 0.0625 * hh * hh + 1e-28)) fails = 1;
+    chunk_fail[j] = (uint8_t)fails;  // walked again in binary64 by k_walk_repair
   }
   warp_add_u64(&ctr->walk_newton, steps);
   warp_add_u64(&ctr->steps_fp32, steps);
@@ -533,7 +535,7 @@ __global__ void k_finish_followers(int64_t count, const double2* __restrict__ st
 }
 
 cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0, int shrink_steps,
-                                   double2* seeds, DevCounters* ctr, cudaStream_t s) {
+                                   double2* seeds, uint8_t* seed_bad, DevCounters* ctr, cudaStream_t s) {
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
   int log2N0 = 0;
   while ((int64_t(1) << log2N0) < N0) ++log2N0;
@@ -542,20 +544,20 @@ cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0,
   const size_t smem = (size_t)P.m * bs * sizeof(float2);
   MT_COUNT_LAUNCH(1);
   k_seed_lift_mixed<<<(unsigned)((n + bs - 1) / bs), bs, smem, s>>>(P, lambda0, N0, log2N0,
-                                                                    shrink_steps, seeds, ctr);
+                                                                    shrink_steps, seeds, seed_bad, ctr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                               int64_t nchunks, int K, const double2* seeds, double2* starts,
-                              DevCounters* ctr, cudaStream_t s, int block) {
+                              uint8_t* chunk_fail, DevCounters* ctr, cudaStream_t s, int block) {
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
   const int bs = (block >= 32 && block <= 256 && block % 32 == 0) ? block : 64;
   const size_t smem = (size_t)P.m * bs * sizeof(float2);
   const int64_t grid = (nchunks + bs - 1) / bs;
   MT_COUNT_LAUNCH(1);
   k_walk_mixed<<<(unsigned)grid, bs, smem, s>>>(P, lambda0, M, every, L, nchunks, K, seeds, starts,
-                                                ctr);
+                                                chunk_fail, ctr);
   return cudaGetLastError();
 }
 

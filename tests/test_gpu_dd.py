@@ -119,7 +119,9 @@ def _tip_checks(mt, n, res, k=24):
     the dd value moves it by less than TOL_DD."""
     z = res.roots[:k].cpu().numpy()
     zl = res.roots_lo[:k].cpu().numpy()
-    assert np.all(z.imag == 0) and np.all(np.diff(z.real) > 0)
+    # increasing in double-double (from p_29 on the tip gap is below one ulp of 2)
+    gaps = (z.real[1:] - z.real[:-1]) + (zl.real[1:] - zl.real[:-1])
+    assert np.all(z.imag == 0) and np.all(gaps > 0)
     for i in range(k):
         c4 = np.array([z[i].real, zl[i].real, 0.0, 0.0])
         out, _ = oracle.polish("hyp", n, c4, steps=3)
@@ -130,11 +132,12 @@ def _tip_checks(mt, n, res, k=24):
     assert abs(gap * 4.0 ** n / 118.4 - 1) < 2e-3
 
 
-@pytest.mark.parametrize("n", [26, 28])
+@pytest.mark.parametrize("n", [26, 28, 29])
 def test_dd_complete_and_certified(mt, n):
-    """p_26 (33.5M roots) and p_28 (134M roots): binary64 cannot separate the
-    tip cluster; MT_DD returns every root, each one certified, with the
-    exact Moebius histogram and Vieta's first sum."""
+    """p_26 (33.5M roots), p_28 (134M) and p_29 (268M): binary64 cannot
+    separate the tip cluster (at p_29 its two left-most roots are 4.1e-16
+    apart, under one ulp of 2); MT_DD returns every root, each one
+    certified, with the exact Moebius histogram and Vieta's first sum."""
     import torch
     res = _split(mt, "hyp", n, max_retries=0)
     st = res.stats
