@@ -163,6 +163,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def separation_stats(mt, torch, n, roots, roots_lo, work, stream, reps=3) -> dict:
+    """mt_separation over Hyp(n) (mask: exact period n from mt_classify) of
+    the last split's roots: device ms per call and the minimum against the
+    118.4 / 4^n law."""
+    z = torch.view_as_complex(roots)
+    mask = (mt.classify("hyp", n, z) == n).to(torch.uint8)
+    lo = None if roots_lo is None else torch.view_as_complex(roots_lo)
+    sw = mt.Workspace()
+    mt.separation(z, roots_lo=lo, mask=mask, work=sw)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        nn, bands, mn = mt.separation(z, roots_lo=lo, mask=mask, work=sw)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    size = int(mask.sum().item())
+    return {"ms": ms, "set": "Hyp(%d)" % n, "roots": size, "roots_per_s": size / (ms / 1e3),
+            "min_dist": mn, "min_x_4n": mn * 4.0 ** n, "law": 118.4,
+            "double_double": roots_lo is not None}
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -396,6 +418,9 @@ def main():
                       "ms_walk": sm["ms_walk"], "ms_descend": sm["ms_descend"],
                       "ms_certify": sm["ms_certify"], "ms_dedup": sm["ms_dedup"],
                       "all_certified": all(x["n_cert_pass"] == d for x in st_mix)}}
+    # separation statistics of the result (Sec. 6.3.2), timed on their own
+    if kind == "hyp" and not args.no_compare:
+        line["separation"] = separation_stats(mt, torch, n, roots, roots_lo, work, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and kind != "misbatch":
         line["cpu_baseline"] = cpu_baseline(kind, l, n)
     if rank == 0:

@@ -209,6 +209,29 @@ MT_API mt_status mt_certify_basin(int kind, int l, int n, const double* d_roots,
                                   int64_t count, const double* d_radius, double eps_max, double* d_basin,
                                   void* d_work, size_t work_bytes, int64_t* n_pass, void* stream);
 
+/* Separation statistics of a root list (Sec. 6.3.2: the minimal distance
+   within Hyp(n) is ~118.4 / 4^n, attained by the two left-most real roots;
+   Fig. separationHistogram bins it over I_k = (-2 + 4^-(k+1), -2 + 4^-k]).
+   d_roots: [count][2]; d_roots_lo: NULL or the low parts (distances then in
+   double-double); d_mask: NULL or [count] bytes, the set = roots with
+   mask != 0 (e.g. the exact period n from mt_classify).  Outputs, all
+   optional: d_nn [count] doubles, the distance from each root of the set
+   to its nearest other root of the set (0 outside the set, +inf if it is
+   alone); h_band_min [64] host doubles, per band k the smallest d_nn over
+   the set's roots with Re c + 2 in (4^-(k+1), 4^-k] (band 0 also takes
+   Re c + 2 > 1, band 63 everything below 4^-63; +inf if empty); *h_min the
+   smallest over the set.  Entries must be finite.  The scan runs over the
+   list sorted by Re; roots whose Re window holds more than 65536 entries
+   (isolated roots) are finished over a (Re strip, Im) index instead, so
+   every distance is exact.  Errors: MT_EINVAL (negative count, count above
+   2^32 - 1, null roots), MT_ENOMEM (workspace smaller than
+   mt_separation_workspace_bytes(count)), MT_ECUDA.  Synchronises the
+   stream before returning. */
+MT_API size_t mt_separation_workspace_bytes(int64_t count);
+MT_API mt_status mt_separation(int64_t count, const double* d_roots, const double* d_roots_lo,
+                               const uint8_t* d_mask, double* d_nn, double* h_band_min,
+                               double* h_min, void* d_work, size_t work_bytes, void* stream);
+
 /* Autotuner (the paper tunes nothing; a GPU-layout choice).  Runs complete
    splits of P for each candidate level-line chunk length 2^c (c = 3 .. 10
    sub-steps per lane) and walk block size (32, 64, 128), three runs each,

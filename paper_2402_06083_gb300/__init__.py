@@ -209,6 +209,27 @@ def certify_basin(kind: str, n: int, roots, radius, l: int = 0, eps_max: float =
     return out, int(npass.value)
 
 
+def separation(roots, *, roots_lo=None, mask=None, work: Workspace | None = None):
+    """Nearest-neighbour distance of each root (Sec. 6.3.2 separation law).
+    Returns (nn float64 tensor, band minima list of 64 floats, overall minimum)."""
+    torch = _torch()
+    L = load()
+    r = torch.view_as_real(roots.contiguous()) if roots.is_complex() else roots.contiguous()
+    rl = None
+    if roots_lo is not None:
+        rl = torch.view_as_real(roots_lo.contiguous()) if roots_lo.is_complex() else roots_lo.contiguous()
+    m = None if mask is None else mask.contiguous().to(torch.uint8)
+    count = r.shape[0]
+    work = work or Workspace()
+    buf = work.ensure(int(L.mt_separation_workspace_bytes(count)))
+    nn = torch.empty(count, dtype=torch.float64, device=r.device)
+    bands = (ctypes.c_double * 64)()
+    mn = ctypes.c_double(0)
+    check(L.mt_separation(count, r.data_ptr(), _ptr(rl), _ptr(m), nn.data_ptr(), bands, ctypes.byref(mn),
+                          buf.data_ptr(), buf.numel(), torch.cuda.current_stream().cuda_stream))
+    return nn, list(bands), mn.value
+
+
 def evaluate(kind: str, n: int, c, l: int = 0):
     """P(c), P'(c) for a complex128 tensor c: returns complex128 [count, 2]."""
     torch = _torch()

@@ -23,7 +23,9 @@ EXPORTS = (
     "mt_default_options", "mt_degree_hyperbolic", "mt_degree_misiurewicz", "mt_workspace_bytes",
     "mt_split_hyperbolic", "mt_split_misiurewicz", "mt_misiurewicz_pairs",
     "mt_workspace_bytes_misiurewicz_batch", "mt_split_misiurewicz_batch",
-    "mt_certify_workspace_bytes", "mt_certify", "mt_certify_basin", "mt_eval", "mt_level_line", "mt_descend",
+    "mt_certify_workspace_bytes", "mt_certify", "mt_certify_basin", "mt_separation_workspace_bytes", "mt_separation",
+    "mt_eval", "mt_level_line",
+    "mt_descend",
     "mt_classify", "mt_certify_static", "mt_autotune", "mt_last_error", "mt_version",
 )
 MT_CERTIFY_STATIC_MAX_ROOTS = 131072
@@ -108,6 +110,8 @@ def load() -> ctypes.CDLL:
                                       vp, vp, vp, ctypes.c_size_t, i64p, vp]),
         "mt_certify_basin": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, i64, vp,
                                             ctypes.c_double, vp, vp, ctypes.c_size_t, i64p, vp]),
+        "mt_separation_workspace_bytes": (ctypes.c_size_t, [i64]),
+        "mt_separation": (ctypes.c_int, [i64, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
         "mt_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64, vp, vp]),
         "mt_level_line": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, op, vp, i64, vp,
                                          ctypes.c_size_t, i64p, sp]),

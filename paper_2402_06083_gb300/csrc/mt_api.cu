@@ -1233,6 +1233,70 @@ mt_status mt_certify_basin(int kind, int l, int n, const double* d_roots, const 
   return MT_OK;
 }
 
+size_t mt_separation_workspace_bytes(int64_t count) {
+  if (count < 0) return 0;
+  Carve c(nullptr, 0);
+  c.take<DevCounters>(1);
+  c.take<uint64_t>(count);
+  c.take<uint64_t>(count);
+  c.take<uint32_t>(count);
+  c.take<uint32_t>(count);
+  c.take_bytes(radix_temp_bytes(count));
+  c.take<uint32_t>(count);
+  c.take<double>(count);
+  c.take<uint32_t>(((int64_t)1 << separation_strips_log2(count)) + 1);
+  return c.off;
+}
+
+mt_status mt_separation(int64_t count, const double* d_roots, const double* d_roots_lo,
+                        const uint8_t* d_mask, double* d_nn, double* h_band_min, double* h_min,
+                        void* d_work, size_t work_bytes, void* stream) {
+  g_err.clear();
+  if (count < 0 || (count > 0 && !d_roots)) return fail(MT_EINVAL, "bad buffers");
+  if (count > 0xffffffffll) return fail(MT_EINVAL, "count too large");
+  const size_t need = mt_separation_workspace_bytes(count);
+  if (!d_work || work_bytes < need) return fail(MT_ENOMEM, "workspace of %zu bytes needed", need);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the counter slot holds the band minima and the isolated-root count
+  static_assert(sizeof(DevCounters) >= 67 * sizeof(unsigned long long), "band minima slot");
+  Carve c(d_work, work_bytes);
+  unsigned long long* band = (unsigned long long*)c.take<DevCounters>(1);
+  uint64_t* keys = c.take<uint64_t>(count);
+  uint64_t* keys_alt = c.take<uint64_t>(count);
+  uint32_t* vals = c.take<uint32_t>(count);
+  uint32_t* vals_alt = c.take<uint32_t>(count);
+  void* rtmp = c.take_bytes(radix_temp_bytes(count));
+  uint32_t* iso_idx = c.take<uint32_t>(count);
+  double* iso_best = c.take<double>(count);
+  const int log2s = separation_strips_log2(count);
+  uint32_t* offs = c.take<uint32_t>(((int64_t)1 << log2s) + 1);
+  const double2* hi = (const double2*)d_roots;
+  const double2* lo = (const double2*)d_roots_lo;
+  // tier 1: Re-window scan over the list sorted by Re
+  if (count > 0) {
+    CK(launch_keys_plain(hi, count, keys, vals, s));
+    CK(radix_sort_pairs(keys, vals, keys_alt, vals_alt, count, rtmp, s));
+  }
+  CK(launch_separation(hi, lo, vals, count, d_mask, d_nn, band, iso_idx, iso_best, s));
+  unsigned long long hb[67];
+  CK(cudaMemcpyAsync(hb, band, sizeof(hb), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // tiers 2 and 3, for the roots tier 1 left: (strip, Im) index, strip
+  // walks; after the sort keys_alt / vals_alt hold tier 3's list
+  if (hb[65] > 0) {
+    CK(launch_strip_index(hi, count, log2s, keys, vals, keys_alt, vals_alt, rtmp, offs, s));
+    CK(launch_separation_strips(hi, lo, d_mask, keys, vals, offs, log2s, iso_idx, iso_best, (int64_t)hb[65],
+                                vals_alt, (double*)keys_alt, d_nn, band, s));
+    CK(cudaMemcpyAsync(hb, band, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  double bd[65];
+  memcpy(bd, hb, sizeof(bd));
+  if (h_band_min) memcpy(h_band_min, bd, 64 * sizeof(double));
+  if (h_min) *h_min = bd[64];
+  return MT_OK;
+}
+
 mt_status mt_eval(int kind, int l, int n, const double* d_c, int64_t count, double* d_out,
                   void* stream) {
   g_err.clear();

@@ -192,6 +192,30 @@ cudaError_t launch_basin(const PolyDev& P, const double2* pts, const uint32_t* o
                          const double* radius, double eps_max, double* basin, DevCounters* ctr,
                          cudaStream_t s);
 
+// Separation statistics, tier 1, over a list sorted by Re through 'order'
+// (lo may be null): nn_out[i] (optional) = distance to the nearest other
+// root of the (masked) list; band_min[0..63] = per-band minima, [64] =
+// overall minimum (bit patterns of doubles), [65] = roots left to the strip
+// tiers, listed in iso_idx / iso_best (room for n each) with the best
+// distance found so far; [66] = roots left by tier 2 to tier 3.
+cudaError_t launch_separation(const double2* hi, const double2* lo, const uint32_t* order, int64_t n,
+                              const uint8_t* mask, double* nn_out, unsigned long long* band_min,
+                              uint32_t* iso_idx, double* iso_best, cudaStream_t s);
+// log2 of the strip count for n roots (about 16 per strip, 2^10 .. 2^20)
+int separation_strips_log2(int64_t n);
+// (Re strip, Im) index: keys / vals sorted (keys_alt, vals_alt, rtmp are
+// the sort's scratch), offs [2^log2s + 1] = each strip's first entry
+cudaError_t launch_strip_index(const double2* hi, int64_t n, int log2s, uint64_t* keys, uint32_t* vals,
+                               uint64_t* keys_alt, uint32_t* vals_alt, void* rtmp, uint32_t* offs,
+                               cudaStream_t s);
+// tiers 2 and 3 over the niso roots of iso_idx / iso_best (iso2_*: room for
+// niso roots passed from tier 2 to tier 3)
+cudaError_t launch_separation_strips(const double2* hi, const double2* lo, const uint8_t* mask,
+                                     const uint64_t* skeys, const uint32_t* sidx, const uint32_t* offs,
+                                     int log2s, const uint32_t* iso_idx, const double* iso_best, int64_t niso,
+                                     uint32_t* iso2_idx, double* iso2_best, double* nn_out,
+                                     unsigned long long* band_min, cudaStream_t s);
+
 // Zero the counters (min radius set to +inf).
 cudaError_t launch_init_counters(DevCounters* ctr, cudaStream_t s);
 // keys[i] = order-preserving key of Re pts[i], vals[i] = i.
