@@ -3,7 +3,8 @@
 A plain, slow CPU implementation of the level-line Newton splitting of the
 hyperbolic polynomials p_n and the simplified Misiurewicz polynomials
 s_{l,n} = p_{l+n-1} + p_{l-1} (Mihalache & Vigneron, arXiv 2402.06083,
-Sec. 4 and Sec. 6.3), plus the closed-form counts the paper gives.
+Sec. 4 and Sec. 6.3), plus the closed-form counts the paper gives and the separation statistics
+of a root list (Sec. 6.3.2, by their definition, in numpy).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
@@ -274,6 +275,78 @@ def join4(a: np.ndarray):
     """4-vectors -> (Re, Im) as pairs of float64 hi + lo (for mpmath use)."""
     a = np.asarray(a, dtype=np.float64).reshape(-1, 4)
     return a[:, 0], a[:, 1], a[:, 2], a[:, 3]
+
+
+def _two_diff(a, b):
+    """a - b = s + e exactly (Knuth's TwoSum applied to a and -b)."""
+    s = a - b
+    bb = s - a
+    e = (a - (s - bb)) + (-b - bb)
+    return s, e
+
+
+def nearest_neighbours(z, mask=None, z_lo=None, idx=None, cells: int = 1 << 23) -> np.ndarray:
+    """Separation (Sec. 6.3.2), by its definition.  For root i of the set
+    S = {j : mask[j] != 0} (every root if mask is None),
+        nn_i = min over j in S, j != i, of |c_j - c_i|,
+    a minimum over all other roots of S (no index, no pruning), taken in
+    blocks of at most `cells` pairs.  nn_i = +inf if i is alone in S.  With
+    z_lo (double-double roots c = z + z_lo) each coordinate difference is
+    (z_j - z_i) split exactly by TwoSum, plus (lo_j - lo_i).  Returns nn for
+    every root (0 outside S) or, with idx, for the roots idx only."""
+    z = np.asarray(z, dtype=np.complex128).ravel()
+    lo = None if z_lo is None else np.asarray(z_lo, dtype=np.complex128).ravel()
+    sel = np.ones(z.size, bool) if mask is None else (np.asarray(mask).ravel() != 0)
+    S = np.nonzero(sel)[0]
+    rows = S if idx is None else np.asarray(idx, dtype=np.int64).ravel()
+    res = np.zeros(rows.size)
+    xs, ys = z.real[S], z.imag[S]
+    xls = None if lo is None else lo.real[S]
+    yls = None if lo is None else lo.imag[S]
+    col = max(1, min(S.size, cells))
+    rb = max(1, cells // col)
+    for a in range(0, rows.size, rb):
+        r = rows[a:a + rb]
+        best = np.full(r.size, np.inf)
+        for b in range(0, S.size, col):
+            dx, ex = _two_diff(xs[None, b:b + col], z.real[r][:, None])
+            dy, ey = _two_diff(ys[None, b:b + col], z.imag[r][:, None])
+            if lo is not None:
+                dx = dx + (ex + (xls[None, b:b + col] - lo.real[r][:, None]))
+                dy = dy + (ey + (yls[None, b:b + col] - lo.imag[r][:, None]))
+            d = np.hypot(dx, dy)
+            d[S[None, b:b + col] == r[:, None]] = np.inf  # not the root itself
+            best = np.minimum(best, d.min(axis=1))
+        res[a:a + rb] = best
+    if idx is not None:
+        return np.where(sel[rows], res, 0.0)
+    out = np.zeros(z.size)
+    out[S] = res
+    return out
+
+
+def separation_band(x: float) -> int:
+    """Fig. separationHistogram: the k >= 0 with Re c + 2 in the bin
+    I_k = (4^-(k+1), 4^-k]; Re c + 2 > 1 counts in bin 0, Re c + 2 <= 4^-63
+    (and c = -2 itself) in bin 63."""
+    t = float(x) + 2.0
+    for k in range(63):
+        if t > 4.0 ** -(k + 1):
+            return k
+    return 63
+
+
+def separation_bands(z, nn, mask=None) -> list:
+    """Per bin I_k (k = 0..63) the minimal nn over the set's roots in it
+    (+inf for an empty bin): the histogram of Fig. separationHistogram."""
+    z = np.asarray(z, dtype=np.complex128).ravel()
+    sel = np.ones(z.size, bool) if mask is None else (np.asarray(mask).ravel() != 0)
+    out = [np.inf] * 64
+    for x, d, s in zip(z.real, np.asarray(nn).ravel(), sel):
+        if s:
+            k = separation_band(x)
+            out[k] = min(out[k], float(d))
+    return out
 
 
 if __name__ == "__main__":  # pragma: no cover

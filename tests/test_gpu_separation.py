@@ -1,10 +1,11 @@
-"""Separation statistics (mt_separation) against their plain definition and
-the paper's separation law.
+"""Separation statistics (mt_separation) against the oracle's definition
+and the paper's separation law (Sec. 6.3.2).
 
-The nearest-neighbour distance of every root is checked against a brute
-force over all pairs of the same list (numpy), with and without a mask and
-per band I_k = (-2 + 4^-(k+1), -2 + 4^-k]; larger lists against scipy's
-k-d tree.  A synthetic column of points (Re spread far below the
+The nearest-neighbour distance of every root is checked against the
+oracle's minimum over all pairs, with and without a mask, and per bin
+I_k = (-2 + 4^-(k+1), -2 + 4^-k] of Fig. separationHistogram; lists too
+large for all pairs against scipy's k-d tree in full and against the
+oracle on sampled roots (one row of all pairs each).  A synthetic column of points (Re spread far below the
 neighbour distance) sends every point of it through the strip pass.  On GPU splits the minimum over
 Hyp(n) (mask: exact period n) must follow 118.4 / 4^n to 0.2 % (Sec. 6.3.2
 reports 0.1 % for n >= 9) and be the gap of the two left-most real roots;
@@ -35,44 +36,18 @@ def _t(x):
     return torch.as_tensor(np.asarray(x, dtype=np.complex128), device="cuda")
 
 
-def _brute_nn(z, mask=None):
-    z = np.asarray(z)
-    sel = np.ones(z.size, bool) if mask is None else np.asarray(mask, bool)
-    idx = np.nonzero(sel)[0]
-    nn = np.zeros(z.size)
-    w = z[idx]
-    for a, i in enumerate(idx):
-        d = np.abs(w - z[i])
-        d[a] = np.inf
-        nn[i] = d.min()
-    return nn
-
-
-def _band(x):
-    t = x + 2.0
-    k = 0
-    up = 1.0
-    while k < 63 and t <= 0.25 * up:
-        up *= 0.25
-        k += 1
-    return k
-
-
 @pytest.mark.parametrize("kind,n,l", [("hyp", 10, 0), ("hyp", 12, 0), ("mis", 6, 3)])
-def test_nearest_neighbours_match_brute_force(mt, kind, n, l):
+def test_nearest_neighbours_match_oracle(mt, kind, n, l):
     ref = oracle.split(kind, n, l=l)
     z = ref["roots"]
     nn, bands, mn = mt.separation(_t(z))
-    want = _brute_nn(z)
+    want = oracle.nearest_neighbours(z)
     got = nn.cpu().numpy()
     assert np.allclose(got, want, rtol=1e-15, atol=0)  # hypot may round the last bit differently
     assert np.isclose(mn, want.min(), rtol=1e-15, atol=0)
-    per = {}
-    for x, d in zip(z.real, want):
-        k = _band(x)
-        per[k] = min(per.get(k, np.inf), d)
+    per = oracle.separation_bands(z, want)
     for k in range(64):
-        w = per.get(k, np.inf)
+        w = per[k]
         assert (bands[k] == w) if np.isinf(w) else np.isclose(bands[k], w, rtol=1e-15, atol=0)
 
 
@@ -84,7 +59,7 @@ def test_mask_restricts_the_set(mt):
     mask = ref["type"][:, 1] == n
     import torch
     nn, bands, mn = mt.separation(_t(z), mask=torch.as_tensor(mask.astype(np.uint8), device="cuda"))
-    want = _brute_nn(z, mask)
+    want = oracle.nearest_neighbours(z, mask)
     got = nn.cpu().numpy()
     assert np.allclose(got[mask], want[mask], rtol=1e-15, atol=0) and np.all(got[~mask] == 0)
     assert np.isclose(mn, want[mask].min(), rtol=1e-15, atol=0)
@@ -142,7 +117,10 @@ def test_separation_law(mt, n):
     if n <= 20:
         m = mask.cpu().numpy().astype(bool)
         got = nn.cpu().numpy()
-        assert np.allclose(got[m], _kd_nn(z.cpu().numpy(), m), rtol=1e-15, atol=0)
+        zc = z.cpu().numpy()
+        assert np.allclose(got[m], _kd_nn(zc, m), rtol=1e-15, atol=0)
+        rows = np.random.default_rng(n).choice(np.nonzero(m)[0], 64, replace=False)
+        assert np.allclose(got[rows], oracle.nearest_neighbours(zc, m, idx=rows), rtol=1e-15, atol=0)
 
 
 def test_separation_law_double_double_p28(mt):
@@ -168,3 +146,9 @@ def test_separation_law_double_double_p28(mt):
     assert abs(mn - gap) <= 1e-12 * gap
     nn_set = torch.where(mask.bool(), nn, torch.full_like(nn, float("inf")))  # 0 outside the set
     assert int(torch.argmin(nn_set)) in (0, 1)
+    # sampled roots against the oracle's row of all pairs, in double-double
+    m = mask.cpu().numpy().astype(bool)
+    rows = np.concatenate([[0, 1], np.random.default_rng(28).choice(np.nonzero(m)[0], 4, replace=False)])
+    zc, zlc = res.roots.cpu().numpy(), res.roots_lo.cpu().numpy()
+    want = oracle.nearest_neighbours(zc, m, z_lo=zlc, idx=rows)
+    assert np.allclose(nn.cpu().numpy()[rows], want, rtol=1e-13, atol=0)
