@@ -57,14 +57,35 @@ constexpr int SEP_BS = 256;
 
 __device__ __forceinline__ double pos_inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 
-__device__ __forceinline__ double pair_dist(const double2* hi, const double2* lo, int64_t a,
-                                            int64_t b) {
+// Coordinate differences of roots a and b (double-double when lo is given).
+__device__ __forceinline__ void pair_diff(const double2* hi, const double2* lo, int64_t a, int64_t b,
+                                          double& dx, double& dy) {
   const double2 u = hi[a], v = hi[b];
   if (lo) {
     const double2 ul = lo[a], vl = lo[b];
-    return hypot(dd_diff(v.x, vl.x, u.x, ul.x), dd_diff(v.y, vl.y, u.y, ul.y));
+    dx = dd_diff(v.x, vl.x, u.x, ul.x);
+    dy = dd_diff(v.y, vl.y, u.y, ul.y);
+  } else {
+    dx = v.x - u.x;
+    dy = v.y - u.y;
   }
-  return hypot(v.x - u.x, v.y - u.y);
+}
+
+// The binary64 pipe is the scarce one on this part: a pair is first tested
+// on its squared distance (two FMA-class operations), and hypot -- the
+// reported value -- is taken only for pairs within thr of the best so far.
+// thr = best^2 (1 + 1e-15) covers the rounding of both squares; below
+// 1e-140 the squares lose digits to underflow and every pair takes hypot.
+__device__ __forceinline__ double sq_threshold(double best) {
+  return best < 1e-140 ? pos_inf() : best * best * (1.0 + 1e-15);
+}
+__device__ __forceinline__ bool consider(double dx, double dy, double& best, double& thr) {
+  if (!(fma(dx, dx, dy * dy) <= thr)) return false;
+  const double h = hypot(dx, dy);
+  if (!(h < best)) return false;
+  best = h;
+  thr = sq_threshold(best);
+  return true;
 }
 
 // band of a root: the k >= 0 with Re c + 2 in (4^-(k+1), 4^-k]; roots with
@@ -157,7 +178,7 @@ __global__ void k_separation(const double2* __restrict__ hi, const double2* __re
     return;
   }
   const double2 c = hi[ip];
-  double best = pos_inf();
+  double best = pos_inf(), thr = pos_inf();
   int scanned = 0;
   bool cut = false;
   for (int dir = -1; dir <= 1 && !cut; dir += 2) {
@@ -171,7 +192,9 @@ __global__ void k_separation(const double2* __restrict__ hi, const double2* __re
         break;
       }
       if (mask && !mask[iq]) continue;
-      best = fmin(best, pair_dist(hi, lo, ip, iq));
+      double dx, dy;
+      pair_diff(hi, lo, ip, iq, dx, dy);
+      consider(dx, dy, best, thr);
     }
   }
   if (cut) {  // left to the strip pass, with best as an upper bound
@@ -219,7 +242,7 @@ __global__ void k_separation_strip_thread(const double2* __restrict__ hi, const 
   if (r >= (int64_t)*niso) return;
   const int64_t ip = iso_idx[r];
   const double2 c = hi[ip];
-  double best = iso_best[r];
+  double best = iso_best[r], thr = sq_threshold(best);
   const int sq = strip_of(c.x, S, scale);
   int strips = 0, points = 0;
   bool defer = false;
@@ -247,9 +270,9 @@ __global__ void k_separation_strip_thread(const double2* __restrict__ hi, const 
         }
         const int64_t q = sidx[pos];
         if (q == ip || (mask && !mask[q])) continue;
-        const double d = pair_dist(hi, lo, ip, q);
-        if (d < best) {
-          best = d;
+        double dx, dy;
+        pair_diff(hi, lo, ip, q, dx, dy);
+        if (consider(dx, dy, best, thr)) {
           m = window_margin(c, best);
           kup = strip_key((int)s, c.y + best + m);
           kdn = strip_key((int)s, c.y - best - m);
@@ -308,7 +331,7 @@ k_separation_strip_block(const double2* __restrict__ hi, const double2* __restri
         __syncthreads();
       }
       const int64_t total = incl[SEP_BS - 1];
-      double mine = best;
+      double mine = best, thr = sq_threshold(best);
       for (int64_t g = t; g < total; g += SEP_BS) {
         int u0 = 0, u1 = SEP_BS - 1;  // first slot with incl > g
         while (u0 < u1) {
@@ -318,7 +341,9 @@ k_separation_strip_block(const double2* __restrict__ hi, const double2* __restri
         const int64_t pos = beg[u0] + g - (u0 ? incl[u0 - 1] : 0);
         const int64_t q = sidx[pos];
         if (q == ip || (mask && !mask[q])) continue;
-        mine = fmin(mine, pair_dist(hi, lo, ip, q));
+        double dx, dy;
+        pair_diff(hi, lo, ip, q, dx, dy);
+        consider(dx, dy, mine, thr);
       }
       red[t] = mine;
       __syncthreads();
