@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
         "degree", "n_roots", "n_real", "n_starts", "n_conv", "n_repeat", "n_diverge",
         "n_timeout", "walk_newton", "desc_newton", "walk_fail")] + [
         ("M", ctypes.c_int), ("cL", ctypes.c_int), ("retries", ctypes.c_int),
-        ("endpoint_ok", ctypes.c_int)]
+        ("endpoint_ok", ctypes.c_int), ("n_mult", ctypes.c_long)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -156,6 +156,8 @@ def _kind_args(kind: str, l: int, n: int):
         return 0, 0, n
     if kind == "mis":
         return 1, l, n
+    if kind == "q":
+        return 2, l, n
     raise ValueError(kind)
 
 
@@ -178,11 +180,14 @@ def split(kind: str, n: int, l: int = 0, *, M: int = 8, cL: int = 4, lambda0: fl
           I_N: float | None = None, eps_dup: float | None = None, max_retries: int = 2,
           frac: float = 1.0, fp64: bool = False, want_starts: bool = False,
           want_types: bool = True) -> dict:
-    """Split P (p_n for kind 'hyp', s_{l,n} for kind 'mis') with the oracle.
+    """Split P (p_n for kind 'hyp', s_{l,n} for kind 'mis', q_{l,n} for kind
+    'q') with the oracle.
 
     Returns a dict with 'roots' (complex128, the rounded values), 'roots4'
     ([N, 4] Re hi, Re lo, Im hi, Im lo), 'type' ([N, 2] (preperiod, period)),
-    'stats' and optionally 'starts4' (upper-half level-line starts)."""
+    'stats' and optionally 'starts4' (upper-half level-line starts).  For
+    q_{l,n} the roots are distinct and 'mult' holds each one's multiplicity
+    (Thm fact_mis: eta_l(k) = floor((l-1)/k) + 2 for Hyp(k), 1 for Mis)."""
     k, ll, nn = _kind_args(kind, l, n)
     L = _lib(fp64)
     d = int(L.or_degree(k, ll, nn))
@@ -213,6 +218,8 @@ def split(kind: str, n: int, l: int = 0, *, M: int = 8, cL: int = 4, lambda0: fl
     }
     if want_types:
         out["type"] = np.stack([ta[:m], tb[:m]], axis=1)
+        if kind == "q":
+            out["mult"] = np.where(ta[:m] == 0, (l - 1) // np.maximum(tb[:m], 1) + 2, 1)
     if want_starts:
         ns = min(int(st.n_starts), scap)
         out["starts4"] = starts4[:ns].copy()

@@ -5,6 +5,8 @@
   with Phi(l,n) = 1 (l = 0), 2^(l-1) - 1 (l != 0 and n | l-1), 2^(l-1) otherwise
 * eq. polyMisSimple: the roots of s_{l,n} are Hyp(k) for k | gcd(n, l-1) and
   Mis(l,k) for k | n, all simple; deg s_{l,n} = 2^(l+n-2).
+* Thm fact_mis: q_{l,n} = prod_{k|n} h_k^eta_l(k) prod_{j=2..l} m_{j,k},
+  eta_l(k) = floor((l-1)/k) + 2; deg q_{l,n} = 2^(l+n-1).
 """
 from __future__ import annotations
 
@@ -72,6 +74,27 @@ def type_histogram_s(l: int, n: int) -> dict[tuple[int, int], int]:
         h[(0, k)] = hyp_count(k)
     for k in divisors(n):
         h[(l, k)] = mis_count(l, k)
+    return h
+
+
+def deg_q(l: int, n: int) -> int:
+    """deg q_{l,n} = deg p_{l+n} = 2^(l+n-1)."""
+    return 2 ** (l + n - 1)
+
+
+def eta(l: int, k: int) -> int:
+    """Multiplicity of Hyp(k) in q_{l,n}, k | n (Thm fact_mis, eq. defMultHyp)."""
+    return (l - 1) // k + 2
+
+
+def type_histogram_q(l: int, n: int) -> dict[tuple[int, int], int]:
+    """Distinct roots of q_{l,n} by type (Thm fact_mis): (0, k) for Hyp(k),
+    k | n, and (j, k) for Mis(j, k), 2 <= j <= l, k | n."""
+    h: dict[tuple[int, int], int] = {}
+    for k in divisors(n):
+        h[(0, k)] = hyp_count(k)
+        for j in range(2, l + 1):
+            h[(j, k)] = mis_count(j, k)
     return h
 
 

@@ -12,6 +12,7 @@
  *   - the c-derivative by differentiating that recurrence:
  *     p'_0 = 0, p'_{k+1} = 2 p_k p'_k + 1                    (Sec. 6.3.2, eq. DerParamDyna)
  *   - s_{l,n} = p_{l+n-1} + p_{l-1}                          (eq. polySimple / polyMisSimple)
+ *   - q_{l,n} = p_{l+n} - p_l, with multiple roots            (eq. def:mis, Thm fact_mis)
  *   - the real end point of |P| = lambda0 by dichotomy       (Sec. 6.3.1)
  *   - the discrete level line walked sequentially, M points per
  *     turn, each point the Newton-with-target limit           (Prop. computeLevelLine,
@@ -24,6 +25,13 @@
  *                                                              computeLevelLine)
  *   - exact period / Misiurewicz type of each root           (eq. def:hyp, def:mis,
  *                                                              Thm countingHyp, eq. polyMisSimple)
+ *   - q_{l,n}: the multiplicity of a root from its type, eta_l(k) =
+ *     floor((l-1)/k) + 2 for Hyp(k), 1 for Mis(j,k); the count check adds
+ *     multiplicities                                          (Thm fact_mis, eq. defMultHyp)
+ *   - q_{l,n}: a descent that contracts linearly, as Newton does near a
+ *     multiple root (ratio -> 1 - 1/mu), takes an accelerated step; one
+ *     that then stalls is finished with Newton on p_n, of which every
+ *     multiple root of q is a simple root             (eq. newtonLin, newtonAcc, Thm fact_mis)
  *
  * Deliberately different from the GPU design: one sequential walk from the
  * real end point (no lifting, no chunks), qsort + linear scan for the set,
@@ -121,7 +129,7 @@ static int cfinite(cplx a) {
 /* ------------------------------------------------------------------ */
 /* The polynomial family.                                               */
 /* kind 0: P = p_n (degree 2^(n-1));  kind 1: P = s_{l,n} = p_{l+n-1} + p_{l-1}
-   (degree 2^(l+n-2)). */
+   (degree 2^(l+n-2));  kind 2: P = q_{l,n} = p_{l+n} - p_l (degree 2^(l+n-1)). */
 typedef struct {
   int kind, l, n;
   int m;        /* length of the critical orbit that is evaluated */
@@ -140,6 +148,10 @@ static int poly_init(poly* P, int kind, int l, int n) {
     if (l < 1 || l + n > 41) return -1;
     P->m = l + n - 1;
     P->degree = 1L << (l + n - 2);
+  } else if (kind == 2) {
+    if (l < 1 || l + n > 40) return -1;
+    P->m = l + n;
+    P->degree = 1L << (l + n - 1);
   } else {
     return -1;
   }
@@ -156,6 +168,7 @@ static void eval_P(const poly* P, cplx c, cplx* v, cplx* dv) {
 #else
   int lcap = (P->kind == 1) ? P->l - 1 : -1;
 #endif
+  if (P->kind == 2) lcap = P->l;
   if (lcap == 0) { zl = z; dzl = dz; }
   for (int k = 1; k <= P->m; ++k) {
 #if ORACLE_MUTANT == 1 /* planted mistake: derivative from p_k instead of p_{k-1} */
@@ -175,6 +188,9 @@ static void eval_P(const poly* P, cplx c, cplx* v, cplx* dv) {
   if (P->kind == 1) {
     z = cadd(z, zl);
     dz = cadd(dz, dzl);
+  } else if (P->kind == 2) { /* q_{l,n} = p_{l+n} - p_l */
+    z = csub(z, zl);
+    dz = csub(dz, dzl);
   }
   *v = z;
   *dv = dz;
@@ -194,8 +210,9 @@ static void eval_pk(int k, cplx c, cplx* v, cplx* dv) {
 
 /* ------------------------------------------------------------------ */
 /* Real end point of the level line |P| = lambda0 on c > 0 (Sec. 6.3.1:
-   "found by dichotomy").  P is increasing on (0, +inf) for both families
-   and P(0) = 0 < lambda0 <= P(lambda0), so [0, lambda0] brackets it. */
+   "found by dichotomy").  P is increasing on (0, +inf) for the three
+   families (every p_k and p'_k grows with c there, and p'_{k+1} >= p'_k for
+   q) and P(0) = 0 < lambda0 <= P(lambda0), so [0, lambda0] brackets it. */
 static real real_endpoint(const poly* P, real lambda0) {
   real lo = 0, hi = lambda0;
   for (int it = 0; it < 400; ++it) {
@@ -245,6 +262,7 @@ typedef struct {
   int M, cL;         /* points per turn and starts per root finally used */
   int retries;       /* number of (M, c_L) doublings */
   int endpoint_ok;   /* the walk ended on the real axis left of the set */
+  long n_mult;       /* roots counted with multiplicity (q_{l,n}; n_roots otherwise) */
 } or_stats;
 
 typedef struct {
@@ -313,28 +331,125 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
     real rdiv = 2 * cabs_(z);
     if (rdiv < 4) rdiv = 4;
     int conv = 0, div = 0, it;
+    /* q_{l,n} only.  Near a root of multiplicity mu Newton contracts
+       linearly, |step_{k+1}| / |step_k| -> 1 - 1/mu (eq. newtonLin).  When
+       three successive ratios agree and give mu within 0.15 of an integer
+       m >= 2, a trial step z - m P/P' is taken (eq. newtonAcc).  Next to a
+       multiple root it lands much closer and the next plain step is short:
+       the multiplicity is then taken as m and every following step is
+       z - m P/P', which converges quadratically to the multiple root.  A
+       cluster of simple roots looks the same from afar, but the trial step
+       then lands at its centre, near a critical point, where the next
+       plain step is long: the trial is undone and the descent goes on with
+       plain Newton, which separates the cluster.  If an accelerated descent
+       stalls (the rounding noise around a multiple root) and Newton on p_n
+       -- of which every multiple root of q is a simple root (Thm fact_mis)
+       -- sees a root well within the trial step, it finishes on p_n; if p_n
+       sees none, the "multiple root" was a tight cluster of simple roots
+       (about which z - m P/P' oscillates) and plain Newton takes over. */
+    int on_pn = 0, lin = 0, mult = 1, pending = 0, trial = 0, no_acc = 0;
+    real s_prev = 0, r_prev = 0, s_acc = 0, r_last = 0;
+    cplx w_pre = w;
     for (it = 0; it < cap; ++it) {
       cplx v, dv;
-      eval_P(P, w, &v, &dv);
+      if (on_pn) eval_pk(P->n, w, &v, &dv); else eval_P(P, w, &v, &dv);
       cplx step = cdiv(v, dv);
-      w = csub(w, step);
       st->desc_newton++;
+      if (trial) { /* the first plain step after the trial step */
+        if (cabs_(step) <= s_acc / 2) {
+          mult = trial;
+        } else { /* the trial overshot into a cluster: undo it */
+          w = w_pre;
+          trial = 0;
+          no_acc = 1;
+          lin = 0;
+          continue;
+        }
+        trial = 0;
+      }
+      if (mult > 1 && !on_pn) step = cx(mult * step.re, mult * step.im);
+      if (pending) {
+        w_pre = w;
+        step = cx(pending * step.re, pending * step.im);
+        s_acc = cabs_(step);
+        trial = pending;
+        pending = 0;
+      }
+      w = csub(w, step);
       if (!cfinite(w) || cabs_(w) > rdiv) { div = 1; break; }
       s = cabs_(step);
+      r_last = (it > 0) ? s / s_prev : 0;
       if (s < 1e-12) { conv = 1; break; }
+      if (P->kind == 2 && !on_pn && it > 0 && !trial) {
+        real r = s / s_prev;
+        if (mult > 1) {
+          if (r >= 0.9) {
+            cplx v2, d2;
+            eval_pk(P->n, w, &v2, &d2);
+            if (cabs_(cdiv(v2, d2)) < s_acc / 2) {
+              on_pn = 1;
+              it = 0; /* the p_n descent gets the cap of its own */
+            } else { /* a cluster of simple roots: plain Newton from here */
+              mult = 1;
+              no_acc = 1;
+              lin = 0;
+            }
+          }
+        } else {
+          lin = (r > 0.35 && r < 0.98 && rabs(r - r_prev) < 0.03 * r) ? lin + 1 : 0;
+          if (lin >= 3 && !no_acc) {
+            real mu = 1 / (1 - r);
+            int m = (int)(mu + 0.5);
+            if (m >= 2 && rabs(mu - m) < 0.15) pending = m;
+            lin = 0;
+          }
+        }
+        r_prev = r;
+      }
+      s_prev = s;
+    }
+    if (!conv && !div && P->kind == 2 && mult > 1 && !on_pn) {
+      /* cap reached on an accelerated descent: accepted if p_n sees its root
+         well within the trial step (then finished on p_n below) */
+      cplx v2, d2;
+      eval_pk(P->n, w, &v2, &d2);
+      if (cabs_(cdiv(v2, d2)) < s_acc / 2) conv = 1;
     }
     if (conv) {
-      /* finish to the working precision (a few quadratic steps) */
+      /* finish to the working precision (a few quadratic steps).  A descent
+         that reached a multiple root of q finishes on p_n, where that root
+         is simple: around a root of multiplicity mu the values of q are
+         rounding noise within ~(unit roundoff)^(1/mu) of it. */
+      /* also a plain descent that was still contracting linearly when it
+         met the stop (a multiple root reached without the acceleration) */
+      if (P->kind == 2 && !on_pn && (mult > 1 || r_last > 0.2)) {
+        cplx v2, d2;
+        eval_pk(P->n, w, &v2, &d2);
+        real s_pn = cabs_(cdiv(v2, d2));
+        if (s_pn < (mult > 1 ? s_acc / 2 : 1e-6 * (1 + cabs_(w)))) {
+          on_pn = 1;
+          s = 1;
+        }
+      }
       for (int k = 0; k < 8 && s > R_TOL_FINAL; ++k) {
         cplx v, dv;
-        eval_P(P, w, &v, &dv);
+        if (on_pn) eval_pk(P->n, w, &v, &dv); else eval_P(P, w, &v, &dv);
         cplx step = cdiv(v, dv);
         real s2 = cabs_(step);
+        /* q_{l,n}: within the rounding noise of a root of high multiplicity
+           a step may fall below the stop by chance; the next one then is
+           not small, and the point is no root */
+        if (P->kind == 2 && k == 0 && !on_pn && !(s2 <= 1e-6 * (1 + cabs_(w)))) {
+          conv = 0;
+          break;
+        }
         w = csub(w, step);
         st->desc_newton++;
         if (!(s2 < s)) { s = s2; break; }
         s = s2;
       }
+    }
+    if (conv) {
 #if ORACLE_MUTANT != 5 /* mutant 5 plants a missing conjugate fold */
       if (w.im < 0) w.im = -w.im; /* conjugate fold: the root set is symmetric */
 #endif
@@ -398,8 +513,33 @@ static int gcd_i(int a, int b) {
   while (b) { int t = a % b; a = b; b = t; }
   return a;
 }
+static int is_zero_q(int j, int k, cplx c, real tau) {
+  /* q_{j,k}(c) = p_{j+k}(c) - p_j(c) */
+  cplx v1, d1, v2, d2;
+  eval_pk(j + k, c, &v1, &d1);
+  eval_pk(j, c, &v2, &d2);
+  return is_zero_step(csub(v1, v2), csub(d1, d2), tau);
+}
 static void classify(const poly* P, cplx c, real tau, int* a, int* b) {
   cplx v, dv;
+  if (P->kind == 2) {
+    /* root of q_{l,n} (Thm fact_mis): Hyp(k) for the smallest k | n with
+       p_k(c) = 0; otherwise Mis(j,k): k the smallest divisor of n with
+       q_{l,k}(c) = 0, then j the smallest preperiod with q_{j,k}(c) = 0
+       (q_{j,k} vanishes on Mis(j0,k0) exactly when j >= j0 and k0 | k) */
+    for (int k = 1; k <= P->n; ++k) {
+      if (P->n % k) continue;
+      eval_pk(k, c, &v, &dv);
+      if (is_zero_step(v, dv, tau)) { *a = 0; *b = k; return; }
+    }
+    for (int k = 1; k <= P->n; ++k) {
+      if (P->n % k || !is_zero_q(P->l, k, c, tau)) continue;
+      for (int j = 2; j <= P->l; ++j)
+        if (is_zero_q(j, k, c, tau)) { *a = j; *b = k; return; }
+    }
+    *a = -1; *b = -1;
+    return;
+  }
   if (P->kind == 0) {
     for (int k = 1; k <= P->n; ++k) {
       if (P->n % k) continue;
@@ -488,6 +628,9 @@ long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
   for (long d = P.degree; d > 1; d >>= 1) log2d += 1;
   int cap_steps = (int)ceil(I_N * log2d);
   if (cap_steps < 20) cap_steps = 20;
+  /* q_{l,n}: descents to multiple roots contract linearly before their
+     multiplicity is recognised: twice the cap of Algorithm S_par */
+  if (P.kind == 2) cap_steps *= 2;
   real eps = (real)eps_dup;
   long nfull = 0;
   cplx* full = NULL;
@@ -504,6 +647,29 @@ long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
     long nreal = 0;
     for (long i = 0; i < nr; ++i) nreal += (reps[i].im == 0);
     nfull = nreal + 2 * (nr - nreal);
+    long nmult = nfull;
+    if (P.kind == 2) {
+      /* q_{l,n}: a hyperbolic root is polished as the simple root of p_k it
+         is, and counts eta_l(k) times (Thm fact_mis) */
+      nmult = 0;
+      for (long i = 0; i < nr; ++i) {
+        int a, b;
+        classify(&P, reps[i], R_TOL_CLASS, &a, &b);
+        long mu = 1;
+        if (a == 0 && b > 0) {
+          for (int k = 0; k < 8; ++k) {
+            cplx v, dv;
+            eval_pk(b, reps[i], &v, &dv);
+            cplx step = cdiv(v, dv);
+            if (!cfinite(step)) break;
+            reps[i] = csub(reps[i], step);
+            if (reps[i].im != 0 && rabs(reps[i].im) < eps / 2) reps[i].im = 0;
+          }
+          mu = (P.l - 1) / b + 2;
+        }
+        nmult += mu * (reps[i].im == 0 ? 1 : 2);
+      }
+    }
     free(full);
     full = (cplx*)malloc(sizeof(cplx) * (size_t)(nfull + 1));
     long w = 0;
@@ -517,11 +683,12 @@ long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
     s1.desc_newton += st->desc_newton;
     s1.retries = attempt;
     s1.n_roots = nfull;
+    s1.n_mult = nmult;
     s1.n_real = nreal;
     s1.M = M;
     s1.cL = cL;
     *st = s1;
-    if (frac < 1.0 || nfull >= P.degree) break;
+    if (frac < 1.0 || nmult >= P.degree) break;
     M *= 2; /* missing roots: a finer level line contains the coarser one */
     cL *= 2;
   }

@@ -1,0 +1,99 @@
+"""Pins of the oracle's split of q_{l,n} = p_{l+n} - p_l, whose roots are
+multiple (Thm fact_mis).  Each pin comes from outside the oracle:
+
+* Thm fact_mis with eq. MisCount and Thm countingHyp: the distinct roots are
+  Hyp(k) (k | n), each of multiplicity eta_l(k) = floor((l-1)/k) + 2, and
+  Mis(j,k) (2 <= j <= l, k | n), simple; the multiplicities add up to
+  deg q_{l,n} = 2^(l+n-1).  Checked type by type for every l + n <= 10.
+* the worked factorisation q_{2,4} = h_1^3 h_2^2 h_4^2 m_{2,1} m_{2,2} m_{2,4}
+  (Appendix, proof of Thm fact_mis).
+* eq. hypCase: q_{1,n} = p_n^2, so its roots are those of p_n, each double.
+* a library root finder on the exact integer coefficients of q_{l,n} (built
+  here with Python integers from p_{k+1} = p_k^2 + c): its roots, clustered,
+  give the same distinct roots and cluster sizes (the multiplicities).
+
+A plausible slip fails one of them: a wrong sign in q (p_{l+n} + p_l is
+s_{l+1,n}, whose roots are simple), p_{l-1} for p_l (then eta is off by one),
+a missed multiple root (the multiplicities fall short of the degree), or a
+multiple root split into close copies (extra distinct roots)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import counts
+
+
+def _hist(r):
+    h = {}
+    for (a, b) in map(tuple, r["type"]):
+        h[(int(a), int(b))] = h.get((int(a), int(b)), 0) + 1
+    return h
+
+
+@pytest.mark.parametrize("l,n", [(l, s - l) for s in range(2, 11) for l in range(1, s)])
+def test_types_and_multiplicities_follow_thm_fact_mis(l, n):
+    r = oracle.split("q", n, l=l)
+    assert _hist(r) == counts.type_histogram_q(l, n)
+    assert int(r["mult"].sum()) == counts.deg_q(l, n) == r["stats"]["n_mult"]
+    hyp = r["type"][:, 0] == 0
+    assert np.all(r["mult"][hyp] == (l - 1) // r["type"][hyp, 1] + 2)
+    assert np.all(r["mult"][~hyp] == 1)
+
+
+def test_worked_factorisation_q_2_4():
+    r = oracle.split("q", 4, l=2)
+    mult = {}
+    for (a, b), m in zip(map(tuple, r["type"]), r["mult"]):
+        mult.setdefault((int(a), int(b)), set()).add(int(m))
+    # h_1^3 h_2^2 h_4^2: c = 0 triple, c = -1 double, the 6 centres of period 4 double
+    assert mult[(0, 1)] == {3} and mult[(0, 2)] == {2} and mult[(0, 4)] == {2}
+    assert mult[(2, 1)] == mult[(2, 2)] == mult[(2, 4)] == {1}
+    z = r["roots"]
+    assert np.min(np.abs(z)) < 1e-30 and np.min(np.abs(z + 1)) < 1e-30
+
+
+@pytest.mark.parametrize("n", [3, 5, 6])
+def test_q_1_n_is_p_n_squared(n):
+    rq = oracle.split("q", n, l=1)
+    rp = oracle.split("hyp", n)
+    assert np.all(rq["mult"] == 2) and rq["n_roots"] == rp["n_roots"]
+    assert np.max(np.abs(np.sort_complex(rq["roots"]) - np.sort_complex(rp["roots"]))) < 1e-25
+
+
+def _q_coeffs(l, n):
+    """Integer coefficients of q_{l,n}(c), highest degree first."""
+    p = [[0]]  # p_0 = 0, as coefficient lists lowest degree first
+    for _ in range(l + n):
+        a = p[-1]
+        sq = [0] * (2 * len(a) - 1)
+        for i, x in enumerate(a):
+            if x:
+                for j, y in enumerate(a):
+                    sq[i + j] += x * y
+        sq += [0]
+        sq[1] += 1  # + c
+        while len(sq) > 1 and sq[-1] == 0:
+            sq.pop()
+        p.append(sq)
+    hi, lo = p[l + n], p[l] + [0] * (len(p[l + n]) - len(p[l]))
+    q = [x - y for x, y in zip(hi, lo)]
+    while q and q[-1] == 0:
+        q.pop()
+    return [float(x) for x in reversed(q)]
+
+
+@pytest.mark.parametrize("l,n", [(2, 2), (3, 2), (2, 3), (4, 1), (1, 4)])
+def test_library_roots_of_exact_coefficients(l, n):
+    """numpy.roots on the exact coefficients: a root of multiplicity mu comes
+    out as mu close copies (spread ~ roundoff^(1/mu)); clustering them gives
+    the distinct roots and their multiplicities."""
+    lib = np.roots(_q_coeffs(l, n))
+    r = oracle.split("q", n, l=l)
+    z, mu = r["roots"], r["mult"]
+    # each library root is nearest to one oracle root; count them per root
+    owner = np.array([np.argmin(np.abs(z - w)) for w in lib])
+    assert np.array_equal(np.bincount(owner, minlength=z.size), mu)
+    for w, k in zip(lib, owner):
+        assert abs(w - z[k]) < 10 * 1e-12 ** (1.0 / mu[k])  # a root of multiplicity mu moves ~ eps^(1/mu)
