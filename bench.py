@@ -41,6 +41,7 @@ CONFIGS = {
     "hyp29dd": ("hyp", 0, 29, "dd"),
     "hyp31dd": ("hyp", 0, 31, "dd"),  # 2^30 roots, ~230 GB of device memory
     "mis16": ("misbatch", 0, 16, "fp64"),  # every s_{l,n}, l >= 2, n >= 1, l + n <= 16, one pass
+    "q18": ("q", 9, 9, "fp64"),  # q_{9,9} = p_18 - p_9 with its multiple roots (Thm fact_mis)
 }
 
 
@@ -75,13 +76,14 @@ SM_MAX_MHZ = 2070.0
 TRAFFIC = {("hyp20", "k_descend"): 16.8e6}
 
 
-def roofline(prec: str, m: int, stats: list, config: str = "") -> dict:
+def roofline(prec: str, m: int, stats: list, config: str = "", desc_flops: int | None = None) -> dict:
     """ALU roofline of the dominant kernel (walk or descent) from the
     library's own CUDA events (on the launch stream, inside the graph) and
     its own step counters.  Binary32 steps of the mixed tier count at the
     binary64/binary32 peak ratio, so frac is the share of the binary64 pipe
     the same work would need.  Walk time excludes the seed lifts."""
     fl = newton_flops(m)
+    dfl = fl if desc_flops is None else desc_flops
     ratio = FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS
     s0 = stats[-1]
     walk_ms = statistics.mean(s["ms_walk"] - s["ms_seeds"] for s in stats)
@@ -89,7 +91,7 @@ def roofline(prec: str, m: int, stats: list, config: str = "") -> dict:
     walk_steps = s0["walk_newton"] - s0["seed_newton"]
     if prec == "fp64":
         walk_eq = walk_steps * fl
-        desc_eq = s0["desc_newton"] * fl
+        desc_eq = s0["desc_newton"] * dfl
     else:  # mixed walk: binary32 sub-steps; descents: binary32 then binary64 finish
         walk_eq = walk_steps * fl * ratio
         desc_eq = (s0["desc_newton"] - s0["desc_fp32"]) * fl + s0["desc_fp32"] * fl * ratio
@@ -103,7 +105,8 @@ def roofline(prec: str, m: int, stats: list, config: str = "") -> dict:
             "ms_per_launch": ms, "flops_per_launch": eq,
             "peak_source": "nominal binary64 1.25 TFLOP/s at 2070 MHz (profiling recipe table)"
                            + ("" if prec == "fp64" else "; binary32 steps weighted by 1.25/80.5"),
-            "work": "Newton steps x (13 m + 24) flops, m = %d, steps counted by the kernel" % m}
+            "work": ("Newton steps x (13 m + 24) flops, m = %d, steps counted by the kernel" % m)
+                    + ("" if desc_flops is None else "; descents %d flops per step (product form)" % desc_flops)}
 
 
 class ClockSampler:
@@ -207,12 +210,21 @@ def whole_job_rate(world: int, units_per_rank: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+def oracle_units(kind: str, l: int, n: int) -> int:
+    """Roots the whole split yields: the degree, or for q_{l,n} its distinct
+    roots (Thm fact_mis, from the oracle's closed-form counts)."""
+    import oracle
+    if kind == "q":
+        return sum(oracle.counts.type_histogram_q(l, n).values())
+    return oracle.degree(kind, n, l)
+
+
 def cpu_baseline(kind: str, l: int, n: int, target_s: float = 15.0) -> dict:
     """The binary64 oracle, as it stands, on a bounded sample of the same
     workload: the first fraction of the level line (walk + descents + set).
     Rate = roots in that fraction of the line / time (single thread)."""
     import oracle
-    d = oracle.degree(kind, n, l)
+    d = oracle_units(kind, l, n)
     frac = 1.0 / 64
     t0 = time.perf_counter()
     oracle.split(kind, n, l=l, fp64=True, frac=frac, want_types=False)
@@ -225,7 +237,7 @@ def cpu_baseline(kind: str, l: int, n: int, target_s: float = 15.0) -> dict:
         dt = time.perf_counter() - t0
     return {"value": d * frac / dt, "unit": "roots/s", "cores": 1, "kind": "oracle",
             "sample": "binary64 oracle (same algorithm, sequential walk), first %.4f of the level line of "
-                      "%s n=%d, %.1f s, 1 thread; rate = degree x fraction / time" % (frac, kind, n, dt)}
+                      "%s n=%d, %.1f s, 1 thread; rate = roots x fraction / time" % (frac, kind, n, dt)}
 
 
 def run_reference(args, cfg):
@@ -234,7 +246,7 @@ def run_reference(args, cfg):
     if rank != 0:
         return
     import oracle
-    d = oracle.degree(kind, n, l)
+    d = oracle_units(kind, l, n)
     frac = 1.0 / 32  # each step: a bounded sample of the same workload
     for _ in range(args.warmup):
         oracle.split(kind, n, l=l, fp64=True, frac=frac, want_types=False)
@@ -286,7 +298,7 @@ def main():
     if kind == "misbatch":
         d = sum(2 ** (a + b - 2) for a, b in mt.misiurewicz_pairs(n))
     else:
-        d = mt.degree(kind, n, l)
+        d = mt.degree(kind, n, l)  # q_{l,n}: the degree bounds the distinct roots
     stream = torch.cuda.current_stream()
     work = mt.Workspace()
     roots = torch.empty((d, 2), dtype=torch.float64, device="cuda")
@@ -312,6 +324,10 @@ def main():
         if kind == "misbatch":
             _, _, _, st, _ = mt.split_misiurewicz_batch(n, pp, work=work)
             return _BatchResult(st)
+        if kind == "q":
+            rq = mt.split_misiurewicz_q(l, n, work=work)
+            roots[:rq.roots.shape[0]].copy_(torch.view_as_real(rq.roots))
+            return rq
         return mt.split_misiurewicz(l, n, pp, work=work, out=roots)
 
     def timed(p, steps):
@@ -331,7 +347,10 @@ def main():
 
     for _ in range(max(args.warmup, 3)):
         r = step()
-    assert r.stats["n_roots"] == d and r.stats["n_cert_pass"] == d, r.stats
+    if kind == "q":  # distinct roots, every one certified, multiplicities adding up to the degree
+        assert r.stats["n_mult"] == d and r.stats["n_cert_pass"] == r.stats["n_roots"], r.stats
+    else:
+        assert r.stats["n_roots"] == d and r.stats["n_cert_pass"] == d, r.stats
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -376,7 +395,11 @@ def main():
     clocks = sampler.stop()
 
     s0 = stats[-1]
-    m = n if kind == "hyp" else (n - 1 if kind == "misbatch" else l + n - 1)
+    m = n if kind == "hyp" else (n - 1 if kind == "misbatch" else (l + n if kind == "q" else l + n - 1))
+    # q_{l,n} descents evaluate the product form: n orbit steps, then l times
+    # two orbit steps (26 flops) and the product update (24 flops), + 24
+    desc_flops = 13 * n + 50 * l + 24 if kind == "q" else None
+    n_e2e = s0["n_roots"] if kind == "q" else d
     line = {
         "metric": METRIC, "value": value, "unit": "roots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -387,13 +410,16 @@ def main():
                        if kind == "hyp" else
                        ("all s_{l,n} with l >= 2, n >= 1, l + n <= %d (%d polynomials, %d roots), one pass, "
                         "binary64, all certified" % (n, len(mt.misiurewicz_pairs(n)), d))
-                       if kind == "misbatch" else "s_{%d,%d}" % (l, n)),
+                       if kind == "misbatch" else
+                       ("q_{%d,%d} = p_%d - p_%d, %d distinct roots (degree %d with multiplicities, Thm fact_mis), "
+                        "binary64, all certified" % (l, n, l + n, l, s0["n_roots"], d))
+                       if kind == "q" else "s_{%d,%d}" % (l, n)),
                    "precision": prec, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "e2e": {"value": whole_job_rate(world, d, e2e_s), "unit": "roots/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": d * 16 * (2 if roots_lo is not None else 1) + 1024,
+        "e2e": {"value": whole_job_rate(world, n_e2e, e2e_s), "unit": "roots/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": n_e2e * 16 * (2 if roots_lo is not None else 1) + 1024,
                 "note": "input is the integer n (no device input); result roots copied to pinned host memory"},
-        "roofline": roofline(prec, m, stats, args.config),
+        "roofline": roofline(prec, m, stats, args.config, desc_flops),
         "gpu_launches": int(sum(s["n_launches"] for s in stats)),
         "clocks": clocks,
         "detail": {"ms_walk": s0["ms_walk"], "ms_descend": s0["ms_descend"], "ms_dedup": s0["ms_dedup"],

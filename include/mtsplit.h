@@ -108,7 +108,9 @@ typedef struct {
   int64_t walk_fail;       /* level-line chunks whose end missed the next seed    */
   int64_t n_cert_pass;     /* roots (full list) that passed the disk certificate  */
   int64_t count_by_type[MT_MAX_TYPES]; /* p_n: [k] = roots of exact period k;
-                                          s_{l,n}: [k] = Mis(l,k), [32+k] = Hyp(k) */
+                                          s_{l,n}: [k] = Mis(l,k), [32+k] = Hyp(k);
+                                          q_{l,n}: the same, and [0] = Mis(j,k),
+                                          j < l (distinct roots, full list)      */
   int32_t M, c_L;          /* values finally used                                  */
   int32_t retries;         /* (M, c_L) doublings performed                         */
   int32_t n_chunks;        /* level-line chunks (lanes of the walk)                */
@@ -133,6 +135,8 @@ typedef struct {
   int32_t reserved;
   int64_t n_finish;        /* binary64 finishes in the mixed tier (one per run of
                               descents that reached the same root in binary32)   */
+  int64_t n_mult;          /* roots counted with multiplicity (q_{l,n}; n_roots
+                              for the polynomials with simple roots)            */
 } mt_stats;
 
 /* Defaults documented field by field above. */
@@ -143,8 +147,8 @@ MT_API int64_t mt_degree_hyperbolic(int n);
 /* deg s_{l,n} = 2^(l+n-2) (l >= 2, n >= 1, l + n <= 41); -1 if out of range. */
 MT_API int64_t mt_degree_misiurewicz(int l, int n);
 
-/* Scratch bytes a split of P needs (kind 0: p_n, kind 1: s_{l,n}) with these
-   options; 0 if the arguments are invalid. */
+/* Scratch bytes a split of P needs (kind 0: p_n, kind 1: s_{l,n}, kind 2:
+   q_{l,n}) with these options; 0 if the arguments are invalid. */
 MT_API size_t mt_workspace_bytes(int kind, int l, int n, const mt_options* opts);
 
 /* Split p_n (Sec. 4.2, Algorithm S_par; hypQuick of Sec. 6.3.1).
@@ -165,6 +169,25 @@ MT_API mt_status mt_split_misiurewicz(int l, int n, const mt_options* opts, doub
                                double* d_roots_lo, int64_t cap, uint8_t* d_is_mis, void* d_work,
                                size_t work_bytes, int64_t* n_out, mt_stats* stats);
 
+/* Split q_{l,n} = p_{l+n} - p_l (eq. def:mis; misQuick of Sec. 6.3.1), whose
+   roots are multiple (Thm fact_mis): Hyp(k), k | n, of multiplicity
+   eta_l(k) = floor((l-1)/k) + 2, and Mis(j,k), 2 <= j <= l, k | n, simple.
+   l >= 1, n >= 1, l + n <= 40; binary64 only (opts->prec = MT_FP64, else
+   MT_EINVAL).  d_roots: [cap][2] doubles, receives the distinct roots sorted
+   by (Re, Im); *n_out their number.  d_mult, d_pre, d_per: NULL or [cap]
+   bytes: multiplicity, preperiod j (0 for Hyp) and period k of each root
+   (255 / 0 where no type matched).  Complete when the multiplicities add up
+   to 2^(l+n-1) (stats->n_mult); else MT_EINCOMPLETE after the retries.
+   Every root is certified (Thm proofRoots): a Mis root as a simple root of
+   q, a Hyp root as a simple root of p_n (MT_ECERT if one fails).
+   Descents on q that contract linearly take the multiplicity step of eq.
+   newtonAcc; q is evaluated in the product form p_n prod_{j<=l} s_{j,n} of
+   eq. polySimple, which keeps its relative accuracy up to a multiple root.
+   Workspace: mt_workspace_bytes(2, l, n, opts). */
+MT_API mt_status mt_split_misiurewicz_q(int l, int n, const mt_options* opts, double* d_roots, int64_t cap,
+                                        uint8_t* d_mult, uint8_t* d_pre, uint8_t* d_per, void* d_work,
+                                        size_t work_bytes, int64_t* n_out, mt_stats* stats);
+
 /* Split every s_{l,n} with l >= 2, n >= 1, l + n <= max_order in ONE pass:
    one persistent launch drains the level-line chunks of all polynomials,
    one persistent launch drains all descents.  Roots of pair number p (pairs
@@ -178,7 +201,8 @@ MT_API mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opt
                                      void* d_work, size_t work_bytes, int64_t* h_offsets,
                                      mt_stats* stats);
 
-/* Certify given roots of P (kind 0: p_n, kind 1: s_{l,n}) with the disk
+/* Certify given roots of P (kind 0: p_n, kind 1: s_{l,n}, kind 2: q_{l,n},
+   binary64 only, a root typed Hyp(k) proven as a root of p_n) with the disk
    test of Thm proofRoots evaluated in disk arithmetic (Thm diskArithmetic):
    root j gets the radius r_j = min(tol, 0.45 * distance to the nearest other
    root or conjugate) and passes iff r_j * dist(0, B') > sup |P(c_j)| where
@@ -204,7 +228,8 @@ MT_API mt_status mt_certify(int kind, int l, int n, const double* d_roots, const
    converges to that root.  d_basin[j] = eps_j, or 0 where no radius passes
    (r_j = 0, or no eps above 3 eta_j).  d_roots_lo: NULL or the low parts
    (double-double centres).  eps_max: 0 -> 1e-6.  *n_pass: roots with a
-   basin radius.  Workspace: mt_certify_workspace_bytes(count). */
+   basin radius.  q_{l,n} (kind 2): MT_EINVAL, the theorem is for simple
+   roots.  Workspace: mt_certify_workspace_bytes(count). */
 MT_API mt_status mt_certify_basin(int kind, int l, int n, const double* d_roots, const double* d_roots_lo,
                                   int64_t count, const double* d_radius, double eps_max, double* d_basin,
                                   void* d_work, size_t work_bytes, int64_t* n_pass, void* stream);
@@ -248,7 +273,8 @@ MT_API mt_status mt_autotune(int kind, int l, int n, const mt_options* opts, dou
 
 /* Orbit evaluation (Sec. 1, eq. def:hyp_poly, and its c-derivative): for
    each point d_c[2i], d_c[2i+1], writes d_out[4i..4i+3] = Re P, Im P,
-   Re P', Im P' in binary64.  No workspace. */
+   Re P', Im P' in binary64 (q_{l,n}: the product form of eq. polySimple).
+   No workspace. */
 MT_API mt_status mt_eval(int kind, int l, int n, const double* d_c, int64_t count, double* d_out,
                   void* stream);
 
@@ -268,8 +294,9 @@ MT_API mt_status mt_descend(int kind, int l, int n, const mt_options* opts, cons
                      size_t work_bytes, mt_stats* stats);
 
 /* Step a6 only: type of each root (eq. def:hyp / def:mis), d_type[i] =
-   period k for p_n, or k (Mis(l,k)) / 32 + k (Hyp(k)) for s_{l,n};
-   255 if no type was recognised.  tau: Newton-size threshold (0 -> default). */
+   period k for p_n, or k (Mis(l,k)) / 32 + k (Hyp(k)) for s_{l,n} and
+   q_{l,n}, and 0 for Mis(j,k), j < l, of q_{l,n}; 255 if no type was
+   recognised.  tau: Newton-size threshold (0 -> default). */
 MT_API mt_status mt_classify(int kind, int l, int n, const double* d_roots, int64_t count, double tau,
                       uint8_t* d_type, void* stream);
 

@@ -18,7 +18,7 @@ from dataclasses import dataclass
 from . import _lib
 from ._lib import MtError, Options, Stats, check, load  # noqa: F401
 
-KIND = {"hyp": 0, "mis": 1}
+KIND = {"hyp": 0, "mis": 1, "q": 2}
 
 
 def _torch():
@@ -48,7 +48,10 @@ def options(prec: str = "fp64", stream=None, **kw) -> Options:
 
 def degree(kind: str, n: int, l: int = 0) -> int:
     L = load()
-    d = L.mt_degree_hyperbolic(n) if kind == "hyp" else L.mt_degree_misiurewicz(l, n)
+    if kind == "q":  # deg q_{l,n} = deg p_{l+n}
+        d = L.mt_degree_hyperbolic(l + n) if l >= 1 else -1
+    else:
+        d = L.mt_degree_hyperbolic(n) if kind == "hyp" else L.mt_degree_misiurewicz(l, n)
     if d < 0:
         raise ValueError("polynomial out of range")
     return int(d)
@@ -99,6 +102,45 @@ def split_misiurewicz(l: int, n: int, prec: str = "fp64", *, work: Workspace | N
                       **kw) -> SplitResult:
     """All 2^(l+n-2) roots of s_{l,n}, with the Mis(l,n) mask (eq. def:mis)."""
     return _split("mis", n, l, prec, work, want_lo, check_status, out, out_lo, kw)
+
+
+@dataclass
+class SplitResultQ:
+    roots: "object"   # complex128 tensor [n_roots]: the distinct roots, sorted by (Re, Im)
+    mult: "object"    # uint8 tensor: multiplicity in q_{l,n} (Thm fact_mis)
+    pre: "object"     # uint8 tensor: preperiod j (0 for a hyperbolic centre)
+    per: "object"     # uint8 tensor: period k
+    stats: dict
+    status: int
+
+
+def split_misiurewicz_q(l: int, n: int, prec: str = "fp64", *, work: Workspace | None = None,
+                        check_status: bool = True, **kw) -> SplitResultQ:
+    """The distinct roots of q_{l,n} = p_{l+n} - p_l with their multiplicities
+    and types (Thm fact_mis), binary64 (mt_split_misiurewicz_q)."""
+    torch = _torch()
+    L = load()
+    o = options(prec, **kw)
+    d = degree("q", n, l)
+    nbytes = int(L.mt_workspace_bytes(2, l, n, ctypes.byref(o)))
+    if nbytes == 0:
+        raise ValueError("invalid options for this polynomial")
+    work = work or Workspace()
+    buf = work.ensure(nbytes)
+    roots = torch.empty((d, 2), dtype=torch.float64, device="cuda")
+    mult = torch.empty(d, dtype=torch.uint8, device="cuda")
+    pre = torch.empty(d, dtype=torch.uint8, device="cuda")
+    per = torch.empty(d, dtype=torch.uint8, device="cuda")
+    n_out = ctypes.c_int64(0)
+    st = Stats()
+    rc = L.mt_split_misiurewicz_q(l, n, ctypes.byref(o), roots.data_ptr(), d, mult.data_ptr(), pre.data_ptr(),
+                                  per.data_ptr(), buf.data_ptr(), buf.numel(), ctypes.byref(n_out),
+                                  ctypes.byref(st))
+    if check_status:
+        check(rc)
+    torch.cuda.current_stream().synchronize()
+    m = min(int(n_out.value), d)
+    return SplitResultQ(torch.view_as_complex(roots[:m]), mult[:m], pre[:m], per[:m], st.as_dict(), rc)
 
 
 def _split(kind, n, l, prec, work, want_lo, check_status, out, out_lo, kw) -> SplitResult:

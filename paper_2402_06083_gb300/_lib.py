@@ -21,7 +21,7 @@ MT_MAX_TYPES = 64
 # every symbol include/mtsplit.h declares
 EXPORTS = (
     "mt_default_options", "mt_degree_hyperbolic", "mt_degree_misiurewicz", "mt_workspace_bytes",
-    "mt_split_hyperbolic", "mt_split_misiurewicz", "mt_misiurewicz_pairs",
+    "mt_split_hyperbolic", "mt_split_misiurewicz", "mt_split_misiurewicz_q", "mt_misiurewicz_pairs",
     "mt_workspace_bytes_misiurewicz_batch", "mt_split_misiurewicz_batch",
     "mt_certify_workspace_bytes", "mt_certify", "mt_certify_basin", "mt_separation_workspace_bytes", "mt_separation",
     "mt_eval", "mt_level_line",
@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
         ("prec_used", ctypes.c_int32), ("ms_dd", ctypes.c_float),
         ("n_zones", ctypes.c_int64), ("n_zone_roots", ctypes.c_int64), ("n_dd_pieces", ctypes.c_int64),
         ("seed_newton", ctypes.c_int64), ("desc_fp32", ctypes.c_int64), ("ms_seeds", ctypes.c_float),
-        ("reserved", ctypes.c_int32), ("n_finish", ctypes.c_int64),
+        ("reserved", ctypes.c_int32), ("n_finish", ctypes.c_int64), ("n_mult", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -100,6 +100,8 @@ def load() -> ctypes.CDLL:
         "mt_split_hyperbolic": (ctypes.c_int, [ctypes.c_int, op, vp, vp, i64, vp, ctypes.c_size_t, i64p, sp]),
         "mt_split_misiurewicz": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, op, vp, vp, i64, vp, vp,
                                                 ctypes.c_size_t, i64p, sp]),
+        "mt_split_misiurewicz_q": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, op, vp, i64, vp, vp, vp, vp,
+                                                  ctypes.c_size_t, i64p, sp]),
         "mt_misiurewicz_pairs": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                 ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
         "mt_workspace_bytes_misiurewicz_batch": (ctypes.c_size_t, [ctypes.c_int, op]),

@@ -73,6 +73,7 @@ struct Carve {
 bool valid_poly(int kind, int l, int n) {
   if (kind == 0) return n >= 1 && n <= 40;
   if (kind == 1) return l >= 2 && n >= 1 && l + n <= 41;
+  if (kind == 2) return l >= 1 && n >= 1 && l + n <= 40;
   return false;
 }
 
@@ -85,10 +86,14 @@ PolyDev make_poly(int kind, int l, int n) {
     P.m = n;
     P.lcap = -1;
     P.log2d = n - 1;
-  } else {
+  } else if (kind == 1) {
     P.m = l + n - 1;
     P.lcap = l - 1;
     P.log2d = l + n - 2;
+  } else {  // q_{l,n} = p_{l+n} - p_l
+    P.m = l + n;
+    P.lcap = l;
+    P.log2d = l + n - 1;
   }
   return P;
 }
@@ -216,6 +221,9 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   p.tol = (o && o->tol > 0 && !dd) ? o->tol : 1e-13;
   const double IN = (kind == 0) ? 1.0 : 2.6;  // Sec. 4.2
   p.cap = std::max(20, (int)std::ceil(IN * p.P.log2d));
+  // q_{l,n}: descents to multiple roots contract linearly until their
+  // multiplicity is recognised: twice the cap of Algorithm S_par
+  if (kind == 2) p.cap *= 2;
   p.eps = (o && o->eps_dup > 0) ? o->eps_dup : default_eps(kind, l, n);
   // the step that meets tol leaves an error ~ tol^2 / (root separation); keep
   // it well inside the separation pixel so duplicates of a root always merge
@@ -406,6 +414,7 @@ void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
   st->max_cert_radius = h.n_cert_pass ? mx : 0.0;
   st->eps_dup = p.eps;
   st->prec_used = p.prec;
+  st->n_mult = (p.kind == 2) ? (int64_t)h.n_mult_full : (int64_t)h.n_full;
 }
 
 // Stage boundaries are marked with events; inside a stream capture they
@@ -457,7 +466,7 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
   CK(launch_classify(p.P, b.reps, &b.ctr->n_reps, p.S, p.eps, 0, b.type, b.mult, b.ctr, s));
   CK(launch_exclusive_scan(b.mult, b.mpos, p.S, b.scan_tmp, &b.ctr->n_full, s));
   CK(launch_certify(p.P, b.reps, &b.ctr->n_reps, p.S, p.cert_tol, b.mult, b.pass, b.radius, b.ctr,
-                    s));
+                    s, SegView(), p.kind == 2 ? b.type : nullptr));
   CK(mark(ev.e[4], s, capturing));
   const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
   CK(launch_emit(b.reps, &b.ctr->n_reps, p.S, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out,
@@ -710,8 +719,10 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
       rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h);
     if (rc != MT_OK) return rc;
     // retry on missing roots or on a level-line chunk that skipped a turn
-    bool done = (int64_t)h.n_full == p.degree && h.walk_fail == 0;
-    const bool certified = (int64_t)h.n_full == p.degree && h.n_cert_pass == h.n_full;
+    // (q_{l,n}: the roots counted with their multiplicities, Thm fact_mis)
+    const int64_t counted = (kind == 2) ? (int64_t)h.n_mult_full : (int64_t)h.n_full;
+    bool done = counted == p.degree && h.walk_fail == 0;
+    const bool certified = counted == p.degree && h.n_cert_pass == h.n_full;
     dd_ran = false;
     if (p.dd && (p.dd_all || !certified)) {
       // MT_DD: a certified complete list is the goal (it proves itself)
@@ -752,9 +763,10 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     }
   }
   if (n_out) *n_out = (int64_t)h.n_full;
-  if ((int64_t)h.n_full != p.degree)
-    return fail(MT_EINCOMPLETE, "found %lld roots, degree %lld (after %d retries)",
-                (long long)h.n_full, (long long)p.degree, retry);
+  const int64_t counted = (kind == 2) ? (int64_t)h.n_mult_full : (int64_t)h.n_full;
+  if (counted != p.degree)
+    return fail(MT_EINCOMPLETE, "found %lld roots%s, degree %lld (after %d retries)", (long long)counted,
+                kind == 2 ? " with multiplicity" : "", (long long)p.degree, retry);
   if ((int64_t)h.n_full > cap)
     return fail(MT_ECAPACITY, "%lld roots do not fit in cap %lld", (long long)h.n_full,
                 (long long)cap);
@@ -987,6 +999,29 @@ mt_status mt_split_misiurewicz(int l, int n, const mt_options* opts, double* d_r
                     stats);
 }
 
+mt_status mt_split_misiurewicz_q(int l, int n, const mt_options* opts, double* d_roots, int64_t cap,
+                                 uint8_t* d_mult, uint8_t* d_pre, uint8_t* d_per, void* d_work,
+                                 size_t work_bytes, int64_t* n_out, mt_stats* stats) {
+  g_err.clear();
+  if (opts && opts->prec != MT_FP64) return fail(MT_EINVAL, "q_{l,n} is split in binary64 (MT_FP64) only");
+  int64_t nr = 0;
+  const mt_status rc = split_impl(2, l, n, opts, d_roots, nullptr, cap, nullptr, d_work, work_bytes, &nr, stats);
+  if (n_out) *n_out = nr;
+  if (rc != MT_OK && rc != MT_EINCOMPLETE && rc != MT_ECERT) return rc;
+  if (d_mult || d_pre || d_per) {  // also for an incomplete or uncertified list
+    mt_options dflt;
+    mt_default_options(&dflt);
+    const mt_options* o = opts ? opts : &dflt;
+    const double tau = (o->eps_dup > 0) ? o->eps_dup : default_eps(2, l, n);
+    cudaStream_t s = (cudaStream_t)o->stream;
+    const std::string err = g_err;  // keep the split's message
+    CK(launch_type_q(make_poly(2, l, n), (const double2*)d_roots, std::min(nr, cap), tau, d_pre, d_per, d_mult,
+                     s));
+    g_err = err;
+  }
+  return rc;
+}
+
 int mt_misiurewicz_pairs(int max_order, int* h_l, int* h_n, int capacity) {
   int k = 0;
   for (int l = 2; l < max_order; ++l)
@@ -1186,11 +1221,20 @@ mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double
   CK(launch_init_counters(ctr, s));
   CK(launch_keys_plain((const double2*)d_roots, count, keys, vals, s));
   CK(radix_sort_pairs(keys, vals, keys_alt, vals_alt, count, rtmp, s));
-  if (d_roots_lo)
+  if (d_roots_lo) {
+    if (kind == 2) return fail(MT_EINVAL, "q_{l,n} roots are certified in binary64 only");
     CK(dd_certify_list(P, (const double2*)d_roots, (const double2*)d_roots_lo, vals, count, tol, d_pass,
                        d_radius, ctr, s));
-  else
-    CK(launch_certify_list(P, (const double2*)d_roots, vals, count, tol, d_pass, d_radius, ctr, s));
+  } else {
+    // q_{l,n}: a root typed Hyp(k) is proven as a (simple) root of p_n; the
+    // types go in vals_alt, free after the sort
+    uint8_t* type = nullptr;
+    if (kind == 2) {
+      type = (uint8_t*)vals_alt;
+      CK(launch_type_only(P, (const double2*)d_roots, count, default_eps(2, l, n), type, s));
+    }
+    CK(launch_certify_list(P, (const double2*)d_roots, vals, count, tol, d_pass, d_radius, ctr, s, type));
+  }
   DevCounters h;
   CK(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1206,6 +1250,7 @@ mt_status mt_certify_basin(int kind, int l, int n, const double* d_roots, const 
   if (count < 0 || (count > 0 && (!d_roots || !d_radius || !d_basin))) return fail(MT_EINVAL, "bad buffers");
   if (count > 0xffffffffll) return fail(MT_EINVAL, "count too large");
   if (!(eps_max >= 0.0)) return fail(MT_EINVAL, "eps_max must be >= 0");
+  if (kind == 2) return fail(MT_EINVAL, "Thm proofContract is for simple roots: q_{l,n} has multiple roots");
   const size_t need = mt_certify_workspace_bytes(count);
   if (!d_work || work_bytes < need) return fail(MT_ENOMEM, "workspace of %zu bytes needed", need);
   cudaStream_t s = (cudaStream_t)stream;

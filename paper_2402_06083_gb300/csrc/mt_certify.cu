@@ -33,17 +33,21 @@ __device__ __forceinline__ bool newton_small_f(double vr, double vi, float dr, f
   return fma(vr, vr, vi * vi) <= tau * tau * fma(ar, ar, ai * ai);
 }
 
+// q_{l,n} (kind 2): 32 + k for Hyp(k), k | n (multiplicity eta_l(k)); k for
+// Mis(l, k); 0 for Mis(j, k) with j < l (a root of q_{l-1,n} too).
 __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, double tau) {
   const int n = P.n;
   const int len = (P.kind == 0) ? n : P.l + n;
-  const int g = (P.kind == 0) ? n : [&] {
+  const int g = (P.kind != 1) ? n : [&] {
     int a = n, b = P.l - 1;
     while (b) { int t = a % b; a = b; b = t; }
     return a;
   }();
   double zr = 0.0, zi = 0.0, lr = 0.0, li = 0.0;  // p_l
   float dzr = 0.f, dzi = 0.f, ldr = 0.f, ldi = 0.f;  // p'_l
-  int hyp = 0, mis = 0;
+  double l1r = 0.0, l1i = 0.0;                       // p_{l-1} (q_{l,n})
+  float l1dr = 0.f, l1di = 0.f;
+  int hyp = 0, mis = 0, earlier = 0;
   for (int k = 1; k <= len; ++k) {
     const float fr = __double2float_rn(zr), fi = __double2float_rn(zi);
     const float tfr = fr + fr, tfi = fi + fi;
@@ -54,15 +58,27 @@ __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, d
     const double nzi = fma(tzr, zi, ci);
     zr = nzr; zi = nzi; dzr = ndr; dzi = ndi;
     if (!hyp && k <= g && (g % k) == 0 && newton_small_f(zr, zi, dzr, dzi, tau)) hyp = k;
-    if (P.kind == 1) {
+    if (P.kind != 0) {
       if (k == P.l) { lr = zr; li = zi; ldr = dzr; ldi = dzi; }
       const int kk = k - P.l;
       if (!mis && kk >= 1 && (n % kk) == 0 &&
           newton_small_f(zr - lr, zi - li, dzr - ldr, dzi - ldi, tau))
         mis = kk;
     }
+    if (P.kind == 2 && P.l >= 2) {  // q_{l-1,k}(c) = 0 for a k | n: preperiod below l
+      if (k == P.l - 1) { l1r = zr; l1i = zi; l1dr = dzr; l1di = dzi; }
+      const int kk = k - (P.l - 1);
+      if (!earlier && kk >= 1 && (n % kk) == 0 &&
+          newton_small_f(zr - l1r, zi - l1i, dzr - l1dr, dzi - l1di, tau))
+        earlier = 1;
+    }
   }
   if (P.kind == 0) return hyp ? hyp : 255;
+  if (P.kind == 2) {
+    if (hyp) return (32 + hyp < 64) ? 32 + hyp : 255;
+    if (earlier) return 0;
+    return (mis && mis < 32) ? mis : 255;
+  }
   if (hyp) return (32 + hyp < 64) ? 32 + hyp : 255;
   if (mis) return mis < 32 ? mis : 255;
   return 255;
@@ -77,7 +93,7 @@ __global__ void k_classify(PolyDev P0, double2* __restrict__ reps,
   __syncthreads();
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nr = (int64_t)*n_reps;
-  unsigned long long nreal = 0;
+  unsigned long long nreal = 0, nmult = 0;
   if (u < cap) {
     if (u < nr) {
       const uint16_t sg = sv.rep_seg ? sv.rep_seg[u] : 0;
@@ -98,6 +114,8 @@ __global__ void k_classify(PolyDev P0, double2* __restrict__ reps,
       type[u] = (uint8_t)t;
       mult[u] = m;
       nreal += (m == 1);
+      // q_{l,n}: Hyp(k) counts eta_l(k) = floor((l-1)/k) + 2 times (Thm fact_mis)
+      nmult += (P.kind == 2 && t > 32 && t < 64) ? (unsigned long long)m * ((P.l - 1) / (t - 32) + 2) : m;
       if (t < 64) atomicAdd(&hist[t], m);
       if (sv.pstat) {
         unsigned long long* ps = sv.pstat + (size_t)sg * PSTAT_W;
@@ -111,6 +129,7 @@ __global__ void k_classify(PolyDev P0, double2* __restrict__ reps,
     }
   }
   warp_add_u64(&ctr->n_reps_real, nreal);
+  warp_add_u64(&ctr->n_mult_full, nmult);
   __syncthreads();
   for (int q = threadIdx.x; q < 64; q += blockDim.x)
     if (hist[q]) atomicAdd(&ctr->type_count[q], (unsigned long long)hist[q]);
@@ -132,6 +151,56 @@ __global__ void k_type_only(PolyDev P, const double2* __restrict__ roots, int64_
   if (i >= count) return;
   const double2 z = roots[i];
   type[i] = (uint8_t)type_of(P, z.x, z.y, tau);
+}
+
+// q_{l,n}: per output root the exact type (eq. def:mis) and its multiplicity
+// (Thm fact_mis).  Hyp(k): the smallest k | n with p_k(c) = 0, preperiod 0,
+// multiplicity eta_l(k) = floor((l-1)/k) + 2.  Otherwise Mis(j, k): k the
+// smallest divisor of n with q_{l,k}(c) = 0, then j the smallest preperiod
+// with q_{j,k}(c) = 0 (q_{j,k} vanishes on Mis(j0,k0) exactly when j >= j0 and
+// k0 | k); multiplicity 1.  255 / 0 where nothing matched.  The orbit (at
+// most 40 steps) is kept whole, in local memory: one pass per root.
+__global__ void k_type_q(PolyDev P, const double2* __restrict__ roots, int64_t count, double tau,
+                         uint8_t* __restrict__ pre, uint8_t* __restrict__ per, uint8_t* __restrict__ mult) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double2 c = roots[i];
+  const int l = P.l, n = P.n, L = P.l + P.n;
+  double zr[41], zi[41];
+  float dr[41], di[41];
+  zr[0] = zi[0] = 0.0;
+  dr[0] = di[0] = 0.f;
+  for (int k = 1; k <= L; ++k) {
+    const float fr = __double2float_rn(zr[k - 1]), fi = __double2float_rn(zi[k - 1]);
+    dr[k] = fmaf(fr + fr, dr[k - 1], fmaf(-(fi + fi), di[k - 1], 1.f));
+    di[k] = fmaf(fr + fr, di[k - 1], (fi + fi) * dr[k - 1]);
+    zr[k] = fma(zr[k - 1], zr[k - 1], fma(-zi[k - 1], zi[k - 1], c.x));
+    zi[k] = fma(zr[k - 1] + zr[k - 1], zi[k - 1], c.y);
+  }
+  int a = -1, b = -1;
+  for (int k = 1; k <= n && a < 0; ++k)
+    if (n % k == 0 && newton_small_f(zr[k], zi[k], dr[k], di[k], tau)) { a = 0; b = k; }
+  for (int k = 1; k <= n && a < 0; ++k) {
+    if (n % k || !newton_small_f(zr[l + k] - zr[l], zi[l + k] - zi[l], dr[l + k] - dr[l], di[l + k] - di[l], tau))
+      continue;
+    for (int j = 2; j <= l; ++j)
+      if (newton_small_f(zr[j + k] - zr[j], zi[j + k] - zi[j], dr[j + k] - dr[j], di[j + k] - di[j], tau)) {
+        a = j;
+        b = k;
+        break;
+      }
+  }
+  if (pre) pre[i] = a < 0 ? 255 : (uint8_t)a;
+  if (per) per[i] = b < 0 ? 255 : (uint8_t)b;
+  if (mult) mult[i] = a < 0 ? 0 : (uint8_t)(a == 0 ? (l - 1) / b + 2 : 1);
+}
+
+cudaError_t launch_type_q(const PolyDev& P, const double2* roots, int64_t count, double tau, uint8_t* pre,
+                          uint8_t* per, uint8_t* mult, cudaStream_t s) {
+  if (count <= 0 || P.l + P.n > 40) return cudaSuccess;
+  MT_COUNT_LAUNCH(1);
+  k_type_q<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, roots, count, tau, pre, per, mult);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t count, double tau,
@@ -238,9 +307,11 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
     rz0 = nrz0; rz = nrz; rd = nrd;
     if (k == P.lcap) { czx = zx; czy = zy; cdx = dx; cdy = dy; crz0 = rz0; crd = rd; }
   }
-  if (P.lcap >= 0) {  // s_{l,n} = p_m + p_{l-1}: one disk sum each
-    const double vx = zx + czx, vy = zy + czy;
-    const float wx = dx + cdx, wy = dy + cdy;
+  if (P.lcap >= 0) {  // s_{l,n} = p_m + p_{l-1}, q_{l,n} = p_m - p_l: one disk sum each
+    const double sg = (P.kind == 2) ? -1.0 : 1.0;
+    const float sgf = (float)sg;
+    const double vx = fma(sg, czx, zx), vy = fma(sg, czy, zy);
+    const float wx = fmaf(sgf, cdx, dx), wy = fmaf(sgf, cdy, dy);
     rz0 = __fadd_ru(__fadd_ru(rz0, crz0), hsum_ru(ulp_ub(vx), ulp_ub(vy)));
     rd = __fadd_ru(__fadd_ru(rd, crd), hsum_ru(ulp32_ub(wx), ulp32_ub(wy)));
     zx = vx; zy = vy; dx = wx; dy = wy;
@@ -252,11 +323,13 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
 // Certify the points of 'pts' (sorted by Re through 'order', or already
 // sorted when order == nullptr).  upper: the list holds one representative
 // per conjugate pair, so conjugates count as neighbours too.
+// q_{l,n}: a root typed Hyp(k) (type 33..63) is a multiple root of q but a
+// simple root of p_n, and is proven as a root of p_n; the others as roots of q.
 __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
                           const uint32_t* __restrict__ order, const unsigned long long* n_pts_dev,
                           int64_t n_pts_host, double tol, int upper, const uint32_t* __restrict__ mult,
                           uint8_t* __restrict__ pass, double* __restrict__ radius,
-                          DevCounters* ctr, SegView sv) {
+                          DevCounters* ctr, SegView sv, const uint8_t* __restrict__ type) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = n_pts_dev ? (int64_t)*n_pts_dev : n_pts_host;
   unsigned long long npass = 0, overflow = 0;
@@ -266,7 +339,12 @@ __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
     const int64_t ip = order ? (int64_t)order[p] : p;
     const double2 c = pts[ip];
     const uint16_t sg = sv.rep_seg ? sv.rep_seg[p] : 0;  // (batch mode: pts are reps, no order)
-    const PolyDev P = sv.tab ? sv.tab[sg] : P0;
+    PolyDev P = sv.tab ? sv.tab[sg] : P0;
+    if (P.kind == 2 && type && type[ip] > 32 && type[ip] < 64) {
+      P.kind = 0;  // p_n
+      P.m = P.n;
+      P.lcap = -1;
+    }
     // nearest neighbour (and conjugates) within the window W = tol / 0.45
     const double W = tol / 0.45;
     double nn2 = W * W;
@@ -389,22 +467,23 @@ cudaError_t launch_basin(const PolyDev& P, const double2* pts, const uint32_t* o
 
 cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
                            int64_t cap, double tol, const uint32_t* mult, uint8_t* pass,
-                           double* radius, DevCounters* ctr, cudaStream_t s, SegView sv) {
+                           double* radius, DevCounters* ctr, cudaStream_t s, SegView sv,
+                           const uint8_t* type) {
   if (cap <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
   k_certify<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, nullptr, n_reps, cap, tol, 1,
-                                                          mult, pass, radius, ctr, sv);
+                                                          mult, pass, radius, ctr, sv, type);
   return cudaGetLastError();
 }
 
 // standalone certificate of an arbitrary list (sorted through 'order')
 cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint32_t* order,
                                 int64_t count, double tol, uint8_t* pass, double* radius,
-                                DevCounters* ctr, cudaStream_t s) {
+                                DevCounters* ctr, cudaStream_t s, const uint8_t* type) {
   if (count <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
   k_certify<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, pts, order, nullptr, count, tol, 0,
-                                                            nullptr, pass, radius, ctr, SegView());
+                                                            nullptr, pass, radius, ctr, SegView(), type);
   return cudaGetLastError();
 }
 

@@ -6,7 +6,8 @@
 // Polynomials (Mihalache & Vigneron, Sec. 1 and eq. polySimple):
 //   p_0 = 0, p_{k+1} = p_k^2 + c                 P = p_n,             deg 2^(n-1)
 //   s_{l,n} = p_{l+n-1} + p_{l-1}                P = s_{l,n},         deg 2^(l+n-2)
-// Both are evaluated through one critical orbit of length m, with the
+//   q_{l,n} = p_{l+n} - p_l                      P = q_{l,n},         deg 2^(l+n-1)
+// All are evaluated through the critical orbit (length m), with the
 // c-derivative carried along by differentiating the recurrence:
 //   p'_{k+1} = 2 p_k p'_k + 1                    (eq. DerParamDyna, parameter form)
 // so one evaluation costs O(m) = O(log d) (Sec. 3, "V_d = O(log_2 d)").
@@ -89,9 +90,61 @@ __device__ __forceinline__ void orbit_f64_d32(int m, int lcap, double cr, double
   }
 }
 
+// q_{l,n} as a product.  eq. polySimple gives s_{j,n} = q_{j,n} / q_{j-1,n},
+// and q_{0,n} = p_n, so q_{l,n} = p_n prod_{j=1..l} s_{j,n}: with u_k =
+// z_{k+n} - z_k (u_0 = p_n), u_{k+1} = z_{k+n}^2 - z_k^2 = u_k (z_{k+n} + z_k),
+// and u_l = q_{l,n}.  Every factor has simple roots only, so near a multiple
+// root of q -- where the difference p_{l+n} - p_l cancels to rounding noise
+// within ~(unit roundoff)^(1/mu) of it -- the product keeps its relative
+// accuracy, and Newton reaches the multiple root in binary64.  Two orbits n
+// apart: n + 2l orbit steps and l complex product updates.
+__device__ __forceinline__ void orbit_q_f64(int l, int n, double cr, double ci, double& vr, double& vi,
+                                            double& dr, double& di) {
+  double br = 0.0, bi = 0.0, dbr = 0.0, dbi = 0.0;  // z_{k+n}, z'_{k+n}
+  for (int k = 1; k <= n; ++k) {
+    const double tzr = br + br, tzi = bi + bi;
+    const double ndr = fma(tzr, dbr, fma(-tzi, dbi, 1.0));
+    const double ndi = fma(tzr, dbi, tzi * dbr);
+    const double nzr = fma(br, br, fma(-bi, bi, cr));
+    const double nzi = fma(tzr, bi, ci);
+    br = nzr; bi = nzi; dbr = ndr; dbi = ndi;
+  }
+  double ar = 0.0, ai = 0.0, dar = 0.0, dai = 0.0;  // z_k, z'_k
+  double ur = br, ui = bi, dur = dbr, dui = dbi;     // u_0 = p_n, u_0'
+  for (int k = 0; k < l; ++k) {
+    const double fr = br + ar, fi = bi + ai, dfr = dbr + dar, dfi = dbi + dai;
+    const double ndur = fma(dur, fr, fma(-dui, fi, fma(ur, dfr, -ui * dfi)));  // (u f)' = u' f + u f'
+    const double ndui = fma(dur, fi, fma(dui, fr, fma(ur, dfi, ui * dfr)));
+    const double nur = fma(ur, fr, -ui * fi);
+    const double nui = fma(ur, fi, ui * fr);
+    ur = nur; ui = nui; dur = ndur; dui = ndui;
+    {
+      const double tzr = ar + ar, tzi = ai + ai;
+      const double ndr = fma(tzr, dar, fma(-tzi, dai, 1.0));
+      const double ndi = fma(tzr, dai, tzi * dar);
+      const double nzr = fma(ar, ar, fma(-ai, ai, cr));
+      const double nzi = fma(tzr, ai, ci);
+      ar = nzr; ai = nzi; dar = ndr; dai = ndi;
+    }
+    {
+      const double tzr = br + br, tzi = bi + bi;
+      const double ndr = fma(tzr, dbr, fma(-tzi, dbi, 1.0));
+      const double ndi = fma(tzr, dbi, tzi * dbr);
+      const double nzr = fma(br, br, fma(-bi, bi, cr));
+      const double nzi = fma(tzr, bi, ci);
+      br = nzr; bi = nzi; dbr = ndr; dbi = ndi;
+    }
+  }
+  vr = ur; vi = ui; dr = dur; di = dui;
+}
+
+// Sign of the captured orbit value in P: +1 for s_{l,n}, -1 for q_{l,n}.
+__device__ __forceinline__ double cap_sign(const PolyDev& P) { return P.kind == 2 ? -1.0 : 1.0; }
+
 __device__ __forceinline__ void eval_P(const PolyDev& P, double cr, double ci, double& vr, double& vi,
                                        double& dr, double& di) {
-  if (P.lcap < 0) orbit_pn_f64(P.m, cr, ci, vr, vi, dr, di);
+  if (P.kind == 2) orbit_q_f64(P.l, P.n, cr, ci, vr, vi, dr, di);
+  else if (P.lcap < 0) orbit_pn_f64(P.m, cr, ci, vr, vi, dr, di);
   else orbit_f64(P.m, P.lcap, 1.0, cr, ci, vr, vi, dr, di);
 }
 

@@ -40,6 +40,7 @@ struct DevCounters {
   unsigned long long seed_newton;   // Newton steps of the seed lifts (part of walk_newton)
   unsigned long long desc_fp32;     // binary32 Newton steps of the descents (part of desc_newton)
   unsigned long long n_finish;      // binary64 finishes of the mixed tier (run heads)
+  unsigned long long n_mult_full;   // q_{l,n}: full list counted with multiplicity (Thm fact_mis)
   unsigned long long type_count[64];
 };
 
@@ -171,7 +172,7 @@ cudaError_t launch_classify(const PolyDev& P, double2* reps, const unsigned long
 cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
                            int64_t cap, double tol, const uint32_t* mult, uint8_t* pass,
                            double* radius, DevCounters* ctr, cudaStream_t s,
-                           SegView sv = SegView());
+                           SegView sv = SegView(), const uint8_t* type = nullptr);
 
 // Emit the full conjugate-closed list sorted by (Re, Im).
 cudaError_t launch_emit(const double2* reps, const unsigned long long* n_reps, int64_t cap_reps,
@@ -221,10 +222,14 @@ cudaError_t launch_init_counters(DevCounters* ctr, cudaStream_t s);
 // keys[i] = order-preserving key of Re pts[i], vals[i] = i.
 cudaError_t launch_keys_plain(const double2* pts, int64_t count, uint64_t* keys, uint32_t* vals,
                               cudaStream_t s);
-// Standalone certificate of an arbitrary list sorted through 'order'.
+// q_{l,n}: exact type (preperiod, period) and multiplicity of each root.
+cudaError_t launch_type_q(const PolyDev& P, const double2* roots, int64_t count, double tau, uint8_t* pre,
+                          uint8_t* per, uint8_t* mult, cudaStream_t s);
+// Standalone certificate of an arbitrary list sorted through 'order'
+// (type: q_{l,n} only, the type codes of the points, or null).
 cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint32_t* order,
                                 int64_t count, double tol, uint8_t* pass, double* radius,
-                                DevCounters* ctr, cudaStream_t s);
+                                DevCounters* ctr, cudaStream_t s, const uint8_t* type = nullptr);
 
 // ---- the double-double tier (mt_ddtier.cu) ----------------------------------
 // dd values are pairs of binary64 (hi, lo), 16 bytes like a double2.

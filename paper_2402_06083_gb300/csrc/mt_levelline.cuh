@@ -70,7 +70,7 @@ __device__ __forceinline__ int newton_target_f64(int m, int lcap, double alpha, 
 // below the last level stop at 1e-2 of their predictor, the last level at
 // 1e-3 (the seed is a start of the walk).  For s_{l,n}, a final homotopy
 // p_m + alpha p_{l-1}, alpha: 0 -> 1, at fixed target moves the point from
-// |p_m| = lambda0 to |s_{l,n}| = lambda0.  A seed that lands on the wrong
+// |p_m| = lambda0 to |s_{l,n}| = lambda0 (p_m - alpha p_l for q_{l,n}).  A seed that lands on the wrong
 // preimage makes the walk of its chunk miss the next seed (walk_fail).
 __device__ __forceinline__ double2 lift_seed(const PolyDev& P, double lambda0, int64_t N0,
                                              int log2N0, int shrink, int64_t j,
@@ -91,14 +91,15 @@ __device__ __forceinline__ double2 lift_seed(const PolyDev& P, double lambda0, i
                                  rp * s, Lq, 0.0);
     }
   }
-  if (P.kind == 1) {
-    // homotopy p_m -> p_m + p_{l-1} at target lambda0 e^{2 i pi d t}, d = 2^(m-1)
+  if (P.kind != 0) {
+    // homotopy p_m -> p_m + p_{l-1} (s_{l,n}) or p_m - p_l (q_{l,n}) at target
+    // lambda0 e^{2 i pi d t}, d = 2^(m-1)
     const int k = P.m - 1;
     const uint64_t num = (k >= log2N0) ? 0 : (((uint64_t)j << k) & (uint64_t)(N0 - 1));
     unit_phase(num, (uint64_t)N0, c, s);
     const int A = 8;
     for (int a = 1; a <= A; ++a) {
-      const double alpha = (double)a / A;
+      const double alpha = cap_sign(P) * a / A;
       steps += newton_target_f64(P.m, P.lcap, alpha, zr, zi, lambda0 * c, lambda0 * s, 1e-3, 40,
                                  nullptr);
     }
@@ -116,7 +117,7 @@ __device__ __forceinline__ double2 lift_seed(const PolyDev& P, double lambda0, i
 // target T then corrects until a step falls below rel * h (h = predictor
 // length) or steps stop shrinking after the third.  Returns the number of
 // Newton evaluations; zp receives z' at this sub-step's first point.
-__device__ __forceinline__ int walk_substep_f64(int m, int lcap, double& zr, double& zi, double tr,
+__device__ __forceinline__ int walk_substep_f64(int m, int lcap, double sgn, double& zr, double& zi, double tr,
                                                 double ti, double tpr, double tpi, double Li,
                                                 bool have_prev, double& zpr, double& zpi,
                                                 double rel, int cap, double& h) {
@@ -125,7 +126,7 @@ __device__ __forceinline__ int walk_substep_f64(int m, int lcap, double& zr, dou
   while (it < cap) {
     double vr, vi, dr, di;
     if (lcap < 0) orbit_pn_f64(m, zr, zi, vr, vi, dr, di);
-    else orbit_f64(m, lcap, 1.0, zr, zi, vr, vi, dr, di);
+    else orbit_f64(m, lcap, sgn, zr, zi, vr, vi, dr, di);
     double qr, qi;
     if (it == 0) {
       // z' = P / P' and dz = z' (L - (P - Tp) / P) + (z' - z'_prev) L / 2
@@ -182,7 +183,8 @@ __device__ __forceinline__ bool walk_chunk_from(const PolyDev& P, const double2*
     // the others to 1e-1 (the next predictor corrects toward the exact
     // previous target, so their error does not carry over)
     const double rel = (((g + 1) & (uint64_t)(every - 1)) == 0) ? 1e-2 : 1e-1;
-    steps += walk_substep_f64(P.m, P.lcap, zr, zi, T.x, T.y, Tp.x, Tp.y, Li, i > 0, zpr, zpi, rel, 16, h);
+    steps += walk_substep_f64(P.m, P.lcap, cap_sign(P), zr, zi, T.x, T.y, Tp.x, Tp.y, Li, i > 0, zpr, zpi, rel,
+                              16, h);
   }
   if (j == nchunks - 1) starts[g / every] = make_double2(zr, 0.0);  // t = 1/2, real
   const double er = zr - zn.x, ei = zi - zn.y;
