@@ -40,6 +40,7 @@ CONFIGS = {
     "hyp28dd": ("hyp", 0, 28, "dd"),  # binary64 cannot separate its tip roots: dd zones
     "hyp29dd": ("hyp", 0, 29, "dd"),
     "hyp31dd": ("hyp", 0, 31, "dd"),  # 2^30 roots, ~230 GB of device memory
+    "hyp32dd": ("hyp", 0, 32, "dd"),  # 2^31 roots, streamed level line, ~245 GB of device memory
     "mis16": ("misbatch", 0, 16, "fp64"),  # every s_{l,n}, l >= 2, n >= 1, l + n <= 16, one pass
     "q18": ("q", 9, 9, "fp64"),  # q_{9,9} = p_18 - p_9 with its multiple roots (Thm fact_mis)
 }

@@ -87,6 +87,13 @@ typedef struct {
      root set, types, certificates).  dd_all = 1 redoes every root. */
   double dd_radius;    /* zone radius (0 -> 1e-9)                                   */
   int dd_all;          /* 1: the whole split in double-double                       */
+  /* Streamed split: the level line is walked and descended in this many
+     pieces (a power of two), each piece's root set appended to one list
+     whose own root set is the result; the starts never all reside in
+     memory.  0 -> automatic: 1, or the fewest pieces of at most 2^28 starts
+     once the upper half holds more than 2^31 starts (p_32 and up).
+     Streamed pieces run in binary64 (MT_MIXED falls back to MT_FP64). */
+  int stream_pieces;
 } mt_options;
 
 #define MT_MAX_TYPES 64

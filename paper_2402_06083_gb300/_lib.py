@@ -47,6 +47,7 @@ class Options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("dd_radius", ctypes.c_double),
         ("dd_all", ctypes.c_int),
+        ("stream_pieces", ctypes.c_int),
     ]
 
 

@@ -123,9 +123,16 @@ struct Plan {
   int64_t dd_nb;      // pieces per dd batch
   int64_t dd_zcap;    // zone candidate capacity
   int64_t dd_near_cap;
+  int64_t dd_pcap;     // redone pieces the id list holds
+  int64_t dd_bad_cap;  // zone centres the dd pass accepts
+  // streamed split (stream_P > 1): the level line in stream_P pieces of at
+  // most S_p starts; their root sets appended to a list of G_cap entries
+  int64_t stream_P;
+  int64_t S_p;
+  int64_t G_cap;
 };
 
-constexpr int DD_MAX_BAD = 1 << 22;  // zone centres the dd pass accepts
+constexpr int DD_MAX_BAD = 1 << 24;  // zone centres the dd pass accepts
 
 // ---------------------------------------------------------------------------
 // Autotune table: (kind, l, n, tier) -> chunk length and walk block size
@@ -206,6 +213,19 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
     // would only add seed lifts
     N0 = std::min<int64_t>(int64_t(1) << 15, Md / 16);
   }
+  // streamed split: when the upper half holds more than 2^31 starts (the
+  // root-set indices are 32-bit), or when asked for
+  int64_t P = (o && o->stream_pieces > 0) ? o->stream_pieces : 1;
+  const int64_t S_all = (Md / 2) / p.every;
+  if (!(o && o->stream_pieces > 0) && S_all > (int64_t(1) << 31))
+    while ((S_all / P) > (int64_t(1) << 28)) P <<= 1;
+  if (P & (P - 1)) return false;
+  if (P > 1) {
+    // one lane per chunk: a piece needs tens of thousands of chunks to fill
+    // the GPU, so streamed splits cut the line finer; pieces run in binary64
+    if (!(o && o->chunk_log2 > 0)) N0 = std::min<int64_t>(int64_t(1) << 20, Md / 16);
+    p.prec = MT_FP64;
+  }
   // L must be a multiple of 'every' and N0 >= 2
   while (N0 > 2 && (Md / N0) % p.every) N0 >>= 1;
   if (N0 < 2) N0 = 2;
@@ -215,6 +235,15 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   p.nchunks = N0 / 2;
   p.L = Md / N0;
   p.S = (Md / 2) / p.every + 1;
+  p.stream_P = P;
+  if (P > 1) {
+    if (p.nchunks % P) return false;
+    p.S_p = (p.nchunks / P) * p.L / p.every + 1;
+    // distinct roots of the upper half (~ deg / 2), with room for the roots
+    // that several pieces reach; checked after the last piece
+    p.G_cap = std::min<int64_t>(p.S, p.degree / 8 * 5 + 4096);
+    if (p.S_p > (int64_t(1) << 31) || p.G_cap > (int64_t(1) << 32) - 1) return false;
+  }
   const bool dd = o && o->prec == MT_DD;
   // the base pass of MT_DD runs with the binary64 settings; the user's tol
   // and cert_tol then apply to the double-double pass
@@ -247,6 +276,17 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
     p.dd_zcap = 2 * p.S + 64;
     if (!p.dd_all) p.dd_zcap = std::min<int64_t>(p.dd_zcap, std::max<int64_t>(int64_t(1) << 21, p.S / 16));
     p.dd_near_cap = p.dd_all ? p.S : std::min<int64_t>(p.S, std::max<int64_t>(int64_t(1) << 21, p.S / 64));
+    // zone centres: at most one per 256 starts (p_31: 1.2 M of 8.4 M; p_32:
+    // 5.7 M of 2^24)
+    p.dd_bad_cap = std::min<int64_t>(DD_MAX_BAD, std::max<int64_t>(4096, p.S / 256));
+    // the ids of redone pieces: all of them in memory; streamed, a sixteenth
+    p.dd_pcap = (P > 1 && !p.dd_all)
+                    ? std::min<int64_t>(p.dd_npieces, std::max<int64_t>(int64_t(1) << 24, p.dd_npieces / 16))
+                    : p.dd_npieces;
+    if (P > 1) {  // the rep arrays of the final stage hold G_cap entries
+      if (p.dd_all) return false;  // the whole streamed line in dd: not offered
+      p.dd_near_cap = std::min<int64_t>(p.dd_near_cap, p.G_cap);
+    }
   }
   *pl = p;
   return true;
@@ -279,6 +319,14 @@ struct Buffers {
   double* radius;
   void *scan_tmp, *radix_tmp, *anchors;
   uint8_t *seed_bad, *chunk_fail;  // mixed tier: items the binary64 repairs redo
+  // streamed split: the appended list, its counters (count, converged
+  // snapshot, valid in the piece), the fixed-point end points of all descents
+  // (for the dd pass) and the drop flags of the final reps
+  double2* G;
+  unsigned long long* gstate;
+  int2* candq;
+  int64_t candq_n;
+  uint8_t* drop;
   DdBuffers d;
   size_t bytes;
 };
@@ -287,9 +335,36 @@ dd* take_dd(Carve& c, int64_t n) { return reinterpret_cast<dd*>(c.take<double2>(
 
 Buffers carve(const Plan& p, void* ws, size_t cap) {
   Carve c(ws, cap);
-  Buffers b;
+  Buffers b{};
   b.ctr = c.take<DevCounters>(1);
   b.seeds = c.take<double2>(p.nchunks + 1);
+  if (p.stream_P > 1) {
+    // one piece of the line at a time; the sort buffers also serve the final
+    // root set over the appended list
+    const int64_t Sp = p.S_p, Gc = p.G_cap, Mx = std::max(Sp, Gc);
+    b.starts = c.take<double2>(Sp);
+    b.cand = c.take<double2>(Sp);
+    b.status = c.take<uint8_t>(Sp);
+    b.keys = c.take<uint64_t>(Mx);
+    b.keys_alt = c.take<uint64_t>(Mx);
+    b.vals = c.take<uint32_t>(Mx);
+    b.vals_alt = c.take<uint32_t>(Mx);
+    b.flag = c.take<uint32_t>(Mx);
+    b.pos = c.take<uint32_t>(Mx);
+    b.mult = b.flag;
+    b.mpos = b.pos;
+    b.scan_tmp = c.take_bytes(scan_temp_bytes(Mx));
+    b.radix_tmp = c.take_bytes(radix_temp_bytes(Mx));
+    b.G = c.take<double2>(Gc);
+    b.gstate = c.take<unsigned long long>(4);
+    b.candq = p.dd ? c.take<int2>(p.S) : nullptr;
+    b.candq_n = p.S;
+    b.reps = c.take<double2>(Gc);
+    b.type = c.take<uint8_t>(Gc);
+    b.pass = c.take<uint8_t>(Gc);
+    b.radius = c.take<double>(Gc);
+    b.drop = c.take<uint8_t>(Gc);
+  } else {
   b.starts = c.take<double2>(p.S);
   b.cand = c.take<double2>(p.S);
   b.reps = b.starts;  // starts are dead once the descents are done
@@ -310,15 +385,16 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
   b.anchors = (p.prec == MT_MIXED) ? c.take_bytes(mixed_anchor_bytes(p.P, p.S)) : nullptr;
   b.seed_bad = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks + 1) : nullptr;
   b.chunk_fail = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks) : nullptr;
+  }
   b.d = DdBuffers{};
   if (p.dd) {
     DdBuffers& d = b.d;
     const int64_t nst = p.dd_nb * (p.dd_Ls / p.every) + 1;
     d.cnt = c.take<unsigned long long>(8);
-    d.bad = c.take<double2>(DD_MAX_BAD);
+    d.bad = c.take<double2>(p.dd_bad_cap);
     d.pflag = c.take<uint32_t>(p.dd_npieces);
     d.ppos = c.take<uint32_t>(p.dd_npieces);
-    d.pids = c.take<int64_t>(p.dd_npieces);
+    d.pids = c.take<int64_t>(p.dd_pcap);
     d.pscan = c.take_bytes(scan_temp_bytes(p.dd_npieces));
     d.sx = take_dd(c, 2 * p.dd_nb);
     d.sy = take_dd(c, 2 * p.dd_nb);
@@ -483,6 +559,94 @@ mt_status read_counters(const Buffers& b, DevCounters* h, cudaStream_t s) {
   return MT_OK;
 }
 
+// Streamed split (stream_P > 1).  The level line is walked and descended a
+// range of chunks at a time; each piece's candidates get their own root set
+// (fold, sort, cluster), whose representatives are appended to the list G.
+// The root set of G -- the same clustering rule over fewer points, roots
+// reached from several pieces merging there -- is the split's, and is typed,
+// certified and emitted as in one pass.  Stage times are summed over the
+// pieces (*tm: walk, descents, piece root sets).
+struct StreamTimes {
+  float walk = 0.f, descend = 0.f, dedup = 0.f;
+};
+
+mt_status run_streamed(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
+                       uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h, StreamTimes* tm) {
+  unsigned long long* gcount = b.gstate;      // entries of G
+  unsigned long long* snap = b.gstate + 1;    // converged descents before this piece
+  unsigned long long* nvalid = b.gstate + 2;  // converged descents of this piece
+  CK(launch_init_counters(b.ctr, s));
+  CK(cudaMemsetAsync(b.gstate, 0, 4 * sizeof(unsigned long long), s));
+  CK(cudaEventRecord(ev.e[0], s));
+  CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+  CK(cudaEventRecord(ev.e[6], s));
+  const int64_t C = p.nchunks / p.stream_P;
+  std::vector<cudaEvent_t> pe((size_t)(4 * p.stream_P), nullptr);
+  struct Guard {
+    std::vector<cudaEvent_t>& v;
+    ~Guard() {
+      for (auto e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } guard{pe};
+  for (auto& e : pe) CK(cudaEventCreate(&e));
+  for (int64_t k = 0; k < p.stream_P; ++k) {
+    const int64_t j0 = k * C;
+    const int64_t Sk = C * p.L / p.every + (k == p.stream_P - 1 ? 1 : 0);
+    CK(cudaEventRecord(pe[4 * k], s));
+    CK(launch_walk_range(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, j0, C, b.seeds, b.starts, b.ctr, s,
+                         p.walk_block));
+    CK(cudaEventRecord(pe[4 * k + 1], s));
+    CK(cudaMemsetAsync(&b.ctr->queue_head, 0, sizeof(unsigned long long), s));
+    CK(launch_descend(p.P, b.starts, Sk, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
+    CK(cudaEventRecord(pe[4 * k + 2], s));
+    CK(launch_piece_valid(b.ctr, snap, nvalid, s));
+    CK(launch_fold_keys(b.status, b.cand, Sk, p.eps, b.keys, b.vals, s));
+    CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, Sk, b.radix_tmp, s));
+    CK(launch_cluster(b.cand, b.vals, Sk, nvalid, p.eps, b.flag, b.ctr, s));
+    CK(launch_exclusive_scan(b.flag, b.pos, Sk, b.scan_tmp, nullptr, s));
+    CK(launch_stream_append(b.cand, b.status, b.vals, b.flag, b.pos, Sk, b.G, gcount, p.G_cap,
+                            b.candq ? b.candq + j0 * p.L / p.every : nullptr, s));
+    CK(cudaEventRecord(pe[4 * k + 3], s));
+  }
+  CK(cudaEventRecord(ev.e[1], s));
+  CK(cudaEventRecord(ev.e[2], s));
+  unsigned long long ng = 0;
+  CK(cudaMemcpyAsync(&ng, gcount, sizeof(ng), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int64_t k = 0; k < p.stream_P; ++k) {
+    float a = 0.f, c = 0.f, d = 0.f;
+    cudaEventElapsedTime(&a, pe[4 * k], pe[4 * k + 1]);
+    cudaEventElapsedTime(&c, pe[4 * k + 1], pe[4 * k + 2]);
+    cudaEventElapsedTime(&d, pe[4 * k + 2], pe[4 * k + 3]);
+    tm->walk += a;
+    tm->descend += c;
+    tm->dedup += d;
+  }
+  if ((int64_t)ng > p.G_cap)
+    return fail(MT_ECAPACITY, "the pieces of the streamed split found %llu representatives, the list holds %lld",
+                ng, (long long)p.G_cap);
+  const int64_t nG = (int64_t)ng;
+  // the root set of G (its points are folded already)
+  CK(launch_keys_plain(b.G, nG, b.keys, b.vals, s));
+  CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, nG, b.radix_tmp, s));
+  CK(launch_cluster(b.G, b.vals, nG, gcount, p.eps, b.flag, b.ctr, s));
+  CK(launch_exclusive_scan(b.flag, b.pos, nG, b.scan_tmp, nullptr, s));
+  CK(launch_compact(b.G, b.vals, b.flag, b.pos, nG, b.reps, b.ctr, s));
+  CK(cudaEventRecord(ev.e[3], s));
+  CK(launch_classify(p.P, b.reps, &b.ctr->n_reps, nG, p.eps, 0, b.type, b.mult, b.ctr, s));
+  CK(launch_exclusive_scan(b.mult, b.mpos, nG, b.scan_tmp, &b.ctr->n_full, s));
+  CK(launch_certify(p.P, b.reps, &b.ctr->n_reps, nG, p.cert_tol, b.mult, b.pass, b.radius, b.ctr, s,
+                    SegView(), p.kind == 2 ? b.type : nullptr));
+  CK(cudaEventRecord(ev.e[4], s));
+  const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
+  CK(launch_emit(b.reps, &b.ctr->n_reps, nG, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out, s));
+  CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s));
+  if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
+  CK(cudaEventRecord(ev.e[5], s));
+  return read_counters(b, h, s);
+}
+
 mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
                    uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h) {
   mt_status rc = enqueue_pass(p, b, out, out_lo, cap_out, is_mis, s, ev, false);
@@ -593,14 +757,14 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
   const unsigned long long* n_main = &d.cnt[6];
   int nbad = -1;  // "all" mode
   if (!p.dd_all) {
-    CK(dd_collect_bad(b.reps, n_main, p.S, b.pass, b.radius, 2.0 * p.eps, d.bad, &d.cnt[0], DD_MAX_BAD,
+    CK(dd_collect_bad(b.reps, n_main, p.S, b.pass, b.radius, 2.0 * p.eps, d.bad, &d.cnt[0], (int)p.dd_bad_cap,
                       s));
     unsigned long long nb_h = 0;
     CK(cudaMemcpyAsync(&nb_h, &d.cnt[0], sizeof(nb_h), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (nb_h > (unsigned long long)DD_MAX_BAD)
-      return fail(MT_ECERT, "%llu roots need the double-double pass, more than its %d zones",
-                  nb_h, DD_MAX_BAD);
+    if (nb_h > (unsigned long long)p.dd_bad_cap)
+      return fail(MT_ECERT, "%llu roots need the double-double pass, more than its %lld zones",
+                  nb_h, (long long)p.dd_bad_cap);
     nbad = (int)nb_h;
     rep->zones = nbad;
     if (nbad == 0) return MT_OK;  // nothing the dd pass can improve
@@ -615,20 +779,27 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
   // pieces of the level line to redo
   int64_t npieces = p.dd_npieces;
   if (p.dd_all) {
-    CK(dd_piece_ids(nullptr, nullptr, p.dd_npieces, d.pids, s));
+    CK(dd_piece_ids(nullptr, nullptr, p.dd_npieces, d.pids, p.dd_pcap, s));
   } else {
     CK(cudaMemsetAsync(d.pflag, 0, sizeof(uint32_t) * (size_t)p.dd_npieces, s));
-    CK(dd_mark_pieces(b.cand, b.status, p.S, p.every, p.dd_Ls, p.dd_npieces, d.bad, nbad, Rm, d.pflag, s));
+    if (b.candq)  // streamed split: from the fixed-point end points of all descents
+      CK(dd_mark_pieces_fix(b.candq, b.candq_n, p.every, p.dd_Ls, p.dd_npieces, d.bad, nbad, Rm, d.pflag, s));
+    else
+      CK(dd_mark_pieces(b.cand, b.status, p.S, p.every, p.dd_Ls, p.dd_npieces, d.bad, nbad, Rm, d.pflag, s));
     CK(launch_exclusive_scan(d.pflag, d.ppos, p.dd_npieces, d.pscan, &d.cnt[7], s));
-    CK(dd_piece_ids(d.pflag, d.ppos, p.dd_npieces, d.pids, s));
+    CK(dd_piece_ids(d.pflag, d.ppos, p.dd_npieces, d.pids, p.dd_pcap, s));
     unsigned long long np_h = 0;
     CK(cudaMemcpyAsync(&np_h, &d.cnt[7], sizeof(np_h), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if ((int64_t)np_h > p.dd_pcap)
+      return fail(MT_EINCOMPLETE, "%llu level-line pieces to redo in double-double, more than the %lld held",
+                  np_h, (long long)p.dd_pcap);
     npieces = (int64_t)np_h;
   }
   rep->pieces = npieces;
   // b.status is dead from here on: it becomes the drop flag of the main reps
-  uint8_t* drop = b.status;
+  // (a streamed split has its own, sized for the final reps)
+  uint8_t* drop = b.drop ? b.drop : b.status;
   CK(cudaMemsetAsync(drop, 0, (size_t)p.S, s));
   CK(dd_near_reps(b.reps, n_main, p.S, d.bad, nbad, Rm, d.near, &d.cnt[1], p.dd_near_cap, s));
   // dd level line and descents, dd_nb pieces at a time
@@ -707,12 +878,16 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   const int max_retries = max_attempts(o);
   EventSet* evp = &ev;
   DdReport ddr;
+  StreamTimes stimes;
   bool dd_ran = false;
   for (;; ++retry) {
     if (!make_plan(kind, l, n, o, retry, &p)) return fail(MT_EINVAL, "no plan for retry %d", retry);
     Buffers b = carve(p, d_work, work_bytes);
     evp = &ev;
-    if (o->use_graph && retry == 0)
+    stimes = StreamTimes();
+    if (p.stream_P > 1)
+      rc = run_streamed(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h, &stimes);
+    else if (o->use_graph && retry == 0)
       rc = run_pass_graph(p, b, d_work, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, &h,
                           &evp);
     else
@@ -727,7 +902,9 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     if (p.dd && (p.dd_all || !certified)) {
       // MT_DD: a certified complete list is the goal (it proves itself)
       ddr = DdReport();
-      rc = run_dd(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, &h, &ddr);
+      Plan pd = p;
+      if (p.stream_P > 1) pd.S = p.G_cap;  // the final reps of a streamed split
+      rc = run_dd(pd, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, &h, &ddr);
       if (rc != MT_OK) return rc;
       dd_ran = true;
       done = (int64_t)h.n_full == p.degree && h.n_cert_pass == h.n_full;
@@ -753,6 +930,11 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     st->ms_dedup = ms[3];
     st->ms_certify = ms[4];
     cudaEventElapsedTime(&st->ms_seeds, evp->e[0], evp->e[6]);
+    if (p.stream_P > 1) {  // summed over the pieces; the piece root sets count as dedup
+      st->ms_walk = st->ms_seeds + stimes.walk;
+      st->ms_descend = stimes.descend;
+      st->ms_dedup += stimes.dedup;
+    }
     if (dd_ran) {
       st->prec_used = MT_DD;
       st->ms_dd = ddr.ms;

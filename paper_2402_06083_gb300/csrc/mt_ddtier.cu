@@ -93,14 +93,36 @@ __global__ void k_mark_pieces(const double2* __restrict__ cand, const uint8_t* _
   flag[G] = 1;
 }
 
+// Streamed splits: the same from the end points kept in 32-bit fixed point
+// (2^-29 per unit, INT_MIN: divergent).  Rounding moved each coordinate by
+// at most 2^-30, so the zone test takes a radius grown by 2^-29: a superset
+// of the pieces the binary64 test marks.
+__global__ void k_mark_pieces_fix(const int2* __restrict__ candq, int64_t S, int every, int64_t Ls,
+                                  int64_t npieces, const double2* __restrict__ bad, int nbad, double R,
+                                  uint32_t* __restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S) return;
+  const int2 c = candq[i];
+  if (c.x == (int)0x80000000) return;
+  const double x = c.x * 1.862645149230957e-09, y = fabs(c.y * 1.862645149230957e-09);  // * 2^-29
+  if (!zone_hit(x, y, bad, nbad, R + 1.862645149230957e-09)) return;
+  int64_t G = (i * (int64_t)every) / Ls;
+  if (G >= npieces) G = npieces - 1;
+  flag[G] = 1;
+}
+
 // ids[pos[G]] = G for the flagged pieces (pos = exclusive scan of flag);
-// flag == nullptr: every piece ("all" mode)
+// flag == nullptr: every piece ("all" mode).  Ids past ids_cap are dropped
+// (the host compares the count with the capacity).
 __global__ void k_piece_ids(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
-                            int64_t npieces, int64_t* __restrict__ ids) {
+                            int64_t npieces, int64_t* __restrict__ ids, int64_t ids_cap) {
   const int64_t G = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (G >= npieces) return;
-  if (!flag) ids[G] = G;
-  else if (flag[G]) ids[pos[G]] = G;
+  if (!flag) {
+    if (G < ids_cap) ids[G] = G;
+  } else if (flag[G] && (int64_t)pos[G] < ids_cap) {
+    ids[pos[G]] = G;
+  }
 }
 
 // Main representatives within R of a centre -> polish list.
@@ -834,9 +856,15 @@ cudaError_t dd_mark_pieces(const double2* cand, const uint8_t* status, int64_t S
   return cudaGetLastError();
 }
 
+cudaError_t dd_mark_pieces_fix(const int2* candq, int64_t S, int every, int64_t Ls, int64_t npieces,
+                               const double2* bad, int nbad, double R, uint32_t* flag, cudaStream_t s) {
+  MT_DD_LAUNCH(k_mark_pieces_fix, S, 256, candq, S, every, Ls, npieces, bad, nbad, R, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t dd_piece_ids(const uint32_t* flag, const uint32_t* pos, int64_t npieces, int64_t* ids,
-                         cudaStream_t s) {
-  MT_DD_LAUNCH(k_piece_ids, npieces, 256, flag, pos, npieces, ids);
+                         int64_t ids_cap, cudaStream_t s) {
+  MT_DD_LAUNCH(k_piece_ids, npieces, 256, flag, pos, npieces, ids, ids_cap);
   return cudaGetLastError();
 }
 

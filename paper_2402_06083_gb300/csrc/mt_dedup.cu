@@ -358,6 +358,68 @@ __global__ void k_compact(const double2* __restrict__ cand, const uint32_t* __re
   if (p == count - 1) ctr->n_reps = (unsigned long long)pos[p] + flag[p];
 }
 
+// Streamed splits.  Each piece's representatives are appended to one list
+// G at *g_count (read here, advanced by k_advance after the launch).
+__global__ void k_compact_append(const double2* __restrict__ cand, const uint32_t* __restrict__ vals,
+                                 const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                                 int64_t count, double2* __restrict__ G,
+                                 const unsigned long long* __restrict__ g_count, int64_t g_cap) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count || !flag[p]) return;
+  const int64_t k = (int64_t)*g_count + pos[p];
+  if (k < g_cap) G[k] = cand[vals[p]];
+}
+__global__ void k_advance(unsigned long long* g_count, const uint32_t* __restrict__ flag,
+                          const uint32_t* __restrict__ pos, int64_t count) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && count > 0)
+    *g_count += (unsigned long long)pos[count - 1] + flag[count - 1];
+}
+// valid entries of this piece: converged descents since the last call
+__global__ void k_piece_valid(const DevCounters* __restrict__ ctr, unsigned long long* snap,
+                              unsigned long long* n_valid) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *n_valid = ctr->n_conv - *snap;
+    *snap = ctr->n_conv;
+  }
+}
+// the end point of every descent in 32-bit fixed point, 2^-29 per unit
+// (|coordinate| <= 4, clamped beyond; INT_MIN marks a divergent descent):
+// the double-double pass marks its level-line pieces from these
+__device__ __forceinline__ int fix29(double x) {
+  const double t = rint(x * 536870912.0);
+  return t > 2147483647.0 ? 2147483647 : (t < -2147483647.0 ? -2147483647 : (int)t);
+}
+__global__ void k_cand_fix(const double2* __restrict__ cand, const uint8_t* __restrict__ status,
+                           int64_t count, int2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double2 z = cand[i];
+  const bool ok = status[i] != 1 && isfinite(z.x) && isfinite(z.y);
+  out[i] = ok ? make_int2(fix29(z.x), fix29(z.y)) : make_int2((int)0x80000000, 0);
+}
+
+cudaError_t launch_stream_append(const double2* cand, const uint8_t* status, const uint32_t* vals,
+                                 const uint32_t* flag, const uint32_t* pos, int64_t count, double2* G,
+                                 unsigned long long* g_count, int64_t g_cap, int2* candq, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((count + 255) / 256);
+  MT_COUNT_LAUNCH(2);
+  k_compact_append<<<grid, 256, 0, s>>>(cand, vals, flag, pos, count, G, g_count, g_cap);
+  k_advance<<<1, 32, 0, s>>>(g_count, flag, pos, count);
+  if (candq) {
+    MT_COUNT_LAUNCH(1);
+    k_cand_fix<<<grid, 256, 0, s>>>(cand, status, count, candq);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_piece_valid(const DevCounters* ctr, unsigned long long* snap, unsigned long long* n_valid,
+                               cudaStream_t s) {
+  MT_COUNT_LAUNCH(1);
+  k_piece_valid<<<1, 32, 0, s>>>(ctr, snap, n_valid);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_compact(const double2* cand, const uint32_t* vals, const uint32_t* flag,
                            const uint32_t* pos, int64_t count, double2* reps, DevCounters* ctr,
                            cudaStream_t s, SegView sv) {

@@ -240,8 +240,20 @@ cudaError_t dd_collect_bad(const double2* reps, const unsigned long long* n_reps
 cudaError_t dd_mark_pieces(const double2* cand, const uint8_t* status, int64_t S, int every,
                            int64_t Ls, int64_t npieces, const double2* bad, int nbad, double R,
                            uint32_t* flag, cudaStream_t s);
+cudaError_t dd_mark_pieces_fix(const int2* candq, int64_t S, int every, int64_t Ls, int64_t npieces,
+                               const double2* bad, int nbad, double R, uint32_t* flag, cudaStream_t s);
+// streamed splits: walk of chunks [j0, j0 + nch) (starts from index j0 L / every
+// written at 0), and the append of a piece's representatives to the list G
+cudaError_t launch_walk_range(const PolyDev& P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
+                              int64_t j0, int64_t nch, const double2* seeds, double2* starts, DevCounters* ctr,
+                              cudaStream_t s, int block);
+cudaError_t launch_stream_append(const double2* cand, const uint8_t* status, const uint32_t* vals,
+                                 const uint32_t* flag, const uint32_t* pos, int64_t count, double2* G,
+                                 unsigned long long* g_count, int64_t g_cap, int2* candq, cudaStream_t s);
+cudaError_t launch_piece_valid(const DevCounters* ctr, unsigned long long* snap, unsigned long long* n_valid,
+                               cudaStream_t s);
 cudaError_t dd_piece_ids(const uint32_t* flag, const uint32_t* pos, int64_t npieces, int64_t* ids,
-                         cudaStream_t s);
+                         int64_t ids_cap, cudaStream_t s);
 cudaError_t dd_near_reps(const double2* reps, const unsigned long long* n_reps, int64_t cap,
                          const double2* bad, int nbad, double R, uint32_t* near,
                          unsigned long long* nnear, int64_t near_cap, cudaStream_t s);

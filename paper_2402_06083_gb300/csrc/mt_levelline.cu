@@ -47,6 +47,42 @@ __global__ void k_walk(PolyDev P, double lambda0, int M, int every, int64_t L, i
   warp_add_u64(&ctr->walk_fail, fails);
 }
 
+// Chunks [j0, j0 + nch) only, starts written from index j0 L / every on
+// (streamed splits, which walk the level line a range of chunks at a time).
+__global__ void k_walk_range(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
+                             int64_t j0, int64_t nch, const double2* __restrict__ seeds,
+                             double2* __restrict__ starts, DevCounters* ctr) {
+  __shared__ double2 ph[64];
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    double c, s;
+    unit_phase((uint64_t)q, (uint64_t)M, c, s);
+    ph[q] = make_double2(lambda0 * c, lambda0 * s);
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long steps = 0, fails = 0;
+  if (i < nch) {
+    const int64_t j = j0 + i;
+    fails = walk_chunk_from(P, ph, M, every, L, nchunks, j, seeds[j], seeds[j + 1], starts, steps,
+                            j0 * L / every)
+                ? 1
+                : 0;
+  }
+  warp_add_u64(&ctr->walk_newton, steps);
+  warp_add_u64(&ctr->walk_fail, fails);
+}
+
+cudaError_t launch_walk_range(const PolyDev& P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
+                              int64_t j0, int64_t nch, const double2* seeds, double2* starts, DevCounters* ctr,
+                              cudaStream_t s, int block) {
+  if (nch <= 0) return cudaSuccess;
+  const int bs = (block >= 32 && block <= 1024 && block % 32 == 0) ? block : 64;
+  MT_COUNT_LAUNCH(1);
+  k_walk_range<<<(unsigned)((nch + bs - 1) / bs), bs, 0, s>>>(P, lambda0, M, every, L, nchunks, j0, nch, seeds,
+                                                              starts, ctr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_seed_lift(const PolyDev& P, double lambda0, int64_t N0, int shrink_steps,
                              double2* seeds, DevCounters* ctr, cudaStream_t s) {
   int log2N0 = 0;

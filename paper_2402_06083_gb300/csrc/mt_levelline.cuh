@@ -170,13 +170,13 @@ __device__ __forceinline__ int walk_substep_f64(int m, int lcap, double sgn, dou
 __device__ __forceinline__ bool walk_chunk_from(const PolyDev& P, const double2* ph, int M, int every,
                                                 int64_t L, int64_t nchunks, int64_t j, double2 z0,
                                                 double2 zn, double2* __restrict__ starts,
-                                                unsigned long long& steps) {
+                                                unsigned long long& steps, int64_t sbase = 0) {
   double zr = z0.x, zi = z0.y;
   uint64_t g = (uint64_t)j * (uint64_t)L;
   double h = 0.0, zpr = 0.0, zpi = 0.0;
   const double Li = 6.283185307179586 / M;  // L = log(T / Tp) = i 2 pi / M
   for (int64_t i = 0; i < L; ++i, ++g) {
-    if ((g & (uint64_t)(every - 1)) == 0) starts[g / every] = make_double2(zr, zi);
+    if ((g & (uint64_t)(every - 1)) == 0) starts[(int64_t)(g / every) - sbase] = make_double2(zr, zi);
     const double2 Tp = ph[g & (uint64_t)(M - 1)];
     const double2 T = ph[(g + 1) & (uint64_t)(M - 1)];
     // a sub-step that ends on a start converges to 1e-2 of its predictor;
@@ -186,7 +186,7 @@ __device__ __forceinline__ bool walk_chunk_from(const PolyDev& P, const double2*
     steps += walk_substep_f64(P.m, P.lcap, cap_sign(P), zr, zi, T.x, T.y, Tp.x, Tp.y, Li, i > 0, zpr, zpi, rel,
                               16, h);
   }
-  if (j == nchunks - 1) starts[g / every] = make_double2(zr, 0.0);  // t = 1/2, real
+  if (j == nchunks - 1) starts[(int64_t)(g / every) - sbase] = make_double2(zr, 0.0);  // t = 1/2, real
   const double er = zr - zn.x, ei = zi - zn.y;
   // the end of the chunk must be the next seed, not a neighbour one turn away
   return !(er * er + ei * ei <= 0.0625 * h * h + 1e-28);

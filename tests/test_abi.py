@@ -72,3 +72,23 @@ def test_invalid_arguments_fail_cleanly(lib):
     o.prec = 7
     rc = L.mt_split_hyperbolic(12, ctypes.byref(o), None, None, 0, None, 0, ctypes.byref(n_out), None)
     assert rc == mt._lib.MT_EINVAL
+
+
+def test_streamed_plans_fit_one_gb300():
+    """Host-only planning: from p_32 on the split streams its level line
+    (more than 2^31 starts), and p_32 in MT_DD -- workspace plus roots and
+    low parts -- fits the GB300's HBM; stream_pieces must be a power of two."""
+    from paper_2402_06083_gb300 import _lib
+    L = _lib.load()
+
+    def ws(n, prec, pieces=0):
+        o = _lib.Options()
+        L.mt_default_options(ctypes.byref(o))
+        o.prec, o.max_retries, o.stream_pieces = prec, 0, pieces
+        return int(L.mt_workspace_bytes(0, 0, n, ctypes.byref(o)))
+
+    d32 = 2 ** 31
+    total = ws(32, 2) + 2 * d32 * 16
+    assert 0 < total < 250e9, total / 1e9
+    assert ws(31, 2) > ws(32, 2) / 2  # p_31 still runs in one pass
+    assert ws(20, 0, 4) > 0 and ws(20, 0, 3) == 0
