@@ -42,6 +42,7 @@ CONFIGS = {
     "hyp31dd": ("hyp", 0, 31, "dd"),  # 2^30 roots, ~230 GB of device memory
     "hyp32dd": ("hyp", 0, 32, "dd"),  # 2^31 roots, streamed level line, ~245 GB of device memory
     "mis16": ("misbatch", 0, 16, "fp64"),  # every s_{l,n}, l >= 2, n >= 1, l + n <= 16, one pass
+    "mis26dd": ("mis", 4, 22, "dd"),  # s_{4,22}: tip pair 4.86e-20 apart (Sec. 6.3.2), beyond FP80
     "q18": ("q", 9, 9, "fp64"),  # q_{9,9} = p_18 - p_9 with its multiple roots (Thm fact_mis)
 }
 
@@ -329,7 +330,7 @@ def main():
             rq = mt.split_misiurewicz_q(l, n, work=work)
             roots[:rq.roots.shape[0]].copy_(torch.view_as_real(rq.roots))
             return rq
-        return mt.split_misiurewicz(l, n, pp, work=work, out=roots)
+        return mt.split_misiurewicz(l, n, pp, work=work, out=roots, out_lo=roots_lo if pp == "dd" else None)
 
     def timed(p, steps):
         for _ in range(3):
@@ -414,7 +415,10 @@ def main():
                        if kind == "misbatch" else
                        ("q_{%d,%d} = p_%d - p_%d, %d distinct roots (degree %d with multiplicities, Thm fact_mis), "
                         "binary64, all certified" % (l, n, l + n, l, s0["n_roots"], d))
-                       if kind == "q" else "s_{%d,%d}" % (l, n)),
+                       if kind == "q" else
+                       "s_{%d,%d} = p_%d + p_%d, %d roots, %s, all certified" % (
+                           l, n, l + n - 1, l - 1, d, {"fp64": "plain binary64", "mixed": "mixed binary32/binary64",
+                                                       "dd": "binary64 + double-double zones"}[prec])),
                    "precision": prec, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": whole_job_rate(world, n_e2e, e2e_s), "unit": "roots/s", "h2d_bytes_per_step": 0,

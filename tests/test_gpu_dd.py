@@ -171,3 +171,37 @@ def test_dd_zone_radius_changes_work_not_roots(mt):
     both = (la != 0) & (lb != 0)
     dd = np.abs((za - zb) + (la - lb))[both]
     assert dd.size > 0 and dd.max() < TOL_DD
+
+
+@pytest.mark.parametrize("l,n", [(3, 23), (4, 22)])
+def test_dd_misiurewicz_order_26(mt, l, n):
+    """s_{3,23} and s_{4,22} (16.8M roots each): the first Misiurewicz order
+    that FP80 cannot resolve (Sec. 6.3.2: two real points of Mis(3,23) and
+    of Mis(4,22) at the left end of M lie less than 4.86e-20 < 2^-64 apart).
+    MT_DD returns every root certified with the exact type histogram, and the
+    closest left-tip pair lies below 2^-64 -- for Mis(4,22) at the paper's
+    4.86e-20 -- as binary128 Newton of the oracle confirms."""
+    res = mt.split_misiurewicz(l, n, "dd", want_lo=True, max_retries=0)
+    st = res.stats
+    d = 2 ** (l + n - 2)
+    assert st["n_roots"] == d and st["n_cert_pass"] == d and st["prec_used"] == 2
+    for (a, k), cnt in counts.type_histogram_s(l, n).items():
+        assert st["count_by_type"][k if a == l else 32 + k] == cnt
+    z, zl = res.roots[:64].cpu().numpy(), res.roots_lo[:64].cpu().numpy()
+    o = np.lexsort((zl.real, z.real))
+    z, zl = z[o], zl[o]
+    assert np.all(z.imag[:16] == 0)
+    gaps = (z.real[1:16] - z.real[:15]) + (zl.real[1:16] - zl.real[:15])
+    i = int(np.argmin(gaps))
+    assert 0 < gaps[i] < 2.0 ** -64
+    # the pair in binary128: the oracle's Newton moves neither point by 1e-28
+    pts = []
+    for j in (i, i + 1):
+        c4 = np.array([z[j].real, zl[j].real, 0.0, 0.0])
+        out, _ = oracle.polish("mis", n, c4, l=l, steps=3)
+        assert abs((out[0] - c4[0]) + (out[1] - c4[1])) < TOL_DD
+        pts.append(out)
+    gap128 = (pts[1][0] - pts[0][0]) + (pts[1][1] - pts[0][1])
+    assert abs(gap128 - gaps[i]) < 1e-27
+    if (l, n) == (4, 22):
+        assert 4.8e-20 < gaps[i] < 4.86e-20
