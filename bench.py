@@ -98,7 +98,7 @@ def roofline(prec: str, m: int, stats: list, config: str = "", desc_flops: int |
         walk_eq = walk_steps * fl * ratio
         desc_eq = (s0["desc_newton"] - s0["desc_fp32"]) * fl + s0["desc_fp32"] * fl * ratio
     kern, eq, ms = ("k_descend", desc_eq, desc_ms) if desc_ms >= walk_ms else ("k_walk", walk_eq, walk_ms)
-    if prec != "fp64":
+    if prec != "fp64" and s0["desc_fp32"] + s0["steps_fp32"] > 0:  # the attempt ran the mixed tier
         kern += "_mixed"
     achieved = eq / (ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -408,7 +408,8 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (inputs fixed by n)",
         "config": {"workload": ("p_%d hyperbolic centres, %d roots, %s, all certified" % (
                        n, d, {"fp64": "plain binary64", "mixed": "mixed binary32/binary64",
-                              "dd": "mixed binary32/binary64 + double-double zones"}[prec])
+                              "dd": ("mixed binary32/binary64" if s0["desc_fp32"] > 0 else "binary64")
+                              + " + double-double zones"}[prec])
                        if kind == "hyp" else
                        ("all s_{l,n} with l >= 2, n >= 1, l + n <= %d (%d polynomials, %d roots), one pass, "
                         "binary64, all certified" % (n, len(mt.misiurewicz_pairs(n)), d))
