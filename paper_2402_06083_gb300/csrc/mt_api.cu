@@ -262,6 +262,9 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   if (dd) {
     p.dd = 1;
     p.dd_all = o->dd_all ? 1 : 0;
+    // a zone must hold the whole cluster binary64 cannot resolve around its
+    // centre.  1e-11 suffices at p_28 and p_29 (a third of the pieces of
+    // 1e-9) but loses roots at p_32, where that cluster by -2 is wider: 1e-9
     p.dd_R = o->dd_radius > 0 ? o->dd_radius : 1e-9;
     p.dd_margin = std::max(1e-11, 100.0 * p.eps);
     p.eps_dd = std::max(1e-28, raw_eps(kind, l, n));
@@ -876,11 +879,22 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   int retry = 0;
   const unsigned long long launches0 = g_launches;
   const int max_retries = max_attempts(o);
+  // a streamed split runs the attempt meant for the mixed tier in binary64,
+  // so the binary64 attempt after it would repeat it: skipped
+  bool skip_repeat = false;
+  if (o->prec == MT_MIXED || o->prec == MT_DD) {
+    Plan p0;
+    skip_repeat = make_plan(kind, l, n, o, 0, &p0) && p0.stream_P > 1;
+  }
   EventSet* evp = &ev;
   DdReport ddr;
   StreamTimes stimes;
   bool dd_ran = false;
   for (;; ++retry) {
+    if (skip_repeat && retry == 1) {
+      if (retry >= max_retries) break;
+      continue;
+    }
     if (!make_plan(kind, l, n, o, retry, &p)) return fail(MT_EINVAL, "no plan for retry %d", retry);
     Buffers b = carve(p, d_work, work_bytes);
     evp = &ev;

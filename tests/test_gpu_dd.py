@@ -157,9 +157,9 @@ def test_dd_complete_and_certified(mt, n):
 
 
 def test_dd_zone_radius_changes_work_not_roots(mt):
-    """A ten times larger zone radius redoes more roots in dd but returns the
-    same certified set (every root within 4e-15, roots redone in dd by both
-    runs within TOL_DD)."""
+    """A larger zone radius (1e-8 against the default 1e-9) redoes more roots
+    in dd but returns the same certified set (every root within 4e-15, roots
+    redone in dd by both runs within TOL_DD)."""
     n = 26
     a = _split(mt, "hyp", n, max_retries=0)
     b = _split(mt, "hyp", n, max_retries=0, dd_radius=1e-8)

@@ -70,3 +70,26 @@ def test_q_rejects_other_tiers(mt):
     from paper_2402_06083_gb300._lib import MtError
     with pytest.raises((MtError, ValueError)):
         mt.split_misiurewicz_q(3, 4, "mixed")
+
+
+def test_q_list_entry_points(mt):
+    """mt_certify(kind 2) on the split's roots: Hyp roots proven on p_n, Mis
+    roots on q, all pass; mt_classify(kind 2): 32 + k for Hyp(k), k for
+    Mis(l,k), 0 for Mis(j,k) with j < l -- consistent with pre / per."""
+    import torch
+    l, n = 4, 6
+    res = mt.split_misiurewicz_q(l, n)
+    ok, rad, npass = mt.certify("q", n, res.roots, l=l)
+    assert npass == res.roots.shape[0] and bool(torch.all(rad > 0))
+    t = mt.classify("q", n, res.roots, l=l).cpu().numpy()
+    pre, per = res.pre.cpu().numpy(), res.per.cpu().numpy()
+    want = np.where(pre == 0, 32 + per, np.where(pre == l, per, 0))
+    assert np.array_equal(t, want)
+
+
+def test_q_rejects_out_of_range(mt):
+    from paper_2402_06083_gb300._lib import MtError
+    with pytest.raises((MtError, ValueError)):
+        mt.split_misiurewicz_q(0, 5)   # l >= 1
+    with pytest.raises((MtError, ValueError)):
+        mt.split_misiurewicz_q(30, 11)  # l + n <= 40
