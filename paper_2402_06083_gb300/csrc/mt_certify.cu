@@ -390,10 +390,10 @@ __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
   }
   warp_add_u64(&ctr->n_cert_pass, npass);
   if (overflow) atomicAdd(&ctr->cluster_overflow, 1ull);
-  if (valid && ok) {
-    atomicMin(&ctr->min_radius_bits, (unsigned long long)__double_as_longlong(rad));
-    atomicMax(&ctr->max_radius_bits, (unsigned long long)__double_as_longlong(rad));
-  }
+  // radii are >= 0: their bit patterns order like the values
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(rad);
+  warp_min_u64(&ctr->min_radius_bits, (valid && ok) ? rb : ~0ull);
+  warp_max_u64(&ctr->max_radius_bits, (valid && ok) ? rb : 0ull);
 }
 
 // ---------------------------------------------------------------------------

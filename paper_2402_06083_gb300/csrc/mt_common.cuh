@@ -197,6 +197,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Min / max of per-lane 64-bit values over the warp, applied once to *dst
+// (all 32 lanes call; a lane with nothing to report passes the neutral
+// value ~0 for min, 0 for max).  One atomic per warp instead of per lane:
+// per-lane atomics on one address serialise in L2.
+__device__ __forceinline__ void warp_min_u64(unsigned long long* dst, unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v != ~0ull) atomicMin(dst, v);
+}
+__device__ __forceinline__ void warp_max_u64(unsigned long long* dst, unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v != 0ull) atomicMax(dst, v);
+}
+
 // Sum a per-lane 64-bit counter over the warp and add it once to *dst.
 __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

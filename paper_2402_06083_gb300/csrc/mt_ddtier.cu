@@ -622,10 +622,9 @@ __global__ void k_dd_type_cert(PolyDev P, const dd* __restrict__ rx, const dd* _
   }
   warp_add_u64(&ctr->n_cert_pass, npass);
   warp_add_u64(&ctr->n_reps_real, nreal);
-  if (u < n && ok) {
-    atomicMin(&ctr->min_radius_bits, (unsigned long long)__double_as_longlong(rad));
-    atomicMax(&ctr->max_radius_bits, (unsigned long long)__double_as_longlong(rad));
-  }
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(rad);
+  warp_min_u64(&ctr->min_radius_bits, (u < n && ok) ? rb : ~0ull);
+  warp_max_u64(&ctr->max_radius_bits, (u < n && ok) ? rb : 0ull);
 }
 
 // Main representatives after the zone pass: kmult = mult of the kept ones;

@@ -110,6 +110,26 @@ __device__ __forceinline__ void record(double best, double x, unsigned long long
   }
 }
 
+// The same for a whole warp (all 32 lanes call; has = the lane has a value):
+// one atomic for the list minimum, and one for the band minimum when the
+// warp's values share a band (roots sorted by Re mostly do), else per lane.
+__device__ __forceinline__ void record_warp(bool has, double best, double x, unsigned long long* band_min) {
+  has = has && best < pos_inf();
+  const unsigned long long bits = has ? (unsigned long long)__double_as_longlong(best) : ~0ull;
+  const int band = has ? sep_band(x) : -1;
+  warp_min_u64(&band_min[64], bits);
+  const int lead = __ffs(__ballot_sync(0xffffffffu, has)) - 1;
+  if (lead < 0) return;
+  const int band0 = __shfl_sync(0xffffffffu, band, lead);
+  if (__all_sync(0xffffffffu, !has || band == band0)) {
+    unsigned long long v = bits;
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&band_min[band0], v);
+  } else if (has) {
+    atomicMin(&band_min[band], bits);
+  }
+}
+
 // Strip of a real part: monotone non-decreasing in x (a subtraction and a
 // multiplication by a positive constant, both correctly rounded, then a
 // clamp), which is all the strip walk relies on.  Points outside [-2.25,
@@ -171,14 +191,16 @@ __global__ void k_separation(const double2* __restrict__ hi, const double2* __re
                              unsigned long long* __restrict__ nisolated,
                              uint32_t* __restrict__ iso_idx, double* __restrict__ iso_best) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+  bool has = false;
+  double best = pos_inf(), cx = 0.0;
+  if (p < n) {
   const int64_t ip = order[p];
   if (mask && !mask[ip]) {
     if (nn_out) nn_out[ip] = 0.0;
-    return;
-  }
+  } else {
   const double2 c = hi[ip];
-  double best = pos_inf(), thr = pos_inf();
+  cx = c.x;
+  double thr = pos_inf();
   int scanned = 0;
   bool cut = false;
   for (int dir = -1; dir <= 1 && !cut; dir += 2) {
@@ -201,10 +223,13 @@ __global__ void k_separation(const double2* __restrict__ hi, const double2* __re
     const unsigned long long k = atomicAdd(nisolated, 1ull);
     iso_idx[k] = (uint32_t)ip;  // k < n: each root is added at most once
     iso_best[k] = best;
-    return;
+  } else {
+    if (nn_out) nn_out[ip] = best;
+    has = true;
   }
-  if (nn_out) nn_out[ip] = best;
-  record(best, c.x, band_min);
+  }
+  }
+  record_warp(has, best, cx, band_min);
 }
 
 __global__ void k_strip_keys(const double2* __restrict__ hi, int64_t n, int S, double scale,
@@ -239,10 +264,14 @@ __global__ void k_separation_strip_thread(const double2* __restrict__ hi, const 
                                           uint32_t* __restrict__ iso2_idx, double* __restrict__ iso2_best,
                                           unsigned long long* __restrict__ niso2) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= (int64_t)*niso) return;
+  bool has = false;
+  double best = pos_inf(), cx = 0.0;
+  if (r < (int64_t)*niso) {
   const int64_t ip = iso_idx[r];
   const double2 c = hi[ip];
-  double best = iso_best[r], thr = sq_threshold(best);
+  cx = c.x;
+  best = iso_best[r];
+  double thr = sq_threshold(best);
   const int sq = strip_of(c.x, S, scale);
   int strips = 0, points = 0;
   bool defer = false;
@@ -284,10 +313,12 @@ __global__ void k_separation_strip_thread(const double2* __restrict__ hi, const 
     const unsigned long long k = atomicAdd(niso2, 1ull);  // k < *niso
     iso2_idx[k] = (uint32_t)ip;
     iso2_best[k] = best;
-    return;
+  } else {
+    if (nn_out) nn_out[ip] = best;
+    has = true;
   }
-  if (nn_out) nn_out[ip] = best;
-  record(best, c.x, band_min);
+  }
+  record_warp(has, best, cx, band_min);
 }
 
 // tier 3: one block per root left by tier 2 walks the strips outward from
