@@ -335,12 +335,13 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
        linearly, |step_{k+1}| / |step_k| -> 1 - 1/mu (eq. newtonLin).  When
        three successive ratios agree and give mu within 0.15 of an integer
        m >= 2, a trial step z - m P/P' is taken (eq. newtonAcc).  Next to a
-       multiple root it lands much closer and the next plain step is short:
-       the multiplicity is then taken as m and every following step is
-       z - m P/P', which converges quadratically to the multiple root.  A
-       cluster of simple roots looks the same from afar, but the trial step
-       then lands at its centre, near a critical point, where the next
-       plain step is long: the trial is undone and the descent goes on with
+       multiple root it lands much closer, the next plain step is short, and
+       the Newton step of p_n (of which the multiple root is a simple root,
+       Thm fact_mis) is m times that of q: the multiplicity is then taken as
+       m and every following step is z - m P/P', which converges
+       quadratically to the multiple root.  A cluster looks the same from
+       afar, but the trial step then lands near its centre, where one of the
+       two tests fails: the trial is undone and the descent goes on with
        plain Newton, which separates the cluster.  If an accelerated descent
        stalls (the rounding noise around a multiple root) and Newton on p_n
        -- of which every multiple root of q is a simple root (Thm fact_mis)
@@ -356,7 +357,17 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
       cplx step = cdiv(v, dv);
       st->desc_newton++;
       if (trial) { /* the first plain step after the trial step */
-        if (cabs_(step) <= s_acc / 2) {
+        int ok = cabs_(step) <= s_acc / 2;
+        if (ok) {
+          /* next to a root of multiplicity m -- a simple root of p_n -- the
+             p_n step is m times the q step (a cluster's centre gives another
+             ratio) */
+          cplx v2, d2;
+          eval_pk(P->n, w, &v2, &d2);
+          real ratio = cabs_(cdiv(v2, d2)) / cabs_(step);
+          ok = ratio >= 0.75 * trial && ratio <= 1.25 * trial;
+        }
+        if (ok) {
           mult = trial;
         } else { /* the trial overshot into a cluster: undo it */
           w = w_pre;
