@@ -221,25 +221,58 @@ def oracle_units(kind: str, l: int, n: int) -> int:
     return oracle.degree(kind, n, l)
 
 
-def cpu_baseline(kind: str, l: int, n: int, target_s: float = 15.0) -> dict:
-    """The binary64 oracle, as it stands, on a bounded sample of the same
-    workload: the first fraction of the level line (walk + descents + set).
-    Rate = roots in that fraction of the line / time (single thread)."""
+def _oracle_sample(args) -> float:
+    """One process: the binary64 oracle on the first `frac` of the level
+    line; returns its wall time."""
+    kind, l, n, frac = args
     import oracle
-    d = oracle_units(kind, l, n)
-    frac = 1.0 / 64
     t0 = time.perf_counter()
     oracle.split(kind, n, l=l, fp64=True, frac=frac, want_types=False)
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def oracle_rate(kind: str, l: int, n: int, frac: float, procs: int) -> tuple[float, float]:
+    """The oracle, as it stands, in `procs` spawned processes (one per host
+    core; spawn, since CUDA is initialised in this process), each splitting
+    the same first `frac` of the level line.  Returns (aggregate roots/s,
+    wall seconds)."""
+    d = oracle_units(kind, l, n)
+    if procs <= 1:
+        dt = _oracle_sample((kind, l, n, frac))
+        return d * frac / dt, dt
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_sample, [(kind, l, n, min(frac, 1.0 / 4096))] * procs)  # import + load the oracle
+        t0 = time.perf_counter()
+        pool.map(_oracle_sample, [(kind, l, n, frac)] * procs)
+        dt = time.perf_counter() - t0
+    return procs * d * frac / dt, dt
+
+
+def host_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def cpu_baseline(kind: str, l: int, n: int, target_s: float = 15.0) -> dict:
+    """The binary64 oracle, as it stands, on a bounded sample of the same
+    workload -- the first fraction of the level line (walk + descents + set)
+    -- in one process per host core.  Rate = roots in that fraction of the
+    line x processes / wall time."""
+    procs = host_cores()
+    frac = 1.0 / 64
+    _, dt = oracle_rate(kind, l, n, frac, 1)
     # grow the sample to about target_s seconds (bounded: at most the whole line)
     if dt < target_s:
         frac = min(1.0, frac * target_s / max(dt, 1e-3))
-        t0 = time.perf_counter()
-        oracle.split(kind, n, l=l, fp64=True, frac=frac, want_types=False)
-        dt = time.perf_counter() - t0
-    return {"value": d * frac / dt, "unit": "roots/s", "cores": 1, "kind": "oracle",
+    rate, dt = oracle_rate(kind, l, n, frac, procs)
+    return {"value": rate, "unit": "roots/s", "cores": procs, "kind": "oracle",
             "sample": "binary64 oracle (same algorithm, sequential walk), first %.4f of the level line of "
-                      "%s n=%d, %.1f s, 1 thread; rate = roots x fraction / time" % (frac, kind, n, dt)}
+                      "%s n=%d in each of %d processes (one per host core), %.1f s wall; rate = roots x "
+                      "fraction x processes / wall time" % (frac, kind, n, procs, dt)}
 
 
 def run_reference(args, cfg):
@@ -247,26 +280,25 @@ def run_reference(args, cfg):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
     d = oracle_units(kind, l, n)
     frac = 1.0 / 32  # each step: a bounded sample of the same workload
+    procs = host_cores()
     for _ in range(args.warmup):
-        oracle.split(kind, n, l=l, fp64=True, frac=frac, want_types=False)
+        oracle_rate(kind, l, n, frac, procs)
     times = []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.split(kind, n, l=l, fp64=True, frac=frac, want_types=False)
-        times.append(time.perf_counter() - t0)
+        times.append(oracle_rate(kind, l, n, frac, procs)[1])
     ms = 1e3 * statistics.mean(times)
-    value = d * frac / (ms / 1e3)
+    value = procs * d * frac / (ms / 1e3)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "roots/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "%s n=%d (%d roots)" % (kind, n, d), "precision": prec,
-                   "sample": "first %.4f of the level line per step" % frac},
-        "cpu_baseline": {"value": value, "unit": "roots/s", "cores": 1, "kind": "oracle",
-                         "sample": "binary64 oracle, first %.4f of the level line per step, 1 thread" % frac},
+                   "sample": "first %.4f of the level line per step, %d processes" % (frac, procs)},
+        "cpu_baseline": {"value": value, "unit": "roots/s", "cores": procs, "kind": "oracle",
+                         "sample": "binary64 oracle, first %.4f of the level line per step in each of %d processes "
+                                   "(one per host core)" % (frac, procs)},
         "e2e": {"value": value, "unit": "roots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
