@@ -197,7 +197,9 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   int64_t N0;
   TuneVal tv{0, 0};
   const bool have_tune = tuned(kind, kind == 0 ? 0 : l, n, p.prec, &tv);
-  p.walk_block = (o && o->block > 0) ? o->block : (have_tune && tv.walk_block > 0 ? tv.walk_block : 64);
+  // one lane per chunk: 32-thread blocks spread the 2^14 - 2^17 lanes over the
+  // 152 SMs more evenly than 64 (mt_autotune, p_20 / p_22 / p_24: best at 32)
+  p.walk_block = (o && o->block > 0) ? o->block : (have_tune && tv.walk_block > 0 ? tv.walk_block : 32);
   if (o && o->chunk_log2 > 0) {
     N0 = Md >> o->chunk_log2;
   } else if (have_tune && tv.chunk_log2 > 0) {
