@@ -47,7 +47,7 @@
 #include <string.h>
 
 #ifndef ORACLE_MUTANT
-#define ORACLE_MUTANT 0 /* 0 = the oracle; 1..5 plant a known mistake (tests only) */
+#define ORACLE_MUTANT 0 /* 0 = the oracle; 1..7 plant a known mistake (tests only) */
 #endif
 
 #if defined(ORACLE_FP64)
@@ -168,7 +168,11 @@ static void eval_P(const poly* P, cplx c, cplx* v, cplx* dv) {
 #else
   int lcap = (P->kind == 1) ? P->l - 1 : -1;
 #endif
+#if ORACLE_MUTANT == 6 /* planted mistake: q_{l,n} built with p_{l-1} instead of p_l */
+  if (P->kind == 2) lcap = P->l - 1;
+#else
   if (P->kind == 2) lcap = P->l;
+#endif
   if (lcap == 0) { zl = z; dzl = dz; }
   for (int k = 1; k <= P->m; ++k) {
 #if ORACLE_MUTANT == 1 /* planted mistake: derivative from p_k instead of p_{k-1} */
@@ -676,7 +680,11 @@ long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
             reps[i] = csub(reps[i], step);
             if (reps[i].im != 0 && rabs(reps[i].im) < eps / 2) reps[i].im = 0;
           }
+#if ORACLE_MUTANT == 7 /* planted mistake: eta_l(k) with l in place of l - 1 */
+          mu = P.l / b + 2;
+#else
           mu = (P.l - 1) / b + 2;
+#endif
         }
         nmult += mu * (reps[i].im == 0 ? 1 : 2);
       }

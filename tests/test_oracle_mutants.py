@@ -2,13 +2,16 @@
 on the CPU with -DORACLE_MUTANT=k) fails at least one pin of
 test_oracle_pins.py.  Mutants: 1 derivative from the wrong orbit index,
 2 wrong sign in Re(z^2), 3 s_{l,n} built with p_l instead of p_{l-1},
-4 level line walked the wrong way, 5 missing conjugate fold."""
+4 level line walked the wrong way, 5 missing conjugate fold, 6 q_{l,n} built
+with p_{l-1} instead of p_l, 7 the multiplicity eta_l(k) of Thm fact_mis off
+by one in the count."""
 from __future__ import annotations
 
 import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_q as qpins
 
 # (mutant, pin function, its arguments)
 CASES = [
@@ -19,6 +22,9 @@ CASES = [
     (3, pins.test_s_2_4_example, ()),
     (4, pins.test_level_line_iso_angle_zero, (4,)),
     (5, pins.test_counts_and_exact_periods, (8,)),
+    (6, qpins.test_worked_factorisation_q_2_4, ()),
+    (6, qpins.test_types_and_multiplicities_follow_thm_fact_mis, (3, 4)),
+    (7, qpins.test_types_and_multiplicities_follow_thm_fact_mis, (4, 2)),
 ]
 
 
