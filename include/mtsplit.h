@@ -92,7 +92,8 @@ typedef struct {
      whose own root set is the result; the starts never all reside in
      memory.  0 -> automatic: 1, or the fewest pieces of at most 2^28 starts
      once the upper half holds more than 2^31 starts (p_32 and up).
-     Streamed pieces run in binary64 (MT_MIXED falls back to MT_FP64). */
+     Given explicitly, the pieces run in the requested tier; the automatic
+     streaming runs its first attempt in binary64. */
   int stream_pieces;
 } mt_options;
 

@@ -224,9 +224,12 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   if (P & (P - 1)) return false;
   if (P > 1) {
     // one lane per chunk: a piece needs tens of thousands of chunks to fill
-    // the GPU, so streamed splits cut the line finer; pieces run in binary64
+    // the GPU, so streamed splits cut the line finer
     if (!(o && o->chunk_log2 > 0)) N0 = std::min<int64_t>(int64_t(1) << 20, Md / 16);
-    p.prec = MT_FP64;
+    // automatic streaming (p_32 and up) starts in binary64: there the mixed
+    // tier leaves roots its dd zones do not recover (as at p_30), and the
+    // binary64 repeat would cost a second full pass
+    if (!(o && o->stream_pieces > 0)) p.prec = MT_FP64;
   }
   // L must be a multiple of 'every' and N0 >= 2
   while (N0 > 2 && (Md / N0) % p.every) N0 >>= 1;
@@ -365,10 +368,13 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
     b.candq = p.dd ? c.take<int2>(p.S) : nullptr;
     b.candq_n = p.S;
     b.reps = c.take<double2>(Gc);
-    b.type = c.take<uint8_t>(Gc);
+    b.type = c.take<uint8_t>(Mx);  // also the finish links of a mixed piece
     b.pass = c.take<uint8_t>(Gc);
     b.radius = c.take<double>(Gc);
     b.drop = c.take<uint8_t>(Gc);
+    b.anchors = (p.prec == MT_MIXED) ? c.take_bytes(mixed_anchor_bytes(p.P, Sp)) : nullptr;
+    b.seed_bad = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks + 1) : nullptr;
+    b.chunk_fail = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks) : nullptr;
   } else {
   b.starts = c.take<double2>(p.S);
   b.cand = c.take<double2>(p.S);
@@ -583,7 +589,13 @@ mt_status run_streamed(const Plan& p, const Buffers& b, double2* out, double2* o
   CK(launch_init_counters(b.ctr, s));
   CK(cudaMemsetAsync(b.gstate, 0, 4 * sizeof(unsigned long long), s));
   CK(cudaEventRecord(ev.e[0], s));
-  CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+  const bool mixed = p.prec == MT_MIXED;
+  if (mixed) {
+    CK(launch_seed_lift_mixed(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.seed_bad, b.ctr, s));
+    CK(launch_mixed_repair_seeds(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.seed_bad, b.ctr, s));
+  } else {
+    CK(launch_seed_lift(p.P, p.lambda0, p.N0, p.shrink, b.seeds, b.ctr, s));
+  }
   CK(cudaEventRecord(ev.e[6], s));
   const int64_t C = p.nchunks / p.stream_P;
   std::vector<cudaEvent_t> pe((size_t)(4 * p.stream_P), nullptr);
@@ -599,11 +611,26 @@ mt_status run_streamed(const Plan& p, const Buffers& b, double2* out, double2* o
     const int64_t j0 = k * C;
     const int64_t Sk = C * p.L / p.every + (k == p.stream_P - 1 ? 1 : 0);
     CK(cudaEventRecord(pe[4 * k], s));
-    CK(launch_walk_range(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, j0, C, b.seeds, b.starts, b.ctr, s,
-                         p.walk_block));
+    if (mixed) {
+      CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts, b.chunk_fail,
+                           b.ctr, s, p.walk_block, j0, C));
+      CK(launch_mixed_repair_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.shrink, b.seeds, b.starts,
+                                  b.chunk_fail, b.ctr, s, j0, C));
+    } else {
+      CK(launch_walk_range(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, j0, C, b.seeds, b.starts, b.ctr, s,
+                           p.walk_block));
+    }
     CK(cudaEventRecord(pe[4 * k + 1], s));
     CK(cudaMemsetAsync(&b.ctr->queue_head, 0, sizeof(unsigned long long), s));
-    CK(launch_descend(p.P, b.starts, Sk, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
+    if (mixed) {
+      // the sort buffers are free until the fold: binary32 deltas and scales
+      // in keys / vals, the finish lists in flag / pos / vals_alt / type
+      FinishScratch fin{b.flag, b.pos, b.vals_alt, b.type, b.scan_tmp, &b.ctr->n_finish};
+      CK(launch_descend_mixed(p.P, b.starts, Sk, p.tol, p.cap, b.cand, (float2*)b.keys, (float*)b.vals,
+                              b.status, b.anchors, fin, b.ctr, s));
+    } else {
+      CK(launch_descend(p.P, b.starts, Sk, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
+    }
     CK(cudaEventRecord(pe[4 * k + 2], s));
     CK(launch_piece_valid(b.ctr, snap, nvalid, s));
     CK(launch_fold_keys(b.status, b.cand, Sk, p.eps, b.keys, b.vals, s));
@@ -881,12 +908,12 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   int retry = 0;
   const unsigned long long launches0 = g_launches;
   const int max_retries = max_attempts(o);
-  // a streamed split runs the attempt meant for the mixed tier in binary64,
-  // so the binary64 attempt after it would repeat it: skipped
+  // a first attempt that could not run in the mixed tier (q_{l,n}, which is
+  // binary64 only) was binary64 already: its binary64 repeat is skipped
   bool skip_repeat = false;
   if (o->prec == MT_MIXED || o->prec == MT_DD) {
     Plan p0;
-    skip_repeat = make_plan(kind, l, n, o, 0, &p0) && p0.stream_P > 1;
+    skip_repeat = make_plan(kind, l, n, o, 0, &p0) && p0.prec != MT_MIXED;
   }
   EventSet* evp = &ev;
   DdReport ddr;

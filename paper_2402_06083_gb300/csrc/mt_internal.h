@@ -91,16 +91,19 @@ cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t coun
 // failures that the binary64 repairs then redo.
 cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0, int shrink_steps,
                                    double2* seeds, uint8_t* seed_bad, DevCounters* ctr, cudaStream_t s);
+// j0 / nch: chunks [j0, j0 + nch) only, their starts written from index 0
+// (a streamed split's piece); nch < 0: the whole line
 cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                               int64_t nchunks, int K, const double2* seeds, double2* starts,
-                              uint8_t* chunk_fail, DevCounters* ctr, cudaStream_t s, int block = 64);
+                              uint8_t* chunk_fail, DevCounters* ctr, cudaStream_t s, int block = 64,
+                              int64_t j0 = 0, int64_t nch = -1);
 cudaError_t launch_mixed_repair_seeds(const PolyDev& P, double lambda0, int64_t N0, int shrink,
                                       double2* seeds, uint8_t* seed_bad, DevCounters* ctr,
                                       cudaStream_t s);
 cudaError_t launch_mixed_repair_walk(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                                      int64_t nchunks, int shrink, const double2* seeds,
                                      double2* starts, uint8_t* chunk_fail, DevCounters* ctr,
-                                     cudaStream_t s);
+                                     cudaStream_t s, int64_t j0 = 0, int64_t nch = -1);
 // Scratch of the binary64 finish of the mixed tier (count entries each).
 struct FinishScratch {
   uint32_t *head, *pos, *list;

@@ -132,7 +132,7 @@ __global__ void k_seed_repair(PolyDev P, double lambda0, int64_t N0, int log2N0,
 __global__ void k_walk_repair(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
                               int64_t N0, int log2N0, int shrink, const double2* __restrict__ seeds,
                               double2* __restrict__ starts, uint8_t* __restrict__ chunk_fail,
-                              DevCounters* ctr) {
+                              DevCounters* ctr, int64_t j0, int64_t nch) {
   __shared__ double2 ph[64];
   for (int q = threadIdx.x; q < M; q += blockDim.x) {
     double c, s;
@@ -140,12 +140,13 @@ __global__ void k_walk_repair(PolyDev P, double lambda0, int M, int every, int64
     ph[q] = make_double2(lambda0 * c, lambda0 * s);
   }
   __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t jl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = j0 + jl;
   unsigned long long steps = 0, fixed = 0;
-  if (j < nchunks && chunk_fail[j]) {
+  if (jl < nch && j < nchunks && chunk_fail[j]) {
     const double2 a = lift_seed(P, lambda0, N0, log2N0, shrink, j, steps);
     const double2 b = lift_seed(P, lambda0, N0, log2N0, shrink, j + 1, steps);
-    if (!walk_chunk_from(P, ph, M, every, L, nchunks, j, a, b, starts, steps)) {
+    if (!walk_chunk_from(P, ph, M, every, L, nchunks, j, a, b, starts, steps, j0 * L / every)) {
       chunk_fail[j] = 0;
       fixed = 1;
     }
@@ -169,15 +170,15 @@ cudaError_t launch_mixed_repair_seeds(const PolyDev& P, double lambda0, int64_t 
 cudaError_t launch_mixed_repair_walk(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                                      int64_t nchunks, int shrink, const double2* seeds,
                                      double2* starts, uint8_t* chunk_fail, DevCounters* ctr,
-                                     cudaStream_t s) {
-  if (nchunks <= 0) return cudaSuccess;
+                                     cudaStream_t s, int64_t j0, int64_t nch) {
+  if (nch < 0) nch = nchunks - j0;
+  if (nch <= 0) return cudaSuccess;
   const int64_t N0 = 2 * nchunks;
   int log2N0 = 0;
   while ((int64_t(1) << log2N0) < N0) ++log2N0;
   MT_COUNT_LAUNCH(1);
-  k_walk_repair<<<(unsigned)((nchunks + 127) / 128), 128, 0, s>>>(P, lambda0, M, every, L, nchunks, N0,
-                                                                  log2N0, shrink, seeds, starts,
-                                                                  chunk_fail, ctr);
+  k_walk_repair<<<(unsigned)((nch + 127) / 128), 128, 0, s>>>(P, lambda0, M, every, L, nchunks, N0, log2N0,
+                                                              shrink, seeds, starts, chunk_fail, ctr, j0, nch);
   return cudaGetLastError();
 }
 

@@ -197,9 +197,12 @@ __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log
 }
 
 // a3 in the mixed tier.  Shared memory: m x blockDim binary32 pairs.
+// j0 / nch / sbase: chunks [j0, j0 + nch) only, start g / every written at
+// g / every - sbase (a streamed split's piece; 0 / nchunks / 0 for the whole line)
 __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
                              int K, const double2* __restrict__ seeds, double2* __restrict__ starts,
-                             uint8_t* __restrict__ chunk_fail, DevCounters* ctr) {
+                             uint8_t* __restrict__ chunk_fail, DevCounters* ctr, int64_t j0, int64_t nch,
+                             int64_t sbase) {
   extern __shared__ float2 zsh[];
   __shared__ float2 ph[64];
   for (int q = threadIdx.x; q < M; q += blockDim.x) {
@@ -210,9 +213,10 @@ __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_
   __syncthreads();
   float2* zs = zsh + threadIdx.x;
   const int stride = blockDim.x;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t jl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = j0 + jl;
   unsigned long long steps = 0, anchors = 0, fails = 0;
-  if (j < nchunks) {
+  if (jl < nch && j < nchunks) {
     const double2 s0 = seeds[j];
     double c0x = s0.x, c0y = s0.y;
     float4 v;
@@ -224,7 +228,7 @@ __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_
     uint64_t g = (uint64_t)j * (uint64_t)L;
     for (int64_t i = 0; i < L; ++i, ++g) {
       if ((g & (uint64_t)(every - 1)) == 0)
-        starts[g / every] = make_double2(c0x + (double)dx, c0y + (double)dy);
+        starts[(int64_t)(g / every) - sbase] = make_double2(c0x + (double)dx, c0y + (double)dy);
       const float2 Tp = ph[g & (uint64_t)(M - 1)];
       const float2 T = ph[(g + 1) & (uint64_t)(M - 1)];
       // tight (1e-2) only on the sub-steps that end on a start, as in walk_chunk
@@ -240,7 +244,7 @@ __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_
       }
     }
     const double cx = c0x + (double)dx, cy = c0y + (double)dy;
-    if (j == nchunks - 1) starts[g / every] = make_double2(cx, 0.0);
+    if (j == nchunks - 1) starts[(int64_t)(g / every) - sbase] = make_double2(cx, 0.0);
     const double2 zn = seeds[j + 1];
     const double er = cx - zn.x, ei = cy - zn.y;
     const double hh = (double)h;
@@ -550,14 +554,17 @@ cudaError_t launch_seed_lift_mixed(const PolyDev& P, double lambda0, int64_t N0,
 
 cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every, int64_t L,
                               int64_t nchunks, int K, const double2* seeds, double2* starts,
-                              uint8_t* chunk_fail, DevCounters* ctr, cudaStream_t s, int block) {
+                              uint8_t* chunk_fail, DevCounters* ctr, cudaStream_t s, int block, int64_t j0,
+                              int64_t nch) {
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
+  if (nch < 0) nch = nchunks - j0;
+  if (nch <= 0) return cudaSuccess;
   const int bs = (block >= 32 && block <= 256 && block % 32 == 0) ? block : 64;
   const size_t smem = (size_t)P.m * bs * sizeof(float2);
-  const int64_t grid = (nchunks + bs - 1) / bs;
+  const int64_t grid = (nch + bs - 1) / bs;
   MT_COUNT_LAUNCH(1);
   k_walk_mixed<<<(unsigned)grid, bs, smem, s>>>(P, lambda0, M, every, L, nchunks, K, seeds, starts,
-                                                chunk_fail, ctr);
+                                                chunk_fail, ctr, j0, nch, j0 * L / every);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,17 @@ def test_streamed_p20_equals_one_pass(mt, pieces):
     assert np.all(np.diff(r.real) >= 0)
 
 
+def test_streamed_mixed_equals_one_pass(mt):
+    """The mixed tier in streamed pieces (binary32 walk and descents with
+    their binary64 repairs and finishes, piece by piece)."""
+    ref = mt.split_hyperbolic(20, "mixed")
+    res = mt.split_hyperbolic(20, "mixed", stream_pieces=8)
+    d = 2 ** 19
+    assert res.stats["n_roots"] == d and res.stats["n_cert_pass"] == d
+    assert res.stats["prec_used"] == 1 and res.stats["steps_fp32"] > 0
+    _same(res.roots.cpu().numpy(), ref.roots.cpu().numpy())
+
+
 def test_streamed_misiurewicz_equals_one_pass(mt):
     ref = mt.split_misiurewicz(4, 12)
     res = mt.split_misiurewicz(4, 12, stream_pieces=8)
