@@ -91,3 +91,37 @@ def test_configs_are_well_formed(cfg):
     kind, l, n, prec = bench.CONFIGS[cfg]
     assert kind in ("hyp", "mis", "misbatch") and prec in ("fp64", "mixed", "dd")
     assert 1 <= n <= 40
+
+
+def _stats(**kw):
+    st = {"ms_walk": 2.0, "ms_seeds": 0.5, "ms_descend": 3.0, "walk_newton": 1000, "seed_newton": 100,
+          "desc_newton": 2000, "desc_fp32": 0, "steps_fp32": 0}
+    st.update(kw)
+    return st
+
+
+def test_roofline_arithmetic():
+    """achieved = counted steps x flops per step / kernel time; frac = / 1.25
+    TFLOP/s; the slower of walk and descents is the roofline kernel; binary32
+    steps count at the peak ratio; the mixed label only when binary32 ran."""
+    import bench
+    r = bench.roofline("fp64", 20, [_stats()])
+    assert r["kernel"] == "k_descend"
+    flops = 2000 * (13 * 20 + 24)
+    assert abs(r["achieved"] - flops / 3e-3 / 1e12) < 1e-12 and abs(r["frac"] - r["achieved"] / 1.25) < 1e-12
+    r = bench.roofline("fp64", 20, [_stats(ms_descend=1.0)])
+    assert r["kernel"] == "k_walk" and abs(r["flops_per_launch"] - 900 * 284) < 1e-6
+    mixed = bench.roofline("mixed", 20, [_stats(desc_fp32=1500, steps_fp32=1500)])
+    ratio = bench.FP64_PEAK_TFLOPS / bench.FP32_PEAK_TFLOPS
+    assert mixed["kernel"] == "k_descend_mixed"
+    assert abs(mixed["flops_per_launch"] - (500 * 284 + 1500 * 284 * ratio)) < 1e-6
+    assert bench.roofline("dd", 20, [_stats()])["kernel"] == "k_descend"  # no binary32 steps: binary64 label
+    q = bench.roofline("fp64", 18, [_stats()], desc_flops=13 * 9 + 50 * 9 + 24)
+    assert abs(q["flops_per_launch"] - 2000 * (13 * 9 + 50 * 9 + 24)) < 1e-6
+
+
+def test_oracle_units_count_distinct_roots_of_q():
+    import bench
+    from oracle import counts
+    assert bench.oracle_units("q", 2, 4) == sum(counts.type_histogram_q(2, 4).values()) == 23  # 8 Hyp + 15 Mis
+    assert bench.oracle_units("hyp", 0, 12) == 2048
