@@ -1,9 +1,9 @@
 """q_{l,n} = p_{l+n} - p_l with its multiple roots (Thm fact_mis) on the GPU
 (mt_split_misiurewicz_q) against the binary128 oracle.
 
-Every pair with l + n <= 12: the same distinct roots (within 1e-12, the
-binary64 parity tolerance of the other splits), the same types (preperiod,
-period) and multiplicities, exactly.  Larger orders: the types follow Thm
+Every pair with l + n <= 12, and three of order 14: the same distinct roots
+(within 1e-12, the binary64 parity tolerance of the other splits), the same
+types (preperiod, period) and multiplicities, exactly.  Larger orders: the types follow Thm
 fact_mis with eq. MisCount, and the multiplicities add up to the degree.
 Every root carries its certificate (Mis as a root of q, Hyp of p_n)."""
 from __future__ import annotations
@@ -37,7 +37,7 @@ def _hist(pre, per):
     return h
 
 
-@pytest.mark.parametrize("l,n", [(l, s - l) for s in range(2, 13) for l in range(1, s)])
+@pytest.mark.parametrize("l,n", [(l, s - l) for s in range(2, 13) for l in range(1, s)] + [(3, 11), (7, 7), (12, 2)])
 def test_q_matches_binary128_oracle(mt, l, n):
     res = mt.split_misiurewicz_q(l, n)
     st = res.stats
