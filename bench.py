@@ -8,6 +8,12 @@ walk, Newton descents, root set, types, certificates, sorted output.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--config hyp20]
     python bench.py --impl reference ...   # the CPU oracle on the same metric
 
+Other configurations: hyp12, hyp20mixed, hyp24, hyp24mixed (p_24 in the
+mixed tier), hyp26dd / hyp28dd / hyp29dd / hyp31dd (double-double zones),
+hyp32dd (streamed level line, ~245 GB), mis16 (every s_{l,n}, l + n <= 16,
+one pass), mis26dd (s_{4,22}, beyond FP80), q18 (q_{9,9} with its multiple
+roots).
+
 For N > 1 (torchrun) every rank splits its own copy of the workload
 (replicas: one polynomial is split on one GPU; sharding it would need a
 cross-rank exchange of the level-line seeds and of the root set), timing
