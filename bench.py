@@ -196,6 +196,23 @@ def separation_stats(mt, torch, n, roots, roots_lo, work, stream, reps=3) -> dic
             "double_double": roots_lo is not None}
 
 
+def error_vs_fp64(mt, torch, n: int, roots) -> dict:
+    """Max distance between the mixed tier's roots and a plain binary64 split
+    of the same p_n (every root of either certified).  Both lists are sorted
+    by (Re, Im); entries whose order differs between the two (near-equal real
+    parts) are re-paired with their nearest neighbour within 16 places."""
+    import numpy as np
+    ref = mt.split_hyperbolic(n, "fp64")
+    a = torch.view_as_complex(roots).cpu().numpy()
+    b = ref.roots.cpu().numpy()
+    d = np.abs(a - b)
+    for i in np.nonzero(d > 1e-10)[0]:
+        lo, hi = max(0, i - 16), min(b.size, i + 17)
+        d[i] = np.min(np.abs(b[lo:hi] - a[i]))
+    return {"max_abs": float(d.max()), "roots": int(a.size),
+            "note": "mixed-tier roots against the plain binary64 split of the same polynomial"}
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -488,6 +505,8 @@ def main():
                       "ms_walk": sm["ms_walk"], "ms_descend": sm["ms_descend"],
                       "ms_certify": sm["ms_certify"], "ms_dedup": sm["ms_dedup"],
                       "all_certified": all(x["n_cert_pass"] == d for x in st_mix)}}
+    if prec == "mixed" and kind == "hyp" and not args.no_compare:
+        line["error_vs_fp64"] = error_vs_fp64(mt, torch, n, roots)
     # separation statistics of the result (Sec. 6.3.2), timed on their own
     if kind == "hyp" and not args.no_compare:
         line["separation"] = separation_stats(mt, torch, n, roots, roots_lo, work, stream)

@@ -125,3 +125,23 @@ def test_oracle_units_count_distinct_roots_of_q():
     from oracle import counts
     assert bench.oracle_units("q", 2, 4) == sum(counts.type_histogram_q(2, 4).values()) == 23  # 8 Hyp + 15 Mis
     assert bench.oracle_units("hyp", 0, 12) == 2048
+
+
+def test_error_vs_fp64_repairs_local_order_swaps():
+    """The mixed-vs-binary64 error report pairs each root with its counterpart
+    even where near-equal real parts put the two lists in different orders."""
+    import numpy as np
+    import torch
+    import bench
+
+    rng = np.random.default_rng(7)
+    b = np.sort_complex(rng.standard_normal(64) + 1j * rng.standard_normal(64))
+    a = b.copy()
+    a[[10, 11]] = a[[11, 10]]          # a local order swap
+    a[30] += 3e-13                      # a small genuine difference
+    ref = type("R", (), {"roots": torch.from_numpy(b)})()
+    fake = type("MT", (), {"split_hyperbolic": staticmethod(lambda n, prec: ref)})()
+    roots = torch.view_as_real(torch.from_numpy(a)).contiguous()
+    e = bench.error_vs_fp64(fake, torch, 6, roots)
+    assert e["roots"] == 64
+    assert e["max_abs"] == pytest.approx(3e-13, rel=1e-3)
