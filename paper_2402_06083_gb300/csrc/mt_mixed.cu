@@ -52,27 +52,35 @@ __device__ __forceinline__ void ref_orbit(const PolyDev& P, double c0x, double c
 }
 
 // binary32 perturbation orbit: e = P(c0 + delta) - P(c0), D = P'(c0 + delta).
+// The derivative is carried as g_k = p'_k / 2^k (g_{k+1} = p_k g_k +
+// 2^-(k+1)): the same binary32 roundings as p'_{k+1} = 2 p_k p'_k + 1 up to
+// powers of two, without doubling p_k (12 binary32 operations a step, not 14).
 __device__ __forceinline__ void pert_eval(const PolyDev& P, const float2* zs, int stride, float dx,
                                           float dy, float& ex, float& ey, float& Dx, float& Dy) {
-  float e_x = 0.f, e_y = 0.f, d_x = 0.f, d_y = 0.f;
-  float ce_x = 0.f, ce_y = 0.f, cd_x = 0.f, cd_y = 0.f;
+  float e_x = 0.f, e_y = 0.f, g_x = 0.f, g_y = 0.f;
+  float ce_x = 0.f, ce_y = 0.f, cg_x = 0.f, cg_y = 0.f;
+  int hexp = (127 - 1) << 23;  // exponent field of 2^-(k+1), k = 0
 #pragma unroll 2
   for (int k = 0; k < P.m; ++k) {
     const float2 Z = zs[k * stride];
     const float zx = Z.x + e_x, zy = Z.y + e_y;  // p_k(c)
-    const float tzx = zx + zx, tzy = zy + zy;
-    const float nd_x = fmaf(tzx, d_x, fmaf(-tzy, d_y, 1.f));
-    const float nd_y = fmaf(tzx, d_y, tzy * d_x);
+    const float h = __int_as_float(hexp);
+    hexp -= 1 << 23;
+    const float ng_x = fmaf(zx, g_x, fmaf(-zy, g_y, h));
+    const float ng_y = fmaf(zx, g_y, zy * g_x);
     const float sx = Z.x + zx, sy = Z.y + zy;  // 2 Z_k + e_k
     const float ne_x = fmaf(sx, e_x, fmaf(-sy, e_y, dx));
     const float ne_y = fmaf(sx, e_y, fmaf(sy, e_x, dy));
-    e_x = ne_x; e_y = ne_y; d_x = nd_x; d_y = nd_y;
-    if (k + 1 == P.lcap) { ce_x = e_x; ce_y = e_y; cd_x = d_x; cd_y = d_y; }
+    e_x = ne_x; e_y = ne_y; g_x = ng_x; g_y = ng_y;
+    if (k + 1 == P.lcap) { ce_x = e_x; ce_y = e_y; cg_x = g_x; cg_y = g_y; }
   }
   ex = e_x + ce_x;
   ey = e_y + ce_y;
-  Dx = d_x + cd_x;
-  Dy = d_y + cd_y;
+  // p'_m + p'_lcap = 2^m (g_m + 2^(lcap-m) g_lcap), exact scalings
+  const float a = P.lcap > 0 ? __int_as_float((127 + P.lcap - P.m) << 23) : 0.f;
+  const float s = __int_as_float((127 + P.m) << 23);
+  Dx = fmaf(a, cg_x, g_x) * s;
+  Dy = fmaf(a, cg_y, g_y) * s;
 }
 
 // binary32 quotient; false when |D|^2 leaves the safe binary32 range.
