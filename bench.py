@@ -61,9 +61,10 @@ def peaks() -> dict:
         return {}
 
 
-# Work of one Newton step on an orbit of length m, in flops (FMA = 2): the
-# orbit step is 2 add + 5 FMA + 1 mul = 13 flops; the quotient with its
-# power-of-two guard, the target subtraction and the update about 24.
+# Work of one Newton step on an orbit of length m, in flops (FMA = 2): an
+# orbit step counts 13 flops (the kernels run it as 6 FMA + 1 mul + 1 add,
+# 14, so the count is on the low side); the quotient with its power-of-two
+# guard, the target subtraction and the update about 24.
 def newton_flops(m: int) -> int:
     return 13 * m + 24
 
@@ -77,11 +78,12 @@ SM_MAX_MHZ = 2070.0
 
 
 # DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
-# capture of the same kernel and workload (profiles/kernels_hyp20_fp64.md:
-# dram__bytes_read.sum 16.8 MB, dram__bytes_write.sum 0; the candidates it
-# writes stay in the 129 MB L2).  Only for kernels unchanged since that
-# capture; everything else reports null.
-TRAFFIC = {("hyp20", "k_descend"): 16.8e6}
+# capture of the same kernel build and workload, keyed by (config, kernel).
+# Only kernels unchanged since their capture are listed; the rest report
+# null.  The last k_descend capture (profiles/kernels_hyp20_fp64.md:
+# dram__bytes_read.sum 16.8 MB, write 0) predates its integer-pipe stop
+# tests, so it is not listed.
+TRAFFIC: dict = {}
 
 
 def roofline(prec: str, m: int, stats: list, config: str = "", desc_flops: int | None = None) -> dict:

@@ -173,10 +173,20 @@ __device__ __forceinline__ void eval_P(const PolyDev& P, double cr, double ci, d
 // scaled by the same power of two 2^-E, E the exponent of max(|c|, |d|)
 // (exact): the "simplify a common large factor" guard of Sec. 6.3.2 (remark
 // on the exponent range).  Non-finite inputs give NaN.
+// Non-negative binary64 values (+0 up to +inf) order as their bit patterns
+// read as signed 64-bit integers, so such compares can run on the integer
+// pipe instead of the binary64 one.  A NaN of either sign falls outside
+// [ord(+0), ord(+inf)].
+__device__ __forceinline__ long long ord_f64(double x) { return __double_as_longlong(x); }
+constexpr long long ORD_1E290 = 0x7c2485ce9e7a065fll;   // ord_f64(1e290)
+constexpr long long ORD_1EM290 = 0x03b8f2b061aea072ll;  // ord_f64(1e-290)
+constexpr long long ORD_QUARTER = 2ll << 52;            // ord(x) - ORD_QUARTER = ord(x / 4), x/4 normal
+
 __device__ __forceinline__ void cdiv_f64(double a, double b, double c, double d, double& qr,
                                          double& qi) {
-  double den = fma(c, c, d * d);
-  if (!(den <= 1e290 && den >= 1e-290)) {
+  double den = fma(c, c, d * d);  // in [+0, +inf], or NaN
+  const long long od = ord_f64(den);
+  if (!(od <= ORD_1E290 && od >= ORD_1EM290)) {
     const double m = fmax(fabs(c), fabs(d));
     const long long eb = __double_as_longlong(m) & 0x7ff0000000000000ll;
     const double sc = __longlong_as_double(0x7fe0000000000000ll - eb);  // 2^-E
@@ -192,8 +202,10 @@ __device__ __forceinline__ void cdiv_f64(double a, double b, double c, double d,
   qi = fma(b, c, -a * d) * inv;
 }
 
+// Both finite: exponent fields below all-ones (integer test on the high words).
 __device__ __forceinline__ bool finite2(double a, double b) {
-  return isfinite(a) && isfinite(b);
+  return ((__double2hiint(a) & 0x7ff00000) != 0x7ff00000) &&
+         ((__double2hiint(b) & 0x7ff00000) != 0x7ff00000);
 }
 
 // e^{2 i pi num / den} for integers with den a power of two <= 2^62.

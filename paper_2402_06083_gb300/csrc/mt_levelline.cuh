@@ -60,6 +60,23 @@ __device__ __forceinline__ int newton_target_f64(int m, int lcap, double alpha, 
   return it;
 }
 
+// Radii lambda0^(2 - i / shrink), i = 0 .. shrink, of the iso-angle shrink
+// steps of the lift: the same at every level, so a seed computes them once
+// (shrink + 1 binary64 pow calls instead of 2 shrink per level).  Larger
+// shrink counts (late retries) evaluate them in place.
+constexpr int LIFT_RADII = 65;
+
+__device__ __forceinline__ bool shrink_radii(double lambda0, int shrink, double* R) {
+  if (shrink >= LIFT_RADII) return false;
+  for (int i = 0; i <= shrink; ++i) R[i] = pow(lambda0, 2.0 - (double)i / shrink);
+  return true;
+}
+
+__device__ __forceinline__ double shrink_radius(const double* R, bool tab, double lambda0, int shrink,
+                                                int i) {
+  return tab ? R[i] : pow(lambda0, 2.0 - (double)i / shrink);
+}
+
 // a1 + a2: the seed at t = j / N0 (j = 0 .. N0/2), lifted through the
 // nested family (Sec. 4.2): a point z on |p_k| = lambda0 at phase 2 pi d_k t
 // satisfies p_{k+1}(z) = lambda0^2 e^{2 i pi d_{k+1} t} + z, i.e. it lies
@@ -79,14 +96,16 @@ __device__ __forceinline__ double2 lift_seed(const PolyDev& P, double lambda0, i
   unit_phase((uint64_t)j, (uint64_t)N0, c, s);
   double zr = lambda0 * c, zi = lambda0 * s;  // |p_1| = |c| = lambda0 at angle t
   const double Lq = -log(lambda0) / shrink;  // log of the radius ratio per shrink step
+  double R[LIFT_RADII];
+  const bool tab = shrink_radii(lambda0, shrink, R);
   for (int k = 1; k < P.m; ++k) {
     // phase of level k+1: d_{k+1} t = 2^k j / N0 (exact in integers)
     const uint64_t num = (k >= log2N0) ? 0 : (((uint64_t)j << k) & (uint64_t)(N0 - 1));
     unit_phase(num, (uint64_t)N0, c, s);
     const double rel = (k + 1 < P.m) ? 1e-2 : 1e-3;
     for (int q = 1; q <= shrink; ++q) {
-      const double rp = pow(lambda0, 2.0 - (double)(q - 1) / shrink);
-      const double r = pow(lambda0, 2.0 - (double)q / shrink);
+      const double rp = shrink_radius(R, tab, lambda0, shrink, q - 1);
+      const double r = shrink_radius(R, tab, lambda0, shrink, q);
       steps += newton_target_f64(k + 1, -1, 0.0, zr, zi, r * c, r * s, rel, 40, nullptr, true, rp * c,
                                  rp * s, Lq, 0.0);
     }

@@ -25,7 +25,7 @@
 // Every anchor orbit and every finishing step is binary64; the chunk-end
 // check of the walk and the count check catch any tracking failure, and the
 // host then repeats the split in plain binary64.
-#include "mt_common.cuh"
+#include "mt_levelline.cuh"
 
 namespace mt {
 
@@ -151,6 +151,8 @@ __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log
     double zr = lambda0 * c, zi = lambda0 * s;
     const float lam2 = (float)(lambda0 * lambda0);
     const float Lq = (float)(-log(lambda0) / shrink);
+    double R[LIFT_RADII];
+    const bool tab = shrink_radii(lambda0, shrink, R);
     bool bad = false;
     for (int k = 1; k < P.m; ++k) {
       const uint64_t num = (k >= log2N0) ? 0 : (((uint64_t)j << k) & (uint64_t)(N0 - 1));
@@ -164,8 +166,8 @@ __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log
       int it = newton_target_pert(Q, zs, stride, v, dx, dy, lam2 * ec, lam2 * es, 1e-3f, 40, nullptr,
                                   false, 0.f, 0.f, 0.f, 0.f, &bad);
       for (int q = 1; q <= shrink; ++q) {
-        const float rp = (float)pow(lambda0, 2.0 - (double)(q - 1) / shrink);
-        const float r = (float)pow(lambda0, 2.0 - (double)q / shrink);
+        const float rp = (float)shrink_radius(R, tab, lambda0, shrink, q - 1);
+        const float r = (float)shrink_radius(R, tab, lambda0, shrink, q);
         it += newton_target_pert(Q, zs, stride, v, dx, dy, r * ec, r * es, 1e-3f, 40, nullptr, true,
                                  rp * ec, rp * es, Lq, 0.f, &bad);
       }

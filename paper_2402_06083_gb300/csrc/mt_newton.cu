@@ -59,12 +59,16 @@ __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __res
       ++steps;
       const double s2 = fma(qr, qr, qi * qi);
       int outcome = -1;
-      if (!finite2(zr, zi) || fma(zr, zr, zi * zi) > rdiv2) outcome = 1;
-      else if (s2 < tol2) outcome = 0;  // the step that met tol also squared the error
+      // Past the finiteness test z, hence q, is finite, so |z|^2, s2, rdiv2,
+      // tol2 and prev2 are all in [+0, +inf], and prev2 >= tol2 >= 1e-300 (a
+      // step below tol2 ends the descent): they compare as integers
+      // (s2 >= prev2 / 4 as ord(s2) >= ord(prev2) - ORD_QUARTER).
+      if (!finite2(zr, zi) || ord_f64(fma(zr, zr, zi * zi)) > ord_f64(rdiv2)) outcome = 1;
+      else if (ord_f64(s2) < ord_f64(tol2)) outcome = 0;  // the step that met tol also squared the error
       // binary64 rounding floor: steps stopped shrinking within a few ulp of z
       // (between two close roots Newton also stalls, at |step| ~ their
       // separation^2 / distance, far above this floor)
-      else if (s2 >= 0.25 * prev2 && s2 < floor2_f64(zr, zi)) outcome = 0;
+      else if (ord_f64(s2) >= ord_f64(prev2) - ORD_QUARTER && s2 < floor2_f64(zr, zi)) outcome = 0;
       else if (it >= cap) outcome = 2;
       prev2 = s2;
       if (outcome >= 0) {
@@ -288,7 +292,8 @@ cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t coun
   if (P.kind == 2)
     k_descend_q<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, tol * tol, cap, cand, status, ctr);
   else
-    k_descend<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, tol * tol, cap, cand, status, ctr);
+    k_descend<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, fmax(tol * tol, 1e-300), cap, cand, status,
+                                            ctr);
   return cudaGetLastError();
 }
 
