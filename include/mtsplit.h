@@ -201,7 +201,10 @@ MT_API mt_status mt_split_misiurewicz_q(int l, int n, const mt_options* opts, do
    one persistent launch drains all descents.  Roots of pair number p (pairs
    ordered by l, then n) are d_roots[h_offsets[p] .. h_offsets[p+1]).
    h_offsets: host array of npairs + 1 entries (npairs = number of pairs).
-   stats: optional array of npairs entries. */
+   stats: optional array of npairs entries.
+   mt_misiurewicz_pairs returns npairs for max_order and, when h_l and h_n
+   are given, writes the first min(npairs, capacity) pairs (l, n) in that
+   order (host arrays, no device work). */
 MT_API int mt_misiurewicz_pairs(int max_order, int* h_l, int* h_n, int capacity);
 MT_API size_t mt_workspace_bytes_misiurewicz_batch(int max_order, const mt_options* opts);
 MT_API mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, double* d_roots,
@@ -253,10 +256,12 @@ MT_API mt_status mt_certify_basin(int kind, int l, int n, const double* d_roots,
    alone); h_band_min [64] host doubles, per band k the smallest d_nn over
    the set's roots with Re c + 2 in (4^-(k+1), 4^-k] (band 0 also takes
    Re c + 2 > 1, band 63 everything below 4^-63; +inf if empty); *h_min the
-   smallest over the set.  Entries must be finite.  The scan runs over the
-   list sorted by Re; roots whose Re window holds more than 65536 entries
-   (isolated roots) are finished over a (Re strip, Im) index instead, so
-   every distance is exact.  Errors: MT_EINVAL (negative count, count above
+   smallest over the set.  Entries must be finite.  Three tiers, each
+   settling some roots and handing the rest on with their best distance so
+   far as a bound: a scan of up to 64 neighbours in the list sorted by Re,
+   then a walk in Im over a (Re strip, Im) index (one thread per root), then
+   the same walk with one block per root for isolated roots.  The index only
+   chooses which pairs are compared, so every distance is exact.  Errors: MT_EINVAL (negative count, count above
    2^32 - 1, null roots), MT_ENOMEM (workspace smaller than
    mt_separation_workspace_bytes(count)), MT_ECUDA.  Synchronises the
    stream before returning. */
