@@ -76,7 +76,9 @@ typedef struct {
   int c_L;             /* descents per root (0 -> 4; Sec. 4.2)                      */
   int chunk_log2;      /* log2 of level-line points walked per lane (0 -> auto)     */
   int block;           /* CUDA block size for the Newton kernels (0 -> auto)        */
-  int max_retries;     /* doublings of (M, c_L) when roots are missing (default 1)  */
+  int max_retries;     /* doublings of (M, c_L) when roots are missing (default 1;
+                          they stop once M would exceed 64, and the last attempt's
+                          result and status stand)                                */
   double eps_dup;      /* separation of the root set (0 -> rule of the library)     */
   double cert_tol;     /* certificate radius cap (0 -> 1e-12 FP64, 1e-20 DD)       */
   int use_graph;       /* 1: capture the launch sequence in a CUDA graph and replay */

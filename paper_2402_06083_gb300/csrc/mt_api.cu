@@ -459,15 +459,19 @@ size_t workspace_for(int kind, int l, int n, const mt_options* o) {
 }
 
 struct EventSet {
-  cudaEvent_t e[8];
+  cudaEvent_t e[8] = {};
   bool ok = false;
   EventSet() {
     ok = true;
     for (auto& x : e)
-      if (cudaEventCreate(&x) != cudaSuccess) ok = false;
+      if (cudaEventCreate(&x) != cudaSuccess) {
+        x = nullptr;
+        ok = false;
+      }
   }
   ~EventSet() {
-    for (auto& x : e) cudaEventDestroy(x);
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
   }
 };
 
@@ -924,7 +928,11 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
       if (retry >= max_retries) break;
       continue;
     }
-    if (!make_plan(kind, l, n, o, retry, &p)) return fail(MT_EINVAL, "no plan for retry %d", retry);
+    if (!make_plan(kind, l, n, o, retry, &p)) {
+      if (retry == 0) return fail(MT_EINVAL, "no plan for this polynomial and these options");
+      --retry;  // (M, c_L) cannot double further: the last attempt's result stands
+      break;
+    }
     Buffers b = carve(p, d_work, work_bytes);
     evp = &ev;
     stimes = StreamTimes();
@@ -1292,7 +1300,11 @@ mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, doub
   int retry = 0;
   bool good = false;
   for (;; ++retry) {
-    if (!make_batch_plan(max_order, o, retry, &b)) return fail(MT_EINVAL, "no plan for retry %d", retry);
+    if (!make_batch_plan(max_order, o, retry, &b)) {
+      if (retry == 0) return fail(MT_EINVAL, "no plan for this batch and these options");
+      --retry;  // (M, c_L) cannot double further: the last pass's result stands
+      break;
+    }
     BatchBuffers r = carve_batch(b, d_work, work_bytes);
     mt_status rc = run_batch_pass(b, r, (double2*)d_roots, cap, d_is_mis, s, ev, &h, &ps);
     if (rc != MT_OK) return rc;
