@@ -1443,6 +1443,7 @@ mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double
   if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range");
   if (count < 0 || (count > 0 && (!d_roots || !d_pass))) return fail(MT_EINVAL, "bad buffers");
   if (count > 0xffffffffll) return fail(MT_EINVAL, "count too large");
+  if (d_roots_lo && kind == 2) return fail(MT_EINVAL, "q_{l,n} roots are certified in binary64 only");
   const size_t need = mt_certify_workspace_bytes(count);
   if (!d_work || work_bytes < need) return fail(MT_ENOMEM, "workspace of %zu bytes needed", need);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1459,7 +1460,6 @@ mt_status mt_certify(int kind, int l, int n, const double* d_roots, const double
   CK(launch_keys_plain((const double2*)d_roots, count, keys, vals, s));
   CK(radix_sort_pairs(keys, vals, keys_alt, vals_alt, count, rtmp, s));
   if (d_roots_lo) {
-    if (kind == 2) return fail(MT_EINVAL, "q_{l,n} roots are certified in binary64 only");
     CK(dd_certify_list(P, (const double2*)d_roots, (const double2*)d_roots_lo, vals, count, tol, d_pass,
                        d_radius, ctr, s));
   } else {
