@@ -92,3 +92,22 @@ def test_streamed_plans_fit_one_gb300():
     assert 0 < total < 250e9, total / 1e9
     assert ws(31, 2) > ws(32, 2) / 2  # p_31 still runs in one pass
     assert ws(20, 0, 4) > 0 and ws(20, 0, 3) == 0
+
+
+def test_retries_stop_at_the_largest_plan():
+    """(M, c_L) double per retry up to M = 64: a larger retry budget sizes the
+    workspace for the largest plan instead of making the query fail."""
+    from paper_2402_06083_gb300 import _lib
+    L = _lib.load()
+
+    def ws(n, prec, retries):
+        o = _lib.Options()
+        L.mt_default_options(ctypes.byref(o))
+        o.prec, o.max_retries = prec, retries
+        return int(L.mt_workspace_bytes(0, 0, n, ctypes.byref(o)))
+
+    for prec in (0, 1):
+        sizes = [ws(12, prec, r) for r in range(7)]
+        assert all(s > 0 for s in sizes)
+        assert sizes == sorted(sizes)                # more retries never need less
+        assert sizes[3] == sizes[4] == sizes[6]      # M = 8 * 2^3 = 64 is the last plan
