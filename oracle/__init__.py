@@ -68,7 +68,7 @@ class Stats(ctypes.Structure):
 
 
 def build_mutant(k: int, outdir: str) -> str:
-    """Build a copy of the oracle with planted mistake number k (1..5) into
+    """Build a copy of the oracle with planted mistake number k (1..12) into
     outdir; used only by the test that shows the pins catch such mistakes."""
     out = os.path.join(outdir, "liboracle_mutant%d.so" % k)
     cmd = ["gcc", "-O2", "-shared", "-fPIC", "-DORACLE_MUTANT=%d" % k, "-o", out, _SRC]

@@ -47,7 +47,7 @@
 #include <string.h>
 
 #ifndef ORACLE_MUTANT
-#define ORACLE_MUTANT 0 /* 0 = the oracle; 1..7 plant a known mistake (tests only) */
+#define ORACLE_MUTANT 0 /* 0 = the oracle; 1..12 plant a known mistake (tests only) */
 #endif
 
 #if defined(ORACLE_FP64)
@@ -415,7 +415,9 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
           if (lin >= 3 && !no_acc) {
             real mu = 1 / (1 - r);
             int m = (int)(mu + 0.5);
+#if ORACLE_MUTANT != 11 /* mutant 11 plants a missing multiplicity step */
             if (m >= 2 && rabs(mu - m) < 0.15) pending = m;
+#endif
             lin = 0;
           }
         }
@@ -446,7 +448,11 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
           s = 1;
         }
       }
+#if ORACLE_MUTANT == 10 /* planted mistake: no finishing steps to the working precision */
+      for (int k = 0; k < 0; ++k) {
+#else
       for (int k = 0; k < 8 && s > R_TOL_FINAL; ++k) {
+#endif
         cplx v, dv;
         if (on_pn) eval_pk(P->n, w, &v, &dv); else eval_P(P, w, &v, &dv);
         cplx step = cdiv(v, dv);
@@ -491,8 +497,10 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
    candidate joins an existing point if max(|dRe|, |dIm|) < eps.  Points with
    |Im| < eps/2 are real.  Returns the number of upper-half representatives. */
 static long dedup(cand* cs, long nc, real eps, cplx* reps, long* n_repeat) {
+#if ORACLE_MUTANT != 8 /* mutant 8 plants a missing real-root rule */
   for (long i = 0; i < nc; ++i)
     if (cs[i].z.im < eps / 2) cs[i].z.im = 0;
+#endif
   qsort(cs, (size_t)nc, sizeof(cand), cand_cmp);
   long nr = 0;
   for (long i = 0; i < nc; ++i) {
@@ -556,7 +564,11 @@ static void classify(const poly* P, cplx c, real tau, int* a, int* b) {
     return;
   }
   if (P->kind == 0) {
+#if ORACLE_MUTANT == 9 /* planted mistake: the largest period that vanishes, not the smallest */
+    for (int k = P->n; k >= 1; --k) {
+#else
     for (int k = 1; k <= P->n; ++k) {
+#endif
       if (P->n % k) continue;
       eval_pk(k, c, &v, &dv);
       if (is_zero_step(v, dv, tau)) { *a = 0; *b = k; return; }
@@ -565,6 +577,9 @@ static void classify(const poly* P, cplx c, real tau, int* a, int* b) {
     return;
   }
   int g = gcd_i(P->n, P->l - 1);
+#if ORACLE_MUTANT == 12 /* planted mistake: Mis(l,k) tested before Hyp(k) */
+  g = 0;
+#endif
   for (int k = 1; k <= g; ++k) {
     if (g % k) continue;
     eval_pk(k, c, &v, &dv);

@@ -4,7 +4,11 @@ test_oracle_pins.py.  Mutants: 1 derivative from the wrong orbit index,
 2 wrong sign in Re(z^2), 3 s_{l,n} built with p_l instead of p_{l-1},
 4 level line walked the wrong way, 5 missing conjugate fold, 6 q_{l,n} built
 with p_{l-1} instead of p_l, 7 the multiplicity eta_l(k) of Thm fact_mis off
-by one in the count."""
+by one in the count, 8 the real-root rule |Im| < eps/2 -> Im = 0 missing,
+9 the exact period taken as the largest vanishing divisor instead of the
+smallest, 10 no finishing steps to the working precision, 11 q_{l,n} without
+the multiplicity step of eq. newtonAcc, 12 s_{l,n} types with Mis(l,k)
+tested before Hyp(k)."""
 from __future__ import annotations
 
 import pytest
@@ -25,6 +29,16 @@ CASES = [
     (6, qpins.test_worked_factorisation_q_2_4, ()),
     (6, qpins.test_types_and_multiplicities_follow_thm_fact_mis, (3, 4)),
     (7, qpins.test_types_and_multiplicities_follow_thm_fact_mis, (4, 2)),
+    (8, pins.test_counts_and_exact_periods, (6,)),
+    (8, pins.test_real_root_count_sturm, (6,)),
+    (9, pins.test_counts_and_exact_periods, (6,)),
+    (9, pins.test_hyp_1_and_2, ()),
+    (10, pins.test_counts_and_exact_periods, (8,)),
+    (10, pins.test_vieta_power_sums, (8,)),
+    (11, qpins.test_types_and_multiplicities_follow_thm_fact_mis, (3, 4)),
+    (11, qpins.test_worked_factorisation_q_2_4, ()),
+    (12, pins.test_s_2_4_example, ()),
+    (12, pins.test_tiny_misiurewicz, ()),
 ]
 
 
