@@ -22,6 +22,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import goldens
 from oracle import counts
 
 
@@ -43,13 +44,15 @@ def test_types_and_multiplicities_follow_thm_fact_mis(l, n):
 
 
 def test_worked_factorisation_q_2_4():
+    """q_{2,4} = h_1^3 h_2^2 h_4^2 m_{2,1} m_{2,2} m_{2,4} (App. A;
+    tests/golden/q_2_4_factorisation.txt): c = 0 triple, c = -1 double, the 6
+    centres of period 4 double, the Misiurewicz points simple."""
     r = oracle.split("q", 4, l=2)
     mult = {}
     for (a, b), m in zip(map(tuple, r["type"]), r["mult"]):
         mult.setdefault((int(a), int(b)), set()).add(int(m))
-    # h_1^3 h_2^2 h_4^2: c = 0 triple, c = -1 double, the 6 centres of period 4 double
-    assert mult[(0, 1)] == {3} and mult[(0, 2)] == {2} and mult[(0, 4)] == {2}
-    assert mult[(2, 1)] == mult[(2, 2)] == mult[(2, 4)] == {1}
+    want = {(j, k): {e} for j, k, e in goldens.rows("q_2_4_factorisation.txt")}
+    assert mult == want
     z = r["roots"]
     assert np.min(np.abs(z)) < 1e-30 and np.min(np.abs(z + 1)) < 1e-30
 
