@@ -18,7 +18,10 @@ import pytest
 
 import oracle
 from oracle import counts
+from tests import goldens
 from tests.rootsets import lexsorted, match_sets
+
+SEP = goldens.table("separation_law.txt")  # Sec. 6.3.2
 
 pytestmark = pytest.mark.gpu
 
@@ -129,7 +132,7 @@ def _tip_checks(mt, n, res, k=24):
         assert move < TOL_DD, (i, move)
     # the two left-most roots are 118.4 / 4^n apart to 0.1 % (Sec. 6.3.2)
     gap = (z[1].real - z[0].real) + (zl[1].real - zl[0].real)
-    assert abs(gap * 4.0 ** n / 118.4 - 1) < 2e-3
+    assert abs(gap * 4.0 ** n / SEP["hyp_constant"] - 1) < 2 * SEP["hyp_rel_error"]
 
 
 @pytest.mark.parametrize("n", [26, 28, 29])
@@ -204,4 +207,4 @@ def test_dd_misiurewicz_order_26(mt, l, n):
     gap128 = (pts[1][0] - pts[0][0]) + (pts[1][1] - pts[0][1])
     assert abs(gap128 - gaps[i]) < 1e-27
     if (l, n) == (4, 22):
-        assert 4.8e-20 < gaps[i] < 4.86e-20
+        assert 4.8e-20 < gaps[i] < SEP["mis_tip_gap"]

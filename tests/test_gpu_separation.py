@@ -17,6 +17,9 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import goldens
+
+SEP = goldens.table("separation_law.txt")  # Sec. 6.3.2
 
 pytestmark = pytest.mark.gpu
 
@@ -111,7 +114,7 @@ def test_separation_law(mt, n):
     t = mt.classify("hyp", n, z)
     mask = (t == n).to(dtype=__import__("torch").uint8)
     nn, bands, mn = mt.separation(z, mask=mask)
-    assert abs(mn * 4.0 ** n / 118.4 - 1) < 2e-3, mn * 4.0 ** n
+    assert abs(mn * 4.0 ** n / SEP["hyp_constant"] - 1) < 2 * SEP["hyp_rel_error"], mn * 4.0 ** n
     zz = z[:2].cpu().numpy()
     assert abs(abs(zz[1] - zz[0]) - mn) <= 1e-12 * mn
     if n <= 20:
@@ -136,7 +139,7 @@ def test_separation_law_double_double_p28(mt):
     _, _, mn_all = mt.separation(res.roots, roots_lo=res.roots_lo)
     nn, bands, mn = mt.separation(res.roots, roots_lo=res.roots_lo, mask=mask)
     assert mn_all < 0.6 * mn
-    assert abs(mn * 4.0 ** n / 118.4 - 1) < 2e-3, mn * 4.0 ** n
+    assert abs(mn * 4.0 ** n / SEP["hyp_constant"] - 1) < 2 * SEP["hyp_rel_error"], mn * 4.0 ** n
     z = res.roots[:2].cpu().numpy()
     zl = res.roots_lo[:2].cpu().numpy()
     # the binary128 oracle's Newton limits of the two left-most roots

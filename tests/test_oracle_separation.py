@@ -16,6 +16,9 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import goldens
+
+SEP = goldens.table("separation_law.txt")  # Sec. 6.3.2
 
 
 def _lattice(nx, ny, h, rng):
@@ -81,7 +84,7 @@ def test_separation_law_on_oracle_roots(n):
     hyp = per == n
     nn = oracle.nearest_neighbours(z, hyp)
     mn = nn[hyp].min()
-    assert abs(mn * 4.0 ** n / 118.4 - 1) < 1e-3, mn * 4.0 ** n  # Sec. 6.3.2, n >= 9
+    assert abs(mn * 4.0 ** n / SEP["hyp_constant"] - 1) < SEP["hyp_rel_error"], mn * 4.0 ** n  # n >= 9
     # attained by the two left-most real roots
     order = np.lexsort((z.imag, z.real))
     a, b = order[0], order[1]
