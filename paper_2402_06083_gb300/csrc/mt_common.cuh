@@ -83,8 +83,9 @@ __device__ __forceinline__ void orbit_pn_f64(int m, double cr, double ci, double
 // P' to a relative error eta: the iteration then contracts by eta per step
 // near the root instead of quadratically, and eta ~ m 2^-24 is far below
 // the 1e-7 relative accuracy the binary32 phase leaves.  The fixed point is
-// decided by P alone, which stays binary64.  5 binary64 operations per step
-// (2 conversions, 2 FMA + 1 FMA + 1 add for the value) instead of 8.
+// decided by P alone, which stays binary64.  6 binary64 operations per step
+// (2 conversions to binary32, 3 FMA and 1 add for the value) instead of the
+// 8 of orbit_f64.
 __device__ __forceinline__ void orbit_f64_d32(int m, int lcap, double cr, double ci, double& vr,
                                               double& vi, float& dr, float& di) {
   double zr = 0.0, zi = 0.0, cap_r = 0.0, cap_i = 0.0;
