@@ -376,26 +376,26 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
     b.seed_bad = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks + 1) : nullptr;
     b.chunk_fail = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks) : nullptr;
   } else {
-  b.starts = c.take<double2>(p.S);
-  b.cand = c.take<double2>(p.S);
-  b.reps = b.starts;  // starts are dead once the descents are done
-  b.status = c.take<uint8_t>(p.S);
-  b.keys = c.take<uint64_t>(p.S);
-  b.keys_alt = c.take<uint64_t>(p.S);
-  b.vals = c.take<uint32_t>(p.S);
-  b.vals_alt = c.take<uint32_t>(p.S);
-  b.flag = c.take<uint32_t>(p.S);
-  b.pos = c.take<uint32_t>(p.S);
-  b.type = c.take<uint8_t>(p.S);
-  b.mult = b.flag;  // flag/pos are dead after compaction
-  b.mpos = b.pos;
-  b.pass = c.take<uint8_t>(p.S);
-  b.radius = c.take<double>(p.S);
-  b.scan_tmp = c.take_bytes(scan_temp_bytes(p.S));
-  b.radix_tmp = c.take_bytes(radix_temp_bytes(p.S));
-  b.anchors = (p.prec == MT_MIXED) ? c.take_bytes(mixed_anchor_bytes(p.P, p.S)) : nullptr;
-  b.seed_bad = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks + 1) : nullptr;
-  b.chunk_fail = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks) : nullptr;
+    b.starts = c.take<double2>(p.S);
+    b.cand = c.take<double2>(p.S);
+    b.reps = b.starts;  // starts are dead once the descents are done
+    b.status = c.take<uint8_t>(p.S);
+    b.keys = c.take<uint64_t>(p.S);
+    b.keys_alt = c.take<uint64_t>(p.S);
+    b.vals = c.take<uint32_t>(p.S);
+    b.vals_alt = c.take<uint32_t>(p.S);
+    b.flag = c.take<uint32_t>(p.S);
+    b.pos = c.take<uint32_t>(p.S);
+    b.type = c.take<uint8_t>(p.S);
+    b.mult = b.flag;  // flag/pos are dead after compaction
+    b.mpos = b.pos;
+    b.pass = c.take<uint8_t>(p.S);
+    b.radius = c.take<double>(p.S);
+    b.scan_tmp = c.take_bytes(scan_temp_bytes(p.S));
+    b.radix_tmp = c.take_bytes(radix_temp_bytes(p.S));
+    b.anchors = (p.prec == MT_MIXED) ? c.take_bytes(mixed_anchor_bytes(p.P, p.S)) : nullptr;
+    b.seed_bad = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks + 1) : nullptr;
+    b.chunk_fail = (p.prec == MT_MIXED) ? c.take<uint8_t>(p.nchunks) : nullptr;
   }
   b.d = DdBuffers{};
   if (p.dd) {
