@@ -417,6 +417,8 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
             int m = (int)(mu + 0.5);
 #if ORACLE_MUTANT != 11 /* mutant 11 plants a missing multiplicity step */
             if (m >= 2 && rabs(mu - m) < 0.15) pending = m;
+#else
+            (void)m;
 #endif
             lin = 0;
           }
