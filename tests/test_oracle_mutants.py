@@ -24,6 +24,7 @@ CASES = [
     (2, pins.test_orbit_off_axis_against_integer_polynomial, ()),
     (3, pins.test_tiny_misiurewicz, ()),
     (3, pins.test_s_2_4_example, ()),
+    (3, pins.test_level_line_iso_angle_zero_misiurewicz, (2, 3)),
     (4, pins.test_level_line_iso_angle_zero, (4,)),
     (5, pins.test_counts_and_exact_periods, (8,)),
     (6, qpins.test_worked_factorisation_q_2_4, ()),

@@ -343,3 +343,28 @@ def test_golden_fixtures_carry_their_citation():
         assert "2402.06083" in cite, name
         assert any(w in cite for w in ("Sec.", "Table", "App.")), name
         assert goldens.rows(name), name
+
+
+@pytest.mark.parametrize("l,n", [(2, 2), (2, 3), (3, 2), (3, 3), (4, 2)])
+def test_level_line_iso_angle_zero_misiurewicz(l, n):
+    """The same for s_{l,n} = p_{l+n-1} + p_{l-1} on its level |s| = 100 (Sec. 4.2):
+    the iso-angle-0 starts and their conjugates are s^{-1}(100), brute force on
+    the exact integer polynomial s_{l,n} - 100."""
+    mpmath.mp.dps = 40
+    r = oracle.split("mis", n, l=l, want_starts=True)
+    st = r["starts"]
+    d = 2 ** (l + n - 2)
+    assert st.size == 2 * d + 1
+    iso0 = st[::4]
+    full = np.concatenate([iso0, np.conj(iso0[(np.abs(iso0.imag) > 1e-12)])])
+    co = s_coeffs(l, n)
+    co[0] -= 100
+    ref = np.array([complex(x) for x in mpmath.polyroots(list(reversed(co)), maxsteps=400,
+                                                          extraprec=8 * len(co))])
+    assert full.size == ref.size == d
+    _, dmax = match_sets(full, ref)
+    assert dmax < 1e-12
+    for j, s4 in enumerate(r["starts4"]):
+        v, _ = oracle.evaluate("mis", n, s4, l=l)
+        val = complex(v[0] + v[1], v[2] + v[3])
+        assert abs(val - 100 * 1j ** (j % 4)) < 1e-18
