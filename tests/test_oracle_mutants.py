@@ -29,6 +29,7 @@ CASES = [
     (5, pins.test_counts_and_exact_periods, (8,)),
     (6, qpins.test_worked_factorisation_q_2_4, ()),
     (6, qpins.test_types_and_multiplicities_follow_thm_fact_mis, (3, 4)),
+    (6, qpins.test_level_line_iso_angle_zero_q, (2, 2)),
     (7, qpins.test_types_and_multiplicities_follow_thm_fact_mis, (4, 2)),
     (8, pins.test_counts_and_exact_periods, (6,)),
     (8, pins.test_real_root_count_sturm, (6,)),

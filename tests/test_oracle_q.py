@@ -100,3 +100,25 @@ def test_library_roots_of_exact_coefficients(l, n):
     assert np.array_equal(np.bincount(owner, minlength=z.size), mu)
     for w, k in zip(lib, owner):
         assert abs(w - z[k]) < 10 * 1e-12 ** (1.0 / mu[k])  # a root of multiplicity mu moves ~ eps^(1/mu)
+
+
+@pytest.mark.parametrize("l,n", [(1, 2), (2, 2), (2, 3), (3, 2)])
+def test_level_line_iso_angle_zero_q(l, n):
+    """The level line |q_{l,n}| = 100 (Sec. 4.2): its iso-angle-0 starts and their
+    conjugates are q^{-1}(100), simple points away from the multiple roots;
+    brute force on the exact integer polynomial q_{l,n} - 100."""
+    import mpmath
+    from tests.rootsets import match_sets
+    mpmath.mp.dps = 40
+    r = oracle.split("q", n, l=l, want_starts=True)
+    st = r["starts"]
+    d = 2 ** (l + n - 1)
+    assert st.size == 2 * d + 1
+    iso0 = st[::4]
+    full = np.concatenate([iso0, np.conj(iso0[(np.abs(iso0.imag) > 1e-12)])])
+    co = [int(x) for x in _q_coeffs(l, n)]  # highest degree first
+    co[-1] -= 100
+    ref = np.array([complex(x) for x in mpmath.polyroots(co, maxsteps=400, extraprec=8 * len(co))])
+    assert full.size == ref.size == d
+    _, dmax = match_sets(full, ref)
+    assert dmax < 1e-12
