@@ -95,6 +95,19 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
                            + [dp, ctypes.c_long, ip, ip, dp, ctypes.c_long, ctypes.POINTER(Stats)])
     L.or_polish.restype = ctypes.c_int
     L.or_polish.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_int, dp, dp]
+    L.or_polish_many.restype = ctypes.c_long
+    L.or_polish_many.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_long, ctypes.c_int, dp, dp, dp]
+    L.or_walk.restype = ctypes.c_long
+    L.or_walk.argtypes = [ctypes.c_int] * 5 + [ctypes.c_double, dp, ctypes.c_long, ctypes.POINTER(Stats)]
+    L.or_lift_seed.restype = ctypes.c_int
+    L.or_lift_seed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_int, dp]
+    L.or_split_window.restype = ctypes.c_long
+    L.or_split_window.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [ctypes.c_long] * 2
+                                  + [ctypes.c_int, dp, ctypes.c_long, ctypes.POINTER(Stats)])
+    L.or_split_q.restype = ctypes.c_long
+    L.or_split_q.argtypes = ([ctypes.c_int] * 4 + [ctypes.c_double] * 4 + [dp, ctypes.c_double, ctypes.c_int]
+                             + [dp, ctypes.c_long, ip, ip, ip, ctypes.POINTER(ctypes.c_long),
+                                ctypes.POINTER(Stats)])
     L.or_classify.restype = ctypes.c_int
     L.or_classify.argtypes = [ctypes.c_int] * 3 + [dp, ctypes.c_double, ip, ip]
     L.or_count_in_disk.restype = ctypes.c_long
@@ -186,8 +199,12 @@ def split(kind: str, n: int, l: int = 0, *, M: int = 8, cL: int = 4, lambda0: fl
     Returns a dict with 'roots' (complex128, the rounded values), 'roots4'
     ([N, 4] Re hi, Re lo, Im hi, Im lo), 'type' ([N, 2] (preperiod, period)),
     'stats' and optionally 'starts4' (upper-half level-line starts).  For
-    q_{l,n} the roots are distinct and 'mult' holds each one's multiplicity
-    (Thm fact_mis: eta_l(k) = floor((l-1)/k) + 2 for Hyp(k), 1 for Mis)."""
+    q_{l,n} (see split_q) the roots are distinct and 'mult' holds each one's
+    multiplicity."""
+    if kind == "q":
+        if frac < 1.0 or want_starts:
+            raise ValueError("q_{l,n}: whole splits only (level_line() gives its starts)")
+        return split_q(l, n, M=M, cL=cL, eps_dup=eps_dup, max_retries=max_retries, fp64=fp64)
     k, ll, nn = _kind_args(kind, l, n)
     L = _lib(fp64)
     d = int(L.or_degree(k, ll, nn))
@@ -218,13 +235,137 @@ def split(kind: str, n: int, l: int = 0, *, M: int = 8, cL: int = 4, lambda0: fl
     }
     if want_types:
         out["type"] = np.stack([ta[:m], tb[:m]], axis=1)
-        if kind == "q":
-            out["mult"] = np.where(ta[:m] == 0, (l - 1) // np.maximum(tb[:m], 1) + 2, 1)
     if want_starts:
         ns = min(int(st.n_starts), scap)
         out["starts4"] = starts4[:ns].copy()
         out["starts"] = starts4[:ns, 0] + 1j * starts4[:ns, 2]
     return out
+
+
+def split_q(l: int, n: int, *, M: int = 8, cL: int = 4, eps_dup: float | None = None, max_retries: int = 2,
+            fp64: bool = False) -> dict:
+    """The distinct roots of q_{l,n} = p_{l+n} - p_l with their multiplicities
+    and types, from eq. polySimple telescoped: q_{l,n} = p_n^2 prod_{j=2..l}
+    s_{j,n} (s_{1,n} = p_n, eq. hypCase).  The factors are split by this
+    oracle (p_n and every s_{j,n}, each with its own defaults); their roots
+    are merged with the Chebyshev rule at the q_{l,n} separation eps_dup; a
+    root's multiplicity is the number of factors it is a root of (p_n
+    counted twice) and its type comes from its factor ((0, k) for Hyp(k),
+    (j, k) for Mis(j, k)).  Returns the dict of split() with 'mult', and
+    'n_conflict' (cluster members whose factor types disagree: 0)."""
+    if l < 1 or n < 1 or l + n > 40:
+        raise ValueError("bad polynomial")
+    L = _lib(fp64)
+    bits = 53 if fp64 else 113
+    epsf = np.zeros(l, dtype=np.float64)
+    epsf[0] = eps_dup_default("hyp", n, bits=bits)
+    for j in range(2, l + 1):
+        epsf[j - 1] = eps_dup_default("mis", n, j, bits=bits)
+    eps = eps_dup_default("q", n, l, bits=bits) if eps_dup is None else eps_dup
+    cap = 2 ** (l + n - 1)
+    roots4 = np.zeros((cap, 4), dtype=np.float64)
+    pre = np.zeros(cap, dtype=np.int32)
+    per = np.zeros(cap, dtype=np.int32)
+    mult = np.zeros(cap, dtype=np.int32)
+    nconf = ctypes.c_long(0)
+    st = Stats()
+    nr = L.or_split_q(l, n, M, cL, default_lambda0("hyp"), default_lambda0("mis"), default_IN("hyp"),
+                      default_IN("mis"), _dp(epsf), eps, max_retries, _dp(roots4), cap, _ip(pre), _ip(per),
+                      _ip(mult), ctypes.byref(nconf), ctypes.byref(st))
+    if nr < 0:
+        raise RuntimeError("oracle split of q failed (%d)" % nr)
+    m = min(nr, cap)
+    return {
+        "roots4": roots4[:m].copy(),
+        "roots": roots4[:m, 0] + 1j * roots4[:m, 2],
+        "n_roots": int(nr),
+        "type": np.stack([pre[:m], per[:m]], axis=1),
+        "mult": mult[:m].copy(),
+        "n_conflict": int(nconf.value),
+        "stats": st.as_dict(),
+        "eps_dup": eps,
+    }
+
+
+def level_line(kind: str, n: int, l: int = 0, *, M: int = 8, cL: int = 4, lambda0: float | None = None,
+               fp64: bool = False) -> dict:
+    """The upper half of the discrete level line |P| = lambda0 walked
+    sequentially from the real end point (no descents): 'starts4' / 'starts',
+    start s with P = lambda0 e^{i pi s / 2} for c_L = 4 (kinds hyp, mis, q)."""
+    k, ll, nn = _kind_args(kind, l, n)
+    L = _lib(fp64)
+    d = int(L.or_degree(k, ll, nn))
+    if d <= 0:
+        raise ValueError("bad polynomial")
+    lam = default_lambda0(kind) if lambda0 is None else lambda0
+    scap = cL * d // 2 + 2
+    starts4 = np.zeros((scap, 4), dtype=np.float64)
+    st = Stats()
+    ns = L.or_walk(k, ll, nn, M, cL, lam, _dp(starts4), scap, ctypes.byref(st))
+    if ns < 0:
+        raise RuntimeError("oracle walk failed (%d)" % ns)
+    ns = min(int(ns), scap)
+    return {"starts4": starts4[:ns].copy(), "starts": starts4[:ns, 0] + 1j * starts4[:ns, 2],
+            "stats": st.as_dict()}
+
+
+def lift_seed(n: int, j: int, *, M: int = 8, lambda0: float = 5.0, shrink: int = 16, fp64: bool = False):
+    """The point of index j of the level line of p_n (M points per turn),
+    lifted through the nested family p_1 -> ... -> p_n (Sec. 4.2).  Returns
+    (4-vector, number of solves that did not converge)."""
+    out = np.zeros(4, dtype=np.float64)
+    f = _lib(fp64).or_lift_seed(n, M, j, lambda0, shrink, _dp(out))
+    if f < 0:
+        raise ValueError("bad arguments")
+    return out, int(f)
+
+
+def split_window(n: int, jbeg: int, jend: int, *, M: int = 8, cL: int = 4, lambda0: float | None = None,
+                 eps_dup: float | None = None, shrink: int = 16, fp64: bool = True,
+                 want_roots: bool = False) -> dict:
+    """One window of the split of p_n: sub-steps jbeg..jend of the upper half
+    (M d / 2 in all, d = 2^(n-1)), walked from the lifted seed of index jbeg,
+    with its descents and its own root set.  Returns 'n_roots' (distinct
+    upper-half roots of the window), 'stats' and, with want_roots, 'roots4'."""
+    L = _lib(fp64)
+    lam = default_lambda0("hyp") if lambda0 is None else lambda0
+    eps = eps_dup_default("hyp", n, bits=53 if fp64 else 113) if eps_dup is None else eps_dup
+    st = Stats()
+    cap = (jend - jbeg) // max(1, M // cL) + 2 if want_roots else 0
+    r4 = np.zeros((max(cap, 1), 4), dtype=np.float64)
+    nr = L.or_split_window(n, M, cL, lam, default_IN("hyp"), eps, jbeg, jend, shrink,
+                           _dp(r4) if want_roots else None, cap, ctypes.byref(st))
+    if nr < 0:
+        raise ValueError("bad window")
+    out = {"n_roots": int(nr), "stats": st.as_dict()}
+    if want_roots:
+        out["roots4"] = r4[:min(int(nr), cap)].copy()
+    return out
+
+
+def polish_many(kind: str, n: int, roots, l: int = 0, steps: int = 3, roots_lo=None, want_points: bool = False):
+    """Binary128 Newton polish of every point of a list (or_polish in one C
+    loop).  roots: complex array (hi parts), roots_lo: optional low parts.
+    Returns (disp, last[, points4]): |polished - given| and the size of the
+    last Newton step per point (+inf where the iterate left the finite
+    numbers), and the polished points as 4-vectors."""
+    k, ll, nn = _kind_args(kind, l, n)
+    z = np.asarray(roots, dtype=np.complex128).ravel()
+    c4 = np.zeros((z.size, 4), dtype=np.float64)
+    c4[:, 0] = z.real
+    c4[:, 2] = z.imag
+    if roots_lo is not None:
+        zl = np.asarray(roots_lo, dtype=np.complex128).ravel()
+        c4[:, 1] = zl.real
+        c4[:, 3] = zl.imag
+    disp = np.zeros(z.size)
+    last = np.zeros(z.size)
+    out4 = np.zeros((z.size, 4)) if want_points else None
+    rc = _lib().or_polish_many(k, ll, nn, _dp(c4), z.size, steps, _dp(out4) if want_points else None,
+                               _dp(disp), _dp(last))
+    if rc < 0:
+        raise ValueError("bad polynomial")
+    return (disp, last, out4) if want_points else (disp, last)
 
 
 def evaluate(kind: str, n: int, c, l: int = 0, fp64: bool = False):

@@ -25,13 +25,18 @@
  *                                                              computeLevelLine)
  *   - exact period / Misiurewicz type of each root           (eq. def:hyp, def:mis,
  *                                                              Thm countingHyp, eq. polyMisSimple)
- *   - q_{l,n}: the multiplicity of a root from its type, eta_l(k) =
- *     floor((l-1)/k) + 2 for Hyp(k), 1 for Mis(j,k); the count check adds
- *     multiplicities                                          (Thm fact_mis, eq. defMultHyp)
- *   - q_{l,n}: a descent that contracts linearly, as Newton does near a
- *     multiple root (ratio -> 1 - 1/mu), takes an accelerated step; one
- *     that then stalls is finished with Newton on p_n, of which every
- *     multiple root of q is a simple root             (eq. newtonLin, newtonAcc, Thm fact_mis)
+ *   - q_{l,n}: no descent on q itself.  eq. polySimple, s_{j,n} =
+ *     q_{j,n} / q_{j-1,n}, telescoped from q_{0,n} = p_n with s_{1,n} = p_n
+ *     (eq. hypCase), gives q_{l,n} = p_n^2 prod_{j=2..l} s_{j,n}, a product
+ *     of polynomials with simple roots.  The distinct roots of q are the
+ *     union of this oracle's own splits of p_n and of s_{j,n}, j = 2..l,
+ *     merged with the Chebyshev rule; a root's multiplicity is the number
+ *     of factors (p_n twice) it is a root of, its type the factor's type
+ *                                                             (eq. polySimple, eq. hypCase)
+ *   - seeds at any external angle: a point of |p_1| = lambda0 lifted
+ *     through the nested family p_k -> p_{k+1} (target lambda0^2 at the
+ *     doubled phase, then the radius brought back to lambda0), so that a
+ *     window of the level line can be walked on its own    (Sec. 4.2)
  *
  * Deliberately different from the GPU design: one sequential walk from the
  * real end point (no lifting, no chunks), qsort + linear scan for the set,
@@ -295,20 +300,23 @@ static int cplx_lex_cmp(const void* a, const void* b) {
   return 0;
 }
 
-/* One pass of the method with given (M, c_L).  Walks the upper half of the
-   level line (external-angle index t in [0, frac/2]), descends from every
-   (M/c_L)-th point, and leaves the folded converged candidates in *out. */
-static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double frac,
-                     cand** out, or_stats* st, double* starts_out, long starts_cap) {
+/* One pass of the method with given (M, c_L) over the sub-steps jbeg ..
+   jend of the upper half of the level line (external-angle index t =
+   j / (M d), t in [0, 1/2]): the walk starts from z0, the point of index
+   jbeg, and, when 'descend' is set, a Newton descent runs from every
+   (M/c_L)-th point; the folded converged candidates are left in *out.
+   With descend = 0 only the starts are recorded (the level line itself). */
+static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, long jbeg, long jend,
+                     cplx z0, int descend, cand** out, or_stats* st, double* starts_out,
+                     long starts_cap) {
   long J = (long)M * P->degree / 2; /* sub-steps from t = 0 to t = 1/2 */
-  long Jstop = (frac >= 1.0) ? J : (long)(frac * (double)J);
   int every = M / cL;
-  long ncap = Jstop / every + 2;
+  long ncap = (jend - jbeg) / every + 2;
   cand* cs = (cand*)malloc(sizeof(cand) * (size_t)ncap);
   long nc = 0, nstart = 0;
-  cplx z = cx(real_endpoint(P, lambda0), 0);
-  for (long j = 0; j <= Jstop; ++j) {
-    if (j > 0) {
+  cplx z = z0;
+  for (long j = jbeg; j <= jend; ++j) {
+    if (j > jbeg) {
       /* target P(z_j) = lambda0 e^{2 i pi j / M}; the phase is reduced mod M
          so that it is exact for every j (Sec. 6.3.1). */
 #if ORACLE_MUTANT == 4 /* planted mistake: the walk turns the wrong way */
@@ -327,6 +335,7 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
       split_real(z.im, &starts_out[4 * nstart + 2], &starts_out[4 * nstart + 3]);
     }
     ++nstart;
+    if (!descend) continue;
     /* Newton descent (Algorithm S_par, capped at max{20, I_N log2 d}). */
     cplx w = z;
     real s = 0;
@@ -335,144 +344,32 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
     real rdiv = 2 * cabs_(z);
     if (rdiv < 4) rdiv = 4;
     int conv = 0, div = 0, it;
-    /* q_{l,n} only.  Near a root of multiplicity mu Newton contracts
-       linearly, |step_{k+1}| / |step_k| -> 1 - 1/mu (eq. newtonLin).  When
-       three successive ratios agree and give mu within 0.15 of an integer
-       m >= 2, a trial step z - m P/P' is taken (eq. newtonAcc).  Next to a
-       multiple root it lands much closer, the next plain step is short, and
-       the Newton step of p_n (of which the multiple root is a simple root,
-       Thm fact_mis) is m times that of q: the multiplicity is then taken as
-       m and every following step is z - m P/P', which converges
-       quadratically to the multiple root.  A cluster looks the same from
-       afar, but the trial step then lands near its centre, where one of the
-       two tests fails: the trial is undone and the descent goes on with
-       plain Newton, which separates the cluster.  If an accelerated descent
-       stalls (the rounding noise around a multiple root) and Newton on p_n
-       -- of which every multiple root of q is a simple root (Thm fact_mis)
-       -- sees a root well within the trial step, it finishes on p_n; if p_n
-       sees none, the "multiple root" was a tight cluster of simple roots
-       (about which z - m P/P' oscillates) and plain Newton takes over. */
-    int on_pn = 0, lin = 0, mult = 1, pending = 0, trial = 0, no_acc = 0;
-    real s_prev = 0, r_prev = 0, s_acc = 0, r_last = 0;
-    cplx w_pre = w;
     for (it = 0; it < cap; ++it) {
       cplx v, dv;
-      if (on_pn) eval_pk(P->n, w, &v, &dv); else eval_P(P, w, &v, &dv);
+      eval_P(P, w, &v, &dv);
       cplx step = cdiv(v, dv);
       st->desc_newton++;
-      if (trial) { /* the first plain step after the trial step */
-        int ok = cabs_(step) <= s_acc / 2;
-        if (ok) {
-          /* next to a root of multiplicity m -- a simple root of p_n -- the
-             p_n step is m times the q step (a cluster's centre gives another
-             ratio) */
-          cplx v2, d2;
-          eval_pk(P->n, w, &v2, &d2);
-          real ratio = cabs_(cdiv(v2, d2)) / cabs_(step);
-          ok = ratio >= 0.75 * trial && ratio <= 1.25 * trial;
-        }
-        if (ok) {
-          mult = trial;
-        } else { /* the trial overshot into a cluster: undo it */
-          w = w_pre;
-          trial = 0;
-          no_acc = 1;
-          lin = 0;
-          continue;
-        }
-        trial = 0;
-      }
-      if (mult > 1 && !on_pn) step = cx(mult * step.re, mult * step.im);
-      if (pending) {
-        w_pre = w;
-        step = cx(pending * step.re, pending * step.im);
-        s_acc = cabs_(step);
-        trial = pending;
-        pending = 0;
-      }
       w = csub(w, step);
       if (!cfinite(w) || cabs_(w) > rdiv) { div = 1; break; }
       s = cabs_(step);
-      r_last = (it > 0) ? s / s_prev : 0;
       if (s < 1e-12) { conv = 1; break; }
-      if (P->kind == 2 && !on_pn && it > 0 && !trial) {
-        real r = s / s_prev;
-        if (mult > 1) {
-          if (r >= 0.9) {
-            cplx v2, d2;
-            eval_pk(P->n, w, &v2, &d2);
-            if (cabs_(cdiv(v2, d2)) < s_acc / 2) {
-              on_pn = 1;
-              it = 0; /* the p_n descent gets the cap of its own */
-            } else { /* a cluster of simple roots: plain Newton from here */
-              mult = 1;
-              no_acc = 1;
-              lin = 0;
-            }
-          }
-        } else {
-          lin = (r > 0.35 && r < 0.98 && rabs(r - r_prev) < 0.03 * r) ? lin + 1 : 0;
-          if (lin >= 3 && !no_acc) {
-            real mu = 1 / (1 - r);
-            int m = (int)(mu + 0.5);
-#if ORACLE_MUTANT != 11 /* mutant 11 plants a missing multiplicity step */
-            if (m >= 2 && rabs(mu - m) < 0.15) pending = m;
-#else
-            (void)m;
-#endif
-            lin = 0;
-          }
-        }
-        r_prev = r;
-      }
-      s_prev = s;
-    }
-    if (!conv && !div && P->kind == 2 && mult > 1 && !on_pn) {
-      /* cap reached on an accelerated descent: accepted if p_n sees its root
-         well within the trial step (then finished on p_n below) */
-      cplx v2, d2;
-      eval_pk(P->n, w, &v2, &d2);
-      if (cabs_(cdiv(v2, d2)) < s_acc / 2) conv = 1;
     }
     if (conv) {
-      /* finish to the working precision (a few quadratic steps).  A descent
-         that reached a multiple root of q finishes on p_n, where that root
-         is simple: around a root of multiplicity mu the values of q are
-         rounding noise within ~(unit roundoff)^(1/mu) of it. */
-      /* also a plain descent that was still contracting linearly when it
-         met the stop (a multiple root reached without the acceleration) */
-      if (P->kind == 2 && !on_pn && (mult > 1 || r_last > 0.2)) {
-        cplx v2, d2;
-        eval_pk(P->n, w, &v2, &d2);
-        real s_pn = cabs_(cdiv(v2, d2));
-        if (s_pn < (mult > 1 ? s_acc / 2 : 1e-6 * (1 + cabs_(w)))) {
-          on_pn = 1;
-          s = 1;
-        }
-      }
+      /* finish to the working precision (a few quadratic steps) */
 #if ORACLE_MUTANT == 10 /* planted mistake: no finishing steps to the working precision */
       for (int k = 0; k < 0; ++k) {
 #else
       for (int k = 0; k < 8 && s > R_TOL_FINAL; ++k) {
 #endif
         cplx v, dv;
-        if (on_pn) eval_pk(P->n, w, &v, &dv); else eval_P(P, w, &v, &dv);
+        eval_P(P, w, &v, &dv);
         cplx step = cdiv(v, dv);
         real s2 = cabs_(step);
-        /* q_{l,n}: within the rounding noise of a root of high multiplicity
-           a step may fall below the stop by chance; the next one then is
-           not small, and the point is no root */
-        if (P->kind == 2 && k == 0 && !on_pn && !(s2 <= 1e-6 * (1 + cabs_(w)))) {
-          conv = 0;
-          break;
-        }
         w = csub(w, step);
         st->desc_newton++;
         if (!(s2 < s)) { s = s2; break; }
         s = s2;
       }
-    }
-    if (conv) {
 #if ORACLE_MUTANT != 5 /* mutant 5 plants a missing conjugate fold */
       if (w.im < 0) w.im = -w.im; /* conjugate fold: the root set is symmetric */
 #endif
@@ -487,7 +384,7 @@ static long one_pass(const poly* P, int M, int cL, real lambda0, int cap, double
     }
   }
   st->n_starts += nstart;
-  if (Jstop == J) {
+  if (jbeg == 0 && jend == J) {
     /* the walk must end at the negative real end point, left of M */
     st->endpoint_ok = (rabs(z.im) < 1e-10 && z.re < -1.9) ? 1 : 0;
   }
@@ -640,29 +537,31 @@ int or_real_endpoint(int kind, int l, int n, double lambda0, double* out2) {
   return 0;
 }
 
-/* The split.  roots: [cap][4] (Re hi, Re lo, Im hi, Im lo), full
-   conjugate-closed list sorted by eq. defLexi.  type_a/type_b: per-root type
-   (or NULL).  starts: [starts_cap][4] level-line start points of the final
-   pass (Re hi, Re lo, Im hi, Im lo), upper half in external-angle order, or
-   NULL.  frac < 1 walks only the first part
-   of the upper half (a bounded sample; no count check, no retries).
-   Returns the number of roots written, or a negative error. */
+static int newton_cap(const poly* P, double I_N) {
+  double log2d = 0;
+  for (long d = P->degree; d > 1; d >>= 1) log2d += 1;
+  int cap_steps = (int)ceil(I_N * log2d);
+  return cap_steps < 20 ? 20 : cap_steps;
+}
+
+/* The split of p_n or s_{l,n} (kinds 0 and 1; q_{l,n} is or_split_q).
+   roots: [cap][4] (Re hi, Re lo, Im hi, Im lo), full conjugate-closed list
+   sorted by eq. defLexi.  type_a/type_b: per-root type (or NULL).  starts:
+   [starts_cap][4] level-line start points of the final pass (Re hi, Re lo,
+   Im hi, Im lo), upper half in external-angle order, or NULL.  frac < 1
+   walks only the first part of the upper half (a bounded sample; no count
+   check, no retries).  Returns the number of roots written, or a negative
+   error. */
 long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
               double eps_dup, int max_retries, double frac,
               double* roots, long cap, int* type_a, int* type_b,
               double* starts, long starts_cap, or_stats* st) {
   poly P;
-  if (poly_init(&P, kind, l, n)) return -1;
+  if (kind == 2 || poly_init(&P, kind, l, n)) return -1;
   if (M < 2 || cL < 1 || M % cL) return -1;
   memset(st, 0, sizeof(*st));
   st->degree = P.degree;
-  double log2d = 0;
-  for (long d = P.degree; d > 1; d >>= 1) log2d += 1;
-  int cap_steps = (int)ceil(I_N * log2d);
-  if (cap_steps < 20) cap_steps = 20;
-  /* q_{l,n}: descents to multiple roots contract linearly before their
-     multiplicity is recognised: twice the cap of Algorithm S_par */
-  if (P.kind == 2) cap_steps *= 2;
+  int cap_steps = newton_cap(&P, I_N);
   real eps = (real)eps_dup;
   long nfull = 0;
   cplx* full = NULL;
@@ -672,40 +571,16 @@ long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
     s1.degree = P.degree;
     cand* cs = NULL;
     if (starts) memset(starts, 0, sizeof(double) * 4 * (size_t)starts_cap);
-    long nc = one_pass(&P, M, cL, (real)lambda0, cap_steps, frac, &cs, &s1, starts, starts_cap);
+    long J = (long)M * P.degree / 2;
+    long jend = (frac >= 1.0) ? J : (long)(frac * (double)J);
+    long nc = one_pass(&P, M, cL, (real)lambda0, cap_steps, 0, jend, cx(real_endpoint(&P, (real)lambda0), 0),
+                       1, &cs, &s1, starts, starts_cap);
     cplx* reps = (cplx*)malloc(sizeof(cplx) * (size_t)(nc + 1));
     long nr = dedup(cs, nc, eps, reps, &s1.n_repeat);
     free(cs);
     long nreal = 0;
     for (long i = 0; i < nr; ++i) nreal += (reps[i].im == 0);
     nfull = nreal + 2 * (nr - nreal);
-    long nmult = nfull;
-    if (P.kind == 2) {
-      /* q_{l,n}: a hyperbolic root is polished as the simple root of p_k it
-         is, and counts eta_l(k) times (Thm fact_mis) */
-      nmult = 0;
-      for (long i = 0; i < nr; ++i) {
-        int a, b;
-        classify(&P, reps[i], R_TOL_CLASS, &a, &b);
-        long mu = 1;
-        if (a == 0 && b > 0) {
-          for (int k = 0; k < 8; ++k) {
-            cplx v, dv;
-            eval_pk(b, reps[i], &v, &dv);
-            cplx step = cdiv(v, dv);
-            if (!cfinite(step)) break;
-            reps[i] = csub(reps[i], step);
-            if (reps[i].im != 0 && rabs(reps[i].im) < eps / 2) reps[i].im = 0;
-          }
-#if ORACLE_MUTANT == 7 /* planted mistake: eta_l(k) with l in place of l - 1 */
-          mu = P.l / b + 2;
-#else
-          mu = (P.l - 1) / b + 2;
-#endif
-        }
-        nmult += mu * (reps[i].im == 0 ? 1 : 2);
-      }
-    }
     free(full);
     full = (cplx*)malloc(sizeof(cplx) * (size_t)(nfull + 1));
     long w = 0;
@@ -719,12 +594,12 @@ long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
     s1.desc_newton += st->desc_newton;
     s1.retries = attempt;
     s1.n_roots = nfull;
-    s1.n_mult = nmult;
+    s1.n_mult = nfull;
     s1.n_real = nreal;
     s1.M = M;
     s1.cL = cL;
     *st = s1;
-    if (frac < 1.0 || nmult >= P.degree) break;
+    if (frac < 1.0 || nfull >= P.degree) break;
     M *= 2; /* missing roots: a finer level line contains the coarser one */
     cL *= 2;
   }
@@ -737,6 +612,236 @@ long or_split(int kind, int l, int n, int M, int cL, double lambda0, double I_N,
   }
   free(full);
   return nfull;
+}
+
+/* The level line alone (kinds 0, 1 and 2): the (c_L/2) d + 1 starts of the
+   upper half walked sequentially from the real end point, as in or_split,
+   with no descents.  starts: [starts_cap][4].  Returns the number of starts. */
+long or_walk(int kind, int l, int n, int M, int cL, double lambda0, double* starts, long starts_cap,
+             or_stats* st) {
+  poly P;
+  if (poly_init(&P, kind, l, n)) return -1;
+  if (M < 2 || cL < 1 || M % cL) return -1;
+  memset(st, 0, sizeof(*st));
+  st->degree = P.degree;
+  cand* cs = NULL;
+  long J = (long)M * P.degree / 2;
+  one_pass(&P, M, cL, (real)lambda0, 0, 0, J, cx(real_endpoint(&P, (real)lambda0), 0), 0, &cs, st,
+           starts, starts_cap);
+  free(cs);
+  st->M = M;
+  st->cL = cL;
+  return st->n_starts;
+}
+
+/* ------------------------------------------------------------------ */
+/* A seed at any external angle (Sec. 4.2, the nested family).  The point
+   of index j of the level line of p_n with M points per turn has external
+   angle t = j / (M 2^(n-1)) and satisfies p_n(z) = lambda0 e^{2 i pi j / M}.
+   On |p_k| = lambda0 the same angle has phase 2 pi 2^(k-1) t, the fraction
+   j / (M 2^(n-k)) of a turn, reduced exactly (a dyadic fraction).  Level 1:
+   p_1(c) = c, so z = lambda0 e^{2 i pi t}.  From level k to k+1: p_{k+1}(z) =
+   p_k(z)^2 + z = lambda0^2 e^{i phi} + z with phi the phase of level k+1, so
+   Newton with target lambda0^2 e^{i phi} moves z onto |p_{k+1}| = lambda0^2;
+   the radius is then brought back to lambda0 at that phase in 'shrink'
+   geometric steps, each a Newton-with-target solve from the previous point.
+   Returns 0, or the number of solves that did not converge. */
+static void unit_phase(long num, long den, real lambda, cplx* out) {
+  long r = num % den;
+  if (r < 0) r += den;
+  real ang = 2 * RPI * ((real)r / (real)den);
+  *out = cx(lambda * RCOS(ang), lambda * RSIN(ang));
+}
+
+static int lift_seed_pn(int n, int M, long j, real lambda0, int shrink, cplx* z_out, long* steps) {
+  poly Pk;
+  int fails = 0;
+  cplx z;
+  /* level 1 */
+  unit_phase(j, (long)M << (n - 1), lambda0, &z);
+  for (int k = 1; k < n; ++k) {
+    poly_init(&Pk, 0, 0, k + 1);
+    long den = (long)M << (n - k - 1);
+    cplx target;
+    int ok;
+    unit_phase(j, den, lambda0 * lambda0, &target);
+    *steps += newton_target(&Pk, &z, target, R_TOL_WALK, 80, &ok);
+    fails += !ok;
+    for (int q = 1; q <= shrink; ++q) {
+      real e = 2 - (real)q / (real)shrink;
+      real r = (real)exp((double)e * log((double)lambda0));
+      if (q == shrink) r = lambda0;
+      unit_phase(j, den, r, &target);
+      *steps += newton_target(&Pk, &z, target, R_TOL_WALK, 80, &ok);
+      fails += !ok;
+    }
+  }
+  if (j == 0 || 2 * j == (long)M << (n - 1)) z.im = 0; /* the two real end points */
+  *z_out = z;
+  return fails;
+}
+
+/* The lifted seed of index j (kind 0 only); out4 as or_eval's layout. */
+int or_lift_seed(int n, int M, long j, double lambda0, int shrink, double* out4) {
+  if (n < 1 || n > 40 || M < 2 || shrink < 1) return -1;
+  cplx z;
+  long steps = 0;
+  int f = lift_seed_pn(n, M, j, (real)lambda0, shrink, &z, &steps);
+  split_real(z.re, &out4[0], &out4[1]);
+  split_real(z.im, &out4[2], &out4[3]);
+  return f;
+}
+
+/* One window of the split of p_n: sub-steps jbeg .. jend of the upper half
+   (0 <= jbeg < jend <= M 2^(n-1) / 2), walked from the lifted seed of index
+   jbeg, a descent from every (M/c_L)-th point, and the window's own root
+   set (Chebyshev rule, conjugate fold).  A bounded sample of the whole
+   split's work at any place of the line (the timed CPU baseline).  Returns
+   the number of distinct upper-half roots found in the window, or a
+   negative error; roots4 (NULL or [cap][4]) receives them in (Re, Im)
+   order, st the window's counters. */
+long or_split_window(int n, int M, int cL, double lambda0, double I_N, double eps_dup, long jbeg, long jend,
+                     int shrink, double* roots4, long cap, or_stats* st) {
+  poly P;
+  if (poly_init(&P, 0, 0, n)) return -1;
+  long J = (long)M * P.degree / 2;
+  if (M < 2 || cL < 1 || M % cL || jbeg < 0 || jend <= jbeg || jend > J || shrink < 1) return -1;
+  memset(st, 0, sizeof(*st));
+  st->degree = P.degree;
+  cplx z0;
+  long steps = 0;
+  st->walk_fail += lift_seed_pn(n, M, jbeg, (real)lambda0, shrink, &z0, &steps);
+  st->walk_newton += steps;
+  cand* cs = NULL;
+  long nc = one_pass(&P, M, cL, (real)lambda0, newton_cap(&P, I_N), jbeg, jend, z0, 1, &cs, st, NULL, 0);
+  cplx* reps = (cplx*)malloc(sizeof(cplx) * (size_t)(nc + 1));
+  long nr = dedup(cs, nc, (real)eps_dup, reps, &st->n_repeat);
+  free(cs);
+  for (long i = 0; roots4 && i < nr && i < cap; ++i) {
+    split_real(reps[i].re, &roots4[4 * i + 0], &roots4[4 * i + 1]);
+    split_real(reps[i].im, &roots4[4 * i + 2], &roots4[4 * i + 3]);
+  }
+  free(reps);
+  st->n_roots = nr;
+  st->M = M;
+  st->cL = cL;
+  return nr;
+}
+
+/* ------------------------------------------------------------------ */
+/* q_{l,n} = p_{l+n} - p_l from the telescoped eq. polySimple:
+       q_{l,n} = q_{0,n} prod_{j=1..l} s_{j,n},  q_{0,n} = p_n,  s_{1,n} = p_n
+   (eq. hypCase: q_{1,n} = p_n^2), i.e. q_{l,n} = p_n^2 prod_{j=2..l} s_{j,n}.
+   Every factor has simple roots (Sec. 2), so the roots of q with their
+   multiplicities are the union of the factors' roots, each counted once per
+   factor it belongs to (p_n twice).  The factors are split by or_split
+   above (each with its own count check and retries); their roots are
+   merged with the Chebyshev rule of eq. nsetAsumption at eps_q.  Each
+   distinct root takes the type its factor gives it: Hyp(k) -> (0, k) from
+   p_n or from s_{j,n}; Mis(j,k) -> (j, k) from s_{j,n}.  Members of one
+   cluster whose types differ are counted in *n_conflict. */
+typedef struct {
+  cplx z;
+  int a, b;   /* type: (preperiod, period) */
+  int w;      /* multiplicity contributed */
+} qent;
+
+static int qent_cmp(const void* x, const void* y) {
+  return cplx_lex_cmp(&((const qent*)x)->z, &((const qent*)y)->z);
+}
+
+long or_split_q(int l, int n, int M, int cL, double lambda_p, double lambda_s, double IN_p, double IN_s,
+                const double* eps_factor, double eps_q, int max_retries, double* roots, long cap, int* pre,
+                int* per, int* mult, long* n_conflict, or_stats* st) {
+  if (l < 1 || n < 1 || l + n > 40) return -1;
+  memset(st, 0, sizeof(*st));
+  st->degree = 1L << (l + n - 1);
+  /* factor list: p_n with weight 2, then s_{j,n}, j = 2..l, weight 1 */
+  int fk[42], fl[42], fw[42], nf = 0;
+#if ORACLE_MUTANT == 11 /* planted mistake: p_n counted once (q_{0,n} without s_{1,n}) */
+  fk[nf] = 0; fl[nf] = 0; fw[nf] = 1; ++nf;
+#else
+  fk[nf] = 0; fl[nf] = 0; fw[nf] = 2; ++nf;
+#endif
+#if ORACLE_MUTANT == 7 /* planted mistake: the product over s_{j,n} taken from j = 1 (s_{1,n} = p_n) */
+  fk[nf] = 0; fl[nf] = 0; fw[nf] = 1; ++nf;
+#endif
+  for (int j = 2; j <= l; ++j) { fk[nf] = 1; fl[nf] = j; fw[nf] = 1; ++nf; }
+  long total = 0;
+  for (int f = 0; f < nf; ++f) total += (fk[f] == 0) ? (1L << (n - 1)) : (1L << (fl[f] + n - 2));
+  qent* e = (qent*)malloc(sizeof(qent) * (size_t)(total + 1));
+  long ne = 0;
+  for (int f = 0; f < nf; ++f) {
+    poly F;
+    if (poly_init(&F, fk[f], fl[f], n)) { free(e); return -1; }
+    double* r4 = (double*)malloc(sizeof(double) * 4 * (size_t)F.degree);
+    int* ta = (int*)malloc(sizeof(int) * (size_t)F.degree);
+    int* tb = (int*)malloc(sizeof(int) * (size_t)F.degree);
+    or_stats fs;
+    /* eps_factor[0] for p_n, eps_factor[j - 1] for s_{j,n} */
+    double eps = eps_factor[fk[f] ? fl[f] - 1 : 0];
+    long nr = or_split(fk[f], fl[f], n, M, cL, fk[f] ? lambda_s : lambda_p, fk[f] ? IN_s : IN_p, eps,
+                       max_retries, 1.0, r4, F.degree, ta, tb, NULL, 0, &fs);
+    st->walk_newton += fs.walk_newton;
+    st->desc_newton += fs.desc_newton;
+    st->n_starts += fs.n_starts;
+    st->n_conv += fs.n_conv;
+    st->n_repeat += fs.n_repeat;
+    st->n_diverge += fs.n_diverge;
+    st->n_timeout += fs.n_timeout;
+    st->walk_fail += fs.walk_fail;
+    if (fs.retries > st->retries) st->retries = fs.retries;
+    if (nr > F.degree) nr = F.degree;
+    for (long i = 0; i < nr; ++i) {
+      e[ne].z = cx(join_real(r4[4 * i], r4[4 * i + 1]), join_real(r4[4 * i + 2], r4[4 * i + 3]));
+      e[ne].a = ta[i];
+      e[ne].b = tb[i];
+      e[ne].w = fw[f];
+      ++ne;
+    }
+    free(r4);
+    free(ta);
+    free(tb);
+  }
+  qsort(e, (size_t)ne, sizeof(qent), qent_cmp);
+  /* greedy Chebyshev clustering in (Re, Im) order, as dedup() does */
+  real eps = (real)eps_q;
+  qent* reps = (qent*)malloc(sizeof(qent) * (size_t)(ne + 1));
+  long nr = 0, nconf = 0, nmult = 0;
+  for (long i = 0; i < ne; ++i) {
+    long hit = -1;
+    for (long k = nr - 1; k >= 0 && e[i].z.re - reps[k].z.re < eps; --k) {
+      if (rabs(e[i].z.im - reps[k].z.im) < eps) { hit = k; break; }
+    }
+    if (hit < 0) {
+      reps[nr++] = e[i];
+      continue;
+    }
+    if (reps[hit].a != e[i].a || reps[hit].b != e[i].b) ++nconf;
+    reps[hit].w += e[i].w;
+  }
+  long nout = nr < cap ? nr : cap;
+  long nreal = 0;
+  for (long i = 0; i < nr; ++i) {
+    nmult += reps[i].w;
+    nreal += (reps[i].z.im == 0);
+    if (i < nout) {
+      split_real(reps[i].z.re, &roots[4 * i + 0], &roots[4 * i + 1]);
+      split_real(reps[i].z.im, &roots[4 * i + 2], &roots[4 * i + 3]);
+      pre[i] = reps[i].a;
+      per[i] = reps[i].b;
+      mult[i] = reps[i].w;
+    }
+  }
+  free(e);
+  free(reps);
+  st->n_roots = nr;
+  st->n_real = nreal;
+  st->n_mult = nmult;
+  st->M = M;
+  st->cL = cL;
+  *n_conflict = nconf;
+  return nr;
 }
 
 /* Newton polish of a given point (used to check roots produced elsewhere):
@@ -757,6 +862,45 @@ int or_polish(int kind, int l, int n, const double* c4, int steps, double* out4,
   split_real(w.im, &out4[2], &out4[3]);
   *disp = (double)cabs_(csub(w, c0));
   return 0;
+}
+
+/* or_polish over a list: points c4[count][4]; out4[count][4] the polished
+   points (or NULL), disp[count] the distances |result - c|, last[count]
+   the size of the last Newton step (quadratic convergence leaves it at the
+   rounding floor).  A point whose iterate is not finite gets disp = +inf.
+   Returns the number of such points. */
+long or_polish_many(int kind, int l, int n, const double* c4, long count, int steps, double* out4,
+                    double* disp, double* last) {
+  poly P;
+  if (poly_init(&P, kind, l, n)) return -1;
+  long bad = 0;
+  for (long i = 0; i < count; ++i) {
+    cplx c0 = cx(join_real(c4[4 * i], c4[4 * i + 1]), join_real(c4[4 * i + 2], c4[4 * i + 3]));
+    cplx w = c0;
+    real s = 0;
+    int ok = 1;
+    for (int k = 0; k < steps; ++k) {
+      cplx v, dv;
+      eval_P(&P, w, &v, &dv);
+      cplx step = cdiv(v, dv);
+      w = csub(w, step);
+      s = cabs_(step);
+      if (!cfinite(w)) { ok = 0; break; }
+    }
+    if (!ok) {
+      disp[i] = HUGE_VAL;
+      last[i] = HUGE_VAL;
+      ++bad;
+      continue;
+    }
+    if (out4) {
+      split_real(w.re, &out4[4 * i + 0], &out4[4 * i + 1]);
+      split_real(w.im, &out4[4 * i + 2], &out4[4 * i + 3]);
+    }
+    disp[i] = (double)cabs_(csub(w, c0));
+    last[i] = (double)s;
+  }
+  return bad;
 }
 
 /* Type of one point (see classify).  tau <= 0 selects the default. */

@@ -368,3 +368,54 @@ def test_level_line_iso_angle_zero_misiurewicz(l, n):
         v, _ = oracle.evaluate("mis", n, s4, l=l)
         val = complex(v[0] + v[1], v[2] + v[3])
         assert abs(val - 100 * 1j ** (j % 4)) < 1e-18
+
+
+@pytest.mark.parametrize("n", [3, 6, 9, 12])
+def test_lifted_seed_is_the_walked_point(n):
+    """Sec. 4.2: a point of |p_1| = lambda0 lifted through the nested family
+    p_k -> p_{k+1} (target lambda0^2 at the doubled phase, radius brought
+    back to lambda0) lands on the level line of p_n at the same external
+    angle: the point the sequential walk from the real end point reaches at
+    that index (pinned above against p_n^{-1}(5)), and P there is
+    lambda0 e^{2 i pi j / M}."""
+    st = oracle.level_line("hyp", n)["starts4"]  # M = 8, c_L = 4: start s is sub-step 2 s
+    idx = sorted(set(np.linspace(0, len(st) - 1, min(len(st), 120)).astype(int)))
+    for s in idx:
+        p, fails = oracle.lift_seed(n, 2 * s)
+        assert fails == 0
+        d = abs(complex((p[0] - st[s, 0]) + (p[1] - st[s, 1]), (p[2] - st[s, 2]) + (p[3] - st[s, 3])))
+        assert d < 1e-24, (s, d)
+        v, _ = oracle.evaluate("hyp", n, p)
+        t = 5 * 1j ** ((2 * s % 8) // 2)  # phase 2 pi (2 s) / 8: a multiple of pi / 2, exact
+        assert abs(complex((v[0] - t.real) + v[1], (v[2] - t.imag) + v[3])) < 1e-24
+
+
+def test_windows_together_find_every_root():
+    """The level line cut into windows, each walked from its lifted seed with
+    its own descents and root set (the bounded sample the timed CPU baseline
+    draws), finds together exactly the upper-half roots of the whole split."""
+    n = 12
+    d = 2 ** (n - 1)
+    J = 8 * d // 2
+    cuts = [0, 1000, 2900, 2901, 4096, 6000, J - 17, J]
+    found = [oracle.split_window(n, a, b, fp64=False, want_roots=True)["roots4"] for a, b in zip(cuts, cuts[1:])]
+    w = np.concatenate(found)
+    z = w[:, 0] + 1j * w[:, 2]
+    uz = np.unique(np.round(z, 11))
+    ref = oracle.split("hyp", n)["roots"]
+    up = ref[ref.imag >= 0]
+    assert uz.size == up.size == (d + int(np.sum(ref.imag == 0))) // 2
+    _, dmax = match_sets(np.sort_complex(uz), np.sort_complex(np.round(up, 11)))
+    assert dmax < 1e-10
+
+
+def test_polish_many_is_polish():
+    """The list form of the binary128 polish gives the one-point form's
+    results, point by point; a true root (Cardano's period-3 centre) does not
+    move."""
+    z = np.array([-1.7548776662466927, -0.12256116687665362 + 0.7448617666197442j, 0.3 + 0.1j])
+    disp, last, pts = oracle.polish_many("hyp", 3, z, steps=3, want_points=True)
+    for i, c in enumerate(z):
+        p, dd = oracle.polish("hyp", 3, c, steps=3)
+        assert np.array_equal(p, pts[i]) and dd == disp[i]
+    assert disp[0] < 1e-15 and last[0] < 1e-30

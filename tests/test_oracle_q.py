@@ -12,10 +12,15 @@ multiple (Thm fact_mis).  Each pin comes from outside the oracle:
   here with Python integers from p_{k+1} = p_k^2 + c): its roots, clustered,
   give the same distinct roots and cluster sizes (the multiplicities).
 
-A plausible slip fails one of them: a wrong sign in q (p_{l+n} + p_l is
-s_{l+1,n}, whose roots are simple), p_{l-1} for p_l (then eta is off by one),
-a missed multiple root (the multiplicities fall short of the degree), or a
-multiple root split into close copies (extra distinct roots)."""
+The oracle's q_{l,n} is the union of its own splits of p_n and s_{j,n},
+j = 2..l (eq. polySimple telescoped: q_{l,n} = p_n^2 prod_{j=2..l} s_{j,n}),
+with a root's multiplicity the number of factors it belongs to.  None of the
+pins above is that identity: Thm fact_mis's eta_l(k) and the worked
+factorisation come from the paper's counting, the library roots from the
+integer coefficients of p_{l+n} - p_l itself.  A plausible slip in the union
+fails one of them: the product taken from s_{1,n} (p_n three times), p_n
+counted once, or a factor missed (the multiplicities fall short of the
+degree)."""
 from __future__ import annotations
 
 import numpy as np
@@ -36,6 +41,7 @@ def _hist(r):
 @pytest.mark.parametrize("l,n", [(l, s - l) for s in range(2, 11) for l in range(1, s)])
 def test_types_and_multiplicities_follow_thm_fact_mis(l, n):
     r = oracle.split("q", n, l=l)
+    assert r["n_conflict"] == 0  # the factors agree on the type of every shared root
     assert _hist(r) == counts.type_histogram_q(l, n)
     assert int(r["mult"].sum()) == counts.deg_q(l, n) == r["stats"]["n_mult"]
     hyp = r["type"][:, 0] == 0
@@ -110,8 +116,7 @@ def test_level_line_iso_angle_zero_q(l, n):
     import mpmath
     from tests.rootsets import match_sets
     mpmath.mp.dps = 40
-    r = oracle.split("q", n, l=l, want_starts=True)
-    st = r["starts"]
+    st = oracle.level_line("q", n, l=l)["starts"]
     d = 2 ** (l + n - 1)
     assert st.size == 2 * d + 1
     iso0 = st[::4]
@@ -122,3 +127,34 @@ def test_level_line_iso_angle_zero_q(l, n):
     assert full.size == ref.size == d
     _, dmax = match_sets(full, ref)
     assert dmax < 1e-12
+
+
+@pytest.mark.parametrize("l,n", [(11, 5), (6, 9)])
+def test_order_16_follows_thm_fact_mis(l, n):
+    """Order 16, where a descent on q itself meets roots of multiplicity 4
+    next to other roots (q_{11,5}: period-5 centres of multiplicity 4): the
+    union of the factors' roots is exact, type by type (Thm fact_mis)."""
+    r = oracle.split("q", n, l=l)
+    assert r["n_conflict"] == 0
+    assert _hist(r) == counts.type_histogram_q(l, n)
+    assert int(r["mult"].sum()) == counts.deg_q(l, n)
+    hyp = r["type"][:, 0] == 0
+    assert np.all(r["mult"][hyp] == (l - 1) // r["type"][hyp, 1] + 2)
+
+
+def test_q_roots_are_roots_of_q():
+    """Every distinct root of the union is a root of q_{l,n} = p_{l+n} - p_l
+    as the paper writes it: binary128 Newton on the difference form, with the
+    multiplicity step z - mu q / q' of eq. newtonAcc (quadratic at a root of
+    multiplicity mu), moves no root by more than 1e-20."""
+    l, n = 4, 4
+    r = oracle.split("q", n, l=l)
+    for z, mu in zip(r["roots4"], r["mult"]):
+        w = np.array(z, dtype=np.float64)
+        v, dv = oracle.evaluate("q", n, w, l=l)
+        P = complex(v[0] + v[1], v[2] + v[3])
+        D = complex(dv[0] + dv[1], dv[2] + dv[3])
+        if mu == 1:
+            assert abs(P) <= 1e-20 * abs(D)
+        else:  # q' vanishes too: the value is tiny next to the scale of q
+            assert abs(P) < 1e-20
