@@ -57,7 +57,9 @@ typedef enum {
   MT_ECAPACITY = 3,    /* cap < number of roots; *n_out holds the required size    */
   MT_ECUDA = 4,        /* a CUDA call failed (message in mt_last_error())          */
   MT_EINCOMPLETE = 5,  /* root count != degree after all retries                   */
-  MT_ETIMEOUT = 6,     /* a bounded device loop hit its iteration limit            */
+  MT_ETIMEOUT = 6,     /* a bounded device scan (root-set clustering, certificate
+                          neighbours) hit its cap and the result is incomplete or
+                          uncertified                                           */
   MT_ECERT = 7         /* at least one root failed the disk certificate            */
 } mt_status;
 
@@ -147,6 +149,20 @@ typedef struct {
                               descents that reached the same root in binary32)   */
   int64_t n_mult;          /* roots counted with multiplicity (q_{l,n}; n_roots
                               for the polynomials with simple roots)            */
+  /* Device time of single kernels (CUDA events around their launches on the
+     call's stream, also inside a captured graph), summed over their
+     launches; 0 where the kernel did not run or was not timed.  For the
+     roofline of each kernel against the FMA rate of its own pipe. */
+  float ms_k_walk;         /* the level-line walk (k_walk / k_walk_mixed)         */
+  float ms_k_desc64;       /* binary64 descents (k_descend)                       */
+  float ms_k_desc32;       /* binary32 descents of the mixed tier (k_descend_mixed) */
+  float ms_k_finish;       /* binary64 finish of the mixed tier (k_finish_f64)    */
+  int64_t finish_newton;   /* binary64 Newton steps of k_finish_f64               */
+  int32_t n_k_timed;       /* kernel launches timed in the four fields above      */
+  int32_t reserved2;
+  int64_t desc_orbit_steps; /* batched split: orbit steps summed over the descents'
+                               Newton steps (the orbit length varies by polynomial;
+                               0 for a single polynomial, whose is fixed)          */
 } mt_stats;
 
 /* Defaults documented field by field above. */
@@ -329,7 +345,8 @@ MT_API mt_status mt_classify(int kind, int l, int n, const double* d_roots, int6
    is no workspace argument and no allocation of any kind.  (The paper has
    no counterpart: this is a deployment variant of mt_certify.)
    Arguments and results are those of mt_certify (without d_roots_lo and
-   the workspace): d_roots [count][2] device, d_pass [count] device bytes,
+   the workspace) for kinds 0 (p_n) and 1 (s_{l,n}); kind 2 (q_{l,n}) returns
+   MT_EINVAL.  d_roots [count][2] device, d_pass [count] device bytes,
    d_radius [count] device doubles or NULL, *n_pass host.
    The scratch is one static device array of MT_CERTIFY_STATIC_BYTES that
    every GPU loading the library keeps until the process exits; count above
@@ -341,6 +358,19 @@ MT_API mt_status mt_classify(int kind, int l, int n, const double* d_roots, int6
 MT_API mt_status mt_certify_static(int kind, int l, int n, const double* d_roots, int64_t count,
                                    double tol, uint8_t* d_pass, double* d_radius, int64_t* n_pass,
                                    void* stream);
+
+/* ---- measurement ------------------------------------------------------- */
+
+/* FMA issue rate of the current GPU in TFLOP/s (2 flops per FMA): every SM
+   runs independent FMA chains (x <- x a + b) in binary64 (prec = MT_FP64)
+   or binary32 (prec = MT_MIXED) for a fixed number of rounds, timed with
+   CUDA events on 'stream'.  The denominator of the ALU roofline of the
+   Newton kernels, whose bound is the FMA pipe of their precision (the paper
+   has no counterpart; it times a CPU).  d_work: at least
+   mt_fma_peak_workspace_bytes() bytes (the chains' final values).
+   Synchronises 'stream'. */
+MT_API size_t mt_fma_peak_workspace_bytes(void);
+MT_API mt_status mt_fma_peak(int prec, void* d_work, size_t work_bytes, double* tflops, void* stream);
 
 /* Thread-local message of the last failure ("" if none). */
 MT_API const char* mt_last_error(void);

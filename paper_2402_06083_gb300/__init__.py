@@ -352,5 +352,17 @@ def autotune(kind: str, n: int, l: int = 0, prec: str = "fp64", *, work: Workspa
     return c.value, b.value, ms.value
 
 
+def fma_peak(prec: str = "fp64") -> float:
+    """FMA issue rate of the current GPU in TFLOP/s (mt_fma_peak): binary64
+    for prec 'fp64', binary32 for 'fp32'."""
+    torch = _torch()
+    L = load()
+    buf = torch.empty(int(L.mt_fma_peak_workspace_bytes()), dtype=torch.uint8, device="cuda")
+    out = ctypes.c_double(0.0)
+    check(L.mt_fma_peak(0 if prec == "fp64" else 1, buf.data_ptr(), buf.numel(), ctypes.byref(out),
+                        torch.cuda.current_stream().cuda_stream))
+    return float(out.value)
+
+
 def version() -> str:
     return load().mt_version().decode()

@@ -26,7 +26,8 @@ EXPORTS = (
     "mt_certify_workspace_bytes", "mt_certify", "mt_certify_basin", "mt_separation_workspace_bytes", "mt_separation",
     "mt_eval", "mt_level_line",
     "mt_descend",
-    "mt_classify", "mt_certify_static", "mt_autotune", "mt_last_error", "mt_version",
+    "mt_classify", "mt_certify_static", "mt_autotune", "mt_fma_peak_workspace_bytes", "mt_fma_peak",
+    "mt_last_error", "mt_version",
 )
 MT_CERTIFY_STATIC_MAX_ROOTS = 131072
 
@@ -66,6 +67,9 @@ class Stats(ctypes.Structure):
         ("n_zones", ctypes.c_int64), ("n_zone_roots", ctypes.c_int64), ("n_dd_pieces", ctypes.c_int64),
         ("seed_newton", ctypes.c_int64), ("desc_fp32", ctypes.c_int64), ("ms_seeds", ctypes.c_float),
         ("reserved", ctypes.c_int32), ("n_finish", ctypes.c_int64), ("n_mult", ctypes.c_int64),
+        ("ms_k_walk", ctypes.c_float), ("ms_k_desc64", ctypes.c_float), ("ms_k_desc32", ctypes.c_float),
+        ("ms_k_finish", ctypes.c_float), ("finish_newton", ctypes.c_int64), ("n_k_timed", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32), ("desc_orbit_steps", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -127,6 +131,8 @@ def load() -> ctypes.CDLL:
         "mt_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, op, vp, i64, vp, ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_float)]),
+        "mt_fma_peak_workspace_bytes": (ctypes.c_size_t, []),
+        "mt_fma_peak": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double), vp]),
         "mt_last_error": (ctypes.c_char_p, []),
         "mt_version": (ctypes.c_char_p, []),
     }

@@ -78,18 +78,5 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
-def build_peak_probe() -> str:
-    """The standalone FMA-rate probe (probe/peak_probe.cu), not part of the library."""
-    os.makedirs(OUT, exist_ok=True)
-    exe = os.path.join(OUT, "peak_probe")
-    src = os.path.join(HERE, "probe", "peak_probe.cu")
-    r = subprocess.run([nvcc(), *ARCH, "-O3", "-std=c++17", "-o", exe, src], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed on %s:\n%s" % (src, r.stderr))
-    return exe
-
-
 if __name__ == "__main__":
-    if "--peak-probe" in sys.argv:  # build and run the FMA-rate probe (needs a GPU)
-        sys.exit(subprocess.call([build_peak_probe()]))
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

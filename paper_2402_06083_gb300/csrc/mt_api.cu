@@ -70,14 +70,17 @@ struct Carve {
   }
 };
 
-bool valid_poly(int kind, int l, int n) {
+}  // namespace
+
+// The polynomial domain and the kernel descriptor, shared with mt_static.cu.
+bool mt::valid_poly(int kind, int l, int n) {
   if (kind == 0) return n >= 1 && n <= 40;
   if (kind == 1) return l >= 2 && n >= 1 && l + n <= 41;
   if (kind == 2) return l >= 1 && n >= 1 && l + n <= 40;
   return false;
 }
 
-PolyDev make_poly(int kind, int l, int n) {
+PolyDev mt::make_poly(int kind, int l, int n) {
   PolyDev P;
   P.kind = kind;
   P.l = l;
@@ -97,6 +100,8 @@ PolyDev make_poly(int kind, int l, int n) {
   }
   return P;
 }
+
+namespace {
 
 struct Plan {
   PolyDev P;
@@ -475,6 +480,79 @@ struct EventSet {
   }
 };
 
+// Per-kernel timers (ktimer_begin / ktimer_end of mt_internal.h): event
+// pairs around single launches.  A plain pass uses the thread's set, whose
+// events are created on first use; a captured graph owns a set created
+// before the capture, its pairs recorded as external event nodes that every
+// replay re-records.  Launches beyond CAP per pass go untimed (counted).
+struct KTimers {
+  static constexpr int CAP = 64;
+  cudaEvent_t a[CAP] = {}, b[CAP] = {};
+  int slot[CAP] = {};
+  int used = 0, open = -1, untimed = 0;
+  bool capturing = false;
+  explicit KTimers(bool eager) {
+    for (int k = 0; eager && k < CAP; ++k) make(k);
+  }
+  ~KTimers() {
+    for (int k = 0; k < CAP; ++k) {
+      if (a[k]) cudaEventDestroy(a[k]);
+      if (b[k]) cudaEventDestroy(b[k]);
+    }
+  }
+  bool make(int k) {
+    if (!a[k] && cudaEventCreate(&a[k]) != cudaSuccess) a[k] = nullptr;
+    if (!b[k] && cudaEventCreate(&b[k]) != cudaSuccess) b[k] = nullptr;
+    return a[k] && b[k];
+  }
+  void reset(bool cap) {
+    used = 0;
+    open = -1;
+    untimed = 0;
+    capturing = cap;
+  }
+  // per-slot sums in ms of the recorded pairs (after the stream synchronised)
+  int sums(float* ms) const {
+    for (int q = 0; q < KS_N; ++q) ms[q] = 0.f;
+    for (int k = 0; k < used; ++k) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, a[k], b[k]) == cudaSuccess) ms[slot[k]] += t;
+    }
+    return used;
+  }
+};
+thread_local KTimers* t_kt = nullptr;        // armed for the pass being enqueued
+thread_local KTimers* t_kt_plain = nullptr;  // the thread's set for plain passes
+
+}  // namespace
+
+namespace mt {
+cudaError_t ktimer_begin(int slot, cudaStream_t s) {
+  KTimers* t = t_kt;
+  if (!t) return cudaSuccess;
+  t->open = -1;
+  if (t->used >= KTimers::CAP || (!t->capturing && !t->make(t->used)) || !t->a[t->used]) {
+    ++t->untimed;
+    return cudaSuccess;
+  }
+  const int k = t->used++;
+  t->slot[k] = slot;
+  t->open = k;
+  return t->capturing ? cudaEventRecordWithFlags(t->a[k], s, cudaEventRecordExternal)
+                      : cudaEventRecord(t->a[k], s);
+}
+cudaError_t ktimer_end(cudaStream_t s) {
+  KTimers* t = t_kt;
+  if (!t || t->open < 0) return cudaSuccess;
+  const int k = t->open;
+  t->open = -1;
+  return t->capturing ? cudaEventRecordWithFlags(t->b[k], s, cudaEventRecordExternal)
+                      : cudaEventRecord(t->b[k], s);
+}
+}  // namespace mt
+
+namespace {
+
 void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
   if (!st) return;
   st->degree = p.degree;
@@ -492,6 +570,7 @@ void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
   st->seed_newton = (int64_t)h.seed_newton;
   st->desc_fp32 = (int64_t)h.desc_fp32;
   st->n_finish = (int64_t)h.n_finish;
+  st->finish_newton = (int64_t)h.finish_newton;
   st->walk_fail = (int64_t)h.walk_fail;
   st->n_cert_pass = (int64_t)h.n_cert_pass;
   for (int i = 0; i < MT_MAX_TYPES; ++i) st->count_by_type[i] = (int64_t)h.type_count[i];
@@ -538,12 +617,11 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
   }
   CK(mark(ev.e[1], s, capturing));
   if (p.prec == MT_MIXED) {
-    // binary32 deltas and descent scales live in the (not yet used) sort buffers
-    // the root-set buffers are free until the fold: binary32 deltas and scales
-    // in keys / vals, the finish lists in flag / pos / vals_alt / type
-    FinishScratch fin{b.flag, b.pos, b.vals_alt, b.type, b.scan_tmp, &b.ctr->n_finish};
-    CK(launch_descend_mixed(p.P, b.starts, p.S, p.tol, p.cap, b.cand, (float2*)b.keys,
-                            (float*)b.vals, b.status, b.anchors, fin, b.ctr, s));
+    // the root-set buffers are free until the fold: the sort of the binary32
+    // end points in keys / vals, the finish lists in flag / pos / vals_alt / type
+    FinishScratch fin{b.keys, b.keys_alt, b.vals, b.vals_alt, b.flag, b.pos, b.vals_alt, b.type,
+                      b.scan_tmp, b.radix_tmp, &b.ctr->n_finish};
+    CK(launch_descend_mixed(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.anchors, fin, b.ctr, s));
   } else {
     CK(launch_descend(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
   }
@@ -627,11 +705,11 @@ mt_status run_streamed(const Plan& p, const Buffers& b, double2* out, double2* o
     CK(cudaEventRecord(pe[4 * k + 1], s));
     CK(cudaMemsetAsync(&b.ctr->queue_head, 0, sizeof(unsigned long long), s));
     if (mixed) {
-      // the sort buffers are free until the fold: binary32 deltas and scales
-      // in keys / vals, the finish lists in flag / pos / vals_alt / type
-      FinishScratch fin{b.flag, b.pos, b.vals_alt, b.type, b.scan_tmp, &b.ctr->n_finish};
-      CK(launch_descend_mixed(p.P, b.starts, Sk, p.tol, p.cap, b.cand, (float2*)b.keys, (float*)b.vals,
-                              b.status, b.anchors, fin, b.ctr, s));
+      // the sort buffers are free until the fold: the sort of the binary32
+      // end points in keys / vals, the finish lists in flag / pos / vals_alt / type
+      FinishScratch fin{b.keys, b.keys_alt, b.vals, b.vals_alt, b.flag, b.pos, b.vals_alt, b.type,
+                        b.scan_tmp, b.radix_tmp, &b.ctr->n_finish};
+      CK(launch_descend_mixed(p.P, b.starts, Sk, p.tol, p.cap, b.cand, b.status, b.anchors, fin, b.ctr, s));
     } else {
       CK(launch_descend(p.P, b.starts, Sk, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
     }
@@ -684,9 +762,14 @@ mt_status run_streamed(const Plan& p, const Buffers& b, double2* out, double2* o
 }
 
 mt_status run_pass(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
-                   uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h) {
+                   uint8_t* is_mis, cudaStream_t s, EventSet& ev, DevCounters* h, KTimers** kt_out) {
+  if (!t_kt_plain) t_kt_plain = new KTimers(false);
+  t_kt_plain->reset(false);
+  t_kt = t_kt_plain;
   mt_status rc = enqueue_pass(p, b, out, out_lo, cap_out, is_mis, s, ev, false);
+  t_kt = nullptr;
   if (rc != MT_OK) return rc;
+  *kt_out = t_kt_plain;
   return read_counters(b, h, s);
 }
 
@@ -702,6 +785,7 @@ struct GraphEntry {
   int device;
   cudaGraphExec_t exec = nullptr;
   EventSet* ev = nullptr;
+  KTimers* kt = nullptr;
   unsigned long long launches = 0;  // kernels in the graph
 };
 thread_local std::vector<GraphEntry> t_graphs;
@@ -712,7 +796,7 @@ bool same_plan(const Plan& a, const Plan& b) { return memcmp(&a, &b, sizeof(Plan
 
 mt_status run_pass_graph(const Plan& p, const Buffers& b, void* work, double2* out, double2* out_lo,
                          int64_t cap_out, uint8_t* is_mis, cudaStream_t s, DevCounters* h,
-                         EventSet** ev_out) {
+                         EventSet** ev_out, KTimers** kt_out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (!t_gstream) CK(cudaStreamCreateWithFlags(&t_gstream, cudaStreamNonBlocking));
@@ -726,6 +810,7 @@ mt_status run_pass_graph(const Plan& p, const Buffers& b, void* work, double2* o
     if (t_graphs.size() >= 8) {  // bounded cache: drop the oldest
       cudaGraphExecDestroy(t_graphs.front().exec);
       delete t_graphs.front().ev;
+      delete t_graphs.front().kt;
       t_graphs.erase(t_graphs.begin());
     }
     GraphEntry e;
@@ -737,9 +822,13 @@ mt_status run_pass_graph(const Plan& p, const Buffers& b, void* work, double2* o
     e.cap = cap_out;
     e.device = dev;
     e.ev = new EventSet();
+    e.kt = new KTimers(true);
+    e.kt->reset(true);
     CK(cudaStreamBeginCapture(t_gstream, cudaStreamCaptureModeThreadLocal));
     const unsigned long long l0 = g_launches;
+    t_kt = e.kt;
     mt_status rc = enqueue_pass(p, b, out, out_lo, cap_out, is_mis, t_gstream, *e.ev, true);
+    t_kt = nullptr;
     e.launches = g_launches - l0;
     g_launches = l0;  // counted when the graph runs
     cudaGraph_t graph = nullptr;
@@ -747,16 +836,19 @@ mt_status run_pass_graph(const Plan& p, const Buffers& b, void* work, double2* o
     if (rc != MT_OK) {
       if (graph) cudaGraphDestroy(graph);
       delete e.ev;
+      delete e.kt;
       return rc;
     }
     if (ce != cudaSuccess) {
       delete e.ev;
+      delete e.kt;
       return fail(MT_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce));
     }
     ce = cudaGraphInstantiate(&e.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) {
       delete e.ev;
+      delete e.kt;
       return fail(MT_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
     }
     t_graphs.push_back(e);
@@ -769,6 +861,7 @@ mt_status run_pass_graph(const Plan& p, const Buffers& b, void* work, double2* o
   CK(cudaEventRecord(t_join->e[1], t_gstream));
   CK(cudaStreamWaitEvent(s, t_join->e[1], 0));  // and the caller's later work after the graph
   *ev_out = g->ev;
+  *kt_out = g->kt;
   return read_counters(b, h, s);
 }
 
@@ -920,6 +1013,7 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     skip_repeat = make_plan(kind, l, n, o, 0, &p0) && p0.prec != MT_MIXED;
   }
   EventSet* evp = &ev;
+  KTimers* ktp = nullptr;
   DdReport ddr;
   StreamTimes stimes;
   bool dd_ran = false;
@@ -935,14 +1029,15 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     }
     Buffers b = carve(p, d_work, work_bytes);
     evp = &ev;
+    ktp = nullptr;
     stimes = StreamTimes();
     if (p.stream_P > 1)
       rc = run_streamed(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h, &stimes);
     else if (o->use_graph && retry == 0)
       rc = run_pass_graph(p, b, d_work, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, &h,
-                          &evp);
+                          &evp, &ktp);
     else
-      rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h);
+      rc = run_pass(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s, ev, &h, &ktp);
     if (rc != MT_OK) return rc;
     // retry on missing roots or on a level-line chunk that skipped a turn
     // (q_{l,n}: the roots counted with their multiplicities, Thm fact_mis)
@@ -981,6 +1076,14 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     st->ms_dedup = ms[3];
     st->ms_certify = ms[4];
     cudaEventElapsedTime(&st->ms_seeds, evp->e[0], evp->e[6]);
+    if (ktp) {
+      float kms[KS_N];
+      st->n_k_timed = ktp->sums(kms);
+      st->ms_k_walk = kms[KS_WALK];
+      st->ms_k_desc64 = kms[KS_DESC64];
+      st->ms_k_desc32 = kms[KS_DESC32];
+      st->ms_k_finish = kms[KS_FINISH];
+    }
     if (p.stream_P > 1) {  // summed over the pieces; the piece root sets count as dedup
       st->ms_walk = st->ms_seeds + stimes.walk;
       st->ms_descend = stimes.descend;
@@ -997,6 +1100,13 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   }
   if (n_out) *n_out = (int64_t)h.n_full;
   const int64_t counted = (kind == 2) ? (int64_t)h.n_mult_full : (int64_t)h.n_full;
+  // a bounded scan of the root set or of the certificate's neighbour search
+  // that stopped at its cap may have kept a duplicate or missed a neighbour;
+  // a count that still matches with every root certified is proven anyway
+  // (Thm certif), so the cap is reported only where the result falls short
+  if (h.cluster_overflow && (counted != p.degree || h.n_cert_pass != h.n_full))
+    return fail(MT_ETIMEOUT, "%llu bounded scans of the root set hit their cap; %lld roots found, degree %lld",
+                h.cluster_overflow, (long long)counted, (long long)p.degree);
   if (counted != p.degree)
     return fail(MT_EINCOMPLETE, "found %lld roots%s, degree %lld (after %d retries)", (long long)counted,
                 kind == 2 ? " with multiplicity" : "", (long long)p.degree, retry);
@@ -1356,6 +1466,8 @@ mt_status mt_split_misiurewicz_batch(int max_order, const mt_options* opts, doub
     st.ms_descend = ms[2];
     st.ms_dedup = ms[3];
     st.ms_certify = ms[4];
+    st.ms_k_desc64 = ms[2];  // the descent stage is the one k_descend_batch launch
+    st.desc_orbit_steps = (int64_t)h.desc_orbit;
     st.prec_used = MT_FP64;
   }
   if (!good) return fail(MT_EINCOMPLETE, "some polynomials of the batch miss roots (after %d retries)", retry);

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(128) k_descend_batch(const BatchEntry* __restr
   int64_t idx = -1;
   double zr = 0.0, zi = 0.0, rdiv2 = 16.0, prev2 = 1e300;
   int it = 0, m = 1, lcap = -1, cap = 20;
-  unsigned long long steps = 0, nconv = 0, ndiv = 0, nto = 0;
+  unsigned long long steps = 0, orbit = 0, nconv = 0, ndiv = 0, nto = 0;
   for (;;) {
     const unsigned need = __ballot_sync(0xffffffffu, idx < 0);
     if (need) {
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(128) k_descend_batch(const BatchEntry* __restr
       zi -= qi;
       ++it;
       ++steps;
+      orbit += (unsigned)m;
       const double s2 = fma(qr, qr, qi * qi);
       int outcome = -1;
       if (!finite2(zr, zi) || fma(zr, zr, zi * zi) > rdiv2) outcome = 1;
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(128) k_descend_batch(const BatchEntry* __restr
     }
   }
   warp_add_u64(&ctr->desc_newton, steps);
+  warp_add_u64(&ctr->desc_orbit, orbit);
   warp_add_u64(&ctr->n_conv, nconv);
   warp_add_u64(&ctr->n_diverge, ndiv);
   warp_add_u64(&ctr->n_timeout, nto);

@@ -41,6 +41,8 @@ struct DevCounters {
   unsigned long long desc_fp32;     // binary32 Newton steps of the descents (part of desc_newton)
   unsigned long long n_finish;      // binary64 finishes of the mixed tier (run heads)
   unsigned long long n_mult_full;   // q_{l,n}: full list counted with multiplicity (Thm fact_mis)
+  unsigned long long finish_newton; // binary64 Newton steps of the mixed tier's finish (part of desc_newton)
+  unsigned long long desc_orbit;    // batched descents: orbit steps summed over their Newton steps
   unsigned long long type_count[64];
 };
 
@@ -67,6 +69,19 @@ struct BatchEntry {
   int64_t nchunks;  // chunks of the upper half (N0 / 2)
   int64_t seed_off, chunk_off, start_off;
 };
+
+// The polynomial domain (kind 0: p_n, 1: s_{l,n}, 2: q_{l,n}) and the
+// kernel descriptor of a polynomial in it.
+bool valid_poly(int kind, int l, int n);
+PolyDev make_poly(int kind, int l, int n);
+
+// Per-kernel timing: CUDA events recorded around single launches on the
+// launch stream (as external event nodes inside a stream capture, so they
+// time the graph replay).  A no-op unless the host orchestration armed a
+// timer set for the current call on this thread.
+enum KSlot { KS_WALK = 0, KS_DESC64 = 1, KS_DESC32 = 2, KS_FINISH = 3, KS_N = 4 };
+cudaError_t ktimer_begin(int slot, cudaStream_t s);
+cudaError_t ktimer_end(cudaStream_t s);
 
 // ---- launchers (each returns the launch error) ----------------------------
 
@@ -104,17 +119,23 @@ cudaError_t launch_mixed_repair_walk(const PolyDev& P, double lambda0, int M, in
                                      int64_t nchunks, int shrink, const double2* seeds,
                                      double2* starts, uint8_t* chunk_fail, DevCounters* ctr,
                                      cudaStream_t s, int64_t j0 = 0, int64_t nch = -1);
-// Scratch of the binary64 finish of the mixed tier (count entries each).
+// Scratch of the binary64 finish of the mixed tier (count entries each):
+// the sort of the binary32 end points, the group heads (in sorted order)
+// and their scan, the list of heads and the links of their followers.
 struct FinishScratch {
+  uint64_t *keys, *keys_alt;
+  uint32_t *vals, *vals_alt;      // sorted permutation; vals_alt then holds the head list
   uint32_t *head, *pos, *list;
   uint8_t* link;
-  void* scan_tmp;                 // scan_temp_bytes(count)
+  void *scan_tmp, *radix_tmp;     // scan_temp_bytes(count), radix_temp_bytes(count)
   unsigned long long* nheads;     // device counter
 };
-cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_t count, double tol,
-                                 int cap, double2* cand, float2* dlt, float* hscale, uint8_t* status,
-                                 void* anchors, const FinishScratch& fin, DevCounters* ctr,
-                                 cudaStream_t s);
+// starts: in, the starts; out, the binary32 end points (binary64 values,
+// folded into the upper half where a finish followed).  cand: the
+// candidates (also the binary32 deltas and scales before the finish).
+cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t count, double tol, int cap,
+                                 double2* cand, uint8_t* status, void* anchors, const FinishScratch& fin,
+                                 DevCounters* ctr, cudaStream_t s);
 size_t mixed_anchor_bytes(const PolyDev& P, int64_t count);
 
 // Batched (several polynomials) seeds, walk and descents.

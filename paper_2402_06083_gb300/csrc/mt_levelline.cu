@@ -101,8 +101,11 @@ cudaError_t launch_walk(const PolyDev& P, double lambda0, int M, int every, int6
   const int bs = (block >= 32 && block <= 1024 && block % 32 == 0) ? block : 64;
   const int64_t grid = (nchunks + bs - 1) / bs;
   MT_COUNT_LAUNCH(1);
+  cudaError_t e = ktimer_begin(KS_WALK, s);
+  if (e != cudaSuccess) return e;
   k_walk<<<(unsigned)grid, bs, 0, s>>>(P, lambda0, M, every, L, nchunks, seeds, starts, ctr);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return ktimer_end(s);
 }
 
 // Repairs of the mixed tier in binary64, inside the same launch sequence

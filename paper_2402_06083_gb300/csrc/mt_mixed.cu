@@ -83,6 +83,45 @@ __device__ __forceinline__ void pert_eval(const PolyDev& P, const float2* zs, in
   Dy = fmaf(a, cg_y, g_y) * s;
 }
 
+// pert_eval for the descents: the capture of p_lcap compiled in only where
+// the polynomial has one (s_{l,n}); p_n runs the bare loop (no compare per
+// step), unrolled by four.
+template <bool CAP>
+__device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* zs, int stride, float dx,
+                                            float dy, float& ex, float& ey, float& Dx, float& Dy) {
+  float e_x = 0.f, e_y = 0.f, g_x = 0.f, g_y = 0.f;
+  float ce_x = 0.f, ce_y = 0.f, cg_x = 0.f, cg_y = 0.f;
+  int hexp = (127 - 1) << 23;  // exponent field of 2^-(k+1), k = 0
+#pragma unroll 4
+  for (int k = 0; k < P.m; ++k) {
+    const float2 Z = zs[k * stride];
+    const float zx = Z.x + e_x, zy = Z.y + e_y;  // p_k(c)
+    const float h = __int_as_float(hexp);
+    hexp -= 1 << 23;
+    const float ng_x = fmaf(zx, g_x, fmaf(-zy, g_y, h));
+    const float ng_y = fmaf(zx, g_y, zy * g_x);
+    const float sx = Z.x + zx, sy = Z.y + zy;  // 2 Z_k + e_k
+    const float ne_x = fmaf(sx, e_x, fmaf(-sy, e_y, dx));
+    const float ne_y = fmaf(sx, e_y, fmaf(sy, e_x, dy));
+    e_x = ne_x; e_y = ne_y; g_x = ng_x; g_y = ng_y;
+    if (CAP && k + 1 == P.lcap) { ce_x = e_x; ce_y = e_y; cg_x = g_x; cg_y = g_y; }
+  }
+  if (CAP) {
+    ex = e_x + ce_x;
+    ey = e_y + ce_y;
+    const float a = P.lcap > 0 ? __int_as_float((127 + P.lcap - P.m) << 23) : 0.f;
+    const float s = __int_as_float((127 + P.m) << 23);
+    Dx = fmaf(a, cg_x, g_x) * s;
+    Dy = fmaf(a, cg_y, g_y) * s;
+  } else {
+    const float s = __int_as_float((127 + P.m) << 23);
+    ex = e_x;
+    ey = e_y;
+    Dx = g_x * s;
+    Dy = g_y * s;
+  }
+}
+
 // binary32 quotient; false when |D|^2 leaves the safe binary32 range.
 __device__ __forceinline__ bool cdiv_f32(float a, float b, float c, float d, float& qr, float& qi) {
   const float den = fmaf(c, c, d * d);
@@ -301,9 +340,9 @@ __device__ __forceinline__ ff ff_twice(ff a) { return ff{a.hi + a.hi, a.lo + a.l
 
 // a4 in the mixed tier, anchors: for starts [base, base + cnt), the
 // reference orbit of each start in float-float, rounded to binary32 and
-// stored k-major (anch[(k - 1) * cnt + i] = Z_k, k = 1 .. m-1) so this write
-// and the descent's reads are coalesced, plus P(start) as binary32 hi + lo
-// and the long-jump bound on |delta|.  The anchor only steers the binary32
+// stored start-major (anch[i * (m - 1) + k - 1] = Z_k, k = 1 .. m-1), so
+// that a warp copies one start's orbit with one coalesced load, plus
+// P(start) as binary32 hi + lo and the long-jump bound on |delta|.  The anchor only steers the binary32
 // descent into the basin of its root (the binary64 finish sets the digits),
 // so float-float's ~1e-14 suffices and keeps this off the binary64 pipe.  A
 // uniform launch: computed inside the persistent descent, the orbit of one
@@ -321,7 +360,7 @@ __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, i
     const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
     zx = nx;
     zy = ny;
-    if (k < P.m) anch[(int64_t)(k - 1) * cnt + i] = make_float2(zx.hi, zy.hi);
+    if (k < P.m) anch[i * (P.m - 1) + (k - 1)] = make_float2(zx.hi, zy.hi);
     if (k == P.lcap) { capx = zx; capy = zy; }
   }
   const ff vx = ff_add(zx, capx), vy = ff_add(zy, capy);
@@ -332,48 +371,83 @@ __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, i
 }
 
 // a4 in the mixed tier, binary32 phase (persistent, per-lane refill as in
-// k_descend) over starts [base, base + cnt).  A refilling lane copies its
-// anchor orbit to its shared-memory slot; the loop is binary32 only.  Each
-// descent runs binary32 Newton steps to the binary32 floor and leaves delta
-// with status 3 ("finish in binary64"), or stops as divergent (1) / timed
-// out (2).  The binary64 finish runs in k_finish_f64, a separate uniform
-// launch.
+// k_descend) over starts [base, base + cnt).  Each lane keeps the anchor
+// orbit of its descent in its own column of shared memory (row k holds
+// Z_k of every lane; the row stride is odd, so the rows of one column fall
+// in different banks).  Lanes that finished are refilled together: the
+// warp takes their start indices from a warp-private range of the work
+// queue (one atomic per 32 starts), then copies each new orbit with one
+// coalesced load across the warp's lanes, so no refill runs a loop of
+// loads on one or two lanes while the others wait.  The Newton loop is
+// binary32 only.  Each descent runs binary32 Newton steps to the binary32
+// floor and leaves (delta, its largest squared step) in pack[] with status
+// 3 ("finish in binary64"), or stops as divergent (1) / timed out (2).  The
+// binary64 finish runs in k_finish_f64, a separate uniform launch, once per
+// root.
+constexpr int DESC_POOL = 32;  // work indices taken per queue atomic
+
+template <bool CAP>
 __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, int64_t cnt,
                                                        const float2* __restrict__ anch,
                                                        const float4* __restrict__ vv,
                                                        const float* __restrict__ rdel, int cap,
-                                                       float2* __restrict__ dlt,
-                                                       float* __restrict__ hscale,
+                                                       float4* __restrict__ pack,
                                                        uint8_t* __restrict__ status,
                                                        unsigned long long* queue,
                                                        DevCounters* ctr) {
   extern __shared__ float2 zsh[];
+  const int stride = blockDim.x + 1;
   float2* zs = zsh + threadIdx.x;
-  const int stride = blockDim.x;
   const unsigned lane = threadIdx.x & 31;
+  const int wbase = threadIdx.x & ~31;
+  const int m1 = P.m - 1;
+  zs[0] = make_float2(0.f, 0.f);  // Z_0 = 0 for every descent
   int64_t idx = -1;
   float dx = 0.f, dy = 0.f, h1 = 0.f, prev2 = 0.f, rdelta = 0.f;
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
   int it = 0;
   unsigned long long s32 = 0, ndiv = 0, nto = 0;
+  unsigned long long pool_next = 0, pool_end = 0;  // the warp's range of queue indices (warp-uniform)
+  bool drained = false;                             // the queue is empty (warp-uniform)
   for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, idx < 0);
+    const unsigned need = drained ? 0u : __ballot_sync(0xffffffffu, idx < 0);
     if (need) {
-      unsigned long long b0 = 0;
-      if (lane == (unsigned)(__ffs(need) - 1)) b0 = atomicAdd(queue, (unsigned long long)__popc(need));
-      b0 = __shfl_sync(0xffffffffu, b0, __ffs(need) - 1);
-      if (idx < 0) {
-        idx = (int64_t)(b0 + __popc(need & lanemask_lt()));
-        if (idx < cnt) {
-          zs[0] = make_float2(0.f, 0.f);
-          for (int k = 1; k < P.m; ++k) zs[k * stride] = anch[(int64_t)(k - 1) * cnt + idx];
-          v = vv[idx];
-          rdelta = rdel[idx];
-          dx = dy = 0.f;
-          it = 0;
-          prev2 = 0.f;
-          h1 = 0.f;
+      const unsigned R = __popc(need);
+      // start index of the r-th lane that needs one: the warp's range, then a new one
+      const unsigned long long rem = pool_end - pool_next;
+      unsigned long long g = 0;
+      if (rem < R) {
+        if (lane == 0) g = atomicAdd(queue, (unsigned long long)DESC_POOL);
+        g = __shfl_sync(0xffffffffu, g, 0);
+      }
+      const unsigned r_me = __popc(need & lanemask_lt());
+      if (idx < 0) idx = (int64_t)(r_me < rem ? pool_next + r_me : g + (r_me - rem));
+      if (rem < R) {
+        pool_next = g + (R - rem);
+        pool_end = g + DESC_POOL;
+      } else {
+        pool_next += R;
+      }
+      // the new orbits, one start at a time across the warp's lanes
+      for (unsigned r = 0; r < R; ++r) {
+        const int tl = __fns(need, 0, (int)r + 1);
+        const int64_t ir = __shfl_sync(0xffffffffu, idx, tl);
+        if (ir >= cnt) {
+          drained = true;
+          continue;
         }
+        const float2* src = anch + ir * m1;
+        float2* dst = zsh + wbase + tl;
+        for (int k = (int)lane; k < m1; k += 32) dst[(k + 1) * stride] = src[k];
+      }
+      __syncwarp();
+      if ((unsigned)lane < 32 && ((need >> lane) & 1u) && idx < cnt) {
+        v = vv[idx];
+        rdelta = rdel[idx];
+        dx = dy = 0.f;
+        it = 0;
+        prev2 = 0.f;
+        h1 = 0.f;
       }
     }
     const bool active = idx >= 0 && idx < cnt;
@@ -381,7 +455,7 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
     if (active) {
       int outcome = -1;
       float ex, ey, Dx, Dy, qr, qi;
-      pert_eval(P, zs, stride, dx, dy, ex, ey, Dx, Dy);
+      pert_eval_t<CAP>(P, zs, stride, dx, dy, ex, ey, Dx, Dy);
       const float nr = (v.x + v.z) + ex, ni = (v.y + v.w) + ey;
       if (!cdiv_f32(nr, ni, Dx, Dy, qr, qi)) {
         outcome = 3;  // out of binary32 range: binary64 decides
@@ -400,8 +474,7 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
         prev2 = s2;
       }
       if (outcome >= 0) {
-        dlt[base + idx] = make_float2(dx, dy);
-        hscale[base + idx] = h1;
+        pack[base + idx] = make_float4(dx, dy, h1, 0.f);
         status[base + idx] = (uint8_t)outcome;
         ndiv += outcome == 1;
         nto += outcome == 2;
@@ -416,49 +489,66 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
   warp_add_u64(&ctr->n_timeout, nto);
 }
 
-// a4 in the mixed tier, binary64 finish.
+// a4 in the mixed tier, binary64 finish, once per root.
 //
-// Nearby starts of the level line mostly descend to the same root (the c_L
-// starts of one turn; about three in four descents are repeats, Table
-// newtonSteps).  Their binary32 end points then agree to the binary32 floor
-// (~1e-5 of the descent's largest step), while distinct roots sit at a
-// distance comparable to that step.  So a candidate whose binary32 end
-// point lies within FINISH_SAME (1e-4) of the descent scale from one of the
-// FINISH_BACK previous candidates' is a follower of that candidate: only
-// the head of each group gets the binary64 Newton steps, and followers take
-// the head's result (the root set merges them anyway).  Links never cross a
-// 64-candidate boundary, so a follower's head is at most 63 back.  A wrong
-// merge can only drop a duplicate or, at worst, one of the c_L descents of a
-// root; the count check then reports it and the tier falls back to binary64
-// (measured: 3e-3 instead of 1e-4 already merges distinct roots at p_24).
+// About three in four descents repeat a root (Table newtonSteps), and the
+// repeats come from starts anywhere along the line, not only from the
+// neighbouring ones.  The binary32 end points of two descents that reached
+// the same root agree to the binary32 floor (~1e-5 of the descent's
+// largest step), while distinct roots sit at distances comparable to that
+// step.  So the end points, conjugate-folded, are sorted by Re, and an end
+// point that lies within FINISH_SAME (1e-4) of the smaller of the two
+// descent scales from one of its FINISH_SCAN sorted predecessors follows
+// that predecessor: only the head of each group gets the binary64 Newton
+// steps, and followers take the head's result (the root set would merge
+// them anyway).  A wrong merge can only drop one of the c_L descents of a
+// root; the count check then reports it and the tier falls back to
+// binary64 (measured: 3e-3 instead of 1e-4 already merges distinct roots
+// at p_24).  A group whose scan would run past FINISH_SCAN predecessors
+// gets a head of its own: one more finish, never a wrong merge.
 constexpr float FINISH_SAME2 = 1e-8f;  // (1e-4)^2 of the squared scale h1
-constexpr int FINISH_BACK = 3;
+constexpr int FINISH_SCAN = 32;
 
-__device__ __forceinline__ double2 mixed_point(const double2* starts, const float2* dlt, int64_t i) {
-  const double2 c0 = starts[i];
-  const float2 d = dlt[i];
-  return make_double2(c0.x + (double)d.x, c0.y + (double)d.y);
-}
-
-// head[i] = 1 for a candidate in status 3 that starts a group; link[i] =
-// offset back to the candidate a follower matched (0 for heads and others)
-__global__ void k_finish_heads(int64_t count, const double2* __restrict__ starts,
-                               const float2* __restrict__ dlt, const float* __restrict__ hscale,
-                               const uint8_t* __restrict__ status, uint32_t* __restrict__ head,
-                               uint8_t* __restrict__ link) {
+// c32 = start + delta in binary64, folded into the upper half for the
+// descents to finish (status 3), whose Re is their sort key; the others
+// keep their end point and sort after them.
+__global__ void k_c32_keys(int64_t count, double2* __restrict__ starts, const float4* __restrict__ pack,
+                           const uint8_t* __restrict__ status, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
+  const float4 q = pack[i];
+  double2 c = starts[i];
+  c.x += (double)q.x;
+  c.y += (double)q.y;
+  const bool fin = status[i] == 3;
+  if (fin && c.y < 0.0) c.y = -c.y;
+  starts[i] = c;
+  keys[i] = fin ? f64_key(c.x) : ~0ull;
+  vals[i] = (uint32_t)i;
+}
+
+// head[p] = 1 for a sorted position p whose end point starts a group;
+// link[p] = p - q for a follower of the sorted position q (0 otherwise)
+__global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals, const double2* __restrict__ c32,
+                               const float4* __restrict__ pack, const uint8_t* __restrict__ status,
+                               uint32_t* __restrict__ head, uint8_t* __restrict__ link) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const uint32_t i = vals[p];
   uint32_t h = 0;
   uint8_t lk = 0;
   if (status[i] == 3) {
     h = 1;
-    const double2 a = mixed_point(starts, dlt, i);
-    const float ha = hscale[i];
-    for (int k = 1; k <= FINISH_BACK && k <= (int)(i & 63); ++k) {
-      if (status[i - k] != 3) continue;
-      const double2 b = mixed_point(starts, dlt, i - k);
-      const double ex = a.x - b.x, ey = a.y - b.y;
-      const double sc = (double)fminf(ha, hscale[i - k]);
+    const double2 a = c32[i];
+    const float ha = pack[i].z;
+    const double reach2 = (double)FINISH_SAME2 * (double)ha;  // min(ha, hb) <= ha
+    for (int k = 1; k <= FINISH_SCAN && k <= p; ++k) {
+      const uint32_t j = vals[p - k];
+      const double2 b = c32[j];
+      const double ex = a.x - b.x, ey = a.y - b.y;  // ex >= 0: sorted by Re
+      if (ex * ex > reach2) break;
+      const double sc = (double)fminf(ha, pack[j].z);
       if (fma(ex, ex, ey * ey) <= (double)FINISH_SAME2 * sc) {
         h = 0;
         lk = (uint8_t)k;
@@ -466,15 +556,15 @@ __global__ void k_finish_heads(int64_t count, const double2* __restrict__ starts
       }
     }
   }
-  head[i] = h;
-  link[i] = lk;
+  head[p] = h;
+  link[p] = lk;
 }
 
-// list[pos[i]] = i for the heads
-__global__ void k_finish_list(int64_t count, const uint32_t* __restrict__ head,
-                              const uint32_t* __restrict__ pos, uint32_t* __restrict__ list) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count && head[i]) list[pos[i]] = (uint32_t)i;
+// list[pos[p]] = original index of the head at sorted position p
+__global__ void k_finish_list(int64_t count, const uint32_t* __restrict__ head, const uint32_t* __restrict__ pos,
+                              const uint32_t* __restrict__ vals, uint32_t* __restrict__ list) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < count && head[p]) list[pos[p]] = vals[p];
 }
 
 // Binary64 Newton steps (eq. Newton) from each head's binary32 end point
@@ -482,8 +572,7 @@ __global__ void k_finish_list(int64_t count, const uint32_t* __restrict__ head,
 __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* __restrict__ list,
                                                     const unsigned long long* __restrict__ nlist,
                                                     int64_t cap_list, double tol2, int cap,
-                                                    const double2* __restrict__ starts,
-                                                    const float2* __restrict__ dlt,
+                                                    const double2* __restrict__ c32,
                                                     double2* __restrict__ cand,
                                                     uint8_t* __restrict__ status,
                                                     DevCounters* ctr) {
@@ -491,7 +580,7 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
   unsigned long long s64 = 0;
   if (t < cap_list && t < (int64_t)*nlist) {
     const int64_t i = list[t];
-    double2 z = mixed_point(starts, dlt, i);
+    double2 z = c32[i];
     int outcome = 2;
     double prev2 = 1e300;
     for (int it = 0; it < cap; ++it) {
@@ -512,30 +601,38 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
     status[i] = (uint8_t)outcome;
   }
   warp_add_u64(&ctr->desc_newton, s64);
+  warp_add_u64(&ctr->finish_newton, s64);
 }
 
-// Followers take their head's result (following the links back, at most
-// 63 steps within the 64-candidate block); descents discarded by the
+// Followers take their head's result (following the links back in sorted
+// order, each at most FINISH_SCAN positions); descents discarded by the
 // binary32 phase (status 1, 2, already counted there) keep their binary32
 // end point.  The outcomes of the finished groups are counted here.
-__global__ void k_finish_followers(int64_t count, const double2* __restrict__ starts,
-                                   const float2* __restrict__ dlt, const uint32_t* __restrict__ head,
-                                   const uint8_t* __restrict__ link, double2* __restrict__ cand,
+__global__ void k_finish_followers(int64_t count, const uint32_t* __restrict__ vals,
+                                   const uint32_t* __restrict__ head, const uint8_t* __restrict__ link,
+                                   const double2* __restrict__ c32, double2* __restrict__ cand,
                                    uint8_t* __restrict__ status, DevCounters* ctr) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long nconv = 0, ndiv = 0, nto = 0;
-  if (i < count) {
+  if (p < count) {
+    const uint32_t i = vals[p];
     uint8_t st = status[i];
-    bool finished = head[i] != 0;
+    bool finished = head[p] != 0;
     if (st == 3 && !finished) {
-      int64_t j = i - link[i];
-      for (int g = 0; g < 64 && !head[j]; ++g) j -= link[j];
-      cand[i] = cand[j];
-      st = status[j];
+      int64_t q = p - link[p];
+      for (int g = 0; g < 4096 && !head[q] && link[q]; ++g) q -= link[q];
+      if (head[q]) {
+        const uint32_t j = vals[q];
+        cand[i] = cand[j];
+        st = status[j];
+      } else {  // unresolved (never seen): no root from this descent
+        cand[i] = c32[i];
+        st = 2;
+      }
       status[i] = st;
       finished = true;
     } else if (!finished) {
-      cand[i] = mixed_point(starts, dlt, i);
+      cand[i] = c32[i];
     }
     if (finished) {
       nconv = st == 0;
@@ -573,9 +670,12 @@ cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every
   const size_t smem = (size_t)P.m * bs * sizeof(float2);
   const int64_t grid = (nch + bs - 1) / bs;
   MT_COUNT_LAUNCH(1);
+  cudaError_t e = ktimer_begin(KS_WALK, s);
+  if (e != cudaSuccess) return e;
   k_walk_mixed<<<(unsigned)grid, bs, smem, s>>>(P, lambda0, M, every, L, nchunks, K, seeds, starts,
                                                 chunk_fail, ctr, j0, nch, j0 * L / every);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return ktimer_end(s);
 }
 
 // Anchors are processed in batches of at most MIX_BATCH starts so their
@@ -588,16 +688,17 @@ size_t mixed_anchor_bytes(const PolyDev& P, int64_t count) {
          al((size_t)b * sizeof(float)) + 256;
 }
 
-cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_t count, double tol,
-                                 int cap, double2* cand, float2* dlt, float* hscale, uint8_t* status,
-                                 void* anchors, const FinishScratch& fin, DevCounters* ctr,
-                                 cudaStream_t s) {
+cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t count, double tol, int cap,
+                                 double2* cand, uint8_t* status, void* anchors, const FinishScratch& fin,
+                                 DevCounters* ctr, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
   const int bs = 128;
-  const size_t smem = (size_t)P.m * bs * sizeof(float2);
+  const size_t smem = (size_t)P.m * (bs + 1) * sizeof(float2);
+  const bool capture = P.lcap >= 0;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_mixed, bs, smem);
+  cudaError_t e = capture ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_mixed<true>, bs, smem)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_mixed<false>, bs, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t B = count < MIX_BATCH ? count : MIX_BATCH;
@@ -606,6 +707,7 @@ cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_
   float2* anch = (float2*)a;
   float4* vv = (float4*)(a + al((size_t)B * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2)));
   float* rdel = (float*)((char*)vv + al((size_t)B * sizeof(float4)));
+  float4* pack = (float4*)cand;  // (delta, scale) until the finish writes the roots
   for (int64_t base = 0; base < count; base += B) {
     const int64_t cnt = (count - base < B) ? count - base : B;
     MT_COUNT_LAUNCH(1);
@@ -618,26 +720,35 @@ cudaError_t launch_descend_mixed(const PolyDev& P, const double2* starts, int64_
     unsigned long long* q = &ctr->queue_head;
     if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
-    k_descend_mixed<<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, dlt, hscale,
-                                                     status, q, ctr);
+    if ((e = ktimer_begin(KS_DESC32, s)) != cudaSuccess) return e;
+    if (capture)
+      k_descend_mixed<true><<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, pack, status, q, ctr);
+    else
+      k_descend_mixed<false><<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, pack, status, q, ctr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = ktimer_end(s)) != cudaSuccess) return e;
   }
-  // binary64 finish, once per run of candidates on the same root
+  // binary64 finish, once per group of end points on the same root
   const unsigned nb = (unsigned)((count + bs - 1) / bs);
   MT_COUNT_LAUNCH(1);
-  k_finish_heads<<<nb, bs, 0, s>>>(count, starts, dlt, hscale, status, fin.head, fin.link);
+  k_c32_keys<<<nb, bs, 0, s>>>(count, starts, pack, status, fin.keys, fin.vals);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_exclusive_scan(fin.head, fin.pos, count, fin.scan_tmp, fin.nheads, s)) != cudaSuccess)
+  if ((e = radix_sort_pairs(fin.keys, fin.vals, fin.keys_alt, fin.vals_alt, count, fin.radix_tmp, s)) != cudaSuccess)
     return e;
   MT_COUNT_LAUNCH(1);
-  k_finish_list<<<nb, bs, 0, s>>>(count, fin.head, fin.pos, fin.list);
+  k_finish_heads<<<nb, bs, 0, s>>>(count, fin.vals, starts, pack, status, fin.head, fin.link);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_exclusive_scan(fin.head, fin.pos, count, fin.scan_tmp, fin.nheads, s)) != cudaSuccess) return e;
+  MT_COUNT_LAUNCH(1);
+  k_finish_list<<<nb, bs, 0, s>>>(count, fin.head, fin.pos, fin.vals, fin.list);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   MT_COUNT_LAUNCH(1);
-  k_finish_f64<<<nb, bs, 0, s>>>(P, fin.list, fin.nheads, count, tol * tol, 6, starts, dlt, cand, status,
-                                 ctr);
+  if ((e = ktimer_begin(KS_FINISH, s)) != cudaSuccess) return e;
+  k_finish_f64<<<nb, bs, 0, s>>>(P, fin.list, fin.nheads, count, tol * tol, 6, starts, cand, status, ctr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = ktimer_end(s)) != cudaSuccess) return e;
   MT_COUNT_LAUNCH(1);
-  k_finish_followers<<<nb, bs, 0, s>>>(count, starts, dlt, fin.head, fin.link, cand, status, ctr);
+  k_finish_followers<<<nb, bs, 0, s>>>(count, fin.vals, fin.head, fin.link, starts, cand, status, ctr);
   return cudaGetLastError();
 }
 

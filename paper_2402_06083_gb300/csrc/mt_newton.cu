@@ -289,12 +289,14 @@ cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t coun
   const int64_t need = (count + bs - 1) / bs;
   if (grid > need) grid = need;
   MT_COUNT_LAUNCH(1);
+  if ((e = ktimer_begin(KS_DESC64, s)) != cudaSuccess) return e;
   if (P.kind == 2)
     k_descend_q<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, tol * tol, cap, cand, status, ctr);
   else
     k_descend<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, fmax(tol * tol, 1e-300), cap, cand, status,
                                             ctr);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return ktimer_end(s);
 }
 
 cudaError_t launch_eval(const PolyDev& P, const double2* c, int64_t count, double2* out,

@@ -71,9 +71,8 @@ extern "C" MT_API mt_status mt_certify_static(int kind, int l, int n, const doub
                                               int64_t count, double tol, uint8_t* d_pass,
                                               double* d_radius, int64_t* n_pass, void* stream) {
   set_error_message("");
-  const bool ok_poly = (kind == 0 && n >= 1 && n <= 40) ||
-                       (kind == 1 && l >= 2 && n >= 1 && l + n <= 41);
-  if (!ok_poly) return static_fail(MT_EINVAL, "polynomial out of range");
+  if (kind == 2) return static_fail(MT_EINVAL, "q_{l,n} (kind 2) is certified by mt_certify only");
+  if (!valid_poly(kind, kind == 0 ? 0 : l, n)) return static_fail(MT_EINVAL, "polynomial out of range");
   if (count < 0 || (count > 0 && (!d_roots || !d_pass))) return static_fail(MT_EINVAL, "bad buffers");
   if (count > MT_CERTIFY_STATIC_MAX_ROOTS)
     return static_fail(MT_ECAPACITY, "mt_certify_static takes at most MT_CERTIFY_STATIC_MAX_ROOTS roots");
@@ -97,13 +96,7 @@ extern "C" MT_API mt_status mt_certify_static(int kind, int l, int n, const doub
   uint32_t* vals2 = (uint32_t*)(b + o_vals2);
   void* rtmp = (void*)(b + o_rtmp);
   cudaStream_t s = (cudaStream_t)stream;
-  PolyDev P;
-  P.kind = kind;
-  P.l = kind == 0 ? 0 : l;
-  P.n = n;
-  P.m = kind == 0 ? n : l + n - 1;
-  P.lcap = kind == 0 ? -1 : l - 1;
-  P.log2d = kind == 0 ? n - 1 : l + n - 2;
+  const PolyDev P = make_poly(kind, kind == 0 ? 0 : l, n);
   if (tol <= 0) tol = 1e-12;
   if ((e = launch_init_counters(ctr, s)) != cudaSuccess) return static_fail(MT_ECUDA, "launch", e);
   if ((e = launch_keys_plain((const double2*)d_roots, count, keys, vals, s)) != cudaSuccess)

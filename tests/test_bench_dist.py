@@ -95,53 +95,71 @@ def test_configs_are_well_formed(cfg):
 
 def _stats(**kw):
     st = {"ms_walk": 2.0, "ms_seeds": 0.5, "ms_descend": 3.0, "walk_newton": 1000, "seed_newton": 100,
-          "desc_newton": 2000, "desc_fp32": 0, "steps_fp32": 0}
+          "desc_newton": 2000, "desc_fp32": 0, "steps_fp32": 0, "finish_newton": 0, "n_starts": 4096,
+          "ms_k_walk": 1.5, "ms_k_desc64": 3.0, "ms_k_desc32": 0.0, "ms_k_finish": 0.0, "desc_orbit_steps": 0}
     st.update(kw)
     return st
 
 
-def test_roofline_arithmetic():
-    """achieved = counted steps x flops per step / kernel time; frac = / 1.25
-    TFLOP/s; the slower of walk and descents is the roofline kernel; binary32
-    steps count at the peak ratio; the mixed label only when binary32 ran."""
+def test_kernel_rooflines_arithmetic():
+    """achieved = counted steps x flops per step / the kernel's own time; frac
+    = achieved / the measured rate of the kernel's pipe; the kernel with the
+    largest time is the line's roofline."""
     import bench
-    r = bench.roofline("fp64", 20, [_stats()])
-    assert r["kernel"] == "k_descend"
+    pk = {"fp64": 1.2, "fp32": 75.0}
+    ks = bench.kernel_rooflines("hyp", 0, 20, [_stats()], pk)
+    by = {k["kernel"]: k for k in ks}
     flops = 2000 * (13 * 20 + 24)
-    assert abs(r["achieved"] - flops / 3e-3 / 1e12) < 1e-12 and abs(r["frac"] - r["achieved"] / 1.25) < 1e-12
-    r = bench.roofline("fp64", 20, [_stats(ms_descend=1.0)])
-    assert r["kernel"] == "k_walk" and abs(r["flops_per_launch"] - 900 * 284) < 1e-6
-    mixed = bench.roofline("mixed", 20, [_stats(desc_fp32=1500, steps_fp32=1500)])
-    ratio = bench.FP64_PEAK_TFLOPS / bench.FP32_PEAK_TFLOPS
-    assert mixed["kernel"] == "k_descend_mixed"
-    assert abs(mixed["flops_per_launch"] - (500 * 284 + 1500 * 284 * ratio)) < 1e-6
-    assert bench.roofline("dd", 20, [_stats()])["kernel"] == "k_descend"  # no binary32 steps: binary64 label
-    q = bench.roofline("fp64", 18, [_stats()], desc_flops=13 * 9 + 50 * 9 + 24)
-    assert abs(q["flops_per_launch"] - 2000 * (13 * 9 + 50 * 9 + 24)) < 1e-6
+    assert abs(by["k_descend"]["achieved"] - flops / 3e-3 / 1e12) < 1e-12
+    assert abs(by["k_descend"]["frac"] - by["k_descend"]["achieved"] / 1.2) < 1e-12
+    assert by["k_walk"]["flops_per_launch"] == 900 * (13 * 20 + 24) and by["k_walk"]["pipe"] == "fp64"
+    assert bench.roofline_of(ks, "x")["kernel"] == "k_descend"
+    # the mixed tier: binary32 descents against the binary32 rate, the finish against binary64
+    st = _stats(ms_k_desc64=0.0, desc_fp32=1500, steps_fp32=1600, finish_newton=500, ms_k_desc32=1.0,
+                ms_k_finish=2.5, n_starts=(1 << 23) + 1)
+    by = {k["kernel"]: k for k in bench.kernel_rooflines("hyp", 0, 20, [st], pk)}
+    assert set(by) == {"k_descend_mixed", "k_finish_f64", "k_walk_mixed"}
+    assert by["k_descend_mixed"]["launches"] == 2 and by["k_descend_mixed"]["peak"] == 75.0
+    assert abs(by["k_descend_mixed"]["achieved"] - 1500 * (19 * 20 + 25) / 1e-3 / 1e12) < 1e-12
+    assert abs(by["k_finish_f64"]["achieved"] - 500 * (7 * 20 + 24) / 2.5e-3 / 1e12) < 1e-12
+    assert bench.roofline_of(list(by.values()), "x")["kernel"] == "k_finish_f64"
+    # the batched split: orbit lengths differ per polynomial, counted by the kernel
+    st = _stats(desc_orbit_steps=30000)
+    k = bench.kernel_rooflines("mis", 0, 15, [st], pk)[0]
+    assert k["kernel"] == "k_descend_batch" and k["flops_per_launch"] == 13 * 30000 + 24 * 2000
 
 
-def test_oracle_units_count_distinct_roots_of_q():
+def test_stratified_windows():
+    """One window centred in each of the equal parts of the upper half of
+    the level line, aligned to whole turns, inside the line, together
+    covering the requested fraction."""
     import bench
-    from oracle import counts
-    assert bench.oracle_units("q", 2, 4) == sum(counts.type_histogram_q(2, 4).values()) == 23  # 8 Hyp + 15 Mis
-    assert bench.oracle_units("hyp", 0, 12) == 2048
+    n = 20
+    J = 8 * 2 ** (n - 1) // 2
+    w = bench.windows(n, 0.1, 64)
+    assert len(w) == 64
+    for i, (what, nn, a, b) in enumerate(w):
+        assert what == "window" and nn == n and 0 <= a < b <= J and a % 8 == 0
+        assert i * J // 64 <= a and b <= (i + 1) * J // 64  # inside its own part
+    cover = sum(b - a for _, _, a, b in w) / J
+    assert 0.09 < cover <= 0.1
 
 
-def test_error_vs_fp64_repairs_local_order_swaps():
-    """The mixed-vs-binary64 error report pairs each root with its counterpart
-    even where near-equal real parts put the two lists in different orders."""
+def test_error_vs_oracle_on_the_host():
+    """The bench's error report: the oracle's own roots of p_10 move by less
+    than binary64 rounding under its binary128 polish; one root moved by
+    1e-9 shows as a 1e-9 error."""
     import numpy as np
-    import torch
     import bench
-
-    rng = np.random.default_rng(7)
-    b = np.sort_complex(rng.standard_normal(64) + 1j * rng.standard_normal(64))
-    a = b.copy()
-    a[[10, 11]] = a[[11, 10]]          # a local order swap
-    a[30] += 3e-13                      # a small genuine difference
-    ref = type("R", (), {"roots": torch.from_numpy(b)})()
-    fake = type("MT", (), {"split_hyperbolic": staticmethod(lambda n, prec: ref)})()
-    roots = torch.view_as_real(torch.from_numpy(a)).contiguous()
-    e = bench.error_vs_fp64(fake, torch, 6, roots)
-    assert e["roots"] == 64
-    assert e["max_abs"] == pytest.approx(3e-13, rel=1e-3)
+    import oracle
+    z = oracle.split("hyp", 10, want_types=False)["roots"]
+    e = bench.error_vs_oracle("hyp", 0, 10, z)
+    assert e["checked_fp64"] == z.size and e["max_abs"] < 1e-15 and e["within_tol"]
+    z2 = z.copy()
+    z2[100] += 1e-9
+    e = bench.error_vs_oracle("hyp", 0, 10, z2)
+    assert abs(e["max_abs"] - 1e-9) < 1e-12 and not e["within_tol"]
+    zl = np.zeros_like(z2)
+    zl[5] = 1e-17  # a double-double root: checked with its low part, against the dd tolerance
+    e = bench.error_vs_oracle("hyp", 0, 10, z, zl, sample=64)
+    assert e["checked_dd"] == 1 and e["checked_fp64"] >= 64 and e["max_abs_dd_roots"] > 5e-18

@@ -193,8 +193,8 @@ def test_split_hyperbolic_n20_full(mt, prec):
         assert disp < TOL_FP64
     ref = oracle.split("hyp", n, fp64=True, want_types=False)
     assert ref["n_roots"] == d
-    dmax, _ = match_sorted(z, ref["roots"], 1e-11)
-    assert dmax < 1e-11  # binary64 oracle: both sides carry binary64 rounding
+    dmax, _ = match_sorted(z, ref["roots"], TOL_FP64)
+    assert dmax < TOL_FP64  # binary64 oracle: both sides carry binary64 rounding (~1e-15)
 
 
 # --- certificate ---------------------------------------------------------------------

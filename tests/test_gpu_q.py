@@ -1,11 +1,17 @@
 """q_{l,n} = p_{l+n} - p_l with its multiple roots (Thm fact_mis) on the GPU
 (mt_split_misiurewicz_q) against the binary128 oracle.
 
-Every pair with l + n <= 12, and three of order 14: the same distinct roots
-(within 1e-12, the binary64 parity tolerance of the other splits), the same
-types (preperiod, period) and multiplicities, exactly.  Larger orders: the types follow Thm
-fact_mis with eq. MisCount, and the multiplicities add up to the degree.
-Every root carries its certificate (Mis as a root of q, Hyp of p_n)."""
+The oracle's q_{l,n} is the union of its own splits of p_n and s_{j,n},
+j = 2..l (eq. polySimple telescoped: q_{l,n} = p_n^2 prod_{j=2..l} s_{j,n}),
+a root's multiplicity the number of factors it belongs to: it shares no
+step with the GPU's descents on q, which take the multiplicity step of
+eq. newtonAcc.  Every pair with l + n <= 12, three of order 14 and two of
+order 16 (q_{11,5}, with period-5 centres of multiplicity 4 among simple
+roots, and q_{6,10}): the same distinct roots (within 1e-12, the binary64
+parity tolerance of the other splits), the same types (preperiod, period)
+and multiplicities, exactly.  Larger orders: the types follow Thm fact_mis
+with eq. MisCount, and the multiplicities add up to the degree.  Every root
+carries its certificate (Mis as a root of q, Hyp of p_n)."""
 from __future__ import annotations
 
 import numpy as np
@@ -37,12 +43,14 @@ def _hist(pre, per):
     return h
 
 
-@pytest.mark.parametrize("l,n", [(l, s - l) for s in range(2, 13) for l in range(1, s)] + [(3, 11), (7, 7), (12, 2)])
+@pytest.mark.parametrize("l,n", [(l, s - l) for s in range(2, 13) for l in range(1, s)]
+                         + [(3, 11), (7, 7), (12, 2), (11, 5), (6, 10)])
 def test_q_matches_binary128_oracle(mt, l, n):
     res = mt.split_misiurewicz_q(l, n)
     st = res.stats
     z = res.roots.cpu().numpy()
     ref = oracle.split("q", n, l=l)
+    assert ref["n_conflict"] == 0
     assert z.size == ref["n_roots"]
     assert st["n_mult"] == counts.deg_q(l, n) and st["n_cert_pass"] == z.size
     perm, dmax = match_sets(z, ref["roots"])

@@ -70,3 +70,30 @@ def test_certify_static_rejects_oversized_lists(env):
                              ctypes.byref(npass), None)
     assert rc == mt._lib.MT_ECAPACITY
     assert b"MT_CERTIFY_STATIC_MAX_ROOTS" in L.mt_last_error()
+
+
+def test_certify_static_at_its_limit(env):
+    """Exactly MT_CERTIFY_STATIC_MAX_ROOTS roots -- all 131,072 roots of p_18
+    -- where the carve of the static array (counters, keys, permutation,
+    radix histograms) is at its largest: bit-identical to mt_certify, twice
+    in a row, every root passing."""
+    torch, mt, L = env
+    n = 18
+    count = mt._lib.MT_CERTIFY_STATIC_MAX_ROOTS
+    assert 2 ** (n - 1) == count
+    roots = mt.split_hyperbolic(n).roots
+    ri = torch.view_as_real(roots).contiguous()
+    ok_w, rad_w, np_w = mt.certify("hyp", n, roots)
+    for _ in range(2):
+        ok_s, rad_s, np_s = _static(torch, L, 0, 0, n, ri)
+        assert np_s == np_w == count
+        assert torch.equal(ok_s, ok_w) and torch.equal(rad_s, rad_w)
+
+
+def test_certify_static_rejects_q(env):
+    """q_{l,n} (kind 2) is certified by mt_certify only."""
+    torch, mt, L = env
+    npass = ctypes.c_int64(0)
+    rc = L.mt_certify_static(2, 3, 4, ctypes.c_void_p(16), 4, 0.0, ctypes.c_void_p(16), None,
+                             ctypes.byref(npass), None)
+    assert rc == mt._lib.MT_EINVAL
