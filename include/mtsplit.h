@@ -163,6 +163,13 @@ typedef struct {
   int64_t desc_orbit_steps; /* batched split: orbit steps summed over the descents'
                                Newton steps (the orbit length varies by polynomial;
                                0 for a single polynomial, whose is fixed)          */
+  /* The first attempt of the call (before any (M, c_L) doubling or binary64
+     repeat): its roots found, roots certified, level-line chunks that
+     skipped a turn, and its tier (MT_DD when its double-double pass ran). */
+  int64_t first_n_roots;
+  int64_t first_n_cert_pass;
+  int32_t first_walk_fail;
+  int32_t first_prec;
 } mt_stats;
 
 /* Defaults documented field by field above. */

@@ -73,6 +73,13 @@ struct Carve {
 }  // namespace
 
 // The polynomial domain and the kernel descriptor, shared with mt_static.cu.
+// The mixed walk re-takes its binary64 anchor every WALK_ANCHOR_TURNS
+// turns of the phase (M sub-steps a turn).  Its binary32 perturbation then
+// spans at most that many turns of the line, still resolved far below the
+// sub-step's 1e-2 stop; each anchor is a binary64 orbit, which at one per
+// turn made half of the walk's time.
+constexpr int WALK_ANCHOR_TURNS = 1;
+
 bool mt::valid_poly(int kind, int l, int n) {
   if (kind == 0) return n >= 1 && n <= 40;
   if (kind == 1) return l >= 2 && n >= 1 && l + n <= 41;
@@ -607,7 +614,7 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
   }
   CK(mark(ev.e[6], s, capturing));
   if (p.prec == MT_MIXED) {
-    CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts,
+    CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, WALK_ANCHOR_TURNS * p.M, b.seeds, b.starts,
                          b.chunk_fail, b.ctr, s, p.walk_block));
     CK(launch_mixed_repair_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.shrink, b.seeds,
                                 b.starts, b.chunk_fail, b.ctr, s));
@@ -626,16 +633,31 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
     CK(launch_descend(p.P, b.starts, p.S, p.tol, p.cap, b.cand, b.status, b.ctr, 0, s));
   }
   CK(mark(ev.e[2], s, capturing));
-  CK(launch_fold_keys(b.status, b.cand, p.S, p.eps, b.keys, b.vals, s));
-  CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, p.S, b.radix_tmp, s));
-  CK(launch_cluster(b.cand, b.vals, p.S, &b.ctr->n_conv, p.eps, b.flag, b.ctr, s));
+  if (p.prec == MT_MIXED) {
+    // the root set of the finished group heads only: every follower holds
+    // its head's root (the list of heads is still in vals_alt)
+    CK(launch_fold_keys_list(b.vals_alt, &b.ctr->n_finish, p.S, b.status, b.cand, p.eps, b.keys, b.vals,
+                             &b.ctr->n_heads_conv, s));
+    CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, p.S, b.radix_tmp, s, &b.ctr->n_finish));
+    CK(launch_cluster(b.cand, b.vals, p.S, &b.ctr->n_heads_conv, p.eps, b.flag, b.ctr, s));
+  } else {
+    CK(launch_fold_keys(b.status, b.cand, p.S, p.eps, b.keys, b.vals, s));
+    CK(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, p.S, b.radix_tmp, s));
+    CK(launch_cluster(b.cand, b.vals, p.S, &b.ctr->n_conv, p.eps, b.flag, b.ctr, s));
+  }
   CK(launch_exclusive_scan(b.flag, b.pos, p.S, b.scan_tmp, nullptr, s));
   CK(launch_compact(b.cand, b.vals, b.flag, b.pos, p.S, b.reps, b.ctr, s));
   CK(mark(ev.e[3], s, capturing));
-  CK(launch_classify(p.P, b.reps, &b.ctr->n_reps, p.S, p.eps, 0, b.type, b.mult, b.ctr, s));
-  CK(launch_exclusive_scan(b.mult, b.mpos, p.S, b.scan_tmp, &b.ctr->n_full, s));
-  CK(launch_certify(p.P, b.reps, &b.ctr->n_reps, p.S, p.cert_tol, b.mult, b.pass, b.radius, b.ctr,
-                    s, SegView(), p.kind == 2 ? b.type : nullptr));
+  if (p.kind == 0) {  // types from the certificate's own orbit
+    CK(launch_certify_typed(p.P, b.reps, &b.ctr->n_reps, p.S, p.cert_tol, p.eps, b.type, b.mult, b.pass,
+                            b.radius, b.ctr, s));
+    CK(launch_exclusive_scan(b.mult, b.mpos, p.S, b.scan_tmp, &b.ctr->n_full, s));
+  } else {
+    CK(launch_classify(p.P, b.reps, &b.ctr->n_reps, p.S, p.eps, 0, b.type, b.mult, b.ctr, s));
+    CK(launch_exclusive_scan(b.mult, b.mpos, p.S, b.scan_tmp, &b.ctr->n_full, s));
+    CK(launch_certify(p.P, b.reps, &b.ctr->n_reps, p.S, p.cert_tol, b.mult, b.pass, b.radius, b.ctr,
+                      s, SegView(), p.kind == 2 ? b.type : nullptr));
+  }
   CK(mark(ev.e[4], s, capturing));
   const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
   CK(launch_emit(b.reps, &b.ctr->n_reps, p.S, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out,
@@ -694,7 +716,7 @@ mt_status run_streamed(const Plan& p, const Buffers& b, double2* out, double2* o
     const int64_t Sk = C * p.L / p.every + (k == p.stream_P - 1 ? 1 : 0);
     CK(cudaEventRecord(pe[4 * k], s));
     if (mixed) {
-      CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.M, b.seeds, b.starts, b.chunk_fail,
+      CK(launch_walk_mixed(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, WALK_ANCHOR_TURNS * p.M, b.seeds, b.starts, b.chunk_fail,
                            b.ctr, s, p.walk_block, j0, C));
       CK(launch_mixed_repair_walk(p.P, p.lambda0, p.M, p.every, p.L, p.nchunks, p.shrink, b.seeds, b.starts,
                                   b.chunk_fail, b.ctr, s, j0, C));
@@ -1014,6 +1036,10 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
   }
   EventSet* evp = &ev;
   KTimers* ktp = nullptr;
+  struct {
+    int64_t n_roots = 0, n_cert = 0;
+    int32_t walk_fail = 0, prec = 0;
+  } first;
   DdReport ddr;
   StreamTimes stimes;
   bool dd_ran = false;
@@ -1057,6 +1083,12 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     } else if (p.dd) {
       done = certified;
     }
+    if (retry == 0) {  // kept for the statistics: why a repeat followed
+      first.n_roots = (int64_t)h.n_full;
+      first.n_cert = (int64_t)h.n_cert_pass;
+      first.walk_fail = (int32_t)h.walk_fail;
+      first.prec = dd_ran ? MT_DD : p.prec;
+    }
     if (done || retry >= max_retries) break;
   }
   if (st) {
@@ -1076,6 +1108,10 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
     st->ms_dedup = ms[3];
     st->ms_certify = ms[4];
     cudaEventElapsedTime(&st->ms_seeds, evp->e[0], evp->e[6]);
+    st->first_n_roots = first.n_roots;
+    st->first_n_cert_pass = first.n_cert;
+    st->first_walk_fail = first.walk_fail;
+    st->first_prec = first.prec;
     if (ktp) {
       float kms[KS_N];
       st->n_k_timed = ktp->sums(kms);

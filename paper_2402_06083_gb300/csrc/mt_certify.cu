@@ -238,9 +238,10 @@ __device__ __forceinline__ float ulp_ub(double x) {
   return __int_as_float(1 << (p + 149));
 }
 
-// upper bound of |x + iy| in binary32
+// upper bound of |x + iy| in binary32 (the components bounded on the
+// integer pipe, f32_abs_up)
 __device__ __forceinline__ float abs_ub(double x, double y) {
-  const float ax = __double2float_ru(fabs(x)), ay = __double2float_ru(fabs(y));
+  const float ax = f32_abs_up(x), ay = f32_abs_up(y);
   return __fsqrt_ru(__fmaf_ru(ax, ax, __fmul_ru(ay, ay)));
 }
 __device__ __forceinline__ float hsum_ru(float a, float b) {
@@ -257,6 +258,11 @@ __device__ __forceinline__ float ulp32_ub(float x) {
   if (p >= -126) return __int_as_float((p + 127) << 23);
   return __int_as_float(1 << (p + 149));
 }
+// upper bound of |x - f32_trunc(x)| from the truncated value t: below one
+// ulp of t, or 2^-126 where x truncated to zero
+__device__ __forceinline__ float trunc_err_ub(float t) {
+  return t == 0.f ? 1.17549435e-38f : ulp32_ub(t);
+}
 __device__ __forceinline__ float abs_ub_f(float x, float y) {
   return __fsqrt_ru(__fmaf_ru(fabsf(x), fabsf(x), __fmul_ru(fabsf(y), fabsf(y))));
 }
@@ -268,11 +274,15 @@ __device__ __forceinline__ float abs_lb_f(float x, float y) {
 // centres): returns the value centre V (binary64) with its point radius rv0,
 // and the derivative centre W with its disk radius rw (W encloses
 // P'(D(c, rc))).  The derivative only has to keep 0 out of B', so its
-// centres run in binary32: z enters it as zf = rn32(Z), and the disk of z
-// around zf is widened by |Z - zf| <= (ulp(zf.x) + ulp(zf.y)) / 2.
+// centres run in binary32: z enters it as zf = f32_trunc(Z) (integer pipe),
+// and the disk of z around zf is widened by |Z - zf| <= ulp(zf.x) +
+// ulp(zf.y) (2^-126 for a component truncated to zero).
+// TYPE: also the exact period of c as a root of p_n (kind 0), by the test
+// of type_of (|p_k| <= tau |p'_k| for the smallest k | n) on these centres.
+template <bool TYPE = false>
 __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double cy, float rc,
                                             double& Vx, double& Vy, float& rv0, float& Wx,
-                                            float& Wy, float& rw) {
+                                            float& Wy, float& rw, double tau = 0.0, int* hyp = nullptr) {
   double zx = 0.0, zy = 0.0, czx = 0.0, czy = 0.0;
   float dx = 0.f, dy = 0.f, cdx = 0.f, cdy = 0.f;
   float rz0 = 0.f, rz = 0.f, rd = 0.f;  // radii: z (point), z (disk), z' (disk)
@@ -280,8 +290,8 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
   for (int k = 1; k <= P.m; ++k) {
     const float mz = abs_ub(zx, zy);
     // z' = 2 z z' + 1 in binary32 around zf = rn32(z)
-    const float fx = __double2float_rn(zx), fy = __double2float_rn(zy);
-    const float ez = hsum_ru(ulp32_ub(fx), ulp32_ub(fy));
+    const float fx = f32_trunc(zx), fy = f32_trunc(zy);
+    const float ez = __fadd_ru(trunc_err_ub(fx), trunc_err_ub(fy));
     const float rzz = __fadd_ru(rz, ez);
     const float md = abs_ub_f(dx, dy), mzf = abs_ub_f(fx, fy);
     const float tfx = fx + fx, tfy = fy + fy;  // exact
@@ -305,6 +315,7 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
     const float nrz = __fadd_ru(__fmaf_ru(rz, rz, __fmaf_ru(mz2, rz, Rz)), rc);
     zx = nz_x; zy = nz_y; dx = nd_x; dy = nd_y;
     rz0 = nrz0; rz = nrz; rd = nrd;
+    if (TYPE && !*hyp && (P.n % k) == 0 && newton_small_f(zx, zy, dx, dy, tau)) *hyp = k;
     if (k == P.lcap) { czx = zx; czy = zy; cdx = dx; cdy = dy; crz0 = rz0; crd = rd; }
   }
   if (P.lcap >= 0) {  // s_{l,n} = p_m + p_{l-1}, q_{l,n} = p_m - p_l: one disk sum each
@@ -394,6 +405,92 @@ __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
   const unsigned long long rb = (unsigned long long)__double_as_longlong(rad);
   warp_min_u64(&ctr->min_radius_bits, (valid && ok) ? rb : ~0ull);
   warp_max_u64(&ctr->max_radius_bits, (valid && ok) ? rb : 0ull);
+}
+
+// a6 + a7 fused for p_n (kind 0, one polynomial): the exact period of
+// each representative comes from the centres of the certificate's first
+// disk orbit (type_of's test on the binary64 point orbit, whose derivative
+// centres differ from type_of's only by binary32 rounding), and
+// its conjugate multiplicity (1 real, 2 otherwise) from Im = 0, which the
+// root set made exact.  Writes what k_classify and k_certify write: type,
+// mult, pass, radius and the counters; one orbit pass per root fewer.
+__global__ void k_certify_typed(PolyDev P, const double2* __restrict__ pts, const unsigned long long* n_pts_dev,
+                                int64_t cap, double tol, double tau, uint8_t* __restrict__ type,
+                                uint32_t* __restrict__ mult, uint8_t* __restrict__ pass,
+                                double* __restrict__ radius, DevCounters* ctr) {
+  __shared__ unsigned int hist[64];
+  for (int q = threadIdx.x; q < 64; q += blockDim.x) hist[q] = 0;
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)*n_pts_dev;
+  unsigned long long npass = 0, overflow = 0, nreal = 0, nmult = 0;
+  double rad = 0.0;
+  bool ok = false;
+  const bool valid = p < n && p < cap;
+  if (valid) {
+    const double2 c = pts[p];
+    const unsigned m = (c.y == 0.0) ? 1u : 2u;
+    const double W = tol / 0.45;
+    double nn2 = W * W;
+    if (c.y != 0.0) nn2 = fmin(nn2, 4.0 * c.y * c.y);
+    int scanned = 0;
+    for (int dir = -1; dir <= 1; dir += 2) {
+      for (int64_t q = p + dir; q >= 0 && q < n; q += dir) {
+        const double2 v = pts[q];
+        const double dx = v.x - c.x;
+        if (fabs(dx) >= W) break;
+        const double dy = v.y - c.y, ey = v.y + c.y;
+        nn2 = fmin(nn2, fmin(fma(dx, dx, dy * dy), fma(dx, dx, ey * ey)));
+        if (++scanned >= 4096) { overflow = 1; break; }
+      }
+    }
+    rad = fmin(tol, 0.45 * sqrt(nn2));
+    int hyp = 0;
+    for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
+      if (attempt) rad *= 0.25;  // exact
+      const float radu = __double2float_ru(rad), radd = __double2float_rd(rad);
+      double Vx, Vy;
+      float rv0, Wx, Wy, rw;
+      if (attempt == 0) disk_orbit2<true>(P, c.x, c.y, radu, Vx, Vy, rv0, Wx, Wy, rw, tau, &hyp);
+      else disk_orbit2<false>(P, c.x, c.y, radu, Vx, Vy, rv0, Wx, Wy, rw);
+      const float fz = __fadd_ru(abs_ub(Vx, Vy), rv0);
+      const float dist = __fsub_rd(abs_lb_f(Wx, Wy), rw);
+      ok = isfinite(fz) && isfinite(dist) && dist > 0.f && radd > 0.f && __fmul_rd(radd, dist) > fz;
+      if (ok) rad = (double)radd;
+    }
+    const int t = hyp ? hyp : 255;
+    type[p] = (uint8_t)t;
+    mult[p] = m;
+    nreal += (m == 1);
+    nmult += m;
+    if (t < 64) atomicAdd(&hist[t], m);
+    pass[p] = ok ? 1 : 0;
+    if (radius) radius[p] = rad;
+    npass = ok ? m : 0u;
+  } else if (p < cap) {
+    mult[p] = 0;
+  }
+  warp_add_u64(&ctr->n_cert_pass, npass);
+  warp_add_u64(&ctr->n_reps_real, nreal);
+  warp_add_u64(&ctr->n_mult_full, nmult);
+  if (overflow) atomicAdd(&ctr->cluster_overflow, 1ull);
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(rad);
+  warp_min_u64(&ctr->min_radius_bits, (valid && ok) ? rb : ~0ull);
+  warp_max_u64(&ctr->max_radius_bits, (valid && ok) ? rb : 0ull);
+  __syncthreads();
+  for (int q = threadIdx.x; q < 64; q += blockDim.x)
+    if (hist[q]) atomicAdd(&ctr->type_count[q], (unsigned long long)hist[q]);
+}
+
+cudaError_t launch_certify_typed(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
+                                 int64_t cap, double tol, double tau, uint8_t* type, uint32_t* mult,
+                                 uint8_t* pass, double* radius, DevCounters* ctr, cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  if (P.kind != 0) return cudaErrorInvalidValue;
+  MT_COUNT_LAUNCH(1);
+  k_certify_typed<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, n_reps, cap, tol, tau, type, mult,
+                                                                 pass, radius, ctr);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

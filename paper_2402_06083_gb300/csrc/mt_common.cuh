@@ -78,21 +78,50 @@ __device__ __forceinline__ void orbit_pn_f64(int m, double cr, double ci, double
   vr = zr; vi = zi; dr = er * s; di = ei * s;
 }
 
+// binary64 -> binary32 on the integer pipe.  A conversion instruction runs
+// on the binary64 pipe, the scarce one on GB300 (2 lanes per SM per clock):
+// in an orbit that converts z every step it is a third of that pipe's work.
+// f32_trunc rounds toward zero: sign, the exponent rebiased (its low eight
+// bits xor 0x80 are e - 896), the top 23 mantissa bits by a funnel shift.
+// |x| below 2^-126 gives +-0 (error < 2^-126), |x| from 2^128 on or a
+// non-finite x gives +-inf.  |x - f32_trunc(x)| < ulp(f32_trunc(x)) else.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+  const unsigned f = __funnelshift_l(lo, (unsigned)hi, 3) ^ 0x40000000u;  // exponent field fixed
+  unsigned b = (f & 0x7fffffffu) | ((unsigned)hi & 0x80000000u);
+  if (e - 897u >= 254u) b = ((unsigned)hi & 0x80000000u) | (e <= 896u ? 0u : 0x7f800000u);
+  return __uint_as_float(b);
+}
+
+// An upper bound of |x| in binary32 on the integer pipe: f32_trunc(|x|)
+// moved up one ulp (2^-126 below the normal range, +inf from 2^128 on or
+// for a non-finite x).
+__device__ __forceinline__ float f32_abs_up(double x) {
+  const int hi = __double2hiint(x) & 0x7fffffff;
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+  unsigned b = ((__funnelshift_l(lo, (unsigned)hi, 3) ^ 0x40000000u) & 0x7fffffffu) + 1u;
+  if (e - 897u >= 254u) b = (e <= 896u) ? 0x00800000u : 0x7f800000u;
+  return __uint_as_float(b);
+}
+
 // The orbit with the value in binary64 and the c-derivative in binary32
 // (the mixed tier's binary64 finish).  A Newton quotient P / P' only needs
 // P' to a relative error eta: the iteration then contracts by eta per step
-// near the root instead of quadratically, and eta ~ m 2^-24 is far below
+// near the root instead of quadratically, and eta ~ m 2^-23 is far below
 // the 1e-7 relative accuracy the binary32 phase leaves.  The fixed point is
-// decided by P alone, which stays binary64.  6 binary64 operations per step
-// (2 conversions to binary32, 3 FMA and 1 add for the value) instead of the
-// 8 of orbit_f64.
+// decided by P alone, which stays binary64.  4 binary64 operations per step
+// (3 FMA and 1 add for the value; z enters the derivative through
+// f32_trunc on the integer pipe) instead of the 8 of orbit_f64.
 __device__ __forceinline__ void orbit_f64_d32(int m, int lcap, double cr, double ci, double& vr,
                                               double& vi, float& dr, float& di) {
   double zr = 0.0, zi = 0.0, cap_r = 0.0, cap_i = 0.0;
   float dzr = 0.f, dzi = 0.f, capd_r = 0.f, capd_i = 0.f;
 #pragma unroll 4
   for (int k = 1; k <= m; ++k) {
-    const float fr = __double2float_rn(zr), fi = __double2float_rn(zi);
+    const float fr = f32_trunc(zr), fi = f32_trunc(zi);
     const float tfr = fr + fr, tfi = fi + fi;
     const float ndr = fmaf(tfr, dzr, fmaf(-tfi, dzi, 1.f));
     const float ndi = fmaf(tfr, dzi, tfi * dzr);

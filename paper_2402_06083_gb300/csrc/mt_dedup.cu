@@ -66,6 +66,45 @@ __global__ void k_fold_keys(const uint8_t* __restrict__ status, double2* __restr
   vals[i] = (uint32_t)i;
 }
 
+// The same over a list of candidates (the mixed tier's finished group
+// heads, list[0 .. *n_list)): entry t holds candidate list[t]; the
+// converged ones are counted in *n_ok (they sort first).
+__global__ void k_fold_keys_list(const uint32_t* __restrict__ list, const unsigned long long* __restrict__ n_list,
+                                 int64_t cap, const uint8_t* __restrict__ status, double2* __restrict__ cand,
+                                 double eps, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                 unsigned long long* n_ok) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nl = (int64_t)*n_list < cap ? (int64_t)*n_list : cap;
+  unsigned long long ok = 0;
+  if (t < nl) {
+    const uint32_t i = list[t];
+    uint64_t key = ~0ull;
+    if (status[i] == 0) {
+      double2 z = cand[i];
+      z.y = fabs(z.y);
+      if (z.y < 0.5 * eps) z.y = 0.0;
+      cand[i] = z;
+      key = f64_key(z.x);
+      ok = 1;
+    }
+    keys[t] = key;
+    vals[t] = i;
+  }
+  warp_add_u64(n_ok, ok);
+}
+
+cudaError_t launch_fold_keys_list(const uint32_t* list, const unsigned long long* n_list, int64_t cap,
+                                  const uint8_t* status, double2* cand, double eps, uint64_t* keys, uint32_t* vals,
+                                  unsigned long long* n_ok, cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(n_ok, 0, sizeof(*n_ok), s);
+  if (e != cudaSuccess) return e;
+  MT_COUNT_LAUNCH(1);
+  k_fold_keys_list<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(list, n_list, cap, status, cand, eps, keys, vals,
+                                                                  n_ok);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fold_keys(const uint8_t* status, double2* cand, int64_t count, double eps,
                              uint64_t* keys, uint32_t* vals, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
@@ -184,10 +223,18 @@ constexpr int RS_BS = 256;
 constexpr int RS_ITEMS = 8;
 constexpr int64_t RS_TILE = (int64_t)RS_BS * RS_ITEMS;
 
+// n_dev: NULL, or the number of entries on the device (at most n)
+__device__ __forceinline__ int64_t rs_count(int64_t n, const unsigned long long* n_dev) {
+  if (!n_dev) return n;
+  const int64_t d = (int64_t)*n_dev;
+  return d < n ? d : n;
+}
+
 __global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                    int shift, uint32_t* __restrict__ hist,
-                                                   int64_t nb) {
+                                                   int64_t nb, const unsigned long long* __restrict__ n_dev) {
   __shared__ uint32_t cnt[256];
+  n = rs_count(n, n_dev);
   cnt[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -204,8 +251,9 @@ __global__ void __launch_bounds__(RS_BS) k_rs_scatter(const uint64_t* __restrict
                                                       uint64_t* __restrict__ kout,
                                                       uint32_t* __restrict__ vout, int64_t n,
                                                       int shift, const uint32_t* __restrict__ offs,
-                                                      int64_t nb) {
+                                                      int64_t nb, const unsigned long long* __restrict__ n_dev) {
   __shared__ uint32_t base[256];
+  n = rs_count(n, n_dev);
   __shared__ uint32_t tot[256];
   __shared__ uint32_t wcnt[RS_BS / 32][256];
   const int t = threadIdx.x, w = t >> 5;
@@ -259,6 +307,7 @@ size_t radix_temp_bytes(int64_t n) {
 cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                             int64_t n, void* temp, int begin_bit, int end_bit, bool* in_alt,
                             cudaStream_t s) {
+  const unsigned long long* n_dev = nullptr;
   *in_alt = false;
   if (n <= 1) return cudaSuccess;
   const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
@@ -272,11 +321,11 @@ cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, 
   uint32_t* v1 = vals_alt;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
     MT_COUNT_LAUNCH(1);
-    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb);
+    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb, n_dev);
     cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
     if (e != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
-    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb);
+    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb, n_dev);
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
     *in_alt = !*in_alt;
@@ -285,7 +334,8 @@ cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, 
 }
 
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
-                             uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s) {
+                             uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s,
+                             const unsigned long long* n_dev) {
   if (n <= 1) return cudaSuccess;
   const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
   const int64_t nh = 256 * nb;
@@ -298,11 +348,11 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
   uint32_t* v1 = vals_alt;
   for (int shift = 0; shift < 64; shift += 8) {
     MT_COUNT_LAUNCH(1);
-    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb);
+    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb, n_dev);
     cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
     if (e != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
-    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb);
+    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb, n_dev);
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
   }

@@ -43,6 +43,7 @@ struct DevCounters {
   unsigned long long n_mult_full;   // q_{l,n}: full list counted with multiplicity (Thm fact_mis)
   unsigned long long finish_newton; // binary64 Newton steps of the mixed tier's finish (part of desc_newton)
   unsigned long long desc_orbit;    // batched descents: orbit steps summed over their Newton steps
+  unsigned long long n_heads_conv;  // mixed tier: finished group heads that converged
   unsigned long long type_count[64];
 };
 
@@ -158,6 +159,11 @@ cudaError_t launch_eval(const PolyDev& P, const double2* c, int64_t count, doubl
 // a5: fold candidates and build sort keys.
 cudaError_t launch_fold_keys(const uint8_t* status, double2* cand, int64_t count, double eps,
                              uint64_t* keys, uint32_t* vals, cudaStream_t s);
+// the fold over list[0 .. *n_list) (entry t = candidate list[t]), the
+// converged entries counted in *n_ok (zeroed here)
+cudaError_t launch_fold_keys_list(const uint32_t* list, const unsigned long long* n_list, int64_t cap,
+                                  const uint8_t* status, double2* cand, double eps, uint64_t* keys, uint32_t* vals,
+                                  unsigned long long* n_ok, cudaStream_t s);
 
 // Exclusive scan of u32 (in place allowed), with total written to *total.
 size_t scan_temp_bytes(int64_t n);
@@ -167,8 +173,11 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 // LSD radix sort of (key, val) pairs on bits [0, 64).  The result ends in
 // (keys, vals); (keys_alt, vals_alt) are scratch of the same size.
 size_t radix_temp_bytes(int64_t n);
+// n_dev: NULL, or a device count (at most n) of the entries to sort; the
+// launches are sized for n
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
-                             uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s);
+                             uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s,
+                             const unsigned long long* n_dev = nullptr);
 // Stable passes on bits [begin_bit, end_bit) only (multiples of 8); the
 // result is in (keys, vals) after an even number of passes, else in the alt
 // buffers (*in_alt = true).
@@ -193,6 +202,11 @@ cudaError_t launch_classify(const PolyDev& P, double2* reps, const unsigned long
                             DevCounters* ctr, cudaStream_t s, SegView sv = SegView());
 
 // a7: certify reps (sorted by Re): radius from nearest neighbours, disk test.
+// a6 + a7 in one pass for p_n (kind 0): type, conjugate multiplicity,
+// certificate and radius of each representative (k_classify + k_certify).
+cudaError_t launch_certify_typed(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
+                                 int64_t cap, double tol, double tau, uint8_t* type, uint32_t* mult,
+                                 uint8_t* pass, double* radius, DevCounters* ctr, cudaStream_t s);
 cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned long long* n_reps,
                            int64_t cap, double tol, const uint32_t* mult, uint8_t* pass,
                            double* radius, DevCounters* ctr, cudaStream_t s,

@@ -17,8 +17,8 @@
 // so binary32 carries only the difference from the anchor and its relative
 // precision applies to |delta|, not to |c|.  The residual P(c) - T is
 // (Z_m - T) + e_m with Z_m split into binary32 hi + lo.
-//   - Walk: the anchor is re-taken every K sub-steps (less than a turn of
-//     the phase) from the current point, so |delta| stays a few sub-steps.
+//   - Walk: the anchor is re-taken every K sub-steps (a few turns of the
+//     phase) from the current point, so |delta| stays a few turns' length.
 //   - Descent: the anchor is the start point; binary32 Newton steps run to
 //     the binary32 floor, then binary64 Newton steps (normally two) finish
 //     to the binary64 tolerance (eq. Newton).
@@ -33,7 +33,8 @@ constexpr int MIX_MAXM = 41;
 constexpr int64_t MIX_BATCH = int64_t(1) << 23;  // starts per anchor batch
 
 // binary64 reference orbit at c0: zs[k * stride] = Z_k in binary32 for
-// k = 0 .. m-1, and v = P(c0) = Z_m (+ Z_lcap) as binary32 hi (x, y) + lo (z, w).
+// k = 0 .. m-1 (truncated on the integer pipe: the binary64 pipe keeps the
+// orbit itself), and v = P(c0) = Z_m (+ Z_lcap) as binary32 hi (x, y) + lo (z, w).
 __device__ __forceinline__ void ref_orbit(const PolyDev& P, double c0x, double c0y, float2* zs,
                                           int stride, float4& v) {
   double zx = 0.0, zy = 0.0, capx = 0.0, capy = 0.0;
@@ -43,7 +44,7 @@ __device__ __forceinline__ void ref_orbit(const PolyDev& P, double c0x, double c
     const double ny = fma(zx + zx, zy, c0y);
     zx = nx;
     zy = ny;
-    if (k < P.m) zs[k * stride] = make_float2((float)zx, (float)zy);
+    if (k < P.m) zs[k * stride] = make_float2(f32_trunc(zx), f32_trunc(zy));  // integer pipe
     if (k == P.lcap) { capx = zx; capy = zy; }
   }
   const double vx = zx + capx, vy = zy + capy;
@@ -340,9 +341,9 @@ __device__ __forceinline__ ff ff_twice(ff a) { return ff{a.hi + a.hi, a.lo + a.l
 
 // a4 in the mixed tier, anchors: for starts [base, base + cnt), the
 // reference orbit of each start in float-float, rounded to binary32 and
-// stored start-major (anch[i * (m - 1) + k - 1] = Z_k, k = 1 .. m-1), so
-// that a warp copies one start's orbit with one coalesced load, plus
-// P(start) as binary32 hi + lo and the long-jump bound on |delta|.  The anchor only steers the binary32
+// stored k-major (anch[(k - 1) * cnt + i] = Z_k, k = 1 .. m-1) so this write
+// and the descent's reads are coalesced, plus P(start) as binary32 hi + lo
+// and the long-jump bound on |delta|.  The anchor only steers the binary32
 // descent into the basin of its root (the binary64 finish sets the digits),
 // so float-float's ~1e-14 suffices and keeps this off the binary64 pipe.  A
 // uniform launch: computed inside the persistent descent, the orbit of one
@@ -360,7 +361,7 @@ __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, i
     const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
     zx = nx;
     zy = ny;
-    if (k < P.m) anch[i * (P.m - 1) + (k - 1)] = make_float2(zx.hi, zy.hi);
+    if (k < P.m) anch[(int64_t)(k - 1) * cnt + i] = make_float2(zx.hi, zy.hi);
     if (k == P.lcap) { capx = zx; capy = zy; }
   }
   const ff vx = ff_add(zx, capx), vy = ff_add(zy, capy);
@@ -376,9 +377,11 @@ __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, i
 // Z_k of every lane; the row stride is odd, so the rows of one column fall
 // in different banks).  Lanes that finished are refilled together: the
 // warp takes their start indices from a warp-private range of the work
-// queue (one atomic per 32 starts), then copies each new orbit with one
-// coalesced load across the warp's lanes, so no refill runs a loop of
-// loads on one or two lanes while the others wait.  The Newton loop is
+// queue (one atomic per 32 starts), then copy the new orbits with all 32
+// lanes: the refilled lanes' starts are consecutive queue indices, so the
+// lanes reading row k of the k-major anchors for them read consecutive
+// addresses, and no refill runs a loop of loads on one or two lanes while
+// the others wait.  The Newton loop is
 // binary32 only.  Each descent runs binary32 Newton steps to the binary32
 // floor and leaves (delta, its largest squared step) in pack[] with status
 // 3 ("finish in binary64"), or stops as divergent (1) / timed out (2).  The
@@ -428,17 +431,18 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
       } else {
         pool_next += R;
       }
-      // the new orbits, one start at a time across the warp's lanes
-      for (unsigned r = 0; r < R; ++r) {
-        const int tl = __fns(need, 0, (int)r + 1);
+      // the new orbits with the whole warp: lane t copies rows kk, kk + rows,
+      // ... of the orbit of the (t mod R)-th refilled lane, kk = t / R
+      {
+        const unsigned rows = 32u / R;  // rows copied per round
+        const unsigned r_t = lane % R, kk = lane / R;
+        const int tl = __fns(need, 0, (int)r_t + 1);
         const int64_t ir = __shfl_sync(0xffffffffu, idx, tl);
-        if (ir >= cnt) {
-          drained = true;
-          continue;
+        if (__any_sync(0xffffffffu, ir >= cnt)) drained = true;
+        if (kk < rows && ir < cnt) {
+          float2* dst = zsh + wbase + tl;
+          for (int k = (int)kk; k < m1; k += (int)rows) dst[(k + 1) * stride] = anch[(int64_t)k * cnt + ir];
         }
-        const float2* src = anch + ir * m1;
-        float2* dst = zsh + wbase + tl;
-        for (int k = (int)lane; k < m1; k += 32) dst[(k + 1) * stride] = src[k];
       }
       __syncwarp();
       if ((unsigned)lane < 32 && ((need >> lane) & 1u) && idx < cnt) {
@@ -569,36 +573,67 @@ __global__ void k_finish_list(int64_t count, const uint32_t* __restrict__ head, 
 
 // Binary64 Newton steps (eq. Newton) from each head's binary32 end point
 // until |step| < tol (normally two steps) or the rounding floor.
+// Persistent, with per-lane refill by warp vote (as k_descend): a lane that
+// finished takes the next head of the list at once, so the warp never waits
+// for its slowest finish (one to six steps) before starting new ones.
 __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* __restrict__ list,
                                                     const unsigned long long* __restrict__ nlist,
                                                     int64_t cap_list, double tol2, int cap,
                                                     const double2* __restrict__ c32,
                                                     double2* __restrict__ cand,
                                                     uint8_t* __restrict__ status,
-                                                    DevCounters* ctr) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                                    unsigned long long* queue, DevCounters* ctr) {
+  const unsigned lane = threadIdx.x & 31;
+  const int64_t nl = (int64_t)*nlist < cap_list ? (int64_t)*nlist : cap_list;
+  int64_t t = -1;  // position in the list of this lane's finish
+  double zx = 0.0, zy = 0.0, prev2 = 1e300;
+  int it = 0;
+  bool drained = false;  // warp-uniform: the list is handed out
   unsigned long long s64 = 0;
-  if (t < cap_list && t < (int64_t)*nlist) {
-    const int64_t i = list[t];
-    double2 z = c32[i];
-    int outcome = 2;
-    double prev2 = 1e300;
-    for (int it = 0; it < cap; ++it) {
+  for (;;) {
+    const unsigned need = drained ? 0u : __ballot_sync(0xffffffffu, t < 0);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long b0 = 0;
+      if ((int)lane == leader) b0 = atomicAdd(queue, (unsigned long long)__popc(need));
+      b0 = __shfl_sync(0xffffffffu, b0, leader);
+      if (t < 0) {
+        t = (int64_t)(b0 + __popc(need & lanemask_lt()));
+        if (t < nl) {
+          const double2 z = c32[list[t]];
+          zx = z.x;
+          zy = z.y;
+          it = 0;
+          prev2 = 1e300;
+        }
+      }
+      if ((int64_t)(b0 + __popc(need)) >= nl) drained = true;
+    }
+    const bool active = t >= 0 && t < nl;
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active) {
       double vr, vi, qr, qi;
       float dr, di;
-      orbit_f64_d32(P.m, P.lcap, z.x, z.y, vr, vi, dr, di);
+      orbit_f64_d32(P.m, P.lcap, zx, zy, vr, vi, dr, di);
       cdiv_f64(vr, vi, (double)dr, (double)di, qr, qi);
-      z.x -= qr;
-      z.y -= qi;
+      zx -= qr;
+      zy -= qi;
+      ++it;
       ++s64;
       const double s2 = fma(qr, qr, qi * qi);
-      if (!finite2(z.x, z.y) || fma(z.x, z.x, z.y * z.y) > 1e4) { outcome = 1; break; }
-      if (s2 < tol2) { outcome = 0; break; }
-      if (s2 >= 0.25 * prev2 && s2 < floor2_f64(z.x, z.y)) { outcome = 0; break; }  // rounding floor
+      int outcome = -1;
+      if (!finite2(zx, zy) || fma(zx, zx, zy * zy) > 1e4) outcome = 1;
+      else if (s2 < tol2) outcome = 0;
+      else if (s2 >= 0.25 * prev2 && s2 < floor2_f64(zx, zy)) outcome = 0;  // rounding floor
+      else if (it >= cap) outcome = 2;
       prev2 = s2;
+      if (outcome >= 0) {
+        const uint32_t i = list[t];
+        cand[i] = make_double2(zx, zy);
+        status[i] = (uint8_t)outcome;
+        t = -1;
+      }
     }
-    cand[i] = z;
-    status[i] = (uint8_t)outcome;
   }
   warp_add_u64(&ctr->desc_newton, s64);
   warp_add_u64(&ctr->finish_newton, s64);
@@ -742,11 +777,23 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   MT_COUNT_LAUNCH(1);
   k_finish_list<<<nb, bs, 0, s>>>(count, fin.head, fin.pos, fin.vals, fin.list);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  MT_COUNT_LAUNCH(1);
-  if ((e = ktimer_begin(KS_FINISH, s)) != cudaSuccess) return e;
-  k_finish_f64<<<nb, bs, 0, s>>>(P, fin.list, fin.nheads, count, tol * tol, 6, starts, cand, status, ctr);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = ktimer_end(s)) != cudaSuccess) return e;
+  {
+    // persistent: 8 warps per SM keep the binary64 pipe busy (as k_descend)
+    int fin_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fin_sm, k_finish_f64, bs, 0)) != cudaSuccess) return e;
+    if (fin_sm > 2) fin_sm = 2;
+    if (fin_sm < 1) fin_sm = 1;
+    int64_t fgrid = (int64_t)device_sm_count() * fin_sm;
+    if (fgrid > (int64_t)nb) fgrid = (int64_t)nb;
+    unsigned long long* q = &ctr->queue_head;
+    if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
+    MT_COUNT_LAUNCH(1);
+    if ((e = ktimer_begin(KS_FINISH, s)) != cudaSuccess) return e;
+    k_finish_f64<<<(unsigned)fgrid, bs, 0, s>>>(P, fin.list, fin.nheads, count, tol * tol, 6, starts, cand, status,
+                                                q, ctr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = ktimer_end(s)) != cudaSuccess) return e;
+  }
   MT_COUNT_LAUNCH(1);
   k_finish_followers<<<nb, bs, 0, s>>>(count, fin.vals, fin.head, fin.link, starts, cand, status, ctr);
   return cudaGetLastError();
