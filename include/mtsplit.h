@@ -80,7 +80,9 @@ typedef struct {
   int block;           /* CUDA block size for the Newton kernels (0 -> auto)        */
   int max_retries;     /* doublings of (M, c_L) when roots are missing (default 1;
                           they stop once M would exceed 64, and the last attempt's
-                          result and status stand)                                */
+                          result and status stand).  MT_MIXED and MT_DD first
+                          repeat a failed attempt in binary64; a negative value
+                          keeps the first attempt only (no repeat of any kind) */
   double eps_dup;      /* separation of the root set (0 -> rule of the library)     */
   double cert_tol;     /* certificate radius cap (0 -> 1e-12 FP64, 1e-20 DD)       */
   int use_graph;       /* 1: capture the launch sequence in a CUDA graph and replay */

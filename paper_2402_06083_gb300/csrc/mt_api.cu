@@ -452,6 +452,7 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
 size_t plan_bytes(const Plan& p) { return carve(p, nullptr, 0).bytes; }
 
 int max_attempts(const mt_options* o) {
+  if (o && o->max_retries < 0) return 0;  // the first attempt only
   const int r = o ? std::max(0, o->max_retries) : 1;
   return (o && (o->prec == MT_MIXED || o->prec == MT_DD)) ? r + 1 : r;
 }

@@ -246,18 +246,45 @@ __global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ 
   hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];  // digit-major
 }
 
+// One pass of the scatter.  The tile's elements are first placed in shared
+// memory in digit order (stable: sub-tile by sub-tile, warp by warp, lane by
+// lane, as the global order requires), then written out in that order, so
+// that consecutive threads write consecutive addresses of one digit's run
+// and the global stores coalesce.  hist: the tiles' digit counts (digit-
+// major), offs: their exclusive scan, the tile's first output position for
+// each digit.
 __global__ void __launch_bounds__(RS_BS) k_rs_scatter(const uint64_t* __restrict__ kin,
                                                       const uint32_t* __restrict__ vin,
                                                       uint64_t* __restrict__ kout,
                                                       uint32_t* __restrict__ vout, int64_t n,
                                                       int shift, const uint32_t* __restrict__ offs,
+                                                      const uint32_t* __restrict__ hist,
                                                       int64_t nb, const unsigned long long* __restrict__ n_dev) {
-  __shared__ uint32_t base[256];
-  n = rs_count(n, n_dev);
+  __shared__ uint64_t sk[RS_TILE];
+  __shared__ uint32_t sv[RS_TILE];
+  __shared__ uint32_t gbase[256];  // output position of the tile's first element of digit d
+  __shared__ uint32_t lbase[256];  // position in the staged tile of its first element of digit d
+  __shared__ uint32_t run[256];    // elements of digit d staged by the earlier sub-tiles
   __shared__ uint32_t tot[256];
+  __shared__ uint32_t wsum[RS_BS / 32];
   __shared__ uint32_t wcnt[RS_BS / 32][256];
-  const int t = threadIdx.x, w = t >> 5;
-  base[t] = offs[(int64_t)t * nb + blockIdx.x];
+  n = rs_count(n, n_dev);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  gbase[t] = offs[(int64_t)t * nb + blockIdx.x];
+  {  // exclusive scan over the digits of the tile's counts
+    const uint32_t c = hist[(int64_t)t * nb + blockIdx.x];
+    uint32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int q = 0; q < w; ++q) before += wsum[q];
+    lbase[t] = before + x - c;
+    run[t] = 0;
+  }
   const int64_t tile = (int64_t)blockIdx.x * RS_TILE;
   for (int k = 0; k < RS_ITEMS; ++k) {
 #pragma unroll
@@ -278,23 +305,35 @@ __global__ void __launch_bounds__(RS_BS) k_rs_scatter(const uint64_t* __restrict
     if (valid && rank == 0) wcnt[w][digit] = __popc(peers);
     __syncthreads();
     {  // thread t owns digit t: exclusive prefix over warps
-      uint32_t run = 0;
+      uint32_t r = 0;
 #pragma unroll
       for (int q = 0; q < RS_BS / 32; ++q) {
         const uint32_t c = wcnt[q][t];
-        wcnt[q][t] = run;
-        run += c;
+        wcnt[q][t] = r;
+        r += c;
       }
-      tot[t] = run;
+      tot[t] = r;
     }
     __syncthreads();
     if (valid) {
-      const uint32_t pos = base[digit] + wcnt[w][digit] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+      const uint32_t p = lbase[digit] + run[digit] + wcnt[w][digit] + rank;
+      sk[p] = key;
+      sv[p] = val;
     }
     __syncthreads();
-    base[t] += tot[t];
+    run[t] += tot[t];
+  }
+  __syncthreads();
+  const int64_t cnt = (n - tile) < RS_TILE ? (n - tile) : RS_TILE;
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int j = k * RS_BS + t;
+    if (j < cnt) {
+      const uint64_t key = sk[j];
+      const unsigned d = (unsigned)(key >> shift) & 255u;
+      const uint32_t pos = gbase[d] + (uint32_t)j - lbase[d];
+      kout[pos] = key;
+      vout[pos] = sv[j];
+    }
   }
 }
 
@@ -325,7 +364,7 @@ cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, 
     cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
     if (e != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
-    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb, n_dev);
+    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, hist, nb, n_dev);
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
     *in_alt = !*in_alt;
@@ -352,7 +391,7 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
     cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
     if (e != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
-    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, nb, n_dev);
+    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, hist, nb, n_dev);
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
   }
