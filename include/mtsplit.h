@@ -156,12 +156,15 @@ typedef struct {
      launches; 0 where the kernel did not run or was not timed.  For the
      roofline of each kernel against the FMA rate of its own pipe. */
   float ms_k_walk;         /* the level-line walk (k_walk / k_walk_mixed)         */
-  float ms_k_desc64;       /* binary64 descents (k_descend)                       */
+  float ms_k_desc64;       /* binary64 descents (k_descend; mixed tier: the tip redo) */
   float ms_k_desc32;       /* binary32 descents of the mixed tier (k_descend_mixed) */
   float ms_k_finish;       /* binary64 finish of the mixed tier (k_finish_f64)    */
   int64_t finish_newton;   /* binary64 Newton steps of k_finish_f64               */
   int32_t n_k_timed;       /* kernel launches timed in the four fields above      */
-  int32_t reserved2;
+  int32_t n_tip64;         /* mixed tier: descents that ended within 1e-3 of the
+                              left tip c = -2 and were redone in binary64 from
+                              their start (Sec. 6.3.2: the tip roots close in
+                              faster than binary32 resolves them)               */
   int64_t desc_orbit_steps; /* batched split: orbit steps summed over the descents'
                                Newton steps (the orbit length varies by polynomial;
                                0 for a single polynomial, whose is fixed)          */

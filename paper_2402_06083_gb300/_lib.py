@@ -69,7 +69,7 @@ class Stats(ctypes.Structure):
         ("reserved", ctypes.c_int32), ("n_finish", ctypes.c_int64), ("n_mult", ctypes.c_int64),
         ("ms_k_walk", ctypes.c_float), ("ms_k_desc64", ctypes.c_float), ("ms_k_desc32", ctypes.c_float),
         ("ms_k_finish", ctypes.c_float), ("finish_newton", ctypes.c_int64), ("n_k_timed", ctypes.c_int32),
-        ("reserved2", ctypes.c_int32), ("desc_orbit_steps", ctypes.c_int64),
+        ("n_tip64", ctypes.c_int32), ("desc_orbit_steps", ctypes.c_int64),
         ("first_n_roots", ctypes.c_int64), ("first_n_cert_pass", ctypes.c_int64),
         ("first_walk_fail", ctypes.c_int32), ("first_prec", ctypes.c_int32),
     ]

@@ -578,6 +578,7 @@ void fill_stats(const Plan& p, const DevCounters& h, mt_stats* st) {
   st->seed_newton = (int64_t)h.seed_newton;
   st->desc_fp32 = (int64_t)h.desc_fp32;
   st->n_finish = (int64_t)h.n_finish;
+  st->n_tip64 = (int32_t)h.n_tip64;
   st->finish_newton = (int64_t)h.finish_newton;
   st->walk_fail = (int64_t)h.walk_fail;
   st->n_cert_pass = (int64_t)h.n_cert_pass;

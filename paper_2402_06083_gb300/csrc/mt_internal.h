@@ -44,6 +44,8 @@ struct DevCounters {
   unsigned long long finish_newton; // binary64 Newton steps of the mixed tier's finish (part of desc_newton)
   unsigned long long desc_orbit;    // batched descents: orbit steps summed over their Newton steps
   unsigned long long n_heads_conv;  // mixed tier: finished group heads that converged
+  unsigned long long n_tip64;       // mixed tier: descents redone in binary64 at the left tip
+  unsigned long long n_c32_fin;     // mixed tier: descents left for the binary64 finish
   unsigned long long type_count[64];
 };
 
@@ -101,6 +103,12 @@ cudaError_t launch_walk(const PolyDev& P, double lambda0, int M, int every, int6
 cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t count, double tol,
                            int cap, double2* cand, uint8_t* status, DevCounters* ctr, int block,
                            cudaStream_t s);
+// The same descents (binary64, stop rules of launch_descend) from the
+// starts list[0 .. *nlist) only; outcomes at the listed indices, not
+// counted in ctr (the caller counts them).
+cudaError_t launch_descend_list(const PolyDev& P, const double2* starts, const uint32_t* list,
+                                const unsigned long long* nlist, int64_t count, double tol, int cap,
+                                double2* cand, uint8_t* status, DevCounters* ctr, cudaStream_t s);
 
 // a1-a4 in the mixed tier (binary32 perturbation around binary64 anchors).
 // seed_bad [N0/2 + 1] and chunk_fail [nchunks] receive the per-item

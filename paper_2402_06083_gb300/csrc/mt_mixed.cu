@@ -513,23 +513,87 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
 constexpr float FINISH_SAME2 = 1e-8f;  // (1e-4)^2 of the squared scale h1
 constexpr int FINISH_SCAN = 32;
 
+// The left tip c = -2 (Sec. 6.3.2): the real roots there close in on one
+// another faster than the binary32 descents resolve (at p_30 two real roots
+// 1.4e-12 apart near -2 + 3.9e-4, one of them reached by no binary32
+// descent).  Descents that end within tip_box of -2 are redone in binary64
+// from their start (status 4).  Near -2 the real roots of a degree-d
+// polynomial of the family are spaced as sqrt(c + 2) / d, so the region of
+// spacings below a fixed threshold shrinks as 1 / d^2: tip_box =
+// 1e-3 (d / 2^29)^2, 2.5 times the p_30 case (0.8 % of the descents there).
+inline double tip_box(const PolyDev& P) { return 1e-3 * exp2(2.0 * (P.log2d - 29)); }
+constexpr uint64_t TIP_KEY = ~0ull - 1;  // above every finite f64_key, below ~0
+
 // c32 = start + delta in binary64, folded into the upper half for the
 // descents to finish (status 3), whose Re is their sort key; the others
-// keep their end point and sort after them.
-__global__ void k_c32_keys(int64_t count, double2* __restrict__ starts, const float4* __restrict__ pack,
-                           const uint8_t* __restrict__ status, uint64_t* __restrict__ keys,
-                           uint32_t* __restrict__ vals) {
+// keep their end point and sort after them.  Descents that end in the tip
+// box keep their start instead (status 4, key TIP_KEY, so that the stable
+// sort lists them in index order between the two).  Counts both.
+__global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ starts, const float4* __restrict__ pack,
+                           uint8_t* __restrict__ status, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals, DevCounters* ctr) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  const float4 q = pack[i];
-  double2 c = starts[i];
-  c.x += (double)q.x;
-  c.y += (double)q.y;
-  const bool fin = status[i] == 3;
-  if (fin && c.y < 0.0) c.y = -c.y;
-  starts[i] = c;
-  keys[i] = fin ? f64_key(c.x) : ~0ull;
-  vals[i] = (uint32_t)i;
+  unsigned long long n3 = 0, n4 = 0;
+  if (i < count) {
+    const float4 q = pack[i];
+    const double2 c0 = starts[i];
+    double2 c = make_double2(c0.x + (double)q.x, c0.y + (double)q.y);
+    const bool fin = status[i] == 3;
+    if (fin && c.y < 0.0) c.y = -c.y;
+    uint64_t key = ~0ull;
+    if (fin && c.x < -2.0 + box && c.y < box) {
+      status[i] = 4;  // redone in binary64 from c0
+      key = TIP_KEY;
+      n4 = 1;
+    } else {
+      starts[i] = c;
+      if (fin) {
+        key = f64_key(c.x);
+        n3 = 1;
+      }
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+  }
+  warp_add_u64(&ctr->n_c32_fin, n3);
+  warp_add_u64(&ctr->n_tip64, n4);
+}
+
+// list2 of the descents to redo in binary64: sorted positions n3 .. n3+n4
+// (status 4, in index order)
+__global__ void k_tip_list(const uint32_t* __restrict__ vals, const unsigned long long* __restrict__ n3,
+                           const unsigned long long* __restrict__ n4, uint32_t* __restrict__ list2) {
+  const int64_t a = (int64_t)*n3, m = (int64_t)*n4;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+    list2[t] = vals[a + t];
+}
+
+// The descents redone in binary64 join the list of finished heads
+// (list[*nlist ..]) and are counted; k_finish_count then moves *nlist.
+// Grid-stride: the list is about 1 % of the descents.
+__global__ void k_finish_append(const uint32_t* __restrict__ list2, const unsigned long long* __restrict__ n2,
+                                uint32_t* __restrict__ list, const unsigned long long* __restrict__ nlist,
+                                int64_t cap, const uint8_t* __restrict__ status, DevCounters* ctr) {
+  const int64_t m = (int64_t)*n2, base = (int64_t)*nlist;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long nconv = 0, ndiv = 0, nto = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m && base + t < cap; t += stride) {
+    const uint32_t i = list2[t];
+    list[base + t] = i;
+    const uint8_t st = status[i];
+    nconv += st == 0;
+    ndiv += st == 1;
+    nto += st == 2;
+  }
+  warp_add_u64(&ctr->n_conv, nconv);
+  warp_add_u64(&ctr->n_diverge, ndiv);
+  warp_add_u64(&ctr->n_timeout, nto);
+}
+__global__ void k_finish_count(unsigned long long* nlist, const unsigned long long* n2, int64_t cap) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const unsigned long long t = *nlist + *n2;
+    *nlist = t < (unsigned long long)cap ? t : (unsigned long long)cap;
+  }
 }
 
 // head[p] = 1 for a sorted position p whose end point starts a group;
@@ -765,8 +829,11 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   }
   // binary64 finish, once per group of end points on the same root
   const unsigned nb = (unsigned)((count + bs - 1) / bs);
+  unsigned long long* n2 = &ctr->n_tip64;
+  if ((e = cudaMemsetAsync(n2, 0, sizeof(*n2), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(&ctr->n_c32_fin, 0, sizeof(*n2), s)) != cudaSuccess) return e;
   MT_COUNT_LAUNCH(1);
-  k_c32_keys<<<nb, bs, 0, s>>>(count, starts, pack, status, fin.keys, fin.vals);
+  k_c32_keys<<<nb, bs, 0, s>>>(count, tip_box(P), starts, pack, status, fin.keys, fin.vals, ctr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = radix_sort_pairs(fin.keys, fin.vals, fin.keys_alt, fin.vals_alt, count, fin.radix_tmp, s)) != cudaSuccess)
     return e;
@@ -796,6 +863,19 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   }
   MT_COUNT_LAUNCH(1);
   k_finish_followers<<<nb, bs, 0, s>>>(count, fin.vals, fin.head, fin.link, starts, cand, status, ctr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the tip box: binary64 descents from the starts (list in fin.pos, free
+  // once the heads are listed), then counted with the heads
+  const unsigned sgrid = (unsigned)device_sm_count() * 4;
+  MT_COUNT_LAUNCH(1);
+  k_tip_list<<<sgrid, bs, 0, s>>>(fin.vals, &ctr->n_c32_fin, n2, fin.pos);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_descend_list(P, starts, fin.pos, n2, count, tol, cap, cand, status, ctr, s)) != cudaSuccess)
+    return e;
+  MT_COUNT_LAUNCH(2);
+  k_finish_append<<<sgrid, bs, 0, s>>>(fin.pos, n2, fin.list, fin.nheads, count, status, ctr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_finish_count<<<1, 32, 0, s>>>(fin.nheads, n2, count);
   return cudaGetLastError();
 }
 

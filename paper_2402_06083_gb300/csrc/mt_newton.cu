@@ -16,12 +16,20 @@
 
 namespace mt {
 
+// LIST: the starts list[0 .. *nlist) only (start list[t] for queue entry
+// t); the queue is ctr->queue_head2 then.
+template <bool LIST>
 __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __restrict__ starts,
                                                  int64_t count, double tol2, int cap,
                                                  double2* __restrict__ cand,
-                                                 uint8_t* __restrict__ status, DevCounters* ctr) {
+                                                 uint8_t* __restrict__ status, DevCounters* ctr,
+                                                 const uint32_t* __restrict__ list = nullptr,
+                                                 const unsigned long long* __restrict__ nlist = nullptr) {
+  if (LIST) count = (int64_t)*nlist < count ? (int64_t)*nlist : count;
+  unsigned long long* queue = LIST ? &ctr->queue_head2 : &ctr->queue_head;
   const unsigned lane = threadIdx.x & 31;
-  int64_t idx = -1;  // current start (-1: idle, >= count: queue drained)
+  int64_t idx = -1;  // current queue entry (-1: idle, >= count: queue drained)
+  int64_t at = 0;    // its start
   double zr = 0.0, zi = 0.0, rdiv2 = 16.0, prev2 = 1e300;
   int it = 0;
   unsigned long long steps = 0, nconv = 0, ndiv = 0, nto = 0;
@@ -30,13 +38,13 @@ __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __res
     const unsigned need = __ballot_sync(0xffffffffu, idx < 0);
     if (need) {
       unsigned long long base = 0;
-      if (lane == (unsigned)(__ffs(need) - 1))
-        base = atomicAdd(&ctr->queue_head, (unsigned long long)__popc(need));
+      if (lane == (unsigned)(__ffs(need) - 1)) base = atomicAdd(queue, (unsigned long long)__popc(need));
       base = __shfl_sync(0xffffffffu, base, __ffs(need) - 1);
       if (idx < 0) {
         idx = (int64_t)(base + __popc(need & lanemask_lt()));
         if (idx < count) {
-          const double2 z0 = starts[idx];
+          at = LIST ? (int64_t)list[idx] : idx;
+          const double2 z0 = starts[at];
           zr = z0.x;
           zi = z0.y;
           it = 0;
@@ -72,8 +80,8 @@ __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __res
       else if (it >= cap) outcome = 2;
       prev2 = s2;
       if (outcome >= 0) {
-        cand[idx] = make_double2(zr, zi);
-        status[idx] = (uint8_t)outcome;
+        cand[at] = make_double2(zr, zi);
+        status[at] = (uint8_t)outcome;
         nconv += outcome == 0;
         ndiv += outcome == 1;
         nto += outcome == 2;
@@ -82,9 +90,11 @@ __global__ void __launch_bounds__(128) k_descend(PolyDev P, const double2* __res
     }
   }
   warp_add_u64(&ctr->desc_newton, steps);
-  warp_add_u64(&ctr->n_conv, nconv);
-  warp_add_u64(&ctr->n_diverge, ndiv);
-  warp_add_u64(&ctr->n_timeout, nto);
+  if (!LIST) {  // a list's outcomes are counted where it joins the others
+    warp_add_u64(&ctr->n_conv, nconv);
+    warp_add_u64(&ctr->n_diverge, ndiv);
+    warp_add_u64(&ctr->n_timeout, nto);
+  }
 }
 
 // Descents on q_{l,n} (multiple roots, Thm fact_mis), evaluated as the
@@ -276,8 +286,8 @@ cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t coun
   const int bs = 128;
   (void)block;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.kind == 2 ? k_descend_q : k_descend,
-                                                                bs, 0);
+  cudaError_t e = P.kind == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_q, bs, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend<false>, bs, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   // The binary64 pipe (2 DFMA lanes per SM on GB300) is saturated by 8 warps
@@ -293,8 +303,31 @@ cudaError_t launch_descend(const PolyDev& P, const double2* starts, int64_t coun
   if (P.kind == 2)
     k_descend_q<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, tol * tol, cap, cand, status, ctr);
   else
-    k_descend<<<(unsigned)grid, bs, 0, s>>>(P, starts, count, fmax(tol * tol, 1e-300), cap, cand, status,
-                                            ctr);
+    k_descend<false><<<(unsigned)grid, bs, 0, s>>>(P, starts, count, fmax(tol * tol, 1e-300), cap, cand, status,
+                                                   ctr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return ktimer_end(s);
+}
+
+cudaError_t launch_descend_list(const PolyDev& P, const double2* starts, const uint32_t* list,
+                                const unsigned long long* nlist, int64_t count, double tol, int cap,
+                                double2* cand, uint8_t* status, DevCounters* ctr, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (P.kind == 2) return cudaErrorInvalidValue;  // q_{l,n} has no mixed tier
+  const int bs = 128;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend<true>, bs, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm > 2) per_sm = 2;  // as launch_descend
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)device_sm_count() * per_sm;
+  const int64_t need = (count + bs - 1) / bs;
+  if (grid > need) grid = need;
+  if ((e = cudaMemsetAsync(&ctr->queue_head2, 0, sizeof(ctr->queue_head2), s)) != cudaSuccess) return e;
+  MT_COUNT_LAUNCH(1);
+  if ((e = ktimer_begin(KS_DESC64, s)) != cudaSuccess) return e;
+  k_descend<true><<<(unsigned)grid, bs, 0, s>>>(P, starts, count, fmax(tol * tol, 1e-300), cap, cand, status, ctr,
+                                                list, nlist);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return ktimer_end(s);
 }

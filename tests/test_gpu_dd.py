@@ -135,12 +135,15 @@ def _tip_checks(mt, n, res, k=24):
     assert abs(gap * 4.0 ** n / SEP["hyp_constant"] - 1) < 2 * SEP["hyp_rel_error"]
 
 
-@pytest.mark.parametrize("n", [26, 28, 29])
+@pytest.mark.parametrize("n", [26, 28, 29, 30, 31])
 def test_dd_complete_and_certified(mt, n):
-    """p_26 (33.5M roots), p_28 (134M) and p_29 (268M): binary64 cannot
-    separate the tip cluster (at p_29 its two left-most roots are 4.1e-16
-    apart, under one ulp of 2); MT_DD returns every root, each one
-    certified, with the exact Moebius histogram and Vieta's first sum."""
+    """p_26 (33.5M roots) up to p_31 (1.07G): binary64 cannot separate the
+    tip cluster (from p_29 on its two left-most roots lie under one ulp of 2
+    apart); MT_DD returns every root, each one certified, with the exact
+    Moebius histogram and Vieta's first sum.  The first attempt (binary32
+    descents with their binary64 finish, binary64 redo of the descents that
+    end at the left tip, dd zones) is complete: no retry ran (max_retries=0
+    would report MT_EINCOMPLETE otherwise)."""
     import torch
     res = _split(mt, "hyp", n, max_retries=0)
     st = res.stats
@@ -148,8 +151,10 @@ def test_dd_complete_and_certified(mt, n):
     assert st["n_roots"] == d and res.roots.shape[0] == d
     assert st["n_cert_pass"] == d
     assert st["prec_used"] == 2 and st["n_zones"] > 0 and st["n_zone_roots"] > 0
-    if n <= 28:  # the mixed pass and its zones complete the split: no binary64 repeat
-        assert st["retries"] == 0 and st["desc_fp32"] > 0, (st["retries"], st["desc_fp32"])
+    assert st["retries"] == 0 and st["desc_fp32"] > 0, (st["retries"], st["desc_fp32"])
+    assert st["first_n_roots"] == d
+    if n >= 29:  # the tip redo ran (about 0.8 % of the descents at p_30)
+        assert 0 < st["n_tip64"] < st["n_starts"] // 50, st["n_tip64"]
     assert _hist(st) == counts.period_histogram(n)
     r = torch.view_as_real(res.roots)
     assert bool(torch.all(r[1:, 0] >= r[:-1, 0]))  # sorted by Re (hi parts)
