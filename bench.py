@@ -132,7 +132,9 @@ def kernel_rooflines(kind: str, l: int, n: int, stats: list, pk: dict, sm_mhz: f
                            "binary64 Newton steps %d: 13 flops x %d orbit steps + 24 x steps" % (steps, orb)))
     elif s0.get("ms_k_desc64", 0) > 0:
         per = 13 * n + 50 * l + 24 if kind == "q" else newton_flops(m)
-        steps = s0["desc_newton"]
+        # in the mixed tier desc_newton also counts the binary32 steps and the
+        # binary64 finish; the binary64 descent kernel ran the tip redo only
+        steps = s0["desc_newton"] - s0.get("desc_fp32", 0) - s0.get("finish_newton", 0)
         out.append(_kernel("k_descend_q" if kind == "q" else "k_descend", "fp64", steps * per, mean("ms_k_desc64"),
                            1, p64, n64, "binary64 Newton steps %d x %d flops" % (steps, per)))
     if s0.get("ms_k_desc32", 0) > 0:

@@ -25,7 +25,9 @@
  *    = Im.  A split returns ALL roots of P (conjugates included, divisor
  *    periods included), sorted by (Re, Im) (eq. defLexi); real roots have
  *    Im = +0.0.  d_roots_lo (optional, same layout) receives the low parts
- *    of double-double roots (zeros in plain FP64 mode).
+ *    of double-double roots (zeros in plain FP64 mode); the order is then
+ *    that of the double-double values (roots whose Re hi parts are equal
+ *    are ordered by their Re low parts first).
  *  - Workspace: d_work / work_bytes is caller-provided scratch of at least
  *    mt_workspace_bytes(...) bytes, 256-byte aligned.  Its contents are
  *    undefined on entry and on exit; calls sharing a workspace must be

@@ -12,6 +12,7 @@
 //   p'_{k+1} = 2 p_k p'_k + 1                    (eq. DerParamDyna, parameter form)
 // so one evaluation costs O(m) = O(log d) (Sec. 3, "V_d = O(log_2 d)").
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 

@@ -73,10 +73,10 @@ __global__ void k_fold_keys_list(const uint32_t* __restrict__ list, const unsign
                                  int64_t cap, const uint8_t* __restrict__ status, double2* __restrict__ cand,
                                  double eps, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                  unsigned long long* n_ok) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nl = (int64_t)*n_list < cap ? (int64_t)*n_list : cap;
   unsigned long long ok = 0;
-  if (t < nl) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl;
+       t += (int64_t)gridDim.x * blockDim.x) {  // grid-stride: few counter atomics
     const uint32_t i = list[t];
     uint64_t key = ~0ull;
     if (status[i] == 0) {
@@ -85,7 +85,7 @@ __global__ void k_fold_keys_list(const uint32_t* __restrict__ list, const unsign
       if (z.y < 0.5 * eps) z.y = 0.0;
       cand[i] = z;
       key = f64_key(z.x);
-      ok = 1;
+      ++ok;
     }
     keys[t] = key;
     vals[t] = i;
@@ -100,8 +100,8 @@ cudaError_t launch_fold_keys_list(const uint32_t* list, const unsigned long long
   cudaError_t e = cudaMemsetAsync(n_ok, 0, sizeof(*n_ok), s);
   if (e != cudaSuccess) return e;
   MT_COUNT_LAUNCH(1);
-  k_fold_keys_list<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(list, n_list, cap, status, cand, eps, keys, vals,
-                                                                  n_ok);
+  const int64_t nb = std::min<int64_t>((cap + 255) / 256, (int64_t)device_sm_count() * 8);
+  k_fold_keys_list<<<(unsigned)nb, 256, 0, s>>>(list, n_list, cap, status, cand, eps, keys, vals, n_ok);
   return cudaGetLastError();
 }
 
@@ -582,13 +582,22 @@ __global__ void k_fix_ties(double2* out, const unsigned long long* __restrict__ 
   if (!same(p + 1, p)) return;
   int64_t e = p + 1;
   while (e < n && same(e, p) && e - p < 4096) ++e;
-  // insertion sort of [p, e) by Im (runs are tiny)
+  // insertion sort of [p, e) (runs are tiny): by Im, or for double-double
+  // roots by the value itself (eq. defLexi): equal Re hi parts are ordered
+  // by Re lo, then by Im hi and Im lo (normalised pairs: a larger hi part
+  // never has a smaller value)
+  auto after = [&](const double2& a, const double2& al, const double2& b, const double2& bl) {
+    if (!out_lo) return a.y > b.y;
+    if (al.x != bl.x) return al.x > bl.x;
+    if (a.y != b.y) return a.y > b.y;
+    return al.y > bl.y;
+  };
   for (int64_t i = p + 1; i < e; ++i) {
     const double2 v = out[i];
     const double2 vl = out_lo ? out_lo[i] : make_double2(0.0, 0.0);
     const uint8_t m = is_mis ? is_mis[i] : 0;
     int64_t j = i - 1;
-    while (j >= p && out[j].y > v.y) {
+    while (j >= p && after(out[j], out_lo ? out_lo[j] : make_double2(0.0, 0.0), v, vl)) {
       out[j + 1] = out[j];
       if (out_lo) out_lo[j + 1] = out_lo[j];
       if (is_mis) is_mis[j + 1] = is_mis[j];

@@ -32,6 +32,38 @@ namespace mt {
 constexpr int MIX_MAXM = 41;
 constexpr int64_t MIX_BATCH = int64_t(1) << 23;  // starts per anchor batch
 
+// Float-float (binary32 pair) arithmetic from the published error-free
+// transforms: Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based TwoProd.
+// ~48-bit accurate; used where a binary64 result is not needed but binary32
+// is not enough (the descents' anchor orbits).
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff ff_from(double x) {
+  ff r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ ff ff_norm(float s, float e) {  // FastTwoSum, |s| >= |e|
+  ff r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.hi + b.hi;  // TwoSum
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+  return ff_norm(s, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;  // TwoProd
+  const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_twice(ff a) { return ff{a.hi + a.hi, a.lo + a.lo}; }
+
 // binary64 reference orbit at c0: zs[k * stride] = Z_k in binary32 for
 // k = 0 .. m-1 (truncated on the integer pipe: the binary64 pipe keeps the
 // orbit itself), and v = P(c0) = Z_m (+ Z_lcap) as binary32 hi (x, y) + lo (z, w).
@@ -84,21 +116,20 @@ __device__ __forceinline__ void pert_eval(const PolyDev& P, const float2* zs, in
   Dy = fmaf(a, cg_y, g_y) * s;
 }
 
-// pert_eval for the descents: the capture of p_lcap compiled in only where
-// the polynomial has one (s_{l,n}); p_n runs the bare loop (no compare per
-// step), unrolled by four.
-template <bool CAP>
-__device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* zs, int stride, float dx,
-                                            float dy, float& ex, float& ey, float& Dx, float& Dy) {
+// pert_eval for the descents.  STRIDE: the shared-memory row stride (a
+// compile-time constant, so each row's load takes an immediate offset).  MC:
+// the orbit length when known at compile time (p_n, m = n: the loop is fully
+// unrolled and 2^-(k+1) is an immediate), else 0 (P.m, unrolled by four).
+// The capture of p_lcap is compiled in only where the polynomial has one
+// (s_{l,n}).
+template <bool CAP, int MC, int STRIDE>
+__device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* zs, float dx, float dy, float& ex,
+                                            float& ey, float& Dx, float& Dy) {
   float e_x = 0.f, e_y = 0.f, g_x = 0.f, g_y = 0.f;
   float ce_x = 0.f, ce_y = 0.f, cg_x = 0.f, cg_y = 0.f;
-  int hexp = (127 - 1) << 23;  // exponent field of 2^-(k+1), k = 0
-#pragma unroll 4
-  for (int k = 0; k < P.m; ++k) {
-    const float2 Z = zs[k * stride];
+  auto step = [&](int k, float h) {
+    const float2 Z = zs[k * STRIDE];
     const float zx = Z.x + e_x, zy = Z.y + e_y;  // p_k(c)
-    const float h = __int_as_float(hexp);
-    hexp -= 1 << 23;
     const float ng_x = fmaf(zx, g_x, fmaf(-zy, g_y, h));
     const float ng_y = fmaf(zx, g_y, zy * g_x);
     const float sx = Z.x + zx, sy = Z.y + zy;  // 2 Z_k + e_k
@@ -106,20 +137,31 @@ __device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* zs, 
     const float ne_y = fmaf(sx, e_y, fmaf(sy, e_x, dy));
     e_x = ne_x; e_y = ne_y; g_x = ng_x; g_y = ng_y;
     if (CAP && k + 1 == P.lcap) { ce_x = e_x; ce_y = e_y; cg_x = g_x; cg_y = g_y; }
+  };
+  if constexpr (MC > 0) {
+#pragma unroll
+    for (int k = 0; k < MC; ++k) step(k, __int_as_float((126 - k) << 23));  // 2^-(k+1)
+  } else {
+    int hexp = (127 - 1) << 23;  // exponent field of 2^-(k+1), k = 0
+#pragma unroll 4
+    for (int k = 0; k < P.m; ++k) {
+      step(k, __int_as_float(hexp));
+      hexp -= 1 << 23;
+    }
   }
+  const int m = MC > 0 ? MC : P.m;
+  const float sc = __int_as_float((127 + m) << 23);
   if (CAP) {
     ex = e_x + ce_x;
     ey = e_y + ce_y;
-    const float a = P.lcap > 0 ? __int_as_float((127 + P.lcap - P.m) << 23) : 0.f;
-    const float s = __int_as_float((127 + P.m) << 23);
-    Dx = fmaf(a, cg_x, g_x) * s;
-    Dy = fmaf(a, cg_y, g_y) * s;
+    const float a = P.lcap > 0 ? __int_as_float((127 + P.lcap - m) << 23) : 0.f;
+    Dx = fmaf(a, cg_x, g_x) * sc;
+    Dy = fmaf(a, cg_y, g_y) * sc;
   } else {
-    const float s = __int_as_float((127 + P.m) << 23);
     ex = e_x;
     ey = e_y;
-    Dx = g_x * s;
-    Dy = g_y * s;
+    Dx = g_x * sc;
+    Dy = g_y * sc;
   }
 }
 
@@ -246,9 +288,80 @@ __global__ void k_seed_lift_mixed(PolyDev P, double lambda0, int64_t N0, int log
   warp_add_u64(&ctr->walk_fail, fails);
 }
 
-// a3 in the mixed tier.  Shared memory: m x blockDim binary32 pairs.
-// j0 / nch / sbase: chunks [j0, j0 + nch) only, start g / every written at
-// g / every - sbase (a streamed split's piece; 0 / nchunks / 0 for the whole line)
+// Float-float reference orbit of the walk, anchored at c0' = the float-float
+// value of c0 (hi + lo, exactly a binary64), so that no bit of the anchor is
+// lost: the caller carries c0 - c0' (below 2^-47 |c0|) in delta.  Z_k
+// (k < m) to shared memory in binary32, P(c0') as binary32 hi + lo.  Its
+// ~1e-14 relative accuracy moves P by far less than the walk's tolerance
+// (1e-2 of a sub-step) and keeps the walk off the binary64 pipe, where one
+// binary64 anchor cost as much as the binary32 sub-steps it served.
+template <bool CAP, int MC, int STRIDE>
+__device__ __forceinline__ void ref_orbit_ff(const PolyDev& P, double c0x, double c0y, float2* zs, float4& v,
+                                             double& ax, double& ay) {
+  const ff cx = ff_from(c0x), cy = ff_from(c0y);
+  ax = (double)cx.hi + (double)cx.lo;
+  ay = (double)cy.hi + (double)cy.lo;
+  ff zx{0.f, 0.f}, zy{0.f, 0.f}, capx{0.f, 0.f}, capy{0.f, 0.f};
+  zs[0] = make_float2(0.f, 0.f);
+  const int m = MC > 0 ? MC : P.m;
+#pragma unroll 2
+  for (int k = 1; k <= m; ++k) {
+    const ff nx = ff_add(ff_add(ff_mul(zx, zx), ff_neg(ff_mul(zy, zy))), cx);
+    const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
+    zx = nx;
+    zy = ny;
+    if (k < m) zs[k * STRIDE] = make_float2(zx.hi, zy.hi);
+    if (CAP && k == P.lcap) { capx = zx; capy = zy; }
+  }
+  const ff vx = CAP ? ff_add(zx, capx) : zx, vy = CAP ? ff_add(zy, capy) : zy;
+  v = make_float4(vx.hi, vy.hi, vx.lo, vy.lo);
+}
+
+// newton_target_pert on the descents' orbit loop (compile-time stride and,
+// for p_n, orbit length).
+template <bool CAP, int MC, int STRIDE>
+__device__ __forceinline__ int newton_target_walk(const PolyDev& P, const float2* zs, const float4& v, float& dx,
+                                                  float& dy, float tx, float ty, float rel, int cap, float* first,
+                                                  float tpx, float tpy, float Li, bool* bad) {
+  float thr2 = 0.f, prev2 = 0.f, h2 = 0.f;
+  int it = 0;
+  while (it < cap) {
+    float ex, ey, Dx, Dy;
+    pert_eval_t<CAP, MC, STRIDE>(P, zs, dx, dy, ex, ey, Dx, Dy);
+    float nr, ni;
+    if (it == 0) {  // predictor: P - Tp - L P, L = i Li
+      const float Pr = v.x + (v.z + ex), Pi = v.y + (v.w + ey);
+      nr = (Pr - tpx) + Li * Pi;
+      ni = (Pi - tpy) - Li * Pr;
+    } else {
+      nr = ((v.x - tx) + v.z) + ex;
+      ni = ((v.y - ty) + v.w) + ey;
+    }
+    float qr, qi;
+    if (!cdiv_f32(nr, ni, Dx, Dy, qr, qi)) { *bad = true; break; }
+    dx -= qr;
+    dy -= qi;
+    ++it;
+    const float s2 = fmaf(qr, qr, qi * qi);
+    if (it == 1) {
+      h2 = s2;
+      thr2 = rel * rel * s2;
+    } else if (s2 <= thr2 || (it >= 3 && s2 > 0.25f * prev2)) {
+      break;
+    }
+    prev2 = s2;
+  }
+  if (first) *first = sqrtf(h2);
+  return it;
+}
+
+// a3 in the mixed tier: one lane per chunk of L sub-steps, binary32
+// perturbation around a float-float anchor re-taken every K sub-steps.
+// Shared memory: each warp owns m rows of 32 binary32 pairs (row stride 32,
+// a compile-time constant).  j0 / nch / sbase: chunks [j0, j0 + nch) only,
+// start g / every written at g / every - sbase (a streamed split's piece;
+// 0 / nchunks / 0 for the whole line).  MC as in k_descend_mixed.
+template <bool CAP, int MC>
 __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_t L, int64_t nchunks,
                              int K, const double2* __restrict__ seeds, double2* __restrict__ starts,
                              uint8_t* __restrict__ chunk_fail, DevCounters* ctr, int64_t j0, int64_t nch,
@@ -261,40 +374,40 @@ __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_
     ph[q] = make_float2((float)(lambda0 * c), (float)(lambda0 * s));
   }
   __syncthreads();
-  float2* zs = zsh + threadIdx.x;
-  const int stride = blockDim.x;
+  const int m = MC > 0 ? MC : P.m;
+  float2* zs = zsh + (threadIdx.x >> 5) * 32 * m + (threadIdx.x & 31);
   const int64_t jl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t j = j0 + jl;
-  unsigned long long steps = 0, anchors = 0, fails = 0;
+  unsigned long long steps = 0, fails = 0;
   if (jl < nch && j < nchunks) {
     const double2 s0 = seeds[j];
-    double c0x = s0.x, c0y = s0.y;
+    double c0x, c0y;
     float4 v;
-    ref_orbit(P, c0x, c0y, zs, stride, v);
-    ++anchors;
-    float dx = 0.f, dy = 0.f, h = 0.f;
+    ref_orbit_ff<CAP, MC, 32>(P, s0.x, s0.y, zs, v, c0x, c0y);
+    float dx = (float)(s0.x - c0x), dy = (float)(s0.y - c0y), h = 0.f;
     bool bad = false;
     const float Li = 6.2831853f / M;
+    const int esh = __ffs(every) - 1;  // every is a power of two
     uint64_t g = (uint64_t)j * (uint64_t)L;
+    int kc = K;  // sub-steps to the next anchor
     for (int64_t i = 0; i < L; ++i, ++g) {
       if ((g & (uint64_t)(every - 1)) == 0)
-        starts[(int64_t)(g / every) - sbase] = make_double2(c0x + (double)dx, c0y + (double)dy);
+        starts[(int64_t)(g >> esh) - sbase] = make_double2(c0x + (double)dx, c0y + (double)dy);
       const float2 Tp = ph[g & (uint64_t)(M - 1)];
       const float2 T = ph[(g + 1) & (uint64_t)(M - 1)];
       // tight (1e-2) only on the sub-steps that end on a start, as in walk_chunk
       const float rel = (((g + 1) & (uint64_t)(every - 1)) == 0) ? 1e-2f : 1e-1f;
-      steps += newton_target_pert(P, zs, stride, v, dx, dy, T.x, T.y, rel, 16, &h, true, Tp.x, Tp.y, 0.f,
-                                  Li, &bad);
-      if (((i + 1) % K) == 0 && i + 1 < L) {  // re-anchor at the current point
-        c0x += (double)dx;
-        c0y += (double)dy;
-        dx = dy = 0.f;
-        ref_orbit(P, c0x, c0y, zs, stride, v);
-        ++anchors;
+      steps += newton_target_walk<CAP, MC, 32>(P, zs, v, dx, dy, T.x, T.y, rel, 16, &h, Tp.x, Tp.y, Li, &bad);
+      if (--kc == 0 && i + 1 < L) {  // re-anchor at the current point
+        kc = K;
+        const double px = c0x + (double)dx, py = c0y + (double)dy;
+        ref_orbit_ff<CAP, MC, 32>(P, px, py, zs, v, c0x, c0y);
+        dx = (float)(px - c0x);
+        dy = (float)(py - c0y);
       }
     }
     const double cx = c0x + (double)dx, cy = c0y + (double)dy;
-    if (j == nchunks - 1) starts[(int64_t)(g / every) - sbase] = make_double2(cx, 0.0);
+    if (j == nchunks - 1) starts[(int64_t)(g >> esh) - sbase] = make_double2(cx, 0.0);
     const double2 zn = seeds[j + 1];
     const double er = cx - zn.x, ei = cy - zn.y;
     const double hh = (double)h;
@@ -304,106 +417,101 @@ __global__ void k_walk_mixed(PolyDev P, double lambda0, int M, int every, int64_
   warp_add_u64(&ctr->walk_newton, steps);
   warp_add_u64(&ctr->steps_fp32, steps);
   warp_add_u64(&ctr->walk_fail, fails);
-  (void)anchors;
 }
 
-// Float-float (binary32 pair) arithmetic from the published error-free
-// transforms: Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based TwoProd.
-// ~48-bit accurate; used where a binary64 result is not needed but binary32
-// is not enough (the descents' anchor orbits).
-struct ff { float hi, lo; };
-
-__device__ __forceinline__ ff ff_from(double x) {
-  ff r;
-  r.hi = (float)x;
-  r.lo = (float)(x - (double)r.hi);
-  return r;
+using WalkMixedFn = void (*)(PolyDev, double, int, int, int64_t, int64_t, int, const double2*, double2*, uint8_t*,
+                             DevCounters*, int64_t, int64_t, int64_t);
+template <int MC>
+WalkMixedFn walk_mixed_fixed(int m) {
+  if constexpr (MC < 16) {
+    (void)m;
+    return nullptr;
+  } else {
+    return m == MC ? &k_walk_mixed<false, MC> : walk_mixed_fixed<MC - 1>(m);
+  }
 }
-__device__ __forceinline__ ff ff_norm(float s, float e) {  // FastTwoSum, |s| >= |e|
-  ff r;
-  r.hi = s + e;
-  r.lo = e - (r.hi - s);
-  return r;
+WalkMixedFn walk_mixed_kernel(const PolyDev& P) {
+  if (P.lcap >= 0) return &k_walk_mixed<true, 0>;
+  WalkMixedFn f = walk_mixed_fixed<33>(P.m);
+  return f ? f : &k_walk_mixed<false, 0>;
 }
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const float s = a.hi + b.hi;  // TwoSum
-  const float bb = s - a.hi;
-  const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
-  return ff_norm(s, e);
-}
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = a.hi * b.hi;  // TwoProd
-  const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
-  return ff_norm(p, e);
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
-__device__ __forceinline__ ff ff_twice(ff a) { return ff{a.hi + a.hi, a.lo + a.lo}; }
 
 // a4 in the mixed tier, anchors: for starts [base, base + cnt), the
 // reference orbit of each start in float-float, rounded to binary32 and
-// stored k-major (anch[(k - 1) * cnt + i] = Z_k, k = 1 .. m-1) so this write
-// and the descent's reads are coalesced, plus P(start) as binary32 hi + lo
-// and the long-jump bound on |delta|.  The anchor only steers the binary32
-// descent into the basin of its root (the binary64 finish sets the digits),
-// so float-float's ~1e-14 suffices and keeps this off the binary64 pipe.  A
+// stored start-major (anch[i (m - 1) + k - 1] = Z_k, k = 1 .. m-1), plus
+// P(start) as binary32 hi + lo and the long-jump bound on |delta|.  The
+// block stages its orbits in shared memory and writes its contiguous run of
+// rows with consecutive threads (coalesced); the descent copies one orbit
+// with consecutive lanes.  The anchor only steers the binary32 descent into
+// the basin of its root (the binary64 finish sets the digits), so
+// float-float's ~1e-14 suffices and keeps this off the binary64 pipe.  A
 // uniform launch: computed inside the persistent descent, the orbit of one
 // refilling lane would be issued by its whole warp at nearly every step.
 __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, int64_t base,
                                 int64_t cnt, float2* __restrict__ anch, float4* __restrict__ vv,
                                 float* __restrict__ rdel) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cnt) return;
-  const double2 c0 = starts[base + i];
-  const ff cx = ff_from(c0.x), cy = ff_from(c0.y);
-  ff zx{0.f, 0.f}, zy{0.f, 0.f}, capx{0.f, 0.f}, capy{0.f, 0.f};
-  for (int k = 1; k <= P.m; ++k) {
-    const ff nx = ff_add(ff_add(ff_mul(zx, zx), ff_neg(ff_mul(zy, zy))), cx);
-    const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
-    zx = nx;
-    zy = ny;
-    if (k < P.m) anch[(int64_t)(k - 1) * cnt + i] = make_float2(zx.hi, zy.hi);
-    if (k == P.lcap) { capx = zx; capy = zy; }
+  extern __shared__ float2 stage[];  // [blockDim.x][m - 1]
+  const int m1 = P.m - 1;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t i = i0 + threadIdx.x;
+  if (i < cnt) {
+    const double2 c0 = starts[base + i];
+    const ff cx = ff_from(c0.x), cy = ff_from(c0.y);
+    ff zx{0.f, 0.f}, zy{0.f, 0.f}, capx{0.f, 0.f}, capy{0.f, 0.f};
+    float2* row = stage + threadIdx.x * m1;
+    for (int k = 1; k <= P.m; ++k) {
+      const ff nx = ff_add(ff_add(ff_mul(zx, zx), ff_neg(ff_mul(zy, zy))), cx);
+      const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
+      zx = nx;
+      zy = ny;
+      if (k < P.m) row[k - 1] = make_float2(zx.hi, zy.hi);
+      if (k == P.lcap) { capx = zx; capy = zy; }
+    }
+    const ff vx = ff_add(zx, capx), vy = ff_add(zy, capy);
+    vv[i] = make_float4(vx.hi, vy.hi, vx.lo, vy.lo);
+    // long jump (as in k_descend: |c| > max(4, 2|c0|)); |delta| beyond rdel implies it
+    const float r0 = sqrtf(fmaf(cx.hi, cx.hi, cy.hi * cy.hi)) * 1.0001f;
+    rdel[i] = fmaxf(4.f, 2.f * r0) + r0;
   }
-  const ff vx = ff_add(zx, capx), vy = ff_add(zy, capy);
-  vv[i] = make_float4(vx.hi, vy.hi, vx.lo, vy.lo);
-  // long jump (as in k_descend: |c| > max(4, 2|c0|)); |delta| beyond rdel implies it
-  const float r0 = sqrtf(fmaf(cx.hi, cx.hi, cy.hi * cy.hi)) * 1.0001f;
-  rdel[i] = fmaxf(4.f, 2.f * r0) + r0;
+  __syncthreads();
+  const int64_t nv = (cnt - i0 < (int64_t)blockDim.x ? cnt - i0 : (int64_t)blockDim.x) * m1;
+  float2* dst = anch + i0 * m1;
+  for (int64_t t = threadIdx.x; t < nv; t += blockDim.x) dst[t] = stage[t];
 }
 
 // a4 in the mixed tier, binary32 phase (persistent, per-lane refill as in
 // k_descend) over starts [base, base + cnt).  Each lane keeps the anchor
 // orbit of its descent in its own column of shared memory (row k holds
-// Z_k of every lane; the row stride is odd, so the rows of one column fall
-// in different banks).  Lanes that finished are refilled together: the
-// warp takes their start indices from a warp-private range of the work
-// queue (one atomic per 32 starts), then copy the new orbits with all 32
-// lanes: the refilled lanes' starts are consecutive queue indices, so the
-// lanes reading row k of the k-major anchors for them read consecutive
-// addresses, and no refill runs a loop of loads on one or two lanes while
-// the others wait.  The Newton loop is
-// binary32 only.  Each descent runs binary32 Newton steps to the binary32
-// floor and leaves (delta, its largest squared step) in pack[] with status
-// 3 ("finish in binary64"), or stops as divergent (1) / timed out (2).  The
-// binary64 finish runs in k_finish_f64, a separate uniform launch, once per
-// root.
+// Z_k of every lane; the row stride DM_BS + 1 is odd, so the rows of one
+// column fall in different banks).  Lanes that finished are refilled
+// together: the warp takes their start indices from a warp-private range of
+// the work queue (one atomic per 32 starts), then copies each new orbit
+// (m - 1 consecutive anchors) with consecutive lanes, one refilled lane
+// after the other, so no refill runs a loop of loads on one or two lanes
+// while the others wait.  The Newton loop is binary32 only.  Each descent
+// runs binary32 Newton steps to the binary32 floor and leaves (delta, its
+// largest squared step) in pack[] with status 3 ("finish in binary64"), or
+// stops as divergent (1) / timed out (2).  The binary64 finish runs in
+// k_finish_f64, a separate uniform launch, once per root.  MC: the orbit
+// length when fixed at compile time (p_n), else 0.
 constexpr int DESC_POOL = 32;  // work indices taken per queue atomic
+constexpr int DM_BS = 128;     // threads per block of the binary32 descent
 
-template <bool CAP>
-__global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, int64_t cnt,
-                                                       const float2* __restrict__ anch,
-                                                       const float4* __restrict__ vv,
-                                                       const float* __restrict__ rdel, int cap,
-                                                       float4* __restrict__ pack,
-                                                       uint8_t* __restrict__ status,
-                                                       unsigned long long* queue,
-                                                       DevCounters* ctr) {
+template <bool CAP, int MC>
+__global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base, int64_t cnt,
+                                                         const float2* __restrict__ anch,
+                                                         const float4* __restrict__ vv,
+                                                         const float* __restrict__ rdel, int cap,
+                                                         float4* __restrict__ pack,
+                                                         uint8_t* __restrict__ status,
+                                                         unsigned long long* queue,
+                                                         DevCounters* ctr) {
   extern __shared__ float2 zsh[];
-  const int stride = blockDim.x + 1;
+  constexpr int stride = DM_BS + 1;
   float2* zs = zsh + threadIdx.x;
   const unsigned lane = threadIdx.x & 31;
   const int wbase = threadIdx.x & ~31;
-  const int m1 = P.m - 1;
+  const int m1 = (MC > 0 ? MC : P.m) - 1;
   zs[0] = make_float2(0.f, 0.f);  // Z_0 = 0 for every descent
   int64_t idx = -1;
   float dx = 0.f, dy = 0.f, h1 = 0.f, prev2 = 0.f, rdelta = 0.f;
@@ -431,21 +539,21 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
       } else {
         pool_next += R;
       }
-      // the new orbits with the whole warp: lane t copies rows kk, kk + rows,
-      // ... of the orbit of the (t mod R)-th refilled lane, kk = t / R
-      {
-        const unsigned rows = 32u / R;  // rows copied per round
-        const unsigned r_t = lane % R, kk = lane / R;
-        const int tl = __fns(need, 0, (int)r_t + 1);
-        const int64_t ir = __shfl_sync(0xffffffffu, idx, tl);
-        if (__any_sync(0xffffffffu, ir >= cnt)) drained = true;
-        if (kk < rows && ir < cnt) {
-          float2* dst = zsh + wbase + tl;
-          for (int k = (int)kk; k < m1; k += (int)rows) dst[(k + 1) * stride] = anch[(int64_t)k * cnt + ir];
+      // the new orbits, one refilled lane after the other, each copied by
+      // consecutive lanes from its m - 1 consecutive anchors
+      for (unsigned todo = need; todo; todo &= todo - 1) {
+        const int tl = __ffs(todo) - 1;
+        const int64_t ir = __shfl_sync(0xffffffffu, idx, tl);  // warp-uniform
+        if (ir >= cnt) {
+          drained = true;
+          continue;
         }
+        const float2* src = anch + ir * m1;
+        float2* dst = zsh + wbase + tl + stride;
+        for (int k = (int)lane; k < m1; k += 32) dst[k * stride] = src[k];
       }
       __syncwarp();
-      if ((unsigned)lane < 32 && ((need >> lane) & 1u) && idx < cnt) {
+      if (((need >> lane) & 1u) && idx < cnt) {
         v = vv[idx];
         rdelta = rdel[idx];
         dx = dy = 0.f;
@@ -459,7 +567,7 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
     if (active) {
       int outcome = -1;
       float ex, ey, Dx, Dy, qr, qi;
-      pert_eval_t<CAP>(P, zs, stride, dx, dy, ex, ey, Dx, Dy);
+      pert_eval_t<CAP, MC, stride>(P, zs, dx, dy, ex, ey, Dx, Dy);
       const float nr = (v.x + v.z) + ex, ni = (v.y + v.w) + ey;
       if (!cdiv_f32(nr, ni, Dx, Dy, qr, qi)) {
         outcome = 3;  // out of binary32 range: binary64 decides
@@ -491,6 +599,26 @@ __global__ void __launch_bounds__(128) k_descend_mixed(PolyDev P, int64_t base, 
   warp_add_u64(&ctr->steps_fp32, s32);
   warp_add_u64(&ctr->n_diverge, ndiv);
   warp_add_u64(&ctr->n_timeout, nto);
+}
+
+using DescMixedFn = void (*)(PolyDev, int64_t, int64_t, const float2*, const float4*, const float*, int, float4*,
+                             uint8_t*, unsigned long long*, DevCounters*);
+
+// The instantiation for a polynomial: p_n with 16 <= n <= 33 has its orbit
+// length fixed at compile time; everything else runs the general loop.
+template <int MC>
+DescMixedFn desc_mixed_fixed(int m) {
+  if constexpr (MC < 16) {
+    (void)m;
+    return nullptr;
+  } else {
+    return m == MC ? &k_descend_mixed<false, MC> : desc_mixed_fixed<MC - 1>(m);
+  }
+}
+DescMixedFn desc_mixed_kernel(const PolyDev& P) {
+  if (P.lcap >= 0) return &k_descend_mixed<true, 0>;
+  DescMixedFn f = desc_mixed_fixed<33>(P.m);
+  return f ? f : &k_descend_mixed<false, 0>;
 }
 
 // a4 in the mixed tier, binary64 finish, once per root.
@@ -532,9 +660,11 @@ constexpr uint64_t TIP_KEY = ~0ull - 1;  // above every finite f64_key, below ~0
 __global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ starts, const float4* __restrict__ pack,
                            uint8_t* __restrict__ status, uint64_t* __restrict__ keys,
                            uint32_t* __restrict__ vals, DevCounters* ctr) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // grid-stride over a bounded grid: the counts reach the two counters in a
+  // few thousand atomics, not one per warp of the 2^28 descents
   unsigned long long n3 = 0, n4 = 0;
-  if (i < count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const float4 q = pack[i];
     const double2 c0 = starts[i];
     double2 c = make_double2(c0.x + (double)q.x, c0.y + (double)q.y);
@@ -544,12 +674,12 @@ __global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ star
     if (fin && c.x < -2.0 + box && c.y < box) {
       status[i] = 4;  // redone in binary64 from c0
       key = TIP_KEY;
-      n4 = 1;
+      ++n4;
     } else {
       starts[i] = c;
       if (fin) {
         key = f64_key(c.x);
-        n3 = 1;
+        ++n3;
       }
     }
     keys[i] = key;
@@ -711,9 +841,9 @@ __global__ void k_finish_followers(int64_t count, const uint32_t* __restrict__ v
                                    const uint32_t* __restrict__ head, const uint8_t* __restrict__ link,
                                    const double2* __restrict__ c32, double2* __restrict__ cand,
                                    uint8_t* __restrict__ status, DevCounters* ctr) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long nconv = 0, ndiv = 0, nto = 0;
-  if (p < count) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count;
+       p += (int64_t)gridDim.x * blockDim.x) {  // grid-stride: few counter atomics
     const uint32_t i = vals[p];
     uint8_t st = status[i];
     bool finished = head[p] != 0;
@@ -734,9 +864,9 @@ __global__ void k_finish_followers(int64_t count, const uint32_t* __restrict__ v
       cand[i] = c32[i];
     }
     if (finished) {
-      nconv = st == 0;
-      ndiv = st == 1;
-      nto = st == 2;
+      nconv += st == 0;
+      ndiv += st == 1;
+      nto += st == 2;
     }
   }
   warp_add_u64(&ctr->n_conv, nconv);
@@ -768,11 +898,12 @@ cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every
   const int bs = (block >= 32 && block <= 256 && block % 32 == 0) ? block : 64;
   const size_t smem = (size_t)P.m * bs * sizeof(float2);
   const int64_t grid = (nch + bs - 1) / bs;
+  const WalkMixedFn kwalk = walk_mixed_kernel(P);
   MT_COUNT_LAUNCH(1);
   cudaError_t e = ktimer_begin(KS_WALK, s);
   if (e != cudaSuccess) return e;
-  k_walk_mixed<<<(unsigned)grid, bs, smem, s>>>(P, lambda0, M, every, L, nchunks, K, seeds, starts,
-                                                chunk_fail, ctr, j0, nch, j0 * L / every);
+  kwalk<<<(unsigned)grid, bs, smem, s>>>(P, lambda0, M, every, L, nchunks, K, seeds, starts, chunk_fail, ctr, j0,
+                                         nch, j0 * L / every);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return ktimer_end(s);
 }
@@ -792,12 +923,12 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
                                  DevCounters* ctr, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
-  const int bs = 128;
+  const int bs = DM_BS;
   const size_t smem = (size_t)P.m * (bs + 1) * sizeof(float2);
-  const bool capture = P.lcap >= 0;
+  const size_t asmem = (size_t)bs * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2);  // anchor staging
+  const DescMixedFn kdesc = desc_mixed_kernel(P);
   int per_sm = 0;
-  cudaError_t e = capture ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_mixed<true>, bs, smem)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_mixed<false>, bs, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kdesc, bs, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t B = count < MIX_BATCH ? count : MIX_BATCH;
@@ -810,7 +941,7 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   for (int64_t base = 0; base < count; base += B) {
     const int64_t cnt = (count - base < B) ? count - base : B;
     MT_COUNT_LAUNCH(1);
-    k_anchor_orbits<<<(unsigned)((cnt + bs - 1) / bs), bs, 0, s>>>(P, starts, base, cnt, anch, vv, rdel);
+    k_anchor_orbits<<<(unsigned)((cnt + bs - 1) / bs), bs, asmem, s>>>(P, starts, base, cnt, anch, vv, rdel);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int64_t grid = (int64_t)device_sm_count() * per_sm;
     const int64_t need = (cnt + bs - 1) / bs;
@@ -820,10 +951,7 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
     if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
     if ((e = ktimer_begin(KS_DESC32, s)) != cudaSuccess) return e;
-    if (capture)
-      k_descend_mixed<true><<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, pack, status, q, ctr);
-    else
-      k_descend_mixed<false><<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, pack, status, q, ctr);
+    kdesc<<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, pack, status, q, ctr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = ktimer_end(s)) != cudaSuccess) return e;
   }
@@ -833,7 +961,8 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   if ((e = cudaMemsetAsync(n2, 0, sizeof(*n2), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(&ctr->n_c32_fin, 0, sizeof(*n2), s)) != cudaSuccess) return e;
   MT_COUNT_LAUNCH(1);
-  k_c32_keys<<<nb, bs, 0, s>>>(count, tip_box(P), starts, pack, status, fin.keys, fin.vals, ctr);
+  const unsigned egrid = std::min<unsigned>(nb, (unsigned)device_sm_count() * 16);  // grid-stride kernels
+  k_c32_keys<<<egrid, bs, 0, s>>>(count, tip_box(P), starts, pack, status, fin.keys, fin.vals, ctr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = radix_sort_pairs(fin.keys, fin.vals, fin.keys_alt, fin.vals_alt, count, fin.radix_tmp, s)) != cudaSuccess)
     return e;
@@ -862,7 +991,7 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
     if ((e = ktimer_end(s)) != cudaSuccess) return e;
   }
   MT_COUNT_LAUNCH(1);
-  k_finish_followers<<<nb, bs, 0, s>>>(count, fin.vals, fin.head, fin.link, starts, cand, status, ctr);
+  k_finish_followers<<<egrid, bs, 0, s>>>(count, fin.vals, fin.head, fin.link, starts, cand, status, ctr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the tip box: binary64 descents from the starts (list in fin.pos, free
   // once the heads are listed), then counted with the heads

@@ -64,14 +64,24 @@ def match_sorted(a: np.ndarray, b: np.ndarray, tol: float) -> tuple[float, int]:
     return max(float(d[~bad].max()) if (~bad).any() else 0.0, dm), int(bad.sum())
 
 
-def lexsorted(z: np.ndarray) -> bool:
-    """True if z is sorted by (Re, Im) (eq. defLexi)."""
+def lexsorted(z: np.ndarray, zl: np.ndarray | None = None) -> bool:
+    """True if z is sorted by (Re, Im) (eq. defLexi).  With low parts zl
+    (double-double values z + zl, normalised pairs) the order is that of the
+    values: equal hi parts are ordered by their low parts."""
     z = np.asarray(z)
     if z.size < 2:
         return True
     r0, r1 = z.real[:-1], z.real[1:]
     i0, i1 = z.imag[:-1], z.imag[1:]
-    return bool(np.all((r0 < r1) | ((r0 == r1) & (i0 <= i1))))
+    if zl is None:
+        return bool(np.all((r0 < r1) | ((r0 == r1) & (i0 <= i1))))
+    zl = np.asarray(zl)
+    rl0, rl1 = zl.real[:-1], zl.real[1:]
+    il0, il1 = zl.imag[:-1], zl.imag[1:]
+    re_lt = (r0 < r1) | ((r0 == r1) & (rl0 < rl1))
+    re_eq = (r0 == r1) & (rl0 == rl1)
+    im_le = (i0 < i1) | ((i0 == i1) & (il0 <= il1))
+    return bool(np.all(re_lt | (re_eq & im_le)))
 
 
 def min_separation(z: np.ndarray) -> float:

@@ -123,6 +123,12 @@ def test_kernel_rooflines_arithmetic():
     assert abs(by["k_descend_mixed"]["achieved"] - 1500 * (19 * 20 + 25) / 1e-3 / 1e12) < 1e-12
     assert abs(by["k_finish_f64"]["achieved"] - 500 * (7 * 20 + 24) / 2.5e-3 / 1e12) < 1e-12
     assert bench.roofline_of(list(by.values()), "x")["kernel"] == "k_finish_f64"
+    # the binary64 descents of the mixed tier (the tip redo): desc_newton less
+    # the binary32 steps and the finish steps
+    st = _stats(ms_k_desc64=0.5, desc_newton=2100, desc_fp32=1500, steps_fp32=1600, finish_newton=500,
+                ms_k_desc32=1.0, ms_k_finish=2.5)
+    by = {k["kernel"]: k for k in bench.kernel_rooflines("hyp", 0, 20, [st], pk)}
+    assert by["k_descend"]["flops_per_launch"] == 100 * (13 * 20 + 24)
     # the batched split: orbit lengths differ per polynomial, counted by the kernel
     st = _stats(desc_orbit_steps=30000)
     k = bench.kernel_rooflines("mis", 0, 15, [st], pk)[0]

@@ -69,7 +69,7 @@ def test_dd_all_matches_binary128_oracle(mt, kind, n, l):
     assert z.size == ref["n_roots"] == d
     assert st["prec_used"] == 2 and st["n_cert_pass"] == d
     assert st["n_zone_roots"] == int(np.sum(z.imag >= 0))  # every root (upper half) came from dd
-    assert lexsorted(z)
+    assert lexsorted(z, zl)
     perm, dmax_hi = match_sets(z, ref["roots"])
     assert dmax_hi < 1e-15
     err = _dd_dist(z, zl, ref["roots4"][perm])

@@ -162,7 +162,7 @@ def test_p28_dd_against_binary128(mt):
     assert {k: st["count_by_type"][k] for k in range(64) if st["count_by_type"][k]} == counts.period_histogram(n)
     z = res.roots.cpu().numpy()
     zl = res.roots_lo.cpu().numpy()
-    assert lexsorted(z)
+    assert lexsorted(z, zl)
     dd = np.nonzero(zl != 0)[0]
     assert dd.size > 0
     disp, last, pts = hostpool.polish_all("hyp", n, z[dd], zl=zl[dd])
