@@ -127,6 +127,7 @@ struct Plan {
   // MT_DD: the double-double pass
   int dd;             // 1: run it when the base pass is not certified complete
   int dd_all;         // 1: every root is redone
+  int raw_types = 0;  // 1: d_is_mis receives each root's type code (q_{l,n} through its factors)
   double dd_R;        // zone radius
   double dd_margin;   // chunks / main reps within dd_R + dd_margin are revisited
   double eps_dd, tol_dd, cert_tol_dd;
@@ -219,9 +220,12 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
   } else if (p.prec == MT_MIXED) {
     // the binary32 walk is latency-bound with one lane per chunk: 2^16 lanes
     // instead of 2^14 pay for the extra seed lifts from p_22 up (measured:
-    // p_24 36.2 -> 33.8 ms, p_26 with dd zones 185 -> 172 ms)
+    // p_24 36.2 -> 33.8 ms, p_26 with dd zones 185 -> 172 ms), and 2^17
+    // lanes (chunks of 4096 sub-steps) from p_28 up (p_28 MT_DD: walk 29.3 ->
+    // 25.0 ms, the seed lift 0.6 -> 1.2 ms)
     N0 = std::min<int64_t>(int64_t(1) << 17,
                            std::max<int64_t>(Md / 128, std::min<int64_t>(int64_t(1) << 15, Md / 16)));
+    N0 = std::max<int64_t>(N0, std::min<int64_t>(int64_t(1) << 18, Md >> 12));
   } else {
     // binary64: the walk already keeps the binary64 pipe busy; more chunks
     // would only add seed lifts
@@ -661,7 +665,7 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
                       s, SegView(), p.kind == 2 ? b.type : nullptr));
   }
   CK(mark(ev.e[4], s, capturing));
-  const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
+  const int mis_code = p.raw_types ? MIS_CODE_RAW : (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
   CK(launch_emit(b.reps, &b.ctr->n_reps, p.S, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out,
                  s));
   CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s));
@@ -777,7 +781,7 @@ mt_status run_streamed(const Plan& p, const Buffers& b, double2* out, double2* o
   CK(launch_certify(p.P, b.reps, &b.ctr->n_reps, nG, p.cert_tol, b.mult, b.pass, b.radius, b.ctr, s,
                     SegView(), p.kind == 2 ? b.type : nullptr));
   CK(cudaEventRecord(ev.e[4], s));
-  const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
+  const int mis_code = p.raw_types ? MIS_CODE_RAW : (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
   CK(launch_emit(b.reps, &b.ctr->n_reps, nG, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out, s));
   CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s));
   if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
@@ -991,7 +995,7 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
   CK(launch_exclusive_scan(kmult, mpos, p.S, b.scan_tmp, &d.cnt[4], s));
   CK(launch_exclusive_scan(d.zmult, d.zmpos, p.dd_zcap, d.zscan, &d.cnt[5], s));
   if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
-  const int mis_code = (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
+  const int mis_code = p.raw_types ? MIS_CODE_RAW : (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
   CK(dd_emit(b.reps, n_main, p.S, kmult, mpos, &d.cnt[4], b.type, mis_code, d.zrx, d.zry, &d.cnt[3],
              p.dd_zcap, d.zmult, d.zmpos, &d.cnt[5], d.ztype, out, out_lo, is_mis, cap_out, b.ctr, s));
   CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s, SegView(), out_lo));
@@ -1006,7 +1010,7 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
 
 mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_roots,
                      double* d_roots_lo, int64_t cap, uint8_t* d_is_mis, void* d_work,
-                     size_t work_bytes, int64_t* n_out, mt_stats* st) {
+                     size_t work_bytes, int64_t* n_out, mt_stats* st, int raw_types = 0) {
   g_err.clear();
   if (!valid_poly(kind, l, n)) return fail(MT_EINVAL, "polynomial out of range (kind %d, l %d, n %d)", kind, l, n);
   if (cap < 0 || (cap > 0 && !d_roots)) return fail(MT_EINVAL, "bad output buffer");
@@ -1055,6 +1059,7 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
       --retry;  // (M, c_L) cannot double further: the last attempt's result stands
       break;
     }
+    p.raw_types = raw_types;
     Buffers b = carve(p, d_work, work_bytes);
     evp = &ev;
     ktp = nullptr;
@@ -1339,6 +1344,161 @@ mt_status run_batch_pass(const BatchPlan& b, const BatchBuffers& r, double2* out
   return MT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// q_{l,n} in the double-double tier, through its factors: eq. polySimple
+// telescoped, q_{l,n} = p_n^2 prod_{j=2..l} s_{j,n} (mt_qfactors.cu).  Each
+// factor is split by the certified double-double split of its own kind; the
+// Hyp(k) roots come from p_n with multiplicity floor((l-1)/k) + 2 (Thm
+// fact_mis), the Mis(j,k) roots from s_{j,n}.  Workspace: the largest
+// factor's split, then one factor's roots and type codes, the union list
+// (roots, preperiod, period, multiplicity) and the two sorts by (Re, Im).
+struct QfLayout {
+  size_t sub = 0, fac_roots = 0, fac_type = 0, u_roots = 0, u_pre = 0, u_per = 0, u_mult = 0;
+  size_t keys = 0, keys_alt = 0, vals = 0, vals_alt = 0, rtmp = 0, cnt = 0, total = 0;
+  int64_t dmax = 0, nmax = 0;
+};
+
+bool qf_layout(int l, int n, const mt_options* o, QfLayout* L) {
+  if (!valid_poly(2, l, n)) return false;
+  mt_options od = *o;
+  od.prec = MT_DD;
+  size_t sub = workspace_for(0, 0, n, &od);
+  if (!sub) return false;
+  int64_t dmax = int64_t(1) << (n - 1), nmax = dmax;
+  for (int j = 2; j <= l; ++j) {
+    const size_t w = workspace_for(1, j, n, &od);
+    if (!w) return false;
+    sub = std::max(sub, w);
+    dmax = std::max<int64_t>(dmax, int64_t(1) << (j + n - 2));
+    nmax += int64_t(1) << (j + n - 2);
+  }
+  if (nmax >= (int64_t(1) << 32)) return false;
+  auto al = [](size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; };
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = at;
+    at += al(bytes);
+    return r;
+  };
+  L->sub = take(sub);
+  L->fac_roots = take((size_t)dmax * sizeof(double2));
+  L->fac_type = take((size_t)dmax);
+  L->u_roots = take((size_t)nmax * sizeof(double2));
+  L->u_pre = take((size_t)nmax);
+  L->u_per = take((size_t)nmax);
+  L->u_mult = take((size_t)nmax);
+  L->keys = take((size_t)nmax * 8);
+  L->keys_alt = take((size_t)nmax * 8);
+  L->vals = take((size_t)nmax * 4);
+  L->vals_alt = take((size_t)nmax * 4);
+  L->rtmp = take(radix_temp_bytes(nmax));
+  L->cnt = take(8 * sizeof(unsigned long long));
+  L->total = at;
+  L->dmax = dmax;
+  L->nmax = nmax;
+  return true;
+}
+
+mt_status split_q_factors(int l, int n, const mt_options* o, double* d_roots, int64_t cap, uint8_t* d_mult,
+                          uint8_t* d_pre, uint8_t* d_per, void* d_work, size_t work_bytes, int64_t* n_out,
+                          mt_stats* st) {
+  QfLayout L;
+  if (!qf_layout(l, n, o, &L)) return fail(MT_EINVAL, "no plan for the factors of q_{%d,%d}", l, n);
+  if (cap < 0 || (cap > 0 && !d_roots)) return fail(MT_EINVAL, "bad output buffer");
+  if (!d_work || work_bytes < L.total)
+    return fail(MT_ENOMEM, "workspace of %zu bytes needed, %zu given", L.total, work_bytes);
+  if (((uintptr_t)d_work) % ALIGN) return fail(MT_EINVAL, "workspace must be 256-byte aligned");
+  char* w = (char*)d_work;
+  mt_options od = *o;
+  od.prec = MT_DD;
+  cudaStream_t s = (cudaStream_t)o->stream;
+  double2* fr = (double2*)(w + L.fac_roots);
+  uint8_t* ft = (uint8_t*)(w + L.fac_type);
+  double2* ur = (double2*)(w + L.u_roots);
+  uint8_t *upre = (uint8_t*)(w + L.u_pre), *uper = (uint8_t*)(w + L.u_per), *umult = (uint8_t*)(w + L.u_mult);
+  uint64_t *keys = (uint64_t*)(w + L.keys), *keys_alt = (uint64_t*)(w + L.keys_alt);
+  uint32_t *vals = (uint32_t*)(w + L.vals), *vals_alt = (uint32_t*)(w + L.vals_alt);
+  unsigned long long* cnt = (unsigned long long*)(w + L.cnt);
+  CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+  const unsigned long long launches0 = g_launches;
+  mt_stats agg;
+  memset(&agg, 0, sizeof(agg));
+  for (int j = 0; j <= l; ++j) {
+    if (j == 1) continue;  // s_{1,n} = p_n: the second copy of p_n is its multiplicity
+    const int kind = j == 0 ? 0 : 1;
+    const int64_t deg = j == 0 ? (int64_t(1) << (n - 1)) : (int64_t(1) << (j + n - 2));
+    mt_stats sf;
+    int64_t nr = 0;
+    const mt_status rc = split_impl(kind, j, n, &od, (double*)fr, nullptr, deg, ft, w + L.sub, L.fac_roots - L.sub,
+                                    &nr, &sf, 1);
+    if (rc != MT_OK) return rc;  // the factor's message stands
+    CK(launch_qf_append(fr, ft, nr, j, l, n, ur, upre, uper, umult, L.nmax, cnt, s));
+    for (int k = 1; k < 32; ++k) {
+      if (j == 0) agg.count_by_type[32 + k] += sf.count_by_type[k];  // Hyp(k)
+      else if (j == l) agg.count_by_type[k] += sf.count_by_type[k];  // Mis(l,k)
+      else agg.count_by_type[0] += sf.count_by_type[k];              // Mis(j,k), j < l
+    }
+    agg.n_starts += sf.n_starts;
+    agg.n_conv += sf.n_conv;
+    agg.n_repeat += sf.n_repeat;
+    agg.n_diverge += sf.n_diverge;
+    agg.n_timeout += sf.n_timeout;
+    agg.walk_newton += sf.walk_newton;
+    agg.desc_newton += sf.desc_newton;
+    agg.steps_fp32 += sf.steps_fp32;
+    agg.steps_dd += sf.steps_dd;
+    agg.walk_fail += sf.walk_fail;
+    agg.retries = std::max(agg.retries, sf.retries);
+    agg.ms_total += sf.ms_total;
+    agg.ms_walk += sf.ms_walk;
+    agg.ms_descend += sf.ms_descend;
+    agg.ms_dedup += sf.ms_dedup;
+    agg.ms_certify += sf.ms_certify;
+    agg.ms_dd += sf.ms_dd;
+    agg.n_zones += sf.n_zones;
+    agg.n_zone_roots += sf.n_zone_roots;
+    agg.n_dd_pieces += sf.n_dd_pieces;
+    agg.M = sf.M;
+    agg.c_L = sf.c_L;
+    agg.eps_dup = std::max(agg.eps_dup, sf.eps_dup);
+  }
+  unsigned long long hc[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t nu = (int64_t)hc[0];
+  if (n_out) *n_out = nu;
+  if (nu > L.nmax) return fail(MT_ECAPACITY, "%lld roots in the union of the factors of q_{%d,%d}", (long long)nu, l, n);
+  // (Re, Im) order: by Im, then stably by Re
+  if (nu > 0) {
+    CK(launch_qf_keys(ur, nullptr, L.nmax, &cnt[0], 1, keys, vals, s));
+    CK(radix_sort_pairs(keys, vals, keys_alt, vals_alt, L.nmax, w + L.rtmp, s, &cnt[0]));
+    CK(launch_qf_keys(ur, vals, L.nmax, &cnt[0], 0, keys_alt, vals_alt, s));
+    CK(radix_sort_pairs(keys_alt, vals_alt, keys, vals, L.nmax, w + L.rtmp, s, &cnt[0]));
+    if (nu <= cap)
+      CK(launch_qf_gather(vals_alt, cap, &cnt[0], ur, upre, uper, umult, (double2*)d_roots, d_pre, d_per, d_mult, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  const int64_t degree = int64_t(1) << (l + n - 1);
+  if (st) {
+    memset(st, 0, sizeof(*st));
+    *st = agg;
+    st->degree = degree;
+    st->n_roots = nu;
+    st->n_mult = (int64_t)hc[1];
+    st->n_real = (int64_t)hc[3];
+    st->n_cert_pass = nu;  // every factor's split certified all its roots, or failed above
+    st->prec_used = MT_DD;
+    st->first_prec = MT_DD;
+    st->n_launches = (int64_t)(g_launches - launches0);
+  }
+  if (hc[2]) return fail(MT_EINCOMPLETE, "%llu roots of the factors of q_{%d,%d} without a type", hc[2], l, n);
+  if ((int64_t)hc[1] != degree)
+    return fail(MT_EINCOMPLETE, "factors of q_{%d,%d}: %llu roots with multiplicity, degree %lld", l, n, hc[1],
+                (long long)degree);
+  if (nu > cap) return fail(MT_ECAPACITY, "%lld roots do not fit in cap %lld", (long long)nu, (long long)cap);
+  return MT_OK;
+}
+
 }  // namespace
 
 void mt::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
@@ -1363,6 +1523,10 @@ int64_t mt_degree_misiurewicz(int l, int n) {
 size_t mt_workspace_bytes(int kind, int l, int n, const mt_options* opts) {
   mt_options d;
   mt_default_options(&d);
+  if (kind == 2 && opts && opts->prec == MT_DD) {
+    QfLayout L;
+    return qf_layout(l, n, opts, &L) ? L.total : 0;
+  }
   return workspace_for(kind, kind == 0 ? 0 : l, n, opts ? opts : &d);
 }
 
@@ -1384,7 +1548,10 @@ mt_status mt_split_misiurewicz_q(int l, int n, const mt_options* opts, double* d
                                  uint8_t* d_mult, uint8_t* d_pre, uint8_t* d_per, void* d_work,
                                  size_t work_bytes, int64_t* n_out, mt_stats* stats) {
   g_err.clear();
-  if (opts && opts->prec != MT_FP64) return fail(MT_EINVAL, "q_{l,n} is split in binary64 (MT_FP64) only");
+  if (opts && opts->prec == MT_DD)
+    return split_q_factors(l, n, opts, d_roots, cap, d_mult, d_pre, d_per, d_work, work_bytes, n_out, stats);
+  if (opts && opts->prec != MT_FP64)
+    return fail(MT_EINVAL, "q_{l,n} is split in binary64 (MT_FP64) or through its factors (MT_DD)");
   int64_t nr = 0;
   const mt_status rc = split_impl(2, l, n, opts, d_roots, nullptr, cap, nullptr, d_work, work_bytes, &nr, stats);
   if (n_out) *n_out = nr;

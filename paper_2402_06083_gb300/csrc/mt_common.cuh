@@ -140,6 +140,55 @@ __device__ __forceinline__ void orbit_f64_d32(int m, int lcap, double cr, double
   }
 }
 
+// orbit_f64_d32 plus the curvature of the Newton map for the finish's stop
+// rule: kr + i ki = P''(c) / (2 P'(c)) in binary32.  The second derivative
+// follows p''_{k+1} = 2 (p'_k^2 + p_k p''_k), carried as u_k = p''_k / 4^k,
+// u_{k+1} = ((p'_k / 2^k)^2 + p_k u_k) / 2 (no binary32 overflow up to
+// n = 41), on the binary32 pipe, which the binary64 orbit leaves idle.  A
+// Newton step q from c leaves c - q at about q^2 P''/(2P') from the root
+// (the next step), which is what the rule reads.
+__device__ __forceinline__ void orbit_f64_d32_k(int m, int lcap, double cr, double ci, double& vr,
+                                                double& vi, float& dr, float& di, float& kr, float& ki) {
+  double zr = 0.0, zi = 0.0, cap_r = 0.0, cap_i = 0.0;
+  float dzr = 0.f, dzi = 0.f, capd_r = 0.f, capd_i = 0.f;
+  float ur = 0.f, ui = 0.f, capu_r = 0.f, capu_i = 0.f;
+  int hexp = 127 << 23;  // exponent field of 2^-(k-1), k = 1
+#pragma unroll 4
+  for (int k = 1; k <= m; ++k) {
+    const float fr = f32_trunc(zr), fi = f32_trunc(zi);
+    const float h = __int_as_float(hexp);
+    hexp -= 1 << 23;
+    const float sr = dzr * h, si = dzi * h;  // p'_{k-1} / 2^(k-1)
+    const float nur = 0.5f * (fmaf(sr, sr, -si * si) + fmaf(fr, ur, -fi * ui));
+    const float nui = 0.5f * fmaf(sr + sr, si, fmaf(fr, ui, fi * ur));
+    const float tfr = fr + fr, tfi = fi + fi;
+    const float ndr = fmaf(tfr, dzr, fmaf(-tfi, dzi, 1.f));
+    const float ndi = fmaf(tfr, dzi, tfi * dzr);
+    const double tzr = zr + zr;
+    const double nzr = fma(zr, zr, fma(-zi, zi, cr));
+    const double nzi = fma(tzr, zi, ci);
+    zr = nzr; zi = nzi; dzr = ndr; dzi = ndi; ur = nur; ui = nui;
+    if (k == lcap) { cap_r = zr; cap_i = zi; capd_r = dzr; capd_i = dzi; capu_r = ur; capu_i = ui; }
+  }
+  float Ur = ur, Ui = ui;  // P'' / 4^m
+  if (lcap >= 0) {
+    vr = zr + cap_r; vi = zi + cap_i;
+    dr = dzr + capd_r; di = dzi + capd_i;
+    const float a = lcap > 0 ? __int_as_float((127 + 2 * (lcap - m)) << 23) : 0.f;  // 4^(lcap - m)
+    Ur = fmaf(a, capu_r, ur);
+    Ui = fmaf(a, capu_i, ui);
+  } else {
+    vr = zr; vi = zi; dr = dzr; di = dzi;
+  }
+  // P''/(2P') = (U 2^(m-1)) / (P' 2^-m), both scalings exact
+  const float up = __int_as_float((127 + m - 1) << 23), dn = __int_as_float((127 - m) << 23);
+  const float ar = Ur * up, ai = Ui * up, cr2 = dr * dn, ci2 = di * dn;
+  const float den = fmaf(cr2, cr2, ci2 * ci2);
+  const float inv = 1.f / den;
+  kr = fmaf(ar, cr2, ai * ci2) * inv;
+  ki = fmaf(ai, cr2, -ar * ci2) * inv;
+}
+
 // q_{l,n} as a product.  eq. polySimple gives s_{j,n} = q_{j,n} / q_{j-1,n},
 // and q_{0,n} = p_n, so q_{l,n} = p_n prod_{j=1..l} s_{j,n}: with u_k =
 // z_{k+n} - z_k (u_0 = p_n), u_{k+1} = z_{k+n}^2 - z_k^2 = u_k (z_{k+n} + z_k),

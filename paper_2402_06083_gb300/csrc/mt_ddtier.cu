@@ -680,7 +680,8 @@ __global__ void k_dd_emit_main(const double2* __restrict__ reps, const unsigned 
     if (zrx[mid].hi < z.x) lo = mid + 1; else hi = mid;
   }
   const int64_t p = (int64_t)mpos[u] + (lo < nz ? (int64_t)zmpos[lo] : (int64_t)*zt);
-  const uint8_t im = (type && mis_code >= 0) ? (uint8_t)(type[u] == mis_code) : 0;
+  const uint8_t im = !type || mis_code < 0 ? 0
+                     : mis_code == MIS_CODE_RAW ? type[u] : (uint8_t)(type[u] == mis_code);
   if (kmult[u] == 1) {
     if (p < cap_out) {
       out[p] = make_double2(z.x, 0.0);
@@ -719,7 +720,7 @@ __global__ void k_dd_emit_zone(const dd* __restrict__ zrx, const dd* __restrict_
   }
   const int64_t mb = (lo < nm) ? (int64_t)mpos[lo] : (int64_t)*mt;
   const int64_t p = (int64_t)zmpos[v] + mb;
-  const uint8_t im = (mis_code >= 0) ? (uint8_t)(ztype[v] == mis_code) : 0;
+  const uint8_t im = mis_code < 0 ? 0 : mis_code == MIS_CODE_RAW ? ztype[v] : (uint8_t)(ztype[v] == mis_code);
   if (zmult[v] == 1) {
     if (p < cap_out) {
       out[p] = make_double2(x.hi, 0.0);

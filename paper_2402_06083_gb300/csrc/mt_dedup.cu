@@ -533,7 +533,8 @@ __global__ void k_emit(const double2* __restrict__ reps, const unsigned long lon
   const int64_t p = pos[u];
   const uint16_t sg = sv.rep_seg ? sv.rep_seg[u] : 0;
   if (sv.tab) mis_code = (sv.tab[sg].kind == 1 && sv.tab[sg].n < 32) ? sv.tab[sg].n : -1;
-  const uint8_t im = (type && mis_code >= 0) ? (uint8_t)(type[u] == mis_code) : 0;
+  const uint8_t im = !type || mis_code < 0 ? 0
+                     : mis_code == MIS_CODE_RAW ? type[u] : (uint8_t)(type[u] == mis_code);
   if (sv.out_seg) {
     if (p < cap_out) sv.out_seg[p] = sg;
     if (mult[u] == 2 && p + 1 < cap_out) sv.out_seg[p + 1] = sg;

@@ -263,6 +263,30 @@ cudaError_t launch_separation_strips(const double2* hi, const double2* lo, const
                                      uint32_t* iso2_idx, double* iso2_best, double* nn_out,
                                      unsigned long long* band_min, cudaStream_t s);
 
+// Emission's per-root byte: mis_code >= 0 writes 1 where the type code is
+// mis_code (Mis(l,n) of s_{l,n}); MIS_CODE_RAW writes the type code itself
+// (period k of p_n; k for Mis(l,k) / 32 + k for Hyp(k) of s_{l,n}).
+constexpr int MIS_CODE_RAW = 256;
+
+// q_{l,n} through its factors (eq. polySimple telescoped, q_{l,n} = p_n^2
+// prod_{j=2..l} s_{j,n}): append the roots of one factor, with their type
+// codes, to the union list.  j == 0: the factor p_n, every root, Hyp(k) of
+// multiplicity floor((l-1)/k) + 2; else s_{j,n}, its Mis(j,k) roots (codes
+// below 32), multiplicity 1.  Counts appended roots, their multiplicities,
+// roots without a valid code and real roots (cnt[0] .. cnt[3]).
+cudaError_t launch_qf_append(const double2* roots, const uint8_t* type, int64_t count, int j, int l, int n,
+                             double2* u_roots, uint8_t* u_pre, uint8_t* u_per, uint8_t* u_mult, int64_t cap,
+                             unsigned long long* cnt, cudaStream_t s);
+// keys[p] = order-preserving key of Re (use_im: Im) of z[perm ? perm[p] : p],
+// vals[p] = perm ? perm[p] : p, for p < *n_dev.
+cudaError_t launch_qf_keys(const double2* z, const uint32_t* perm, int64_t cap, const unsigned long long* n_dev,
+                           int use_im, uint64_t* keys, uint32_t* vals, cudaStream_t s);
+// out[p] = u[perm[p]] for roots and the three type bytes (null outputs skipped).
+cudaError_t launch_qf_gather(const uint32_t* perm, int64_t cap, const unsigned long long* n_dev,
+                             const double2* u_roots, const uint8_t* u_pre, const uint8_t* u_per,
+                             const uint8_t* u_mult, double2* roots, uint8_t* pre, uint8_t* per, uint8_t* mult,
+                             cudaStream_t s);
+
 // Zero the counters (min radius set to +inf).
 cudaError_t launch_init_counters(DevCounters* ctr, cudaStream_t s);
 // keys[i] = order-preserving key of Re pts[i], vals[i] = i.

@@ -116,19 +116,22 @@ __device__ __forceinline__ void pert_eval(const PolyDev& P, const float2* zs, in
   Dy = fmaf(a, cg_y, g_y) * s;
 }
 
-// pert_eval for the descents.  STRIDE: the shared-memory row stride (a
-// compile-time constant, so each row's load takes an immediate offset).  MC:
-// the orbit length when known at compile time (p_n, m = n: the loop is fully
-// unrolled and 2^-(k+1) is an immediate), else 0 (P.m, unrolled by four).
-// The capture of p_lcap is compiled in only where the polynomial has one
-// (s_{l,n}).
+// pert_eval for the descents and the walk.  z1 points to row 1 of the
+// lane's orbit column (row k at z1[(k - 1) * STRIDE]); row 0 is Z_0 = 0, so
+// the first step is exact and skipped: e_1 = delta, g_1 = 2^-1.  STRIDE: the
+// shared-memory row stride (a compile-time constant, so each row's load
+// takes an immediate offset).  MC: the orbit length when known at compile
+// time (p_n, m = n: the loop is fully unrolled and 2^-(k+1) is an
+// immediate), else 0 (P.m, unrolled by four).  The capture of p_lcap is
+// compiled in only where the polynomial has one (s_{l,n}).
 template <bool CAP, int MC, int STRIDE>
-__device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* zs, float dx, float dy, float& ex,
+__device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* z1, float dx, float dy, float& ex,
                                             float& ey, float& Dx, float& Dy) {
-  float e_x = 0.f, e_y = 0.f, g_x = 0.f, g_y = 0.f;
+  float e_x = dx, e_y = dy, g_x = 0.5f, g_y = 0.f;
   float ce_x = 0.f, ce_y = 0.f, cg_x = 0.f, cg_y = 0.f;
+  if (CAP && P.lcap == 1) { ce_x = e_x; ce_y = e_y; cg_x = g_x; cg_y = g_y; }
   auto step = [&](int k, float h) {
-    const float2 Z = zs[k * STRIDE];
+    const float2 Z = z1[(k - 1) * STRIDE];
     const float zx = Z.x + e_x, zy = Z.y + e_y;  // p_k(c)
     const float ng_x = fmaf(zx, g_x, fmaf(-zy, g_y, h));
     const float ng_y = fmaf(zx, g_y, zy * g_x);
@@ -140,11 +143,11 @@ __device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* zs, 
   };
   if constexpr (MC > 0) {
 #pragma unroll
-    for (int k = 0; k < MC; ++k) step(k, __int_as_float((126 - k) << 23));  // 2^-(k+1)
+    for (int k = 1; k < MC; ++k) step(k, __int_as_float((126 - k) << 23));  // 2^-(k+1)
   } else {
-    int hexp = (127 - 1) << 23;  // exponent field of 2^-(k+1), k = 0
+    int hexp = (127 - 2) << 23;  // exponent field of 2^-(k+1), k = 1
 #pragma unroll 4
-    for (int k = 0; k < P.m; ++k) {
+    for (int k = 1; k < P.m; ++k) {
       step(k, __int_as_float(hexp));
       hexp -= 1 << 23;
     }
@@ -164,6 +167,7 @@ __device__ __forceinline__ void pert_eval_t(const PolyDev& P, const float2* zs, 
     Dy = g_y * sc;
   }
 }
+
 
 // binary32 quotient; false when |D|^2 leaves the safe binary32 range.
 __device__ __forceinline__ bool cdiv_f32(float a, float b, float c, float d, float& qr, float& qi) {
@@ -327,7 +331,7 @@ __device__ __forceinline__ int newton_target_walk(const PolyDev& P, const float2
   int it = 0;
   while (it < cap) {
     float ex, ey, Dx, Dy;
-    pert_eval_t<CAP, MC, STRIDE>(P, zs, dx, dy, ex, ey, Dx, Dy);
+    pert_eval_t<CAP, MC, STRIDE>(P, zs + STRIDE, dx, dy, ex, ey, Dx, Dy);
     float nr, ni;
     if (it == 0) {  // predictor: P - Tp - L P, L = i Li
       const float Pr = v.x + (v.z + ex), Pi = v.y + (v.w + ey);
@@ -480,12 +484,13 @@ __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, i
 }
 
 // a4 in the mixed tier, binary32 phase (persistent, per-lane refill as in
-// k_descend) over starts [base, base + cnt).  Each lane keeps the anchor
-// orbit of its descent in its own column of shared memory (row k holds
-// Z_k of every lane; the row stride DM_BS + 1 is odd, so the rows of one
-// column fall in different banks).  Lanes that finished are refilled
-// together: the warp takes their start indices from a warp-private range of
-// the work queue (one atomic per 32 starts), then copies each new orbit
+// k_descend) over starts [base, base + cnt), cnt < 2^31.  Each lane keeps
+// the anchor orbit of its descent (Z_1 .. Z_{m-1}) in its own column of
+// shared memory (row k - 1 holds Z_k of every lane; the row stride DM_BS + 1
+// is odd, so the rows of one column fall in different banks).  Lanes that
+// finished are refilled together once DM_REFILL of them wait (or none is
+// running): the warp takes their start indices from a warp-private range
+// of the work queue (one atomic per 32 starts), then copies each new orbit
 // (m - 1 consecutive anchors) with consecutive lanes, one refilled lane
 // after the other, so no refill runs a loop of loads on one or two lanes
 // while the others wait.  The Newton loop is binary32 only.  Each descent
@@ -496,6 +501,7 @@ __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, i
 // length when fixed at compile time (p_n), else 0.
 constexpr int DESC_POOL = 32;  // work indices taken per queue atomic
 constexpr int DM_BS = 128;     // threads per block of the binary32 descent
+constexpr int DM_REFILL = 4;   // idle lanes that trigger a refill
 
 template <bool CAP, int MC>
 __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base, int64_t cnt,
@@ -504,35 +510,37 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
                                                          const float* __restrict__ rdel, int cap,
                                                          float4* __restrict__ pack,
                                                          uint8_t* __restrict__ status,
-                                                         unsigned long long* queue,
-                                                         DevCounters* ctr) {
+                                                         unsigned* queue, DevCounters* ctr) {
   extern __shared__ float2 zsh[];
   constexpr int stride = DM_BS + 1;
-  float2* zs = zsh + threadIdx.x;
+  const float2* zs = zsh + threadIdx.x;  // row 0 (Z_1) of this lane's column
   const unsigned lane = threadIdx.x & 31;
   const int wbase = threadIdx.x & ~31;
   const int m1 = (MC > 0 ? MC : P.m) - 1;
-  zs[0] = make_float2(0.f, 0.f);  // Z_0 = 0 for every descent
-  int64_t idx = -1;
+  const unsigned n = (unsigned)cnt;
+  unsigned idx = ~0u;  // this lane's start (~0u: none)
   float dx = 0.f, dy = 0.f, h1 = 0.f, prev2 = 0.f, rdelta = 0.f;
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
   int it = 0;
   unsigned long long s32 = 0, ndiv = 0, nto = 0;
-  unsigned long long pool_next = 0, pool_end = 0;  // the warp's range of queue indices (warp-uniform)
-  bool drained = false;                             // the queue is empty (warp-uniform)
+  unsigned pool_next = 0, pool_end = 0;  // the warp's range of queue indices (warp-uniform)
+  bool drained = false;                  // the queue is empty (warp-uniform)
   for (;;) {
-    const unsigned need = drained ? 0u : __ballot_sync(0xffffffffu, idx < 0);
-    if (need) {
-      const unsigned R = __popc(need);
+    const unsigned need = drained ? 0u : __ballot_sync(0xffffffffu, idx == ~0u);
+    const unsigned R = __popc(need);
+    if (R >= DM_REFILL || (R == 32u && need)) {
       // start index of the r-th lane that needs one: the warp's range, then a new one
-      const unsigned long long rem = pool_end - pool_next;
-      unsigned long long g = 0;
+      const unsigned rem = pool_end - pool_next;
+      unsigned g = 0;
       if (rem < R) {
-        if (lane == 0) g = atomicAdd(queue, (unsigned long long)DESC_POOL);
+        if (lane == 0) g = atomicAdd(queue, (unsigned)DESC_POOL);
         g = __shfl_sync(0xffffffffu, g, 0);
       }
       const unsigned r_me = __popc(need & lanemask_lt());
-      if (idx < 0) idx = (int64_t)(r_me < rem ? pool_next + r_me : g + (r_me - rem));
+      if (idx == ~0u) {
+        const unsigned j = r_me < rem ? pool_next + r_me : g + (r_me - rem);
+        idx = j < n ? j : n;  // n: the queue is drained (never refilled again)
+      }
       if (rem < R) {
         pool_next = g + (R - rem);
         pool_end = g + DESC_POOL;
@@ -543,17 +551,17 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
       // consecutive lanes from its m - 1 consecutive anchors
       for (unsigned todo = need; todo; todo &= todo - 1) {
         const int tl = __ffs(todo) - 1;
-        const int64_t ir = __shfl_sync(0xffffffffu, idx, tl);  // warp-uniform
-        if (ir >= cnt) {
+        const unsigned ir = __shfl_sync(0xffffffffu, idx, tl);  // warp-uniform
+        if (ir >= n) {
           drained = true;
           continue;
         }
-        const float2* src = anch + ir * m1;
-        float2* dst = zsh + wbase + tl + stride;
+        const float2* src = anch + (size_t)ir * m1;
+        float2* dst = zsh + wbase + tl;
         for (int k = (int)lane; k < m1; k += 32) dst[k * stride] = src[k];
       }
       __syncwarp();
-      if (((need >> lane) & 1u) && idx < cnt) {
+      if (((need >> lane) & 1u) && idx < n) {
         v = vv[idx];
         rdelta = rdel[idx];
         dx = dy = 0.f;
@@ -562,8 +570,11 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
         h1 = 0.f;
       }
     }
-    const bool active = idx >= 0 && idx < cnt;
-    if (!__any_sync(0xffffffffu, active)) break;
+    const bool active = idx < n;
+    if (!__any_sync(0xffffffffu, active)) {
+      if (drained) break;
+      continue;  // every lane idle: the next pass refills all 32
+    }
     if (active) {
       int outcome = -1;
       float ex, ey, Dx, Dy, qr, qi;
@@ -590,7 +601,7 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
         status[base + idx] = (uint8_t)outcome;
         ndiv += outcome == 1;
         nto += outcome == 2;
-        idx = -1;
+        idx = ~0u;
       }
     }
   }
@@ -602,7 +613,7 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
 }
 
 using DescMixedFn = void (*)(PolyDev, int64_t, int64_t, const float2*, const float4*, const float*, int, float4*,
-                             uint8_t*, unsigned long long*, DevCounters*);
+                             uint8_t*, unsigned*, DevCounters*);
 
 // The instantiation for a polynomial: p_n with 16 <= n <= 33 has its orbit
 // length fixed at compile time; everything else runs the general loop.
@@ -779,6 +790,7 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
                                                     unsigned long long* queue, DevCounters* ctr) {
   const unsigned lane = threadIdx.x & 31;
   const int64_t nl = (int64_t)*nlist < cap_list ? (int64_t)*nlist : cap_list;
+  const float tol2q = 0.0625f * f32_trunc(tol2);  // (tol / 4)^2
   int64_t t = -1;  // position in the list of this lane's finish
   double zx = 0.0, zy = 0.0, prev2 = 1e300;
   int it = 0;
@@ -807,17 +819,26 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
     if (!__any_sync(0xffffffffu, active)) break;
     if (active) {
       double vr, vi, qr, qi;
-      float dr, di;
-      orbit_f64_d32(P.m, P.lcap, zx, zy, vr, vi, dr, di);
+      float dr, di, kr, ki;
+      orbit_f64_d32_k(P.m, P.lcap, zx, zy, vr, vi, dr, di, kr, ki);
       cdiv_f64(vr, vi, (double)dr, (double)di, qr, qi);
       zx -= qr;
       zy -= qi;
       ++it;
       ++s64;
       const double s2 = fma(qr, qr, qi * qi);
+      // the next step, predicted: q^2 P''/(2P') (binary32; z to binary32 on
+      // the integer pipe); NaN or inf never accepts
+      const float fqr = f32_trunc(qr), fqi = f32_trunc(qi);
+      const float q2r = fmaf(fqr, fqr, -fqi * fqi), q2i = 2.f * fqr * fqi;
+      const float pr = fmaf(q2r, kr, -q2i * ki), pi = fmaf(q2r, ki, q2i * kr);
+      const float pred2 = fmaf(pr, pr, pi * pi);
       int outcome = -1;
       if (!finite2(zx, zy) || fma(zx, zx, zy * zy) > 1e4) outcome = 1;
       else if (s2 < tol2) outcome = 0;
+      // quadratic regime (the next step under a quarter of this one) and the
+      // next step under tol / 4: c - q is the root to within tol / 4
+      else if (pred2 <= tol2q && pred2 <= 0.0625f * f32_trunc(s2)) outcome = 0;
       else if (s2 >= 0.25 * prev2 && s2 < floor2_f64(zx, zy)) outcome = 0;  // rounding floor
       else if (it >= cap) outcome = 2;
       prev2 = s2;
@@ -924,11 +945,15 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   if (count <= 0) return cudaSuccess;
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
   const int bs = DM_BS;
-  const size_t smem = (size_t)P.m * (bs + 1) * sizeof(float2);
+  const size_t smem = (size_t)(P.m > 1 ? P.m - 1 : 1) * (bs + 1) * sizeof(float2);
   const size_t asmem = (size_t)bs * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2);  // anchor staging
   const DescMixedFn kdesc = desc_mixed_kernel(P);
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024 &&  // long orbits: opt in to more than 48 KB
+      (e = cudaFuncSetAttribute(kdesc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kdesc, bs, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kdesc, bs, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t B = count < MIX_BATCH ? count : MIX_BATCH;
@@ -946,8 +971,9 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
     int64_t grid = (int64_t)device_sm_count() * per_sm;
     const int64_t need = (cnt + bs - 1) / bs;
     if (grid > need) grid = need;
-    // the work queue restarts at 0 for every batch
-    unsigned long long* q = &ctr->queue_head;
+    // the work queue (32-bit: a batch holds fewer than 2^31 starts) restarts
+    // at 0 for every batch
+    unsigned* q = (unsigned*)&ctr->queue_head;
     if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
     if ((e = ktimer_begin(KS_DESC32, s)) != cudaSuccess) return e;
