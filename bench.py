@@ -84,7 +84,7 @@ def newton_flops(m: int) -> int:
 
 
 def newton_flops_fp32(m: int) -> int:
-    return 19 * m + 25
+    return 19 * (m - 1) + 25  # the first orbit step (from Z_0 = 0) is exact and skipped
 
 
 def finish_flops_fp64(m: int) -> int:

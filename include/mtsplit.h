@@ -212,18 +212,27 @@ MT_API mt_status mt_split_misiurewicz(int l, int n, const mt_options* opts, doub
 /* Split q_{l,n} = p_{l+n} - p_l (eq. def:mis; misQuick of Sec. 6.3.1), whose
    roots are multiple (Thm fact_mis): Hyp(k), k | n, of multiplicity
    eta_l(k) = floor((l-1)/k) + 2, and Mis(j,k), 2 <= j <= l, k | n, simple.
-   l >= 1, n >= 1, l + n <= 40; binary64 only (opts->prec = MT_FP64, else
-   MT_EINVAL).  d_roots: [cap][2] doubles, receives the distinct roots sorted
+   l >= 1, n >= 1, l + n <= 40.  opts->prec = MT_FP64: Newton descents on
+   q itself (below); MT_DD: through its factors, q_{l,n} = p_n^2
+   prod_{j=2..l} s_{j,n} (eq. polySimple telescoped from q_{0,n} = p_n, with
+   s_{1,n} = p_n), each factor split by the certified double-double split of
+   its own kind (mt_split_hyperbolic / mt_split_misiurewicz); Hyp(k) roots
+   come from p_n, Mis(j,k) roots from s_{j,n}, the union sorted by (Re, Im)
+   and every root certified as a simple root of its factor (the tip Mis
+   points from order 20 on lie closer than binary64 descents on q resolve);
+   MT_MIXED: MT_EINVAL.  d_roots: [cap][2] doubles, receives the distinct roots sorted
    by (Re, Im); *n_out their number.  d_mult, d_pre, d_per: NULL or [cap]
    bytes: multiplicity, preperiod j (0 for Hyp) and period k of each root
    (255 / 0 where no type matched).  Complete when the multiplicities add up
    to 2^(l+n-1) (stats->n_mult); else MT_EINCOMPLETE after the retries.
-   Every root is certified (Thm proofRoots): a Mis root as a simple root of
-   q, a Hyp root as a simple root of p_n (MT_ECERT if one fails).
+   Every root is certified (Thm proofRoots): in MT_FP64 a Mis root as a
+   simple root of q, a Hyp root as a simple root of p_n (MT_ECERT if one
+   fails); in MT_DD each root as a simple root of its factor.
    Descents on q that contract linearly take the multiplicity step of eq.
    newtonAcc; q is evaluated in the product form p_n prod_{j<=l} s_{j,n} of
    eq. polySimple, which keeps its relative accuracy up to a multiple root.
-   Workspace: mt_workspace_bytes(2, l, n, opts). */
+   Workspace: mt_workspace_bytes(2, l, n, opts) (for MT_DD: the largest
+   factor's split plus the union list and its sort). */
 MT_API mt_status mt_split_misiurewicz_q(int l, int n, const mt_options* opts, double* d_roots, int64_t cap,
                                         uint8_t* d_mult, uint8_t* d_pre, uint8_t* d_per, void* d_work,
                                         size_t work_bytes, int64_t* n_out, mt_stats* stats);

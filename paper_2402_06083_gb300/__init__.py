@@ -117,7 +117,9 @@ class SplitResultQ:
 def split_misiurewicz_q(l: int, n: int, prec: str = "fp64", *, work: Workspace | None = None,
                         check_status: bool = True, **kw) -> SplitResultQ:
     """The distinct roots of q_{l,n} = p_{l+n} - p_l with their multiplicities
-    and types (Thm fact_mis), binary64 (mt_split_misiurewicz_q)."""
+    and types (Thm fact_mis), mt_split_misiurewicz_q: "fp64" descends on q
+    in binary64, "dd" splits its factors p_n, s_{j,n} (eq. polySimple) in
+    double-double."""
     torch = _torch()
     L = load()
     o = options(prec, **kw)

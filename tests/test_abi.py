@@ -56,6 +56,12 @@ def test_host_only_entry_points(lib):
     assert nb > 2 ** 19 * 16 * 4
     assert L.mt_workspace_bytes(0, 0, 0, ctypes.byref(o)) == 0  # invalid n
     assert L.mt_workspace_bytes(1, 1, 3, ctypes.byref(o)) == 0  # l < 2
+    # q_{l,n} in MT_DD goes through its factors: room for the largest
+    # factor's split (s_{l,n} or p_n) and the union list of the distinct roots
+    od = mt.options("dd", stream=0)
+    nq = L.mt_workspace_bytes(2, 6, 16, ctypes.byref(od))
+    assert nq > L.mt_workspace_bytes(1, 6, 16, ctypes.byref(od)) + 2 ** 21 * 16
+    assert L.mt_workspace_bytes(2, 30, 11, ctypes.byref(od)) == 0  # l + n <= 40
     assert mt.version().startswith("mtsplit")
 
 

@@ -120,7 +120,7 @@ def test_kernel_rooflines_arithmetic():
     by = {k["kernel"]: k for k in bench.kernel_rooflines("hyp", 0, 20, [st], pk)}
     assert set(by) == {"k_descend_mixed", "k_finish_f64", "k_walk_mixed"}
     assert by["k_descend_mixed"]["launches"] == 2 and by["k_descend_mixed"]["peak"] == 75.0
-    assert abs(by["k_descend_mixed"]["achieved"] - 1500 * (19 * 20 + 25) / 1e-3 / 1e12) < 1e-12
+    assert abs(by["k_descend_mixed"]["achieved"] - 1500 * (19 * 19 + 25) / 1e-3 / 1e12) < 1e-12
     assert abs(by["k_finish_f64"]["achieved"] - 500 * (7 * 20 + 24) / 2.5e-3 / 1e12) < 1e-12
     assert bench.roofline_of(list(by.values()), "x")["kernel"] == "k_finish_f64"
     # the binary64 descents of the mixed tier (the tip redo): desc_newton less

@@ -19,7 +19,7 @@ import pytest
 
 import oracle
 from oracle import counts
-from tests.rootsets import match_sets
+from tests.rootsets import lexsorted, match_sets
 
 pytestmark = pytest.mark.gpu
 
@@ -78,6 +78,61 @@ def test_q_rejects_other_tiers(mt):
     from paper_2402_06083_gb300._lib import MtError
     with pytest.raises((MtError, ValueError)):
         mt.split_misiurewicz_q(3, 4, "mixed")
+
+
+@pytest.mark.parametrize("l,n", [(1, 5), (2, 4), (3, 4), (4, 6), (5, 3), (6, 6), (9, 3)])
+def test_q_dd_factors_match_binary128_oracle(mt, l, n):
+    """MT_DD: q_{l,n} through its factors (eq. polySimple telescoped), each
+    split by its certified double-double split, against the binary128
+    oracle: the same distinct roots, types and multiplicities."""
+    res = mt.split_misiurewicz_q(l, n, "dd")
+    st = res.stats
+    z = res.roots.cpu().numpy()
+    ref = oracle.split("q", n, l=l)
+    assert z.size == ref["n_roots"] and st["prec_used"] == 2
+    assert st["n_mult"] == counts.deg_q(l, n) and st["n_cert_pass"] == z.size
+    perm, dmax = match_sets(z, ref["roots"])
+    assert dmax < TOL_FP64, dmax
+    pre, per, mu = res.pre.cpu().numpy(), res.per.cpu().numpy(), res.mult.cpu().numpy()
+    assert np.array_equal(pre, ref["type"][perm, 0]) and np.array_equal(per, ref["type"][perm, 1])
+    assert np.array_equal(mu, ref["mult"][perm])
+    assert lexsorted(z)
+    assert st["n_real"] == int(np.sum(z.imag == 0))
+
+
+@pytest.mark.parametrize("l,n", [(11, 5), (6, 10), (3, 13)])
+def test_q_dd_factors_equal_the_binary64_descents(mt, l, n):
+    """Two GPU routes to q_{l,n} of order 16: the binary64 descents on q
+    itself (misQuick, multiplicity step of eq. newtonAcc) and the union of
+    the double-double splits of its factors give the same roots (1e-12),
+    types and multiplicities."""
+    a = mt.split_misiurewicz_q(l, n)
+    b = mt.split_misiurewicz_q(l, n, "dd")
+    za, zb = a.roots.cpu().numpy(), b.roots.cpu().numpy()
+    assert za.size == zb.size
+    perm, dmax = match_sets(za, zb)
+    assert dmax < TOL_FP64, dmax
+    for f in ("pre", "per", "mult"):
+        assert np.array_equal(getattr(a, f).cpu().numpy(), getattr(b, f).cpu().numpy()[perm])
+
+
+@pytest.mark.parametrize("order", [20, 22])
+def test_q_dd_orders_20_and_22_complete(mt, order):
+    """Orders where binary64 descents on q lose tip Mis points (about
+    6.4e3/8^(l+n) apart, 5.6e-15 at order 20: below the binary64 pixel of
+    64 ulp(2)): through the double-double factors every pair (l, n) of the
+    order is complete, with Thm fact_mis' type histogram and multiplicities,
+    every root certified, sorted by (Re, Im)."""
+    work = mt.Workspace()
+    for l in range(1, order):
+        n = order - l
+        res = mt.split_misiurewicz_q(l, n, "dd", work=work)
+        st = res.stats
+        pre, per, mu = res.pre.cpu().numpy(), res.per.cpu().numpy(), res.mult.cpu().numpy()
+        assert _hist(pre, per) == counts.type_histogram_q(l, n), (l, n)
+        assert int(mu.sum()) == st["n_mult"] == counts.deg_q(l, n), (l, n)
+        assert st["n_cert_pass"] == res.roots.shape[0], (l, n)
+        assert lexsorted(res.roots.cpu().numpy()), (l, n)
 
 
 def test_q_list_entry_points(mt):
