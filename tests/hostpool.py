@@ -34,13 +34,15 @@ def _polish(args):
     return oracle.polish_many(kind, n, z, l=l, roots_lo=zl, steps=steps, want_points=True)
 
 
-def polish_all(kind: str, n: int, z, l: int = 0, zl=None, chunk: int = 1 << 15, steps: int = 4):
+def polish_all(kind: str, n: int, z, l: int = 0, zl=None, chunk: int = 0, steps: int = 4):
     """(disp, last, points4) for every point of z (+ low parts zl), each
     polished by 'steps' binary128 Newton steps (4: at the left tip of p_24,
     where roots lie 4.2e-13 apart, a binary64 root's third step is still
     ~1e-24)."""
     z = np.asarray(z, dtype=np.complex128).ravel()
     zl = None if zl is None else np.asarray(zl, dtype=np.complex128).ravel()
+    if chunk <= 0:  # about four chunks per host core
+        chunk = max(256, -(-z.size // (4 * cores())))
     parts = [(kind, l, n, z[a:a + chunk], None if zl is None else zl[a:a + chunk], steps)
              for a in range(0, z.size, chunk)]
     if not parts:
