@@ -982,7 +982,7 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
                 c_h[1], c_h[2]);
   // the zone's root set
   CK(dd_keys(d.zcx, d.zcy, &d.cnt[2], p.dd_zcap, p.eps_dd, d.zkeys, d.zvals, s));
-  CK(radix_sort_pairs(d.zkeys, d.zvals, d.zkeys_alt, d.zvals_alt, p.dd_zcap, d.zradix, s));
+  CK(radix_sort_pairs(d.zkeys, d.zvals, d.zkeys_alt, d.zvals_alt, p.dd_zcap, d.zradix, s, &d.cnt[2]));
   CK(dd_cluster(d.zcx, d.zcy, d.zvals, &d.cnt[2], p.dd_zcap, p.eps_dd, d.zflag, s));
   CK(launch_exclusive_scan(d.zflag, d.zpos, p.dd_zcap, d.zscan, &d.cnt[3], s));
   CK(dd_compact(d.zcx, d.zcy, d.zvals, d.zflag, d.zpos, p.dd_zcap, d.zrx, d.zry, s));

@@ -281,32 +281,66 @@ __device__ __forceinline__ bool dd_converged(double s2, double prev2, double tol
 
 // dd descents from the dd starts; converged roots in a zone (folded to the
 // upper half, P having real coefficients) are appended to the zone list.
-__global__ void k_dd_descend(PolyDev P, int64_t count, const dd* __restrict__ zx0,
-                             const dd* __restrict__ zy0, const uint8_t* __restrict__ ok0, double tol2,
-                             int cap, const double2* __restrict__ bad, int nbad, double R,
-                             dd* __restrict__ ox, dd* __restrict__ oy, unsigned long long* nout,
-                             int64_t out_cap, DevCounters* ctr) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Persistent, with per-lane refill by warp vote (as k_descend): descents
+// from the level line take from a few to ~30 double-double Newton steps, so
+// a lane that finished takes the next start at once instead of idling until
+// its warp's slowest descent ends.  queue: zeroed before the launch.
+__global__ void __launch_bounds__(64) k_dd_descend(PolyDev P, int64_t count, const dd* __restrict__ zx0,
+                                                   const dd* __restrict__ zy0, const uint8_t* __restrict__ ok0,
+                                                   double tol2, int cap, const double2* __restrict__ bad,
+                                                   int nbad, double R, dd* __restrict__ ox, dd* __restrict__ oy,
+                                                   unsigned long long* nout, int64_t out_cap,
+                                                   unsigned long long* queue, DevCounters* ctr) {
+  const unsigned lane = threadIdx.x & 31;
+  int64_t i = -1;  // current start (-1: idle, >= count: queue drained)
+  dd zr = dd_make(0.0), zi = dd_make(0.0);
+  double rdiv2 = 16.0, prev2 = 1e300;
+  int it = 0;
   unsigned long long steps = 0;
-  if (i < count && ok0[i]) {
-    dd zr = zx0[i], zi = zy0[i];
-    const double rdiv2 = fmax(16.0, 4.0 * fma(zr.hi, zr.hi, zi.hi * zi.hi));
-    bool conv = false;
-    double prev2 = 1e300;
-    for (int it = 0; it < cap; ++it) {
-      double s2;
-      if (!dd_newton_step(P, zr, zi, s2)) break;
-      ++steps;
-      if (!(fma(zr.hi, zr.hi, zi.hi * zi.hi) <= rdiv2)) break;
-      if (dd_converged(s2, prev2, tol2, zr, zi)) {
-        conv = true;
-        break;
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, i < 0);
+    if (need) {
+      unsigned long long b0 = 0;
+      const int leader = __ffs(need) - 1;
+      if ((int)lane == leader) b0 = atomicAdd(queue, (unsigned long long)__popc(need));
+      b0 = __shfl_sync(0xffffffffu, b0, leader);
+      if (i < 0) {
+        i = (int64_t)(b0 + __popc(need & lanemask_lt()));
+        if (i < count) {
+          if (ok0[i]) {
+            zr = zx0[i];
+            zi = zy0[i];
+            rdiv2 = fmax(16.0, 4.0 * fma(zr.hi, zr.hi, zi.hi * zi.hi));
+            prev2 = 1e300;
+            it = 0;
+          } else {
+            i = -1;  // no start here: take another next time
+          }
+        }
       }
-      prev2 = s2;
     }
-    if (conv) {
-      if (zi.hi < 0.0) zi = dd_neg(zi);
-      if (zone_hit(zr.hi, zi.hi, bad, nbad, R)) push_zone(zr, zi, ox, oy, nout, out_cap);
+    const bool active = i >= 0 && i < count;
+    if (!__any_sync(0xffffffffu, active || i < 0)) break;  // every lane drained
+    if (active) {
+      double s2;
+      bool done = false, conv = false;
+      if (!dd_newton_step(P, zr, zi, s2)) {
+        done = true;
+      } else {
+        ++steps;
+        ++it;
+        if (!(fma(zr.hi, zr.hi, zi.hi * zi.hi) <= rdiv2)) done = true;
+        else if (dd_converged(s2, prev2, tol2, zr, zi)) done = conv = true;
+        else if (it >= cap) done = true;
+        prev2 = s2;
+      }
+      if (done) {
+        if (conv) {
+          if (zi.hi < 0.0) zi = dd_neg(zi);
+          if (zone_hit(zr.hi, zi.hi, bad, nbad, R)) push_zone(zr, zi, ox, oy, nout, out_cap);
+        }
+        i = -1;
+      }
     }
   }
   warp_add_u64(&ctr->steps_dd, steps);
@@ -902,8 +936,19 @@ cudaError_t dd_descend(const PolyDev& P, int64_t count, const dd* zx0, const dd*
                        const uint8_t* ok0, double tol, int cap, const double2* bad, int nbad,
                        double R, dd* ox, dd* oy, unsigned long long* nout, int64_t out_cap,
                        DevCounters* ctr, cudaStream_t s) {
-  MT_DD_LAUNCH(k_dd_descend, count, 64, P, count, zx0, zy0, ok0, tol * tol, cap, bad, nbad, R, ox, oy,
-               nout, out_cap, ctr);
+  if (count <= 0) return cudaSuccess;
+  // persistent: at most the blocks the GPU holds at once
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dd_descend, 64, 0);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+  const int64_t need = (count + 63) / 64;
+  if (grid > need) grid = need;
+  unsigned long long* q = &ctr->queue_head;
+  if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
+  MT_COUNT_LAUNCH(1);
+  k_dd_descend<<<(unsigned)grid, 64, 0, s>>>(P, count, zx0, zy0, ok0, tol * tol, cap, bad, nbad, R, ox, oy, nout,
+                                             out_cap, q, ctr);
   return cudaGetLastError();
 }
 

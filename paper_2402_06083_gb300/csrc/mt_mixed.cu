@@ -661,7 +661,24 @@ constexpr int FINISH_SCAN = 32;
 // spacings below a fixed threshold shrinks as 1 / d^2: tip_box =
 // 1e-3 (d / 2^29)^2, 2.5 times the p_30 case (0.8 % of the descents there).
 inline double tip_box(const PolyDev& P) { return 1e-3 * exp2(2.0 * (P.log2d - 29)); }
-constexpr uint64_t TIP_KEY = ~0ull - 1;  // above every finite f64_key, below ~0
+// Sort keys of the binary32 end points: Re in fixed point, 2^-37 per unit
+// over [-2.25, 1.75) (every root of the family lies in Re in [-2, 1/4]),
+// FINISH_KEY_BITS = 40 bits, so that five radix passes order them.  The map
+// c -> round((c + 2.25) 2^37) is monotone (non-decreasing), so the sort
+// orders the end points by Re up to one bucket, FINISH_BUCKET wide.
+constexpr int FINISH_KEY_BITS = 40;
+constexpr double FINISH_BUCKET = 7.275957614183426e-12;  // 2^-37
+constexpr uint64_t TIP_KEY = (1ull << FINISH_KEY_BITS) - 2;  // above every finite key, below the rest
+constexpr uint64_t REST_KEY = (1ull << FINISH_KEY_BITS) - 1;
+__device__ __forceinline__ uint64_t finish_key(double re) {
+  // round(re 2^37 + 2.25 2^37) as an integer, by adding 2^52 (exact below 2^52):
+  // two binary64 operations, the rest on the integer pipe
+  const double f = fma(re, 137438953472.0, 309237645312.0);  // (re + 2.25) 2^37
+  const double g = f + 4503599627370496.0;                     // 2^52
+  const long long k = __double_as_longlong(g) - 0x4330000000000000ll;
+  const long long top = (long long)(1ull << (FINISH_KEY_BITS - 1)) - 1;
+  return (uint64_t)(k < 0 ? 0 : k > top ? top : k);
+}
 
 // c32 = start + delta in binary64, folded into the upper half for the
 // descents to finish (status 3), whose Re is their sort key; the others
@@ -681,7 +698,7 @@ __global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ star
     double2 c = make_double2(c0.x + (double)q.x, c0.y + (double)q.y);
     const bool fin = status[i] == 3;
     if (fin && c.y < 0.0) c.y = -c.y;
-    uint64_t key = ~0ull;
+    uint64_t key = REST_KEY;
     if (fin && c.x < -2.0 + box && c.y < box) {
       status[i] = 4;  // redone in binary64 from c0
       key = TIP_KEY;
@@ -689,7 +706,7 @@ __global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ star
     } else {
       starts[i] = c;
       if (fin) {
-        key = f64_key(c.x);
+        key = finish_key(c.x);
         ++n3;
       }
     }
@@ -755,8 +772,11 @@ __global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals,
     for (int k = 1; k <= FINISH_SCAN && k <= p; ++k) {
       const uint32_t j = vals[p - k];
       const double2 b = c32[j];
-      const double ex = a.x - b.x, ey = a.y - b.y;  // ex >= 0: sorted by Re
-      if (ex * ex > reach2) break;
+      const double ex = a.x - b.x, ey = a.y - b.y;
+      // sorted by Re up to one bucket: every earlier entry lies below
+      // b.x + FINISH_BUCKET, so none is within reach once ex - bucket is
+      const double eb = ex - FINISH_BUCKET;
+      if (eb > 0.0 && eb * eb > reach2) break;
       const double sc = (double)fminf(ha, pack[j].z);
       if (fma(ex, ex, ey * ey) <= (double)FINISH_SAME2 * sc) {
         h = 0;
@@ -990,8 +1010,16 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   const unsigned egrid = std::min<unsigned>(nb, (unsigned)device_sm_count() * 16);  // grid-stride kernels
   k_c32_keys<<<egrid, bs, 0, s>>>(count, tip_box(P), starts, pack, status, fin.keys, fin.vals, ctr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = radix_sort_pairs(fin.keys, fin.vals, fin.keys_alt, fin.vals_alt, count, fin.radix_tmp, s)) != cudaSuccess)
-    return e;
+  {
+    bool in_alt = false;
+    if ((e = radix_sort_bits(fin.keys, fin.vals, fin.keys_alt, fin.vals_alt, count, fin.radix_tmp, 0,
+                             FINISH_KEY_BITS, &in_alt, s)) != cudaSuccess)
+      return e;
+    // the permutation is read from vals (vals_alt becomes the head list)
+    if (in_alt && (e = cudaMemcpyAsync(fin.vals, fin.vals_alt, (size_t)count * sizeof(uint32_t),
+                                       cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
+  }
   MT_COUNT_LAUNCH(1);
   k_finish_heads<<<nb, bs, 0, s>>>(count, fin.vals, starts, pack, status, fin.head, fin.link);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
