@@ -112,6 +112,22 @@ def _kernel(name, pipe, flops, ms, launches, peak, peak_nominal, work) -> dict:
             "flops_per_launch": flops / max(1, launches), "traffic": None, "work": work}
 
 
+# DRAM traffic per unit of work, from one ncu capture of the current kernels
+# (profiles/kernels_hyp24_mixed.md: p_24 mixed and p_20 binary64, dram__bytes
+# read + write per launch divided by the units that launch processed), as a
+# function of the orbit length m; a bench launch's traffic is this times its
+# own units.  k_descend_mixed reads each start's m - 1 anchors (8 B), P(start)
+# (16 B) and its jump bound (4 B) and writes its (delta, scale) (16 B): 1.712 GB
+# + 136 MB per 2^23 starts at m = 24, exactly 8(m-1) + 20 + 16 B a start.
+# k_descend (binary64 tier) reads its start (16 B; 16.8 MB per 2^20 starts).
+# k_finish_f64: 404 MB + 143 MB per 4.47 M finishes at p_24, 122 B each.
+TRAFFIC = {
+    "k_descend_mixed": (lambda m: 8 * (m - 1) + 36, "start"),
+    "k_descend": (lambda m: 16, "start"),
+    "k_finish_f64": (lambda m: 122, "finish"),
+}
+
+
 def kernel_rooflines(kind: str, l: int, n: int, stats: list, pk: dict, sm_mhz: float | None = None) -> list:
     """ALU roofline of each timed hot kernel against the FMA rate of its own
     pipe: algorithmic flops (the kernels' own step counters x flops per step)
@@ -155,6 +171,14 @@ def kernel_rooflines(kind: str, l: int, n: int, stats: list, pk: dict, sm_mhz: f
         else:
             out.append(_kernel("k_walk", "fp64", steps * newton_flops(m), mean("ms_k_walk"), 1, p64, n64,
                                "binary64 walk steps %d x %d flops" % (steps, newton_flops(m))))
+    mixed = s0.get("desc_fp32", 0) > 0
+    for k in out:  # DRAM bytes per launch: measured bytes per unit x this launch's units
+        t = TRAFFIC.get(k["kernel"])
+        if t is None or (k["kernel"] == "k_descend" and mixed) or kind != "hyp":
+            continue
+        units = s0.get("n_finish", 0) if t[1] == "finish" else s0.get("n_starts", 0)
+        k["traffic"] = t[0](m) * units / max(1, k["launches"])
+        k["traffic_unit"] = "bytes per launch (%d B per %s, from the ncu capture)" % (t[0](m), t[1])
     return out
 
 

@@ -129,6 +129,12 @@ def test_kernel_rooflines_arithmetic():
                 ms_k_desc32=1.0, ms_k_finish=2.5)
     by = {k["kernel"]: k for k in bench.kernel_rooflines("hyp", 0, 20, [st], pk)}
     assert by["k_descend"]["flops_per_launch"] == 100 * (13 * 20 + 24)
+    # DRAM traffic per launch: the captured bytes per unit x this launch's units
+    assert by["k_descend"]["traffic"] is None  # the tip redo (a list), not captured
+    assert by["k_descend_mixed"]["traffic"] == (8 * 19 + 36) * 4096 / 1
+    st = _stats(n_starts=1 << 20)
+    by = {k["kernel"]: k for k in bench.kernel_rooflines("hyp", 0, 20, [st], pk)}
+    assert by["k_descend"]["traffic"] == 16 * (1 << 20)
     # the batched split: orbit lengths differ per polynomial, counted by the kernel
     st = _stats(desc_orbit_steps=30000)
     k = bench.kernel_rooflines("mis", 0, 15, [st], pk)[0]
