@@ -53,7 +53,7 @@ __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, d
     const float tfr = fr + fr, tfi = fi + fi;
     const float ndr = fmaf(tfr, dzr, fmaf(-tfi, dzi, 1.f));
     const float ndi = fmaf(tfr, dzi, tfi * dzr);
-    const double tzr = zr + zr;
+    const double tzr = twice_f64(zr);
     const double nzr = fma(zr, zr, fma(-zi, zi, cr));
     const double nzi = fma(tzr, zi, ci);
     zr = nzr; zi = nzi; dzr = ndr; dzi = ndi;
@@ -304,7 +304,7 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
     const float prod = __fmaf_ru(rzz, rd, __fmaf_ru(rzz, md, __fmul_ru(rd, mzf)));
     const float nrd = __fmaf_ru(2.f, prod, Rd);
     // z = z^2 + c in binary64: re = fma(zx, zx, fma(-zy, zy, cx)), im = fma(2zx, zy, cy)
-    const double tzx = zx + zx;
+    const double tzx = twice_f64(zx);
     const double in_z = fma(-zy, zy, cx);
     const double nz_x = fma(zx, zx, in_z);
     const double nz_y = fma(tzx, zy, cy);

@@ -20,6 +20,31 @@
 
 namespace mt {
 
+// twice_f64(x) = x + x, bit for bit, on the integer pipe: a normal x below
+// 2^1023 gets its exponent field incremented; zero and subnormals shift
+// their significand left (becoming normal where it carries into the
+// exponent); 2^1023 and up overflow to inf; inf and NaN are returned as
+// they are.  On GB300 binary64 arithmetic issues at 1/64 of the binary32
+// rate, so every orbit step's doubling moves off the binary64 pipe.
+__device__ __forceinline__ double twice_f64(double x) {
+  const int hi = __double2hiint(x);
+  const int lo = __double2loint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+  const int sgn = hi & (int)0x80000000;
+  int rh = hi + 0x00100000, rl = lo;  // normal: exponent + 1
+  if (e == 0u) {                      // zero, subnormal
+    rh = sgn | (int)(((unsigned)hi << 1) & 0x7fffffffu) | (int)((unsigned)lo >> 31);
+    rl = (int)((unsigned)lo << 1);
+  } else if (e == 0x7feu) {  // overflow
+    rh = sgn | 0x7ff00000;
+    rl = 0;
+  } else if (e == 0x7ffu) {  // inf, NaN
+    rh = hi;
+  }
+  return __hiloint2double(rh, rl);
+}
+
+
 // ---------------------------------------------------------------------------
 // 2^k as a binary64 built from its exponent field (-1022 <= k <= 1023):
 // integer work only, off the binary64 pipe.
@@ -48,7 +73,7 @@ __device__ __forceinline__ void orbit_f64(int m, int lcap, double alpha, double 
     const double ner = fma(zr, er, fma(-zi, ei, h));      // Re(z e + 2^-k)
     const double nei = fma(zr, ei, zi * er);               // Im(z e)
     const double nzr = fma(zr, zr, fma(-zi, zi, cr));      // Re(z^2 + c)
-    const double nzi = fma(zr + zr, zi, ci);               // Im(z^2 + c)
+    const double nzi = fma(twice_f64(zr), zi, ci);               // Im(z^2 + c)
     zr = nzr; zi = nzi; er = ner; ei = nei;
     if (k == lcap) { cap_r = zr; cap_i = zi; cape_r = er; cape_i = ei; }
   }
@@ -72,7 +97,7 @@ __device__ __forceinline__ void orbit_pn_f64(int m, double cr, double ci, double
     const double ner = fma(zr, er, fma(-zi, ei, h));
     const double nei = fma(zr, ei, zi * er);
     const double nzr = fma(zr, zr, fma(-zi, zi, cr));
-    const double nzi = fma(zr + zr, zi, ci);
+    const double nzi = fma(twice_f64(zr), zi, ci);
     zr = nzr; zi = nzi; er = ner; ei = nei;
   }
   const double s = pow2_f64(m);
@@ -82,6 +107,38 @@ __device__ __forceinline__ void orbit_pn_f64(int m, double cr, double ci, double
 // binary64 -> binary32 on the integer pipe.  A conversion instruction runs
 // on the binary64 pipe, the scarce one on GB300 (2 lanes per SM per clock):
 // in an orbit that converts z every step it is a third of that pipe's work.
+// The binary64 value of a binary32 f, built on the integer pipe (exact for
+// normal f and zero; binary32 subnormals, below 1.2e-38, give +-0).
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sg = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi = sg, lo = 0u;
+  if (e == 0xffu) {  // inf, NaN
+    hi = sg | 0x7ff00000u | (m >> 3);
+    lo = m << 29;
+  } else if (e != 0u) {
+    hi = sg | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// (a + ib) / (c + id) in binary32 with c + id first scaled by a power of two
+// (exactly) into [1, 2) in modulus, so that |c + id|^2 cannot leave the
+// binary32 range; false for a zero, subnormal, huge or non-finite divisor.
+__device__ __forceinline__ bool cdiv_f32s(float a, float b, float c, float d, float& qr, float& qi) {
+  const float mx = fmaxf(fabsf(c), fabsf(d));
+  const int eb = __float_as_int(mx) & 0x7f800000;
+  if (eb == 0 || eb >= 0x7f000000) return false;
+  const float sc = __int_as_float(0x7f000000 - eb);  // 2^-E for mx in [2^E, 2^(E+1))
+  c *= sc;
+  d *= sc;
+  const float inv = 1.0f / fmaf(c, c, d * d);
+  qr = fmaf(a, c, b * d) * inv * sc;
+  qi = fmaf(b, c, -a * d) * inv * sc;
+  return isfinite(qr) && isfinite(qi);
+}
+
 // f32_trunc rounds toward zero: sign, the exponent rebiased (its low eight
 // bits xor 0x80 are e - 896), the top 23 mantissa bits by a funnel shift.
 // |x| below 2^-126 gives +-0 (error < 2^-126), |x| from 2^128 on or a
@@ -126,7 +183,7 @@ __device__ __forceinline__ void orbit_f64_d32(int m, int lcap, double cr, double
     const float tfr = fr + fr, tfi = fi + fi;
     const float ndr = fmaf(tfr, dzr, fmaf(-tfi, dzi, 1.f));
     const float ndi = fmaf(tfr, dzi, tfi * dzr);
-    const double tzr = zr + zr;
+    const double tzr = twice_f64(zr);
     const double nzr = fma(zr, zr, fma(-zi, zi, cr));
     const double nzi = fma(tzr, zi, ci);
     zr = nzr; zi = nzi; dzr = ndr; dzi = ndi;
@@ -164,7 +221,7 @@ __device__ __forceinline__ void orbit_f64_d32_k(int m, int lcap, double cr, doub
     const float tfr = fr + fr, tfi = fi + fi;
     const float ndr = fmaf(tfr, dzr, fmaf(-tfi, dzi, 1.f));
     const float ndi = fmaf(tfr, dzi, tfi * dzr);
-    const double tzr = zr + zr;
+    const double tzr = twice_f64(zr);
     const double nzr = fma(zr, zr, fma(-zi, zi, cr));
     const double nzi = fma(tzr, zi, ci);
     zr = nzr; zi = nzi; dzr = ndr; dzi = ndi; ur = nur; ui = nui;
@@ -201,7 +258,7 @@ __device__ __forceinline__ void orbit_q_f64(int l, int n, double cr, double ci, 
                                             double& dr, double& di) {
   double br = 0.0, bi = 0.0, dbr = 0.0, dbi = 0.0;  // z_{k+n}, z'_{k+n}
   for (int k = 1; k <= n; ++k) {
-    const double tzr = br + br, tzi = bi + bi;
+    const double tzr = twice_f64(br), tzi = twice_f64(bi);
     const double ndr = fma(tzr, dbr, fma(-tzi, dbi, 1.0));
     const double ndi = fma(tzr, dbi, tzi * dbr);
     const double nzr = fma(br, br, fma(-bi, bi, cr));
@@ -226,7 +283,7 @@ __device__ __forceinline__ void orbit_q_f64(int l, int n, double cr, double ci, 
       ar = nzr; ai = nzi; dar = ndr; dai = ndi;
     }
     {
-      const double tzr = br + br, tzi = bi + bi;
+      const double tzr = twice_f64(br), tzi = twice_f64(bi);
       const double ndr = fma(tzr, dbr, fma(-tzi, dbi, 1.0));
       const double ndi = fma(tzr, dbi, tzi * dbr);
       const double nzr = fma(br, br, fma(-bi, bi, cr));

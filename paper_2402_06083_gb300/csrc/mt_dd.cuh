@@ -74,7 +74,7 @@ __device__ __forceinline__ dd dd_mul_d(dd a, double b) {
   c.lo = fma(a.lo, b, c.lo);
   return fast_two_sum(c.hi, c.lo);
 }
-__device__ __forceinline__ dd dd_twice(dd a) { return dd{a.hi + a.hi, a.lo + a.lo}; }  // exact
+__device__ __forceinline__ dd dd_twice(dd a) { return dd{twice_f64(a.hi), twice_f64(a.lo)}; }  // exact
 __device__ __forceinline__ double dd_to_d(dd a) { return a.hi + a.lo; }
 
 // ---------------------------------------------------------------------------

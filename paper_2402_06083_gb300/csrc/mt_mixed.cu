@@ -73,7 +73,7 @@ __device__ __forceinline__ void ref_orbit(const PolyDev& P, double c0x, double c
   zs[0] = make_float2(0.f, 0.f);
   for (int k = 1; k <= P.m; ++k) {
     const double nx = fma(zx, zx, fma(-zy, zy, c0x));
-    const double ny = fma(zx + zx, zy, c0y);
+    const double ny = fma(twice_f64(zx), zy, c0y);
     zx = nx;
     zy = ny;
     if (k < P.m) zs[k * stride] = make_float2(f32_trunc(zx), f32_trunc(zy));  // integer pipe
@@ -810,9 +810,10 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
                                                     unsigned long long* queue, DevCounters* ctr) {
   const unsigned lane = threadIdx.x & 31;
   const int64_t nl = (int64_t)*nlist < cap_list ? (int64_t)*nlist : cap_list;
-  const float tol2q = 0.0625f * f32_trunc(tol2);  // (tol / 4)^2
+  const float tol2f = f32_trunc(tol2), tol2q = 0.0625f * tol2f;  // tol^2, (tol / 4)^2
   int64_t t = -1;  // position in the list of this lane's finish
-  double zx = 0.0, zy = 0.0, prev2 = 1e300;
+  double zx = 0.0, zy = 0.0;
+  float prev2 = 3.0e38f;
   int it = 0;
   bool drained = false;  // warp-uniform: the list is handed out
   unsigned long long s64 = 0;
@@ -830,7 +831,7 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
           zx = z.x;
           zy = z.y;
           it = 0;
-          prev2 = 1e300;
+          prev2 = 3.0e38f;
         }
       }
       if ((int64_t)(b0 + __popc(need)) >= nl) drained = true;
@@ -838,28 +839,39 @@ __global__ void __launch_bounds__(128) k_finish_f64(PolyDev P, const uint32_t* _
     const bool active = t >= 0 && t < nl;
     if (!__any_sync(0xffffffffu, active)) break;
     if (active) {
-      double vr, vi, qr, qi;
+      double vr, vi;
       float dr, di, kr, ki;
       orbit_f64_d32_k(P.m, P.lcap, zx, zy, vr, vi, dr, di, kr, ki);
-      cdiv_f64(vr, vi, (double)dr, (double)di, qr, qi);
-      zx -= qr;
-      zy -= qi;
+      // the quotient in binary32: the derivative is binary32 already, and a
+      // step accurate to 1e-7 of itself leaves ~1e-7 q besides the quadratic
+      // K q^2 -- far below tol for the q ~ 1e-5 of a descent's scale that
+      // the binary32 phase leaves; binary64 only for the value and z - q
+      float qr, qi;
+      if (!cdiv_f32s(f32_trunc(vr), f32_trunc(vi), dr, di, qr, qi)) {
+        double qd, qe;  // a derivative out of binary32's scaled range: binary64
+        cdiv_f64(vr, vi, (double)dr, (double)di, qd, qe);
+        qr = f32_trunc(qd);
+        qi = f32_trunc(qe);
+      }
+      zx -= f64_of_f32(qr);
+      zy -= f64_of_f32(qi);
       ++it;
       ++s64;
-      const double s2 = fma(qr, qr, qi * qi);
-      // the next step, predicted: q^2 P''/(2P') (binary32; z to binary32 on
-      // the integer pipe); NaN or inf never accepts
-      const float fqr = f32_trunc(qr), fqi = f32_trunc(qi);
-      const float q2r = fmaf(fqr, fqr, -fqi * fqi), q2i = 2.f * fqr * fqi;
+      const float s2 = fmaf(qr, qr, qi * qi);
+      // the next step, predicted: q^2 P''/(2P') (binary32); NaN or inf never accepts
+      const float q2r = fmaf(qr, qr, -qi * qi), q2i = 2.f * qr * qi;
       const float pr = fmaf(q2r, kr, -q2i * ki), pi = fmaf(q2r, ki, q2i * kr);
       const float pred2 = fmaf(pr, pr, pi * pi);
+      const float fzx = f32_trunc(zx), fzy = f32_trunc(zy);
+      // binary64 rounding floor (16 ulp of the larger of 1 and |z|), in binary32
+      const float fl = (1.f + fabsf(fzx) + fabsf(fzy)) * 3.552713678800501e-15f;
       int outcome = -1;
-      if (!finite2(zx, zy) || fma(zx, zx, zy * zy) > 1e4) outcome = 1;
-      else if (s2 < tol2) outcome = 0;
+      if (!finite2(zx, zy) || fmaf(fzx, fzx, fzy * fzy) > 1e4f) outcome = 1;
+      else if (s2 < tol2f) outcome = 0;
       // quadratic regime (the next step under a quarter of this one) and the
       // next step under tol / 4: c - q is the root to within tol / 4
-      else if (pred2 <= tol2q && pred2 <= 0.0625f * f32_trunc(s2)) outcome = 0;
-      else if (s2 >= 0.25 * prev2 && s2 < floor2_f64(zx, zy)) outcome = 0;  // rounding floor
+      else if (pred2 <= tol2q && pred2 <= 0.0625f * s2) outcome = 0;
+      else if (s2 >= 0.25f * prev2 && s2 < fl * fl) outcome = 0;  // rounding floor
       else if (it >= cap) outcome = 2;
       prev2 = s2;
       if (outcome >= 0) {

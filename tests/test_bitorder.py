@@ -116,3 +116,42 @@ def test_scaled_derivative_recurrence_matches_plain_one_bit_for_bit():
     s = 2.0 ** m
     assert np.array_equal(er[ok] * s, dr[ok])
     assert np.array_equal(ei[ok] * s, di[ok])
+
+
+def _twice_bits(x: np.ndarray) -> np.ndarray:
+    """The integer-pipe doubling of twice_f64 (csrc/mt_common.cuh), restated
+    on the two 32-bit halves with numpy."""
+    b = np.asarray(x, dtype=np.float64).view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.uint32)
+    lo = (b & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    e = (hi >> np.uint32(20)) & np.uint32(0x7FF)
+    sgn = hi & np.uint32(0x80000000)
+    rh = hi + np.uint32(0x00100000)
+    rl = lo.copy()
+    z = e == 0
+    rh[z] = sgn[z] | ((hi[z] << np.uint32(1)) & np.uint32(0x7FFFFFFF)) | (lo[z] >> np.uint32(31))
+    rl[z] = lo[z] << np.uint32(1)
+    o = e == 0x7FE
+    rh[o] = sgn[o] | np.uint32(0x7FF00000)
+    rl[o] = 0
+    f = e == 0x7FF
+    rh[f] = hi[f]
+    return ((rh.astype(np.uint64) << np.uint64(32)) | rl.astype(np.uint64)).view(np.float64)
+
+
+def test_twice_by_exponent_is_x_plus_x():
+    """twice_f64 doubles on the integer pipe; it must equal x + x bit for bit
+    for every finite and infinite binary64: normal, subnormal (becoming
+    normal), zero of both signs, and overflow to inf."""
+    rng = np.random.default_rng(7)
+    bits = rng.integers(0, 2 ** 63, 2_000_000, dtype=np.int64).view(np.uint64)
+    bits[::2] |= np.uint64(1) << np.uint64(63)
+    x = bits.view(np.float64)
+    x = x[~np.isnan(x)]
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072009e-308, 2.2250738585072014e-308,
+                        8.98846567431158e307, -8.98846567431158e307, 1.7976931348623157e308, np.inf, -np.inf,
+                        1.0, -3.0, 1e-310])
+    x = np.concatenate([x, special])
+    with np.errstate(over="ignore"):
+        want = x + x
+    assert np.array_equal(_twice_bits(x).view(np.uint64), want.view(np.uint64))
