@@ -86,7 +86,7 @@ __device__ __forceinline__ void orbit_dd(int m, int lcap, double alpha, dd cr, d
   dd zr = dd_make(0.0), zi = dd_make(0.0), capr = dd_make(0.0), capi = dd_make(0.0);
   double dzr = 0.0, dzi = 0.0, capdr = 0.0, capdi = 0.0;
   for (int k = 1; k <= m; ++k) {
-    const double tzr = zr.hi + zr.hi, tzi = zi.hi + zi.hi;
+    const double tzr = twice_f64(zr.hi), tzi = twice_f64(zi.hi);
     const double ndr = fma(tzr, dzr, fma(-tzi, dzi, 1.0));
     const double ndi = fma(tzr, dzi, tzi * dzr);
     const dd xx = dd_mul(zr, zr), yy = dd_mul(zi, zi), xy = dd_mul(zr, zi);

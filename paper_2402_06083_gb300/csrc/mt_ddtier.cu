@@ -28,6 +28,7 @@
 //      parts going to the caller's lo buffer.
 // "all" mode makes every root a zone member: the whole split is redone in dd.
 #include "mt_dd.cuh"
+#include "mt_pert.cuh"
 #include "mt_levelline.cuh"
 
 namespace mt {
@@ -151,34 +152,32 @@ __device__ __forceinline__ void push_zone(dd zr, dd zi, dd* __restrict__ zx, dd*
 
 // ---- dd level line of the redone chunks ----------------------------------------------
 
-// lift_seed in double-double: the point at t = jq / NQ on |P| = lambda0.
-__device__ void lift_seed_dd(const PolyDev& P, double lambda0, int64_t NQ, int log2NQ, int shrink,
-                             int64_t jq, dd& zr, dd& zi, unsigned long long& steps) {
-  double c, s;
-  unit_phase((uint64_t)jq, (uint64_t)NQ, c, s);
-  zr = dd_make(lambda0 * c);
-  zi = dd_make(lambda0 * s);
-  const double Lq = -log(lambda0) / shrink;
-  for (int k = 1; k < P.m; ++k) {
-    const uint64_t num = (k >= log2NQ) ? 0 : (((uint64_t)jq << k) & (uint64_t)(NQ - 1));
-    unit_phase(num, (uint64_t)NQ, c, s);
-    const double rel = (k + 1 < P.m) ? 1e-2 : 1e-3;  // as lift_seed
-    for (int q = 1; q <= shrink; ++q) {
-      const double rp = pow(lambda0, 2.0 - (double)(q - 1) / shrink);
-      const double r = pow(lambda0, 2.0 - (double)q / shrink);
-      steps += newton_target_dd(k + 1, -1, 0.0, zr, zi, dd_make(r * c), dd_make(r * s), rel, 40,
-                                nullptr, true, rp * c, rp * s, Lq, 0.0);
-    }
+
+// The double-double pass's walk and descents in binary32 perturbation
+// form (mt_pert.cuh) around double-double anchors.  Near the left tip the
+// points of the level line lie closer than binary64 resolves, but the walk
+// only has to follow |P| = lambda0 to 1e-2 of a sub-step, and a descent only
+// has to reach its root's basin before the double-double finish: what needs
+// the 106 bits is the position, which the anchor (double-double) carries,
+// not the arithmetic of each step, which binary32 does relative to |delta|.
+// The anchor's orbit Z_1 .. Z_{m-1} goes to shared memory in binary32
+// (truncated on the integer pipe), P(anchor) as binary32 hi + lo; the
+// binary64 pipe then issues one double-double orbit per anchor instead of
+// one per Newton step.
+template <bool CAP, int STRIDE>
+__device__ __forceinline__ void dd_ref_orbit(const PolyDev& P, dd cr, dd ci, float2* zs, float4& v) {
+  dd zr = dd_make(0.0), zi = dd_make(0.0), capr = dd_make(0.0), capi = dd_make(0.0);
+  zs[0] = make_float2(0.f, 0.f);
+  for (int k = 1; k <= P.m; ++k) {
+    const dd xx = dd_mul(zr, zr), yy = dd_mul(zi, zi), xy = dd_mul(zr, zi);
+    zr = dd_add(dd_sub(xx, yy), cr);
+    zi = dd_add(dd_twice(xy), ci);
+    if (k < P.m) zs[k * STRIDE] = make_float2(f32_trunc(zr.hi), f32_trunc(zi.hi));
+    if (CAP && k == P.lcap) { capr = zr; capi = zi; }
   }
-  if (P.kind == 1) {
-    const int k = P.m - 1;
-    const uint64_t num = (k >= log2NQ) ? 0 : (((uint64_t)jq << k) & (uint64_t)(NQ - 1));
-    unit_phase(num, (uint64_t)NQ, c, s);
-    for (int a = 1; a <= 8; ++a)
-      steps += newton_target_dd(P.m, P.lcap, a / 8.0, zr, zi, dd_make(lambda0 * c),
-                                dd_make(lambda0 * s), 1e-3, 40, nullptr);
-  }
-  if (jq == 0 || jq == NQ / 2) zi = dd_make(0.0);
+  const dd vr = CAP ? dd_add(zr, capr) : zr, vi = CAP ? dd_add(zi, capi) : zi;
+  const float hx = f32_trunc(vr.hi), hy = f32_trunc(vi.hi);
+  v = make_float4(hx, hy, f32_trunc((vr.hi - f64_of_f32(hx)) + vr.lo), f32_trunc((vi.hi - f64_of_f32(hy)) + vi.lo));
 }
 
 // Seeds of the redone pieces.  Piece k of the batch (line piece ids[k])
@@ -195,29 +194,82 @@ __global__ void k_dd_seed_count(const int64_t* __restrict__ ids, int64_t nb,
   cnt[k] = (k + 1 < nb && ids[k + 1] == ids[k] + 1) ? 1u : 2u;
 }
 
-// thread (k, e): e = 0 the start seed of piece k, e = 1 its own end seed
+// thread (k, e): e = 0 the start seed of piece k, e = 1 its own end seed.
+// The lift of the seed through the nested family (Sec. 4.2: at level k a
+// Newton solve of p_{k+1} from the level-k point, with the shrink steps back
+// to lambda0, as lift_seed) with each level's solves in binary32
+// perturbation form around the double-double point reached at the level
+// below (dd_ref_orbit of p_{k+1}: one double-double orbit per level instead
+// of one per Newton step); a level whose binary32 solves fail is redone by
+// double-double solves.  Shared memory: m rows of 32
+// binary32 pairs per warp.
 __global__ void k_dd_seeds(PolyDev P, double lambda0, int64_t NQ, int log2NQ, int shrink,
                            const int64_t* __restrict__ ids, const uint32_t* __restrict__ cnt,
                            const uint32_t* __restrict__ off, int64_t nb, dd* __restrict__ sx,
                            dd* __restrict__ sy, DevCounters* ctr) {
+  extern __shared__ float2 zsh[];
+  float2* zs = zsh + (threadIdx.x >> 5) * 32 * P.m + (threadIdx.x & 31);
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long steps = 0;
+  unsigned long long steps = 0, s32 = 0;
   const int64_t k = g >> 1;
   const int e = (int)(g & 1);
   if (k < nb && (e == 0 || cnt[k] == 2)) {
-    dd zr, zi;
-    lift_seed_dd(P, lambda0, NQ, log2NQ, shrink, ids[k] + e, zr, zi, steps);
+    const int64_t jq = ids[k] + e;
+    double c, s;
+    unit_phase((uint64_t)jq, (uint64_t)NQ, c, s);
+    dd zr = dd_make(lambda0 * c), zi = dd_make(lambda0 * s);
+    const double Lq = -log(lambda0) / shrink;
+    for (int lv = 1; lv < P.m; ++lv) {
+      const uint64_t num = (lv >= log2NQ) ? 0 : (((uint64_t)jq << lv) & (uint64_t)(NQ - 1));
+      unit_phase(num, (uint64_t)NQ, c, s);
+      const double rel = (lv + 1 < P.m) ? 1e-2 : 1e-3;  // as lift_seed
+      PolyDev Q;
+      Q.kind = 0; Q.l = 0; Q.n = lv + 1; Q.m = lv + 1; Q.lcap = -1; Q.log2d = lv;
+      float4 v;
+      dd_ref_orbit<false, 32>(Q, zr, zi, zs, v);
+      float dx = 0.f, dy = 0.f;
+      bool bad = false;
+      int it = 0;
+      for (int q = 1; q <= shrink && !bad; ++q) {
+        const double rp = pow(lambda0, 2.0 - (double)(q - 1) / shrink);
+        const double r = pow(lambda0, 2.0 - (double)q / shrink);
+        it += newton_target_walk<false, 0, 32, true>(Q, zs, v, dx, dy, (float)(r * c), (float)(r * s), (float)rel,
+                                                     40, nullptr, (float)(rp * c), (float)(rp * s), 0.f, &bad,
+                                                     (float)Lq, true);
+      }
+      s32 += it;
+      if (!bad) {
+        zr = dd_add_d(zr, f64_of_f32(dx));
+        zi = dd_add_d(zi, f64_of_f32(dy));
+      } else {  // double-double solves from the level's start
+        for (int q = 1; q <= shrink; ++q) {
+          const double rp = pow(lambda0, 2.0 - (double)(q - 1) / shrink);
+          const double r = pow(lambda0, 2.0 - (double)q / shrink);
+          steps += newton_target_dd(lv + 1, -1, 0.0, zr, zi, dd_make(r * c), dd_make(r * s), rel, 40, nullptr,
+                                    true, rp * c, rp * s, Lq, 0.0);
+        }
+      }
+    }
+    if (P.kind == 1) {  // the homotopy p_m -> p_m + p_{l-1}, in double-double
+      const int kk = P.m - 1;
+      const uint64_t num = (kk >= log2NQ) ? 0 : (((uint64_t)jq << kk) & (uint64_t)(NQ - 1));
+      unit_phase(num, (uint64_t)NQ, c, s);
+      for (int a = 1; a <= 8; ++a)
+        steps += newton_target_dd(P.m, P.lcap, a / 8.0, zr, zi, dd_make(lambda0 * c), dd_make(lambda0 * s), 1e-3,
+                                  40, nullptr);
+    }
+    if (jq == 0 || jq == NQ / 2) zi = dd_make(0.0);
     sx[off[k] + e] = zr;
     sy[off[k] + e] = zi;
   }
   warp_add_u64(&ctr->steps_dd, steps);
+  warp_add_u64(&ctr->steps_fp32, s32);
 }
 
-// Walk piece k of the batch: Ls sub-steps from its seed, writing the starts
-// of the line's sub-steps g = ids[k] Ls + i with g % every == 0 to slot
-// (k Ls + i) / every; the line's last point (t = 1/2, end of the last
-// piece) goes to slot nb Ls / every.  A piece that does not end on its end
-// seed (a skipped turn) counts in walk_fail.
+// The same walk with every Newton step in double-double (s_{l,n}: at order
+// 26 the binary32 walk's starts, valid to the walk's tolerance, left 66 of
+// the tip roots of s_{3,23} unfound, so the Misiurewicz family keeps the
+// double-double walk).
 __global__ void k_dd_walk(PolyDev P, double lambda0, int M, int every, int64_t Ls, int64_t npieces,
                           const int64_t* __restrict__ ids, const uint32_t* __restrict__ off, int64_t nb,
                           const dd* __restrict__ sx, const dd* __restrict__ sy, dd* __restrict__ stx,
@@ -258,6 +310,73 @@ __global__ void k_dd_walk(PolyDev P, double lambda0, int M, int every, int64_t L
   warp_add_u64(&ctr->walk_fail, fails);
 }
 
+// a3 of the dd pass: one lane per piece of Ls sub-steps from its dd seed,
+// re-anchored every K sub-steps.  The start of the line's sub-step g =
+// ids[k] Ls + i with g % every == 0 goes to slot (k Ls + i) / every, the
+// line's last point (t = 1/2, end of the last piece) to slot nb Ls / every.
+// A piece whose end misses its end seed (a skipped turn) counts in
+// walk_fail.  Shared memory: m rows of 32 binary32 pairs per warp.
+template <bool CAP>
+__global__ void k_dd_walk_pert(PolyDev P, double lambda0, int M, int every, int64_t Ls, int64_t npieces,
+                               const int64_t* __restrict__ ids, const uint32_t* __restrict__ off, int64_t nb,
+                               const dd* __restrict__ sx, const dd* __restrict__ sy, dd* __restrict__ stx,
+                               dd* __restrict__ sty, uint8_t* __restrict__ st_ok, int K, DevCounters* ctr) {
+  extern __shared__ float2 zsh[];
+  __shared__ float2 ph[64];
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    double c, s;
+    unit_phase((uint64_t)q, (uint64_t)M, c, s);
+    ph[q] = make_float2((float)(lambda0 * c), (float)(lambda0 * s));
+  }
+  __syncthreads();
+  float2* zs = zsh + (threadIdx.x >> 5) * 32 * P.m + (threadIdx.x & 31);
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long steps = 0, fails = 0;
+  if (k < nb) {
+    const int64_t G = ids[k];
+    const int64_t s0 = off[k];
+    dd ar = sx[s0], ai = sy[s0];
+    float4 v;
+    dd_ref_orbit<CAP, 32>(P, ar, ai, zs, v);
+    float dx = 0.f, dy = 0.f, h = 0.f;
+    bool bad = false;
+    const float Li = 6.2831853f / M;
+    uint64_t g = (uint64_t)G * (uint64_t)Ls;
+    int kc = K;
+    for (int64_t i = 0; i < Ls; ++i, ++g) {
+      if ((g & (uint64_t)(every - 1)) == 0) {
+        const int64_t slot = (k * Ls + i) / every;
+        stx[slot] = dd_add_d(ar, f64_of_f32(dx));
+        sty[slot] = dd_add_d(ai, f64_of_f32(dy));
+        st_ok[slot] = 1;
+      }
+      const float2 Tp = ph[g & (uint64_t)(M - 1)];
+      const float2 T = ph[(g + 1) & (uint64_t)(M - 1)];
+      const float rel = (((g + 1) & (uint64_t)(every - 1)) == 0) ? 1e-2f : 1e-1f;
+      steps += newton_target_walk<CAP, 0, 32, true>(P, zs, v, dx, dy, T.x, T.y, rel, 16, &h, Tp.x, Tp.y, Li, &bad);
+      if (--kc == 0 && i + 1 < Ls) {  // re-anchor at the current point
+        kc = K;
+        ar = dd_add_d(ar, f64_of_f32(dx));
+        ai = dd_add_d(ai, f64_of_f32(dy));
+        dx = dy = 0.f;
+        dd_ref_orbit<CAP, 32>(P, ar, ai, zs, v);
+      }
+    }
+    const dd fr = dd_add_d(ar, f64_of_f32(dx)), fi = dd_add_d(ai, f64_of_f32(dy));
+    const double er = dd_to_d(dd_sub(fr, sx[s0 + 1])), ei = dd_to_d(dd_sub(fi, sy[s0 + 1]));
+    const double hh = (double)h;
+    if (bad || !(er * er + ei * ei <= 0.0625 * hh * hh)) fails = 1;
+    if (G == npieces - 1) {
+      const int64_t slot = (nb * Ls) / every;
+      stx[slot] = fr;
+      sty[slot] = dd_make(0.0);
+      st_ok[slot] = 1;
+    }
+  }
+  warp_add_u64(&ctr->steps_fp32, steps);
+  warp_add_u64(&ctr->walk_fail, fails);
+}
+
 // One dd Newton step of eq. Newton; false if the quotient is not finite.
 __device__ __forceinline__ bool dd_newton_step(const PolyDev& P, dd& zr, dd& zi, double& s2) {
   dd vr, vi;
@@ -281,69 +400,42 @@ __device__ __forceinline__ bool dd_converged(double s2, double prev2, double tol
 
 // dd descents from the dd starts; converged roots in a zone (folded to the
 // upper half, P having real coefficients) are appended to the zone list.
-// Persistent, with per-lane refill by warp vote (as k_descend): descents
-// from the level line take from a few to ~30 double-double Newton steps, so
-// a lane that finished takes the next start at once instead of idling until
-// its warp's slowest descent ends.  queue: zeroed before the launch.
+// a4 of the dd pass, one thread per start: double-double Newton steps (eq.
+// Newton) from the start to the dd tolerance or the divergence bound.  (A
+// binary32 perturbation phase ahead of them, handing over at 1e-2 of the
+// descent's scale, measured slower: its divergent lanes cost more than the
+// dd steps it saved.)  Converged descents that end in a zone are appended to
+// the zone list.
 __global__ void __launch_bounds__(64) k_dd_descend(PolyDev P, int64_t count, const dd* __restrict__ zx0,
                                                    const dd* __restrict__ zy0, const uint8_t* __restrict__ ok0,
                                                    double tol2, int cap, const double2* __restrict__ bad,
                                                    int nbad, double R, dd* __restrict__ ox, dd* __restrict__ oy,
-                                                   unsigned long long* nout, int64_t out_cap,
-                                                   unsigned long long* queue, DevCounters* ctr) {
-  const unsigned lane = threadIdx.x & 31;
-  int64_t i = -1;  // current start (-1: idle, >= count: queue drained)
-  dd zr = dd_make(0.0), zi = dd_make(0.0);
-  double rdiv2 = 16.0, prev2 = 1e300;
-  int it = 0;
-  unsigned long long steps = 0;
-  for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, i < 0);
-    if (need) {
-      unsigned long long b0 = 0;
-      const int leader = __ffs(need) - 1;
-      if ((int)lane == leader) b0 = atomicAdd(queue, (unsigned long long)__popc(need));
-      b0 = __shfl_sync(0xffffffffu, b0, leader);
-      if (i < 0) {
-        i = (int64_t)(b0 + __popc(need & lanemask_lt()));
-        if (i < count) {
-          if (ok0[i]) {
-            zr = zx0[i];
-            zi = zy0[i];
-            rdiv2 = fmax(16.0, 4.0 * fma(zr.hi, zr.hi, zi.hi * zi.hi));
-            prev2 = 1e300;
-            it = 0;
-          } else {
-            i = -1;  // no start here: take another next time
-          }
-        }
+                                                   unsigned long long* nout, int64_t out_cap, DevCounters* ctr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long sdd = 0;
+  if (i < count && ok0[i]) {
+    dd zr = zx0[i], zi = zy0[i];
+    // long jump (as k_descend): |c| beyond max(4, 2 |start|)
+    const double rdiv2 = fmax(16.0, 4.0 * fma(zr.hi, zr.hi, zi.hi * zi.hi));
+    bool conv = false;
+    double pv2 = 1e300;
+    for (int t = 0; t < cap; ++t) {
+      double q2;
+      if (!dd_newton_step(P, zr, zi, q2)) break;
+      ++sdd;
+      if (!(fma(zr.hi, zr.hi, zi.hi * zi.hi) <= rdiv2)) break;
+      if (dd_converged(q2, pv2, tol2, zr, zi)) {
+        conv = true;
+        break;
       }
+      pv2 = q2;
     }
-    const bool active = i >= 0 && i < count;
-    if (!__any_sync(0xffffffffu, active || i < 0)) break;  // every lane drained
-    if (active) {
-      double s2;
-      bool done = false, conv = false;
-      if (!dd_newton_step(P, zr, zi, s2)) {
-        done = true;
-      } else {
-        ++steps;
-        ++it;
-        if (!(fma(zr.hi, zr.hi, zi.hi * zi.hi) <= rdiv2)) done = true;
-        else if (dd_converged(s2, prev2, tol2, zr, zi)) done = conv = true;
-        else if (it >= cap) done = true;
-        prev2 = s2;
-      }
-      if (done) {
-        if (conv) {
-          if (zi.hi < 0.0) zi = dd_neg(zi);
-          if (zone_hit(zr.hi, zi.hi, bad, nbad, R)) push_zone(zr, zi, ox, oy, nout, out_cap);
-        }
-        i = -1;
-      }
+    if (conv) {
+      if (zi.hi < 0.0) zi = dd_neg(zi);
+      if (zone_hit(zr.hi, zi.hi, bad, nbad, R)) push_zone(zr, zi, ox, oy, nout, out_cap);
     }
   }
-  warp_add_u64(&ctr->steps_dd, steps);
+  warp_add_u64(&ctr->steps_dd, sdd);
 }
 
 // dd polish of the main representatives in the polish list.  drop[u] = 1
@@ -462,7 +554,7 @@ __device__ int type_of_dd(const PolyDev& P, dd cr, dd ci, double tau) {
   double dzr = 0.0, dzi = 0.0, ldr = 0.0, ldi = 0.0;
   int hyp = 0, mis = 0;
   for (int k = 1; k <= len; ++k) {
-    const double tzr = zr.hi + zr.hi, tzi = zi.hi + zi.hi;
+    const double tzr = twice_f64(zr.hi), tzi = twice_f64(zi.hi);
     const double ndr = fma(tzr, dzr, fma(-tzi, dzi, 1.0));
     const double ndi = fma(tzr, dzi, tzi * dzr);
     const dd xx = dd_mul(zr, zr), yy = dd_mul(zi, zi), xy = dd_mul(zr, zi);
@@ -528,7 +620,7 @@ __device__ void dd_disk_eval(const PolyDev& P, dd cr, dd ci, double rad, double&
     const double mz = dd_abs_ub(zr, zi);
     const double md = abs_ub64(dx, dy);
     // z' = 2 z z' + 1 from the hi parts of z
-    const double tzx = zr.hi + zr.hi, tzy = zi.hi + zi.hi;
+    const double tzx = twice_f64(zr.hi), tzy = twice_f64(zi.hi);
     const double in_re = fma(-tzy, dy, 1.0);
     const double nd_x = fma(tzx, dx, in_re);
     const double p_im = tzy * dx;
@@ -920,15 +1012,33 @@ cudaError_t dd_seeds(const PolyDev& P, double lambda0, int64_t NQ, int shrink, c
   MT_DD_LAUNCH(k_dd_seed_count, nb, 256, ids, nb, cnt);
   cudaError_t e = launch_exclusive_scan(cnt, off, nb, scan_tmp, nullptr, s);
   if (e != cudaSuccess) return e;
-  MT_DD_LAUNCH(k_dd_seeds, 2 * nb, 64, P, lambda0, NQ, log2NQ, shrink, ids, cnt, off, nb, sx, sy, ctr);
+  {
+    const int bs = 64;
+    const size_t smem = (size_t)P.m * bs * sizeof(float2);
+    MT_COUNT_LAUNCH(1);
+    k_dd_seeds<<<blocks_for(2 * nb, bs), bs, smem, s>>>(P, lambda0, NQ, log2NQ, shrink, ids, cnt, off, nb, sx, sy,
+                                                         ctr);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t dd_walk(const PolyDev& P, double lambda0, int M, int every, int64_t Ls, int64_t npieces,
                     const int64_t* ids, const uint32_t* off, int64_t nb, const dd* sx, const dd* sy,
                     dd* stx, dd* sty, uint8_t* st_ok, DevCounters* ctr, cudaStream_t s) {
-  MT_DD_LAUNCH(k_dd_walk, nb, 64, P, lambda0, M, every, Ls, npieces, ids, off, nb, sx, sy, stx, sty, st_ok,
-               ctr);
+  if (nb <= 0) return cudaSuccess;
+  if (P.kind != 0) {  // s_{l,n}: the double-double walk
+    MT_DD_LAUNCH(k_dd_walk, nb, 32, P, lambda0, M, every, Ls, npieces, ids, off, nb, sx, sy, stx, sty, st_ok, ctr);
+    return cudaGetLastError();
+  }
+  const int bs = 32;  // one lane per piece: spread the few warps over the SMs
+  const size_t smem = (size_t)P.m * bs * sizeof(float2);
+  MT_COUNT_LAUNCH(1);
+  if (P.lcap >= 0)
+    k_dd_walk_pert<true><<<blocks_for(nb, bs), bs, smem, s>>>(P, lambda0, M, every, Ls, npieces, ids, off, nb, sx, sy,
+                                                              stx, sty, st_ok, M, ctr);
+  else
+    k_dd_walk_pert<false><<<blocks_for(nb, bs), bs, smem, s>>>(P, lambda0, M, every, Ls, npieces, ids, off, nb, sx,
+                                                               sy, stx, sty, st_ok, M, ctr);
   return cudaGetLastError();
 }
 
@@ -937,18 +1047,8 @@ cudaError_t dd_descend(const PolyDev& P, int64_t count, const dd* zx0, const dd*
                        double R, dd* ox, dd* oy, unsigned long long* nout, int64_t out_cap,
                        DevCounters* ctr, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  // persistent: at most the blocks the GPU holds at once
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dd_descend, 64, 0);
-  if (e != cudaSuccess) return e;
-  int64_t grid = (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
-  const int64_t need = (count + 63) / 64;
-  if (grid > need) grid = need;
-  unsigned long long* q = &ctr->queue_head;
-  if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
-  MT_COUNT_LAUNCH(1);
-  k_dd_descend<<<(unsigned)grid, 64, 0, s>>>(P, count, zx0, zy0, ok0, tol * tol, cap, bad, nbad, R, ox, oy, nout,
-                                             out_cap, q, ctr);
+  MT_DD_LAUNCH(k_dd_descend, count, 64, P, count, zx0, zy0, ok0, tol * tol, cap, bad, nbad, R, ox, oy, nout,
+               out_cap, ctr);
   return cudaGetLastError();
 }
 
