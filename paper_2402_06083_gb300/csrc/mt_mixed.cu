@@ -425,16 +425,35 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
   unsigned long long s32 = 0, ndiv = 0, nto = 0;
   unsigned pool_next = 0, pool_end = 0;  // the warp's range of queue indices (warp-uniform)
   bool drained = false;                  // the queue is empty (warp-uniform)
+  // The warp takes its next range of queue indices one range ahead and
+  // prefetches that range's anchors into L2, so that the refills' loads
+  // (waited on before the next Newton step) find them there.
+  auto take_range = [&]() -> unsigned {
+    unsigned g = 0;
+    if (lane == 0) g = atomicAdd(queue, (unsigned)DESC_POOL);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    const unsigned i = g + lane;
+    if (i < n) {
+      const char* a = (const char*)(anch + (size_t)i * m1);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a + 128));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a + (size_t)(m1 > 0 ? m1 - 1 : 0) * sizeof(float2)));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(vv + i));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(rdel + i));
+    }
+    return g;
+  };
+  unsigned ahead = take_range();  // the next range (warp-uniform)
   for (;;) {
     const unsigned need = drained ? 0u : __ballot_sync(0xffffffffu, idx == ~0u);
     const unsigned R = __popc(need);
     if (R >= DM_REFILL || (R == 32u && need)) {
-      // start index of the r-th lane that needs one: the warp's range, then a new one
+      // start index of the r-th lane that needs one: the warp's range, then the next one
       const unsigned rem = pool_end - pool_next;
       unsigned g = 0;
       if (rem < R) {
-        if (lane == 0) g = atomicAdd(queue, (unsigned)DESC_POOL);
-        g = __shfl_sync(0xffffffffu, g, 0);
+        g = ahead;
+        ahead = take_range();
       }
       const unsigned r_me = __popc(need & lanemask_lt());
       if (idx == ~0u) {
