@@ -76,9 +76,9 @@ TOL_DD = 1e-20
 #  - binary32 perturbation orbit (mixed tier): 19 flops per step in 12
 #    instructions (two FMA pairs for e, one FMA pair and an FMA/mul for g,
 #    four adds); the binary32 quotient, update and tests 25;
-#  - binary64 finish of the mixed tier (value in binary64, derivative in
-#    binary32): 7 binary64 flops per step (the doubled Re, three FMA), the
-#    binary64 quotient and tests 24.
+#  - binary64 finish of the mixed tier (value in binary64, derivatives in
+#    binary32): 7 binary64 flops per orbit step (three FMA, the doubling on
+#    the integer pipe) and 2 for z - q; the quotient and tests run in binary32.
 def newton_flops(m: int) -> int:
     return 13 * m + 24
 
@@ -88,7 +88,7 @@ def newton_flops_fp32(m: int) -> int:
 
 
 def finish_flops_fp64(m: int) -> int:
-    return 7 * m + 24
+    return 7 * m + 2  # the orbit's value and z - q; the quotient and the tests run in binary32
 
 
 MIX_BATCH = 1 << 23  # starts per launch of the binary32 descent
@@ -116,15 +116,17 @@ def _kernel(name, pipe, flops, ms, launches, peak, peak_nominal, work) -> dict:
 # (profiles/kernels_hyp24_mixed.md: p_24 mixed and p_20 binary64, dram__bytes
 # read + write per launch divided by the units that launch processed), as a
 # function of the orbit length m; a bench launch's traffic is this times its
-# own units.  k_descend_mixed reads each start's m - 1 anchors (8 B), P(start)
-# (16 B) and its jump bound (4 B) and writes its (delta, scale) (16 B): 1.712 GB
-# + 136 MB per 2^23 starts at m = 24, exactly 8(m-1) + 20 + 16 B a start.
-# k_descend (binary64 tier) reads its start (16 B; 16.8 MB per 2^20 starts).
-# k_finish_f64: 404 MB + 143 MB per 4.47 M finishes at p_24, 122 B each.
+# own units.  k_descend_mixed needs 8(m-1) + 20 B a start (its m - 1 anchors,
+# P(start), the jump bound) and writes 16 (its delta and scale): 220 B at
+# m = 24, where the capture reads 2.404 GB and writes 138 MB per 2^23 starts,
+# 303 B a start (the L2 prefetch of the next range re-reads some lines); the
+# measured ratio is kept for other m.  k_descend (binary64 tier) reads its
+# start (16 B; 16.8 MB per 2^20 starts).  k_finish_f64: 389 + 141 MB per
+# 4.47 M finishes at p_24, 118.5 B each.
 TRAFFIC = {
-    "k_descend_mixed": (lambda m: 8 * (m - 1) + 36, "start"),
+    "k_descend_mixed": (lambda m: 303.0 * (8 * (m - 1) + 36) / 220.0, "start"),
     "k_descend": (lambda m: 16, "start"),
-    "k_finish_f64": (lambda m: 122, "finish"),
+    "k_finish_f64": (lambda m: 118.5, "finish"),
 }
 
 
@@ -178,7 +180,7 @@ def kernel_rooflines(kind: str, l: int, n: int, stats: list, pk: dict, sm_mhz: f
             continue
         units = s0.get("n_finish", 0) if t[1] == "finish" else s0.get("n_starts", 0)
         k["traffic"] = t[0](m) * units / max(1, k["launches"])
-        k["traffic_unit"] = "bytes per launch (%d B per %s, from the ncu capture)" % (t[0](m), t[1])
+        k["traffic_unit"] = "bytes per launch (%.1f B per %s, from the ncu capture)" % (t[0](m), t[1])
     return out
 
 
