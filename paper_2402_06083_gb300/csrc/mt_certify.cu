@@ -20,6 +20,10 @@
 // bijectively with the roots (proof of Thm certif).
 #include "mt_common.cuh"
 
+#include <cmath>
+#include <cstring>
+#include <limits>
+
 namespace mt {
 
 // ---------------------------------------------------------------------------
@@ -27,15 +31,20 @@ namespace mt {
 
 // Type code: p_n -> k (1..63); s_{l,n} -> k for Mis(l,k), 32 + k for Hyp(k);
 // 255 if nothing matched.  The test |f| <= tau |f'| compares magnitudes, so
-// the derivatives run in binary32 (from rn32 of the binary64 orbit values).
-__device__ __forceinline__ bool newton_small_f(double vr, double vi, float dr, float di, double tau) {
-  const double ar = dr, ai = di;
-  return fma(vr, vr, vi * vi) <= tau * tau * fma(ar, ar, ai * ai);
+// it runs in binary32: the derivatives are binary32 (from rn32 of the
+// binary64 orbit values), the value is truncated to binary32 on the integer
+// pipe, and tau2 is tau^2 rounded to binary32 on the host.  A value whose
+// square underflows binary32 passes (its Newton size is below tau unless
+// |f'| is as small), and so does a derivative whose square overflows (a
+// bounded orbit value over it has a Newton size far below tau).
+__device__ __forceinline__ bool newton_small_f(double vr, double vi, float dr, float di, float tau2) {
+  const float ar = f32_trunc(vr), ai = f32_trunc(vi);
+  return fmaf(ar, ar, ai * ai) <= tau2 * fmaf(dr, dr, di * di);
 }
 
 // q_{l,n} (kind 2): 32 + k for Hyp(k), k | n (multiplicity eta_l(k)); k for
 // Mis(l, k); 0 for Mis(j, k) with j < l (a root of q_{l-1,n} too).
-__device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, double tau) {
+__device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, float tau2) {
   const int n = P.n;
   const int len = (P.kind == 0) ? n : P.l + n;
   const int g = (P.kind != 1) ? n : [&] {
@@ -57,19 +66,19 @@ __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, d
     const double nzr = fma(zr, zr, fma(-zi, zi, cr));
     const double nzi = fma(tzr, zi, ci);
     zr = nzr; zi = nzi; dzr = ndr; dzi = ndi;
-    if (!hyp && k <= g && (g % k) == 0 && newton_small_f(zr, zi, dzr, dzi, tau)) hyp = k;
+    if (!hyp && k <= g && (g % k) == 0 && newton_small_f(zr, zi, dzr, dzi, tau2)) hyp = k;
     if (P.kind != 0) {
       if (k == P.l) { lr = zr; li = zi; ldr = dzr; ldi = dzi; }
       const int kk = k - P.l;
       if (!mis && kk >= 1 && (n % kk) == 0 &&
-          newton_small_f(zr - lr, zi - li, dzr - ldr, dzi - ldi, tau))
+          newton_small_f(zr - lr, zi - li, dzr - ldr, dzi - ldi, tau2))
         mis = kk;
     }
     if (P.kind == 2 && P.l >= 2) {  // q_{l-1,k}(c) = 0 for a k | n: preperiod below l
       if (k == P.l - 1) { l1r = zr; l1i = zi; l1dr = dzr; l1di = dzi; }
       const int kk = k - (P.l - 1);
       if (!earlier && kk >= 1 && (n % kk) == 0 &&
-          newton_small_f(zr - l1r, zi - l1i, dzr - l1dr, dzi - l1di, tau))
+          newton_small_f(zr - l1r, zi - l1i, dzr - l1dr, dzi - l1di, tau2))
         earlier = 1;
     }
   }
@@ -84,8 +93,11 @@ __device__ __forceinline__ int type_of(const PolyDev& P, double cr, double ci, d
   return 255;
 }
 
+// tau^2 for newton_small_f, rounded to binary32 on the host
+static float tau2_of(double tau) { return (float)(tau * tau); }
+
 __global__ void k_classify(PolyDev P0, double2* __restrict__ reps,
-                           const unsigned long long* __restrict__ n_reps, int64_t cap, double tau,
+                           const unsigned long long* __restrict__ n_reps, int64_t cap, float tau2,
                            int polish, uint8_t* __restrict__ type, uint32_t* __restrict__ mult,
                            DevCounters* ctr, SegView sv) {
   __shared__ unsigned int hist[64];
@@ -109,7 +121,7 @@ __global__ void k_classify(PolyDev P0, double2* __restrict__ reps,
           reps[u] = z;
         }
       }
-      const int t = type_of(P, z.x, z.y, tau);
+      const int t = type_of(P, z.x, z.y, tau2);
       const unsigned m = (z.y == 0.0) ? 1u : 2u;
       type[u] = (uint8_t)t;
       mult[u] = m;
@@ -140,17 +152,17 @@ cudaError_t launch_classify(const PolyDev& P, double2* reps, const unsigned long
                             DevCounters* ctr, cudaStream_t s, SegView sv) {
   if (cap <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_classify<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, n_reps, cap, tau, polish, type,
-                                                           mult, ctr, sv);
+  k_classify<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, n_reps, cap, tau2_of(tau), polish,
+                                                           type, mult, ctr, sv);
   return cudaGetLastError();
 }
 
-__global__ void k_type_only(PolyDev P, const double2* __restrict__ roots, int64_t count, double tau,
+__global__ void k_type_only(PolyDev P, const double2* __restrict__ roots, int64_t count, float tau2,
                             uint8_t* __restrict__ type) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const double2 z = roots[i];
-  type[i] = (uint8_t)type_of(P, z.x, z.y, tau);
+  type[i] = (uint8_t)type_of(P, z.x, z.y, tau2);
 }
 
 // q_{l,n}: per output root the exact type (eq. def:mis) and its multiplicity
@@ -160,7 +172,7 @@ __global__ void k_type_only(PolyDev P, const double2* __restrict__ roots, int64_
 // with q_{j,k}(c) = 0 (q_{j,k} vanishes on Mis(j0,k0) exactly when j >= j0 and
 // k0 | k); multiplicity 1.  255 / 0 where nothing matched.  The orbit (at
 // most 40 steps) is kept whole, in local memory: one pass per root.
-__global__ void k_type_q(PolyDev P, const double2* __restrict__ roots, int64_t count, double tau,
+__global__ void k_type_q(PolyDev P, const double2* __restrict__ roots, int64_t count, float tau2,
                          uint8_t* __restrict__ pre, uint8_t* __restrict__ per, uint8_t* __restrict__ mult) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
@@ -179,12 +191,12 @@ __global__ void k_type_q(PolyDev P, const double2* __restrict__ roots, int64_t c
   }
   int a = -1, b = -1;
   for (int k = 1; k <= n && a < 0; ++k)
-    if (n % k == 0 && newton_small_f(zr[k], zi[k], dr[k], di[k], tau)) { a = 0; b = k; }
+    if (n % k == 0 && newton_small_f(zr[k], zi[k], dr[k], di[k], tau2)) { a = 0; b = k; }
   for (int k = 1; k <= n && a < 0; ++k) {
-    if (n % k || !newton_small_f(zr[l + k] - zr[l], zi[l + k] - zi[l], dr[l + k] - dr[l], di[l + k] - di[l], tau))
+    if (n % k || !newton_small_f(zr[l + k] - zr[l], zi[l + k] - zi[l], dr[l + k] - dr[l], di[l + k] - di[l], tau2))
       continue;
     for (int j = 2; j <= l; ++j)
-      if (newton_small_f(zr[j + k] - zr[j], zi[j + k] - zi[j], dr[j + k] - dr[j], di[j + k] - di[j], tau)) {
+      if (newton_small_f(zr[j + k] - zr[j], zi[j + k] - zi[j], dr[j + k] - dr[j], di[j + k] - di[j], tau2)) {
         a = j;
         b = k;
         break;
@@ -199,7 +211,7 @@ cudaError_t launch_type_q(const PolyDev& P, const double2* roots, int64_t count,
                           uint8_t* per, uint8_t* mult, cudaStream_t s) {
   if (count <= 0 || P.l + P.n > 40) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_type_q<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, roots, count, tau, pre, per, mult);
+  k_type_q<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, roots, count, tau2_of(tau), pre, per, mult);
   return cudaGetLastError();
 }
 
@@ -207,7 +219,7 @@ cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t cou
                              uint8_t* type, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_type_only<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, roots, count, tau, type);
+  k_type_only<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, roots, count, tau2_of(tau), type);
   return cudaGetLastError();
 }
 
@@ -282,7 +294,7 @@ __device__ __forceinline__ float abs_lb_f(float x, float y) {
 template <bool TYPE = false>
 __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double cy, float rc,
                                             double& Vx, double& Vy, float& rv0, float& Wx,
-                                            float& Wy, float& rw, double tau = 0.0, int* hyp = nullptr) {
+                                            float& Wy, float& rw, float tau2 = 0.f, int* hyp = nullptr) {
   double zx = 0.0, zy = 0.0, czx = 0.0, czy = 0.0;
   float dx = 0.f, dy = 0.f, cdx = 0.f, cdy = 0.f;
   float rz0 = 0.f, rz = 0.f, rd = 0.f;  // radii: z (point), z (disk), z' (disk)
@@ -315,7 +327,7 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
     const float nrz = __fadd_ru(__fmaf_ru(rz, rz, __fmaf_ru(mz2, rz, Rz)), rc);
     zx = nz_x; zy = nz_y; dx = nd_x; dy = nd_y;
     rz0 = nrz0; rz = nrz; rd = nrd;
-    if (TYPE && !*hyp && (P.n % k) == 0 && newton_small_f(zx, zy, dx, dy, tau)) *hyp = k;
+    if (TYPE && !*hyp && (P.n % k) == 0 && newton_small_f(zx, zy, dx, dy, tau2)) *hyp = k;
     if (k == P.lcap) { czx = zx; czy = zy; cdx = dx; cdy = dy; crz0 = rz0; crd = rd; }
   }
   if (P.lcap >= 0) {  // s_{l,n} = p_m + p_{l-1}, q_{l,n} = p_m - p_l: one disk sum each
@@ -331,6 +343,41 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
   Wx = dx; Wy = dy; rw = rd;
 }
 
+// The radius r = min(tol, 0.45 nn), nn the distance to the nearest other
+// root or conjugate, kept as a binary32 lower bound: tol32 is the largest
+// binary32 <= tol (host), the binary32 literals 0.45f and 0.9f lie below
+// 0.45 and 0.9, and every step rounds down.  Two neighbours' radii then add
+// to at most 0.9 of their binary64 distance, whose rounding (relative
+// 2^-51) cannot close the gap, so passing disks stay disjoint.  The scan
+// over the Re-sorted list stops at the first point with |Re dv| >= W, W >=
+// tol / 0.45 (host, rounded up); |dx| >= W is an integer compare of the
+// binary64 bit patterns (both non-negative), and only the rare points inside
+// the window reach the binary64 distance.
+__device__ __forceinline__ float rad_conj(double cy) {  // 0.45 |c - conj(c)| = 0.9 |Im c|
+  return __fmul_rd(0.9f, fabsf(f32_trunc(cy)));
+}
+__device__ __forceinline__ float rad_near(double d2) {  // 0.45 sqrt(d2)
+  return __fmul_rd(0.45f, __fsqrt_rd(f32_trunc(d2)));
+}
+__device__ __forceinline__ bool outside_window(double dx, long long Wbits) {
+  return (__double_as_longlong(dx) & 0x7fffffffffffffffll) >= Wbits;
+}
+struct RadCap {
+  float tol32;     // largest binary32 <= tol
+  long long Wbits; // bits of W >= tol / 0.45
+};
+static RadCap rad_cap_of(double tol) {
+  RadCap r;
+  float t = (float)tol;
+  if ((double)t > tol) t = std::nextafter(t, 0.f);
+  r.tol32 = t;
+  const double W = std::nextafter(tol / 0.45, std::numeric_limits<double>::infinity());
+  std::memcpy(&r.Wbits, &W, sizeof W);
+  return r;
+}
+// radii at least 2^-126 (normal binary32) are reported exactly in binary64
+#define MT_RAD_MIN 1.17549435e-38f
+
 // Certify the points of 'pts' (sorted by Re through 'order', or already
 // sorted when order == nullptr).  upper: the list holds one representative
 // per conjugate pair, so conjugates count as neighbours too.
@@ -338,13 +385,13 @@ __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double 
 // simple root of p_n, and is proven as a root of p_n; the others as roots of q.
 __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
                           const uint32_t* __restrict__ order, const unsigned long long* n_pts_dev,
-                          int64_t n_pts_host, double tol, int upper, const uint32_t* __restrict__ mult,
+                          int64_t n_pts_host, RadCap rc, int upper, const uint32_t* __restrict__ mult,
                           uint8_t* __restrict__ pass, double* __restrict__ radius,
                           DevCounters* ctr, SegView sv, const uint8_t* __restrict__ type) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = n_pts_dev ? (int64_t)*n_pts_dev : n_pts_host;
   unsigned long long npass = 0, overflow = 0;
-  double rad = 0.0;
+  double radd = 0.0;
   bool ok = false, valid = p < n;
   if (valid) {
     const int64_t ip = order ? (int64_t)order[p] : p;
@@ -356,53 +403,49 @@ __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
       P.m = P.n;
       P.lcap = -1;
     }
-    // nearest neighbour (and conjugates) within the window W = tol / 0.45
-    const double W = tol / 0.45;
-    double nn2 = W * W;
-    if (upper && c.y != 0.0) nn2 = fmin(nn2, 4.0 * c.y * c.y);
+    // nearest neighbour (and conjugates) within the window W
+    float rad = rc.tol32;
+    if (upper && c.y != 0.0) rad = fminf(rad, rad_conj(c.y));
     int scanned = 0;
     for (int dir = -1; dir <= 1; dir += 2) {
       for (int64_t q = p + dir; q >= 0 && q < n; q += dir) {
         if (sv.rep_seg && sv.rep_seg[q] != sg) break;  // another polynomial of the batch
         const double2 v = pts[order ? (int64_t)order[q] : q];
         const double dx = v.x - c.x;
-        if (fabs(dx) >= W) break;
+        if (outside_window(dx, rc.Wbits)) break;
         const double dy = v.y - c.y;
-        nn2 = fmin(nn2, fma(dx, dx, dy * dy));
+        double d2 = fma(dx, dx, dy * dy);
         if (upper) {
           const double ey = v.y + c.y;
-          nn2 = fmin(nn2, fma(dx, dx, ey * ey));
+          d2 = fmin(d2, fma(dx, dx, ey * ey));
         }
+        rad = fminf(rad, rad_near(d2));
         if (++scanned >= 4096) { overflow = 1; break; }
       }
     }
-    rad = fmin(tol, 0.45 * sqrt(nn2));
     // sup |P(c)| from the point orbit, B' = D(W, rw) encloses P'(D(c, rad)).
     // Between two close roots the critical point sits about half-way, so a
     // disk of 0.45 nn may bring 0 into B'; then retry with rad / 4, / 16, / 64
     // (any passing radius proves the root; the disks stay disjoint).
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
-      if (attempt) rad *= 0.25;  // exact
-      // the disk radius must be >= rad: round the binary32 copy upward
-      const float radu = __double2float_ru(rad), radd = __double2float_rd(rad);
+      if (attempt) rad = __fmul_rd(rad, 0.25f);
       double Vx, Vy;
       float rv0, Wx, Wy, rw;
-      disk_orbit2(P, c.x, c.y, radu, Vx, Vy, rv0, Wx, Wy, rw);
+      disk_orbit2(P, c.x, c.y, rad, Vx, Vy, rv0, Wx, Wy, rw);
       const float fz = __fadd_ru(abs_ub(Vx, Vy), rv0);
       const float dist = __fsub_rd(abs_lb_f(Wx, Wy), rw);
-      // any radius in [radd, radu] is proven: report the lower one
-      ok = isfinite(fz) && isfinite(dist) && dist > 0.f && radd > 0.f && __fmul_rd(radd, dist) > fz;
-      if (ok) rad = (double)radd;
+      ok = isfinite(fz) && isfinite(dist) && dist > 0.f && rad >= MT_RAD_MIN && __fmul_rd(rad, dist) > fz;
     }
+    radd = f64_of_f32(rad);
     pass[ip] = ok ? 1 : 0;
-    if (radius) radius[ip] = rad;
+    if (radius) radius[ip] = radd;
     npass = ok ? (mult ? mult[p] : 1u) : 0u;
     if (sv.pstat && npass) atomicAdd(&sv.pstat[(size_t)sg * PSTAT_W + 3], npass);
   }
   warp_add_u64(&ctr->n_cert_pass, npass);
   if (overflow) atomicAdd(&ctr->cluster_overflow, 1ull);
   // radii are >= 0: their bit patterns order like the values
-  const unsigned long long rb = (unsigned long long)__double_as_longlong(rad);
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(radd);
   warp_min_u64(&ctr->min_radius_bits, (valid && ok) ? rb : ~0ull);
   warp_max_u64(&ctr->max_radius_bits, (valid && ok) ? rb : 0ull);
 }
@@ -415,7 +458,7 @@ __global__ void k_certify(PolyDev P0, const double2* __restrict__ pts,
 // root set made exact.  Writes what k_classify and k_certify write: type,
 // mult, pass, radius and the counters; one orbit pass per root fewer.
 __global__ void k_certify_typed(PolyDev P, const double2* __restrict__ pts, const unsigned long long* n_pts_dev,
-                                int64_t cap, double tol, double tau, uint8_t* __restrict__ type,
+                                int64_t cap, RadCap rc, float tau2, uint8_t* __restrict__ type,
                                 uint32_t* __restrict__ mult, uint8_t* __restrict__ pass,
                                 double* __restrict__ radius, DevCounters* ctr) {
   __shared__ unsigned int hist[64];
@@ -424,40 +467,39 @@ __global__ void k_certify_typed(PolyDev P, const double2* __restrict__ pts, cons
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n = (int64_t)*n_pts_dev;
   unsigned long long npass = 0, overflow = 0, nreal = 0, nmult = 0;
-  double rad = 0.0;
+  double radd = 0.0;
   bool ok = false;
   const bool valid = p < n && p < cap;
   if (valid) {
     const double2 c = pts[p];
-    const unsigned m = (c.y == 0.0) ? 1u : 2u;
-    const double W = tol / 0.45;
-    double nn2 = W * W;
-    if (c.y != 0.0) nn2 = fmin(nn2, 4.0 * c.y * c.y);
+    // Im c = 0 tested on the bits (+0 or -0)
+    const bool real = (__double_as_longlong(c.y) << 1) == 0;
+    const unsigned m = real ? 1u : 2u;
+    float rad = rc.tol32;
+    if (!real) rad = fminf(rad, rad_conj(c.y));
     int scanned = 0;
     for (int dir = -1; dir <= 1; dir += 2) {
       for (int64_t q = p + dir; q >= 0 && q < n; q += dir) {
         const double2 v = pts[q];
         const double dx = v.x - c.x;
-        if (fabs(dx) >= W) break;
+        if (outside_window(dx, rc.Wbits)) break;
         const double dy = v.y - c.y, ey = v.y + c.y;
-        nn2 = fmin(nn2, fmin(fma(dx, dx, dy * dy), fma(dx, dx, ey * ey)));
+        rad = fminf(rad, rad_near(fmin(fma(dx, dx, dy * dy), fma(dx, dx, ey * ey))));
         if (++scanned >= 4096) { overflow = 1; break; }
       }
     }
-    rad = fmin(tol, 0.45 * sqrt(nn2));
     int hyp = 0;
     for (int attempt = 0; attempt < 4 && !ok; ++attempt) {
-      if (attempt) rad *= 0.25;  // exact
-      const float radu = __double2float_ru(rad), radd = __double2float_rd(rad);
+      if (attempt) rad = __fmul_rd(rad, 0.25f);
       double Vx, Vy;
       float rv0, Wx, Wy, rw;
-      if (attempt == 0) disk_orbit2<true>(P, c.x, c.y, radu, Vx, Vy, rv0, Wx, Wy, rw, tau, &hyp);
-      else disk_orbit2<false>(P, c.x, c.y, radu, Vx, Vy, rv0, Wx, Wy, rw);
+      if (attempt == 0) disk_orbit2<true>(P, c.x, c.y, rad, Vx, Vy, rv0, Wx, Wy, rw, tau2, &hyp);
+      else disk_orbit2<false>(P, c.x, c.y, rad, Vx, Vy, rv0, Wx, Wy, rw);
       const float fz = __fadd_ru(abs_ub(Vx, Vy), rv0);
       const float dist = __fsub_rd(abs_lb_f(Wx, Wy), rw);
-      ok = isfinite(fz) && isfinite(dist) && dist > 0.f && radd > 0.f && __fmul_rd(radd, dist) > fz;
-      if (ok) rad = (double)radd;
+      ok = isfinite(fz) && isfinite(dist) && dist > 0.f && rad >= MT_RAD_MIN && __fmul_rd(rad, dist) > fz;
     }
+    radd = f64_of_f32(rad);
     const int t = hyp ? hyp : 255;
     type[p] = (uint8_t)t;
     mult[p] = m;
@@ -465,7 +507,7 @@ __global__ void k_certify_typed(PolyDev P, const double2* __restrict__ pts, cons
     nmult += m;
     if (t < 64) atomicAdd(&hist[t], m);
     pass[p] = ok ? 1 : 0;
-    if (radius) radius[p] = rad;
+    if (radius) radius[p] = radd;
     npass = ok ? m : 0u;
   } else if (p < cap) {
     mult[p] = 0;
@@ -474,7 +516,7 @@ __global__ void k_certify_typed(PolyDev P, const double2* __restrict__ pts, cons
   warp_add_u64(&ctr->n_reps_real, nreal);
   warp_add_u64(&ctr->n_mult_full, nmult);
   if (overflow) atomicAdd(&ctr->cluster_overflow, 1ull);
-  const unsigned long long rb = (unsigned long long)__double_as_longlong(rad);
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(radd);
   warp_min_u64(&ctr->min_radius_bits, (valid && ok) ? rb : ~0ull);
   warp_max_u64(&ctr->max_radius_bits, (valid && ok) ? rb : 0ull);
   __syncthreads();
@@ -488,8 +530,8 @@ cudaError_t launch_certify_typed(const PolyDev& P, const double2* reps, const un
   if (cap <= 0) return cudaSuccess;
   if (P.kind != 0) return cudaErrorInvalidValue;
   MT_COUNT_LAUNCH(1);
-  k_certify_typed<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, n_reps, cap, tol, tau, type, mult,
-                                                                 pass, radius, ctr);
+  k_certify_typed<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, n_reps, cap, rad_cap_of(tol),
+                                                                 tau2_of(tau), type, mult, pass, radius, ctr);
   return cudaGetLastError();
 }
 
@@ -568,8 +610,8 @@ cudaError_t launch_certify(const PolyDev& P, const double2* reps, const unsigned
                            const uint8_t* type) {
   if (cap <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_certify<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, nullptr, n_reps, cap, tol, 1,
-                                                          mult, pass, radius, ctr, sv, type);
+  k_certify<<<(unsigned)((cap + 127) / 128), 128, 0, s>>>(P, reps, nullptr, n_reps, cap, rad_cap_of(tol),
+                                                          1, mult, pass, radius, ctr, sv, type);
   return cudaGetLastError();
 }
 
@@ -579,8 +621,9 @@ cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint
                                 DevCounters* ctr, cudaStream_t s, const uint8_t* type) {
   if (count <= 0) return cudaSuccess;
   MT_COUNT_LAUNCH(1);
-  k_certify<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, pts, order, nullptr, count, tol, 0,
-                                                            nullptr, pass, radius, ctr, SegView(), type);
+  k_certify<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(P, pts, order, nullptr, count,
+                                                            rad_cap_of(tol), 0, nullptr, pass, radius, ctr,
+                                                            SegView(), type);
   return cudaGetLastError();
 }
 

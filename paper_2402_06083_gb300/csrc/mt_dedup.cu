@@ -218,10 +218,30 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort, 8-bit digits, stable.
+// LSD radix sort, 8-bit digits, stable, bound by HBM traffic (a pass reads
+// each key once for the counts, then reads and writes key and value: 32
+// bytes per element for 64-bit keys and 32-bit values).
+//
+// A pass is three launches over one persistent grid of G blocks.  Block b
+// owns the contiguous tiles [nt b / G, nt (b+1) / G) of the nt tiles of
+// RS_TILE elements.  k_rs_hist counts the digits of each block's range;
+// k_rs_offsets scans those counts digit-major (digit d of block b starts
+// after every smaller digit and after digit d of blocks before b); the
+// scatter then walks its range tile by tile, carrying per-digit output
+// positions, so the order within a digit is the input order (stability).
+// Inside a tile, warp w holds elements [256 w, 256 w + 256) of it, item k of
+// lane j being element 256 w + 32 k + j: loads coalesce per item, and the
+// rank of an element among its digit is counted within its warp (a running
+// count per digit and warp in shared memory) plus the counts of the warps
+// before it.  The tile is then staged in shared memory in digit order and
+// written out with consecutive threads on consecutive addresses of a digit's
+// run.  The next tile's keys and values are loaded into registers while the
+// current one is ranked and written.
 constexpr int RS_BS = 256;
+constexpr int RS_WARPS = RS_BS / 32;
 constexpr int RS_ITEMS = 8;
 constexpr int64_t RS_TILE = (int64_t)RS_BS * RS_ITEMS;
+constexpr int RS_GRID_MAX = 2048;
 
 // n_dev: NULL, or the number of entries on the device (at most n)
 __device__ __forceinline__ int64_t rs_count(int64_t n, const unsigned long long* n_dev) {
@@ -230,49 +250,88 @@ __device__ __forceinline__ int64_t rs_count(int64_t n, const unsigned long long*
   return d < n ? d : n;
 }
 
-__global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n,
-                                                   int shift, uint32_t* __restrict__ hist,
-                                                   int64_t nb, const unsigned long long* __restrict__ n_dev) {
-  __shared__ uint32_t cnt[256];
-  n = rs_count(n, n_dev);
-  cnt[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  for (int k = 0; k < RS_ITEMS; ++k) {
-    const int64_t i = base + (int64_t)k * RS_BS + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];  // digit-major
+// block b's tiles [t0, t1) of the ceil(n / RS_TILE) tiles
+__device__ __forceinline__ void rs_range(int64_t n, int64_t& t0, int64_t& t1) {
+  const int64_t nt = (n + RS_TILE - 1) / RS_TILE;
+  t0 = nt * blockIdx.x / gridDim.x;
+  t1 = nt * (blockIdx.x + 1) / gridDim.x;
 }
 
-// One pass of the scatter.  The tile's elements are first placed in shared
-// memory in digit order (stable: sub-tile by sub-tile, warp by warp, lane by
-// lane, as the global order requires), then written out in that order, so
-// that consecutive threads write consecutive addresses of one digit's run
-// and the global stores coalesce.  hist: the tiles' digit counts (digit-
-// major), offs: their exclusive scan, the tile's first output position for
-// each digit.
-__global__ void __launch_bounds__(RS_BS) k_rs_scatter(const uint64_t* __restrict__ kin,
-                                                      const uint32_t* __restrict__ vin,
-                                                      uint64_t* __restrict__ kout,
-                                                      uint32_t* __restrict__ vout, int64_t n,
-                                                      int shift, const uint32_t* __restrict__ offs,
-                                                      const uint32_t* __restrict__ hist,
-                                                      int64_t nb, const unsigned long long* __restrict__ n_dev) {
-  __shared__ uint64_t sk[RS_TILE];
-  __shared__ uint32_t sv[RS_TILE];
-  __shared__ uint32_t gbase[256];  // output position of the tile's first element of digit d
-  __shared__ uint32_t lbase[256];  // position in the staged tile of its first element of digit d
-  __shared__ uint32_t run[256];    // elements of digit d staged by the earlier sub-tiles
-  __shared__ uint32_t tot[256];
-  __shared__ uint32_t wsum[RS_BS / 32];
-  __shared__ uint32_t wcnt[RS_BS / 32][256];
+__global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n,
+                                                   int shift, uint32_t* __restrict__ hist,
+                                                   const unsigned long long* __restrict__ n_dev) {
+  __shared__ uint32_t cnt[256];
   n = rs_count(n, n_dev);
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  gbase[t] = offs[(int64_t)t * nb + blockIdx.x];
-  {  // exclusive scan over the digits of the tile's counts
-    const uint32_t c = hist[(int64_t)t * nb + blockIdx.x];
+  cnt[t] = 0;
+  __syncthreads();
+  int64_t t0, t1;
+  rs_range(n, t0, t1);
+  for (int64_t tl = t0; tl < t1; ++tl) {
+    const int64_t base = tl * RS_TILE + w * (RS_ITEMS * 32) + lane;
+    unsigned dg[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      const int64_t i = base + k * 32;
+      dg[k] = i < n ? (unsigned)(keys[i] >> shift) & 255u : 256u;
+    }
+    // lanes of a warp that share a digit add once (high digits repeat)
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      const unsigned peers = __match_any_sync(0xffffffffu, dg[k]);
+      if (dg[k] < 256u && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[dg[k]], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  hist[(int64_t)t * gridDim.x + blockIdx.x] = cnt[t];  // digit-major
+}
+
+// per digit d (block d): exclusive scan of the G block counts of d into
+// offs[d][.], and their total into tot[d]; the scatter adds the digit's base
+// (the totals of the smaller digits).  G <= RS_GRID_MAX = 2 * blockDim.x.
+__global__ void k_rs_offsets(const uint32_t* __restrict__ hist, uint32_t* __restrict__ offs,
+                             uint32_t* __restrict__ tot, int G) {
+  __shared__ unsigned long long sh[32];
+  const int64_t row = (int64_t)blockIdx.x * G;
+  const int b0 = 2 * threadIdx.x;
+  const uint32_t c0 = b0 < G ? hist[row + b0] : 0u;
+  const uint32_t c1 = b0 + 1 < G ? hist[row + b0 + 1] : 0u;
+  unsigned long long total;
+  const unsigned long long off = block_excl_scan_u64((unsigned long long)c0 + c1, sh, &total);
+  if (b0 < G) offs[row + b0] = (uint32_t)off;
+  if (b0 + 1 < G) offs[row + b0 + 1] = (uint32_t)(off + c0);
+  if (threadIdx.x == 0) tot[blockIdx.x] = (uint32_t)total;
+}
+
+__device__ __forceinline__ void rs_load(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                        int64_t base, int64_t n, uint64_t* key, uint32_t* val) {
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int64_t i = base + k * 32;
+    key[k] = i < n ? kin[i] : 0ull;
+    val[k] = i < n ? vin[i] : 0u;
+  }
+}
+
+__global__ void __launch_bounds__(RS_BS, 3) k_rs_scatter(const uint64_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin,
+                                                         uint64_t* __restrict__ kout,
+                                                         uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                         const uint32_t* __restrict__ offs,
+                                                         const uint32_t* __restrict__ dtot,
+                                                         const unsigned long long* __restrict__ n_dev) {
+  __shared__ uint64_t sk[RS_TILE];
+  __shared__ uint32_t sv[RS_TILE];
+  __shared__ uint32_t wc[RS_WARPS][256];  // per warp: running count, then the warps-before prefix
+  __shared__ uint32_t lbase[256];         // staged position of the tile's first element of digit d
+  __shared__ uint32_t gpos[256];          // output position of the next element of digit d
+  __shared__ uint32_t wsum[RS_WARPS];
+  n = rs_count(n, n_dev);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  int64_t t0, t1;
+  rs_range(n, t0, t1);
+  {  // digit t starts after the smaller digits' totals and digit t of the blocks before
+    const uint32_t c = dtot[t];
     uint32_t x = c;
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -282,121 +341,157 @@ __global__ void __launch_bounds__(RS_BS) k_rs_scatter(const uint64_t* __restrict
     __syncthreads();
     uint32_t before = 0;
     for (int q = 0; q < w; ++q) before += wsum[q];
-    lbase[t] = before + x - c;
-    run[t] = 0;
+    gpos[t] = before + x - c + offs[(int64_t)t * gridDim.x + blockIdx.x];
   }
-  const int64_t tile = (int64_t)blockIdx.x * RS_TILE;
-  for (int k = 0; k < RS_ITEMS; ++k) {
+  uint64_t key[RS_ITEMS];
+  uint32_t val[RS_ITEMS];
+  const int64_t wl = w * (RS_ITEMS * 32) + lane;  // the thread's first element within a tile
+  if (t0 < t1) rs_load(kin, vin, t0 * RS_TILE + wl, n, key, val);
+  for (int64_t tl = t0; tl < t1; ++tl) {
+    uint64_t nkey[RS_ITEMS];
+    uint32_t nval[RS_ITEMS];
+    if (tl + 1 < t1) rs_load(kin, vin, (tl + 1) * RS_TILE + wl, n, nkey, nval);
 #pragma unroll
-    for (int q = 0; q < RS_BS / 32; ++q) wcnt[q][t] = 0;
-    __syncthreads();
-    const int64_t i = tile + (int64_t)k * RS_BS + t;
-    const bool valid = i < n;
-    uint64_t key = 0;
-    uint32_t val = 0;
-    unsigned digit = 256;
-    if (valid) {
-      key = kin[i];
-      val = vin[i];
-      digit = (unsigned)(key >> shift) & 255u;
+    for (int q = 0; q < 256 / 32; ++q) wc[w][lane + 32 * q] = 0;
+    __syncwarp();
+    const int64_t base = tl * RS_TILE + wl;
+    unsigned dg[RS_ITEMS], rk[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      const bool valid = base + k * 32 < n;
+      dg[k] = valid ? (unsigned)(key[k] >> shift) & 255u : 256u;
+      const unsigned peers = __match_any_sync(0xffffffffu, dg[k]);
+      const unsigned lt = __popc(peers & lanemask_lt());
+      const uint32_t before = valid ? wc[w][dg[k]] : 0u;
+      __syncwarp();
+      if (valid && lt == 0) wc[w][dg[k]] = before + __popc(peers);
+      __syncwarp();
+      rk[k] = before + lt;
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, digit);
-    const unsigned rank = __popc(peers & lanemask_lt());
-    if (valid && rank == 0) wcnt[w][digit] = __popc(peers);
     __syncthreads();
-    {  // thread t owns digit t: exclusive prefix over warps
-      uint32_t r = 0;
+    // thread t owns digit t: prefix over the warps, and the tile's count r
+    uint32_t r = 0;
 #pragma unroll
-      for (int q = 0; q < RS_BS / 32; ++q) {
-        const uint32_t c = wcnt[q][t];
-        wcnt[q][t] = r;
-        r += c;
+    for (int q = 0; q < RS_WARPS; ++q) {
+      const uint32_t c = wc[q][t];
+      wc[q][t] = r;
+      r += c;
+    }
+    {  // exclusive scan of the counts over the digits
+      uint32_t x = r;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      tot[t] = r;
+      if (lane == 31) wsum[w] = x;
+      __syncthreads();
+      uint32_t before = 0;
+      for (int q = 0; q < w; ++q) before += wsum[q];
+      lbase[t] = before + x - r;
     }
     __syncthreads();
-    if (valid) {
-      const uint32_t p = lbase[digit] + run[digit] + wcnt[w][digit] + rank;
-      sk[p] = key;
-      sv[p] = val;
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      if (dg[k] < 256u) {
+        const uint32_t p = lbase[dg[k]] + wc[w][dg[k]] + rk[k];
+        sk[p] = key[k];
+        sv[p] = val[k];
+      }
     }
     __syncthreads();
-    run[t] += tot[t];
-  }
-  __syncthreads();
-  const int64_t cnt = (n - tile) < RS_TILE ? (n - tile) : RS_TILE;
-  for (int k = 0; k < RS_ITEMS; ++k) {
-    const int j = k * RS_BS + t;
-    if (j < cnt) {
-      const uint64_t key = sk[j];
-      const unsigned d = (unsigned)(key >> shift) & 255u;
-      const uint32_t pos = gbase[d] + (uint32_t)j - lbase[d];
-      kout[pos] = key;
-      vout[pos] = sv[j];
+    const int64_t cnt = (n - tl * RS_TILE) < RS_TILE ? (n - tl * RS_TILE) : RS_TILE;
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      const int j = k * RS_BS + t;
+      if (j < cnt) {
+        const uint64_t kk = sk[j];
+        const unsigned d = (unsigned)(kk >> shift) & 255u;
+        const uint32_t pos = gpos[d] + (uint32_t)j - lbase[d];
+        kout[pos] = kk;
+        vout[pos] = sv[j];
+      }
+    }
+    __syncthreads();
+    gpos[t] += r;
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+      key[k] = nkey[k];
+      val[k] = nval[k];
     }
   }
 }
 
+// blocks of the persistent grid: as many as are resident at once, at most
+// one per tile and RS_GRID_MAX
+static int64_t rs_grid(int64_t n) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rs_scatter, RS_BS, 0) != cudaSuccess || b < 1) b = 1;
+    per_sm = b;
+  }
+  const int64_t nt = (n + RS_TILE - 1) / RS_TILE;
+  return std::max<int64_t>(1, std::min<int64_t>({nt, (int64_t)device_sm_count() * per_sm, (int64_t)RS_GRID_MAX}));
+}
+
 size_t radix_temp_bytes(int64_t n) {
-  const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
-  const int64_t nh = 256 * nb;
-  return (size_t)nh * 2 * sizeof(uint32_t) + scan_temp_bytes(nh) + 256;
+  const int64_t nt = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t nh = 256 * std::max<int64_t>(1, std::min<int64_t>(nt, RS_GRID_MAX));
+  return (size_t)nh * 2 * sizeof(uint32_t) + 256 * sizeof(uint32_t);
+}
+
+// one pass: digit [shift, shift + 8) from (k0, v0) to (k1, v1)
+static cudaError_t rs_pass(const uint64_t* k0, const uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
+                           int shift, void* temp, const unsigned long long* n_dev, cudaStream_t s) {
+  const int64_t G = rs_grid(n);
+  const int64_t nh = 256 * G;
+  uint32_t* hist = (uint32_t*)temp;
+  uint32_t* offs = hist + nh;
+  uint32_t* dtot = offs + nh;
+  MT_COUNT_LAUNCH(1);
+  k_rs_hist<<<(unsigned)G, RS_BS, 0, s>>>(k0, n, shift, hist, n_dev);
+  MT_COUNT_LAUNCH(1);
+  k_rs_offsets<<<256, RS_GRID_MAX / 2, 0, s>>>(hist, offs, dtot, (int)G);
+  MT_COUNT_LAUNCH(1);
+  k_rs_scatter<<<(unsigned)G, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, dtot, n_dev);
+  return cudaGetLastError();
 }
 
 cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                             int64_t n, void* temp, int begin_bit, int end_bit, bool* in_alt,
                             cudaStream_t s) {
-  const unsigned long long* n_dev = nullptr;
   *in_alt = false;
   if (n <= 1) return cudaSuccess;
-  const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
-  const int64_t nh = 256 * nb;
-  uint32_t* hist = (uint32_t*)temp;
-  uint32_t* offs = hist + nh;
-  void* stemp = (void*)(offs + nh);
   uint64_t* k0 = keys;
   uint32_t* v0 = vals;
   uint64_t* k1 = keys_alt;
   uint32_t* v1 = vals_alt;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
-    MT_COUNT_LAUNCH(1);
-    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb, n_dev);
-    cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
+    cudaError_t e = rs_pass(k0, v0, k1, v1, n, shift, temp, nullptr, s);
     if (e != cudaSuccess) return e;
-    MT_COUNT_LAUNCH(1);
-    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, hist, nb, n_dev);
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
     *in_alt = !*in_alt;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, void* temp, cudaStream_t s,
                              const unsigned long long* n_dev) {
   if (n <= 1) return cudaSuccess;
-  const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
-  const int64_t nh = 256 * nb;
-  uint32_t* hist = (uint32_t*)temp;
-  uint32_t* offs = hist + nh;
-  void* stemp = (void*)(offs + nh);
   uint64_t* k0 = keys;
   uint32_t* v0 = vals;
   uint64_t* k1 = keys_alt;
   uint32_t* v1 = vals_alt;
   for (int shift = 0; shift < 64; shift += 8) {
-    MT_COUNT_LAUNCH(1);
-    k_rs_hist<<<(unsigned)nb, RS_BS, 0, s>>>(k0, n, shift, hist, nb, n_dev);
-    cudaError_t e = launch_exclusive_scan(hist, offs, nh, stemp, nullptr, s);
+    cudaError_t e = rs_pass(k0, v0, k1, v1, n, shift, temp, n_dev, s);
     if (e != cudaSuccess) return e;
-    MT_COUNT_LAUNCH(1);
-    k_rs_scatter<<<(unsigned)nb, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, hist, nb, n_dev);
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
   }
   // 8 passes: the result is back in (keys, vals)
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
