@@ -31,7 +31,7 @@
 namespace mt {
 
 constexpr int MIX_MAXM = 41;
-constexpr int64_t MIX_BATCH = int64_t(1) << 23;  // starts per anchor batch
+constexpr int64_t MIX_BATCH = int64_t(1) << 23;  // starts per launch of the binary32 descent
 
 // Float-float (binary32 pair) arithmetic from the published error-free
 // transforms: Knuth's TwoSum, Dekker's FastTwoSum and the FMA-based TwoProd.
@@ -340,47 +340,50 @@ WalkMixedFn walk_mixed_kernel(const PolyDev& P) {
   return f ? f : &k_walk_mixed<false, 0>;
 }
 
-// a4 in the mixed tier, anchors: for starts [base, base + cnt), the
-// reference orbit of each start in float-float, rounded to binary32 and
-// stored start-major (anch[i (m - 1) + k - 1] = Z_k, k = 1 .. m-1), plus
-// P(start) as binary32 hi + lo and the long-jump bound on |delta|.  The
-// block stages its orbits in shared memory and writes its contiguous run of
-// rows with consecutive threads (coalesced); the descent copies one orbit
-// with consecutive lanes.  The anchor only steers the binary32 descent into
-// the basin of its root (the binary64 finish sets the digits), so
-// float-float's ~1e-14 suffices and keeps this off the binary64 pipe.  A
-// uniform launch: computed inside the persistent descent, the orbit of one
-// refilling lane would be issued by its whole warp at nearly every step.
-__global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, int64_t base,
-                                int64_t cnt, float2* __restrict__ anch, float4* __restrict__ vv,
-                                float* __restrict__ rdel) {
-  extern __shared__ float2 stage[];  // [blockDim.x][m - 1]
-  const int m1 = P.m - 1;
-  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
-  const int64_t i = i0 + threadIdx.x;
-  if (i < cnt) {
-    const double2 c0 = starts[base + i];
-    const ff cx = ff_from(c0.x), cy = ff_from(c0.y);
-    ff zx{0.f, 0.f}, zy{0.f, 0.f}, capx{0.f, 0.f}, capy{0.f, 0.f};
-    float2* row = stage + threadIdx.x * m1;
-    for (int k = 1; k <= P.m; ++k) {
-      const ff nx = ff_add(ff_add(ff_mul(zx, zx), ff_neg(ff_mul(zy, zy))), cx);
-      const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
-      zx = nx;
-      zy = ny;
-      if (k < P.m) row[k - 1] = make_float2(zx.hi, zy.hi);
-      if (k == P.lcap) { capx = zx; capy = zy; }
-    }
-    const ff vx = ff_add(zx, capx), vy = ff_add(zy, capy);
-    vv[i] = make_float4(vx.hi, vy.hi, vx.lo, vy.lo);
-    // long jump (as in k_descend: |c| > max(4, 2|c0|)); |delta| beyond rdel implies it
-    const float r0 = sqrtf(fmaf(cx.hi, cx.hi, cy.hi * cy.hi)) * 1.0001f;
-    rdel[i] = fmaxf(4.f, 2.f * r0) + r0;
+// a4 in the mixed tier, anchors: the reference orbit of a start c0 in
+// float-float, rounded to binary32 (Z_k, k = 1 .. m-1), plus P(c0) as
+// binary32 hi + lo and the long-jump bound on |delta|.  The anchor only
+// steers the binary32 descent into the basin of its root (the binary64
+// finish sets the digits), so float-float's ~1e-14 suffices and keeps this
+// off the binary64 pipe.  A warp computes the orbits of the 32 starts of a
+// queue range together, lane j the orbit of start g + j, into its own slot
+// of the buffer: Z_k of lane j at za[(k - 1) * 32 + j] (each store
+// instruction writes 256 contiguous bytes), P(c0) at zv[j], the bound at
+// zr[j].  The slots are small (32 orbits per warp) and are read back by the
+// same warp moments later, so they stay in L2.
+struct WarpSlot {
+  float2* za;  // [m - 1][32]
+  float4* zv;  // [32]
+  float* zr;   // [32]
+};
+__device__ __forceinline__ WarpSlot warp_slot(float2* wbuf, int m1, unsigned warp) {
+  const size_t per = (size_t)32 * m1 + 80;  // float2 units: anchors, 32 float4, 32 float
+  float2* b = wbuf + per * warp;
+  WarpSlot w;
+  w.za = b;
+  w.zv = (float4*)(b + (size_t)32 * m1);
+  w.zr = (float*)(b + (size_t)32 * m1 + 64);
+  return w;
+}
+template <bool CAP, int MC>
+__device__ __forceinline__ void anchor_orbit(const PolyDev& P, double2 c0, const WarpSlot& w, unsigned j) {
+  const int m = MC > 0 ? MC : P.m;
+  const ff cx = ff_from(c0.x), cy = ff_from(c0.y);
+  ff zx{0.f, 0.f}, zy{0.f, 0.f}, capx{0.f, 0.f}, capy{0.f, 0.f};
+#pragma unroll 4
+  for (int k = 1; k <= m; ++k) {
+    const ff nx = ff_add(ff_add(ff_mul(zx, zx), ff_neg(ff_mul(zy, zy))), cx);
+    const ff ny = ff_add(ff_twice(ff_mul(zx, zy)), cy);
+    zx = nx;
+    zy = ny;
+    if (k < m) w.za[(k - 1) * 32 + j] = make_float2(zx.hi, zy.hi);
+    if (CAP && k == P.lcap) { capx = zx; capy = zy; }
   }
-  __syncthreads();
-  const int64_t nv = (cnt - i0 < (int64_t)blockDim.x ? cnt - i0 : (int64_t)blockDim.x) * m1;
-  float2* dst = anch + i0 * m1;
-  for (int64_t t = threadIdx.x; t < nv; t += blockDim.x) dst[t] = stage[t];
+  const ff vx = ff_add(zx, capx), vy = ff_add(zy, capy);
+  w.zv[j] = make_float4(vx.hi, vy.hi, vx.lo, vy.lo);
+  // long jump (as in k_descend: |c| > max(4, 2|c0|)); |delta| beyond rdel implies it
+  const float r0 = sqrtf(fmaf(cx.hi, cx.hi, cy.hi * cy.hi)) * 1.0001f;
+  w.zr[j] = fmaxf(4.f, 2.f * r0) + r0;
 }
 
 // a4 in the mixed tier, binary32 phase (persistent, per-lane refill as in
@@ -389,25 +392,26 @@ __global__ void k_anchor_orbits(PolyDev P, const double2* __restrict__ starts, i
 // shared memory (row k - 1 holds Z_k of every lane; the row stride DM_BS + 1
 // is odd, so the rows of one column fall in different banks).  Lanes that
 // finished are refilled together once DM_REFILL of them wait (or none is
-// running): the warp takes their start indices from a warp-private range
-// of the work queue (one atomic per 32 starts), then copies each new orbit
-// (m - 1 consecutive anchors) with consecutive lanes, one refilled lane
-// after the other, so no refill runs a loop of loads on one or two lanes
-// while the others wait.  The Newton loop is binary32 only.  Each descent
-// runs binary32 Newton steps to the binary32 floor and leaves (delta, its
-// largest squared step) in pack[] with status 3 ("finish in binary64"), or
-// stops as divergent (1) / timed out (2).  The binary64 finish runs in
-// k_finish_f64, a separate uniform launch, once per root.  MC: the orbit
-// length when fixed at compile time (p_n), else 0.
-constexpr int DESC_POOL = 32;  // work indices taken per queue atomic
+// running): they take the next start indices of the warp's range of the
+// work queue, and a refilled lane copies its orbit from the warp's slot
+// into its column (m - 1 independent loads, L2 hits).  When the range runs
+// out the warp takes the next one (one atomic per 32 starts) and computes
+// its 32 anchor orbits with every lane (anchor_orbit): the orbits cost one
+// full-width pass per 32 starts and never travel through HBM.  The Newton
+// loop is binary32 only.  Each descent runs binary32 Newton steps to the
+// binary32 floor and leaves (delta, its largest squared step) in pack[]
+// with status 3 ("finish in binary64"), or stops as divergent (1) / timed
+// out (2).  The binary64 finish runs in k_finish_f64, a separate uniform
+// launch, once per root.  MC: the orbit length when fixed at compile time
+// (p_n), else 0.
+constexpr int DESC_POOL = 32;  // work indices taken per queue atomic (one per lane of a range)
 constexpr int DM_BS = 128;     // threads per block of the binary32 descent
 constexpr int DM_REFILL = 4;   // idle lanes that trigger a refill
+constexpr int DM_MAX_WARPS = 16384;  // warp slots of the anchor buffer (grids are capped to fit)
 
 template <bool CAP, int MC>
-__global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base, int64_t cnt,
-                                                         const float2* __restrict__ anch,
-                                                         const float4* __restrict__ vv,
-                                                         const float* __restrict__ rdel, int cap,
+__global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, const double2* __restrict__ starts,
+                                                         int64_t base, int64_t cnt, float2* wbuf, int cap,
                                                          float4* __restrict__ pack,
                                                          uint8_t* __restrict__ status,
                                                          unsigned* queue, DevCounters* ctr) {
@@ -415,79 +419,67 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
   constexpr int stride = DM_BS + 1;
   const float2* zs = zsh + threadIdx.x;  // row 0 (Z_1) of this lane's column
   const unsigned lane = threadIdx.x & 31;
-  const int wbase = threadIdx.x & ~31;
   const int m1 = (MC > 0 ? MC : P.m) - 1;
   const unsigned n = (unsigned)cnt;
+  const WarpSlot ws = warp_slot(wbuf, m1, (blockIdx.x * DM_BS + threadIdx.x) >> 5);
   unsigned idx = ~0u;  // this lane's start (~0u: none)
   float dx = 0.f, dy = 0.f, h1 = 0.f, prev2 = 0.f, rdelta = 0.f;
   float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
   int it = 0;
   unsigned long long s32 = 0, ndiv = 0, nto = 0;
-  unsigned pool_next = 0, pool_end = 0;  // the warp's range of queue indices (warp-uniform)
-  bool drained = false;                  // the queue is empty (warp-uniform)
-  // The warp takes its next range of queue indices one range ahead and
-  // prefetches that range's anchors into L2, so that the refills' loads
-  // (waited on before the next Newton step) find them there.
-  auto take_range = [&]() -> unsigned {
-    unsigned g = 0;
-    if (lane == 0) g = atomicAdd(queue, (unsigned)DESC_POOL);
-    g = __shfl_sync(0xffffffffu, g, 0);
-    const unsigned i = g + lane;
-    if (i < n) {
-      const char* a = (const char*)(anch + (size_t)i * m1);
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(a + 128));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(a + (size_t)(m1 > 0 ? m1 - 1 : 0) * sizeof(float2)));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(vv + i));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(rdel + i));
+  // the warp's range [pool_base, pool_base + 32) and its next unused index
+  // (warp-uniform; none taken yet: pool_next at the range's end)
+  unsigned pool_base = 0, pool_next = DESC_POOL;
+  bool drained = false;                   // the queue is empty (warp-uniform)
+  // a refilled lane with start i of the range in the slot: its orbit into
+  // its column, and the state of a new descent
+  auto take_orbit = [&](unsigned i) {
+    const unsigned j = i - pool_base;
+    float2* dst = zsh + threadIdx.x;
+    if (MC > 0) {
+#pragma unroll
+      for (int k = 0; k < (MC > 0 ? MC - 1 : 1); ++k) dst[k * stride] = ws.za[k * 32 + j];
+    } else {
+      for (int k = 0; k < m1; ++k) dst[k * stride] = ws.za[k * 32 + j];
     }
-    return g;
+    v = ws.zv[j];
+    rdelta = ws.zr[j];
+    dx = dy = 0.f;
+    it = 0;
+    prev2 = 0.f;
+    h1 = 0.f;
   };
-  unsigned ahead = take_range();  // the next range (warp-uniform)
   for (;;) {
     const unsigned need = drained ? 0u : __ballot_sync(0xffffffffu, idx == ~0u);
     const unsigned R = __popc(need);
     if (R >= DM_REFILL || (R == 32u && need)) {
-      // start index of the r-th lane that needs one: the warp's range, then the next one
-      const unsigned rem = pool_end - pool_next;
-      unsigned g = 0;
-      if (rem < R) {
-        g = ahead;
-        ahead = take_range();
-      }
+      // the r-th lane that needs a start takes the r-th unused index of the
+      // range, then of the next range
+      const bool mine = (need >> lane) & 1u;
       const unsigned r_me = __popc(need & lanemask_lt());
-      if (idx == ~0u) {
-        const unsigned j = r_me < rem ? pool_next + r_me : g + (r_me - rem);
-        idx = j < n ? j : n;  // n: the queue is drained (never refilled again)
+      const unsigned rem = pool_base + DESC_POOL - pool_next;
+      if (mine && r_me < rem) {
+        idx = pool_next + r_me;
+        if (idx < n) take_orbit(idx);
       }
-      if (rem < R) {
-        pool_next = g + (R - rem);
-        pool_end = g + DESC_POOL;
-      } else {
+      if (rem >= R) {
         pool_next += R;
-      }
-      // the new orbits, one refilled lane after the other, each copied by
-      // consecutive lanes from its m - 1 consecutive anchors
-      for (unsigned todo = need; todo; todo &= todo - 1) {
-        const int tl = __ffs(todo) - 1;
-        const unsigned ir = __shfl_sync(0xffffffffu, idx, tl);  // warp-uniform
-        if (ir >= n) {
-          drained = true;
-          continue;
+      } else {
+        __syncwarp();  // the copies above have read the slot
+        unsigned g = 0;
+        if (lane == 0) g = atomicAdd(queue, (unsigned)DESC_POOL);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g + lane < n) anchor_orbit<CAP, MC>(P, starts[base + g + lane], ws, lane);
+        __syncwarp();  // the slot is written before any lane reads it
+        pool_base = g;
+        pool_next = g + (R - rem);
+        if (mine && r_me >= rem) {
+          idx = g + (r_me - rem);
+          if (idx < n) take_orbit(idx);
         }
-        const float2* src = anch + (size_t)ir * m1;
-        float2* dst = zsh + wbase + tl;
-        for (int k = (int)lane; k < m1; k += 32) dst[k * stride] = src[k];
       }
-      __syncwarp();
-      if (((need >> lane) & 1u) && idx < n) {
-        v = vv[idx];
-        rdelta = rdel[idx];
-        dx = dy = 0.f;
-        it = 0;
-        prev2 = 0.f;
-        h1 = 0.f;
-      }
+      if (mine && idx >= n) idx = n;  // the queue is drained: never refilled again
+      if (__any_sync(0xffffffffu, mine && idx == n)) drained = true;
     }
     const bool active = idx < n;
     if (!__any_sync(0xffffffffu, active)) {
@@ -531,8 +523,8 @@ __global__ void __launch_bounds__(DM_BS) k_descend_mixed(PolyDev P, int64_t base
   warp_add_u64(&ctr->n_timeout, nto);
 }
 
-using DescMixedFn = void (*)(PolyDev, int64_t, int64_t, const float2*, const float4*, const float*, int, float4*,
-                             uint8_t*, unsigned*, DevCounters*);
+using DescMixedFn = void (*)(PolyDev, const double2*, int64_t, int64_t, float2*, int, float4*, uint8_t*,
+                             unsigned*, DevCounters*);
 
 // The instantiation for a polynomial: p_n with 16 <= n <= 33 has its orbit
 // length fixed at compile time; everything else runs the general loop.
@@ -880,14 +872,12 @@ cudaError_t launch_walk_mixed(const PolyDev& P, double lambda0, int M, int every
   return ktimer_end(s);
 }
 
-// Anchors are processed in batches of at most MIX_BATCH starts so their
-// buffer stays bounded.
+// The anchor buffer: one slot of 32 orbits per warp of the descent's grid
+// (at most DM_MAX_WARPS warps).
 size_t mixed_anchor_bytes(const PolyDev& P, int64_t count) {
-  const int64_t B = count < MIX_BATCH ? count : MIX_BATCH;
-  const int64_t b = B > 0 ? B : 1;
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  return al((size_t)b * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2)) + al((size_t)b * sizeof(float4)) +
-         al((size_t)b * sizeof(float)) + 256;
+  (void)count;
+  const int m1 = P.m > 1 ? P.m - 1 : 1;
+  return (size_t)DM_MAX_WARPS * ((size_t)32 * m1 + 80) * sizeof(float2) + 256;
 }
 
 cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t count, double tol, int cap,
@@ -897,7 +887,6 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   if (P.m > MIX_MAXM) return cudaErrorInvalidValue;
   const int bs = DM_BS;
   const size_t smem = (size_t)(P.m > 1 ? P.m - 1 : 1) * (bs + 1) * sizeof(float2);
-  const size_t asmem = (size_t)bs * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2);  // anchor staging
   const DescMixedFn kdesc = desc_mixed_kernel(P);
   cudaError_t e = cudaSuccess;
   if (smem > 48 * 1024 &&  // long orbits: opt in to more than 48 KB
@@ -907,28 +896,21 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kdesc, bs, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const int64_t B = count < MIX_BATCH ? count : MIX_BATCH;
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  char* a = (char*)anchors;
-  float2* anch = (float2*)a;
-  float4* vv = (float4*)(a + al((size_t)B * (P.m > 1 ? P.m - 1 : 1) * sizeof(float2)));
-  float* rdel = (float*)((char*)vv + al((size_t)B * sizeof(float4)));
+  float2* wbuf = (float2*)anchors;
   float4* pack = (float4*)cand;  // (delta, scale) until the finish writes the roots
-  for (int64_t base = 0; base < count; base += B) {
-    const int64_t cnt = (count - base < B) ? count - base : B;
-    MT_COUNT_LAUNCH(1);
-    k_anchor_orbits<<<(unsigned)((cnt + bs - 1) / bs), bs, asmem, s>>>(P, starts, base, cnt, anch, vv, rdel);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int64_t base = 0; base < count; base += MIX_BATCH) {
+    const int64_t cnt = (count - base < MIX_BATCH) ? count - base : MIX_BATCH;
     int64_t grid = (int64_t)device_sm_count() * per_sm;
     const int64_t need = (cnt + bs - 1) / bs;
     if (grid > need) grid = need;
+    if (grid > DM_MAX_WARPS / (bs / 32)) grid = DM_MAX_WARPS / (bs / 32);
     // the work queue (32-bit: a batch holds fewer than 2^31 starts) restarts
     // at 0 for every batch
     unsigned* q = (unsigned*)&ctr->queue_head;
     if ((e = cudaMemsetAsync(q, 0, sizeof(*q), s)) != cudaSuccess) return e;
     MT_COUNT_LAUNCH(1);
     if ((e = ktimer_begin(KS_DESC32, s)) != cudaSuccess) return e;
-    kdesc<<<(unsigned)grid, bs, smem, s>>>(P, base, cnt, anch, vv, rdel, cap, pack, status, q, ctr);
+    kdesc<<<(unsigned)grid, bs, smem, s>>>(P, starts, base, cnt, wbuf, cap, pack, status, q, ctr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = ktimer_end(s)) != cudaSuccess) return e;
   }

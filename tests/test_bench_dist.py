@@ -126,12 +126,13 @@ def test_kernel_rooflines_arithmetic():
     # the binary64 descents of the mixed tier (the tip redo): desc_newton less
     # the binary32 steps and the finish steps
     st = _stats(ms_k_desc64=0.5, desc_newton=2100, desc_fp32=1500, steps_fp32=1600, finish_newton=500,
-                ms_k_desc32=1.0, ms_k_finish=2.5)
+                ms_k_desc32=1.0, ms_k_finish=2.5, n_finish=300)
     by = {k["kernel"]: k for k in bench.kernel_rooflines("hyp", 0, 20, [st], pk)}
     assert by["k_descend"]["flops_per_launch"] == 100 * (13 * 20 + 24)
     # DRAM traffic per launch: the captured bytes per unit x this launch's units
     assert by["k_descend"]["traffic"] is None  # the tip redo (a list), not captured
-    assert abs(by["k_descend_mixed"]["traffic"] - 303.0 * (8 * 19 + 36) / 220.0 * 4096) < 1e-6
+    assert by["k_descend_mixed"]["traffic"] is None  # changed since its last capture
+    assert abs(by["k_finish_f64"]["traffic"] - 118.5 * st["n_finish"]) < 1e-6
     st = _stats(n_starts=1 << 20)
     by = {k["kernel"]: k for k in bench.kernel_rooflines("hyp", 0, 20, [st], pk)}
     assert by["k_descend"]["traffic"] == 16 * (1 << 20)
