@@ -395,6 +395,15 @@ MT_API mt_status mt_certify_static(int kind, int l, int n, const double* d_roots
 MT_API size_t mt_fma_peak_workspace_bytes(void);
 MT_API mt_status mt_fma_peak(int prec, void* d_work, size_t work_bytes, double* tflops, void* stream);
 
+/* Self-check of the certificate's binary32 square-root upper bound (Thm
+   proofRoots needs upper bounds of |z| and |p'|; the disk orbit takes them
+   as sqrt.approx.f32 times 1 + 2^-19, rounded upward): over every normal
+   binary32 x, *n_fail = how many x have bound^2 < x (exact in binary64;
+   0 means the bound holds on this GPU) and *max_rel = the largest relative
+   error of the approximation itself.  Runs on 'stream' (about 2^31
+   evaluations, a few milliseconds) and synchronises it. */
+MT_API mt_status mt_check_sqrt_up(unsigned long long* n_fail, double* max_rel, void* stream);
+
 /* Thread-local message of the last failure ("" if none). */
 MT_API const char* mt_last_error(void);
 

@@ -366,5 +366,17 @@ def fma_peak(prec: str = "fp64") -> float:
     return float(out.value)
 
 
+def check_sqrt_up() -> tuple:
+    """mt_check_sqrt_up: (failures, largest relative error) of the
+    certificate's binary32 square-root upper bound over every normal
+    binary32 on the current GPU."""
+    torch = _torch()
+    L = load()
+    nf = ctypes.c_ulonglong(0)
+    mr = ctypes.c_double(0.0)
+    check(L.mt_check_sqrt_up(ctypes.byref(nf), ctypes.byref(mr), torch.cuda.current_stream().cuda_stream))
+    return int(nf.value), float(mr.value)
+
+
 def version() -> str:
     return load().mt_version().decode()

@@ -27,6 +27,7 @@ EXPORTS = (
     "mt_eval", "mt_level_line",
     "mt_descend",
     "mt_classify", "mt_certify_static", "mt_autotune", "mt_fma_peak_workspace_bytes", "mt_fma_peak",
+    "mt_check_sqrt_up",
     "mt_last_error", "mt_version",
 )
 MT_CERTIFY_STATIC_MAX_ROOTS = 131072
@@ -135,6 +136,7 @@ def load() -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_float)]),
         "mt_fma_peak_workspace_bytes": (ctypes.c_size_t, []),
         "mt_fma_peak": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double), vp]),
+        "mt_check_sqrt_up": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_double), vp]),
         "mt_last_error": (ctypes.c_char_p, []),
         "mt_version": (ctypes.c_char_p, []),
     }

@@ -235,9 +235,10 @@ cudaError_t launch_type_only(const PolyDev& P, const double2* roots, int64_t cou
 // product terms assume every product is rounded.  Radii are upper bounds
 // kept in binary32 with every operation rounded upward (__f*_ru): a radius
 // only needs a few correct bits, and this keeps the binary64 pipe for the
-// centres.  ulp terms are built from the binary64 exponent bits as binary32
-// powers of two rounded upward (2^-149 when the true ulp is smaller).
-// Modulus bounds |z| use upward-rounded binary32 conversions and square root.
+// centres.  Along the orbit the ulp terms are bounded through the moduli
+// of the rounded results (below); the two sums of s_{l,n} and q_{l,n} take
+// them from the binary64 exponent bits as binary32 powers of two rounded
+// upward (2^-149 when the true ulp is smaller).
 
 // upper bound, in binary32, of the paper's ulp(x) = 2^(e(x) - 53) for a
 // binary64 x (2^-1074 for subnormals and zero)
@@ -270,16 +271,34 @@ __device__ __forceinline__ float ulp32_ub(float x) {
   if (p >= -126) return __int_as_float((p + 127) << 23);
   return __int_as_float(1 << (p + 149));
 }
-// upper bound of |x - f32_trunc(x)| from the truncated value t: below one
-// ulp of t, or 2^-126 where x truncated to zero
-__device__ __forceinline__ float trunc_err_ub(float t) {
-  return t == 0.f ? 1.17549435e-38f : ulp32_ub(t);
-}
-__device__ __forceinline__ float abs_ub_f(float x, float y) {
-  return __fsqrt_ru(__fmaf_ru(fabsf(x), fabsf(x), __fmul_ru(fabsf(y), fabsf(y))));
-}
 __device__ __forceinline__ float abs_lb_f(float x, float y) {
   return __fsqrt_rd(__fmaf_rd(fabsf(x), fabsf(x), __fmul_rd(fabsf(y), fabsf(y))));
+}
+
+// Per-step bounds on the binary32 pipe.  Half an ulp of a rounded result x
+// is at most 2^-53 |x| in binary64 and 2^-24 |x| in binary32 (x normal;
+// below the normal range a floor of 2^-149, resp. 2^-150, per rounding
+// covers it), so the rounding terms come from upper bounds of the results'
+// moduli by binary32 operations rounded upward, instead of from their
+// exponent bits.  |x| for a binary64 x is bounded by the next binary32 above
+// |f32_trunc(x)| (trunc_abs_up), which also bounds |x - f32_trunc(x)| by
+// the exact difference of the two.
+__device__ __forceinline__ float trunc_abs_up(float t) {  // t = f32_trunc(x): >= |x|
+  const int b = (__float_as_int(t) & 0x7fffffff) + 1;      // 2^-126 for t = 0, inf from the largest on
+  return __int_as_float(min(max(b, 0x00800000), 0x7f800000));
+}
+// Upper bound of sqrt(x), x >= 0: sqrt.approx.f32 times 1 + 2^-19 rounded
+// up; the argument is raised to 2^-126 first.  The approximation's relative
+// error, measured on GB300 over every normal binary32, is below 2^-23.2;
+// mt_check_sqrt_up repeats that check on the GPU at hand.
+__device__ __forceinline__ float sqrt_up(float x) {
+  float s;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(fmaxf(x, 1.17549435e-38f)));
+  return __fmul_ru(s, 1.0000019073486328f);
+}
+// the Newton-size test of newton_small_f on the truncated value
+__device__ __forceinline__ bool newton_small_ff(float ar, float ai, float dr, float di, float tau2) {
+  return fmaf(ar, ar, ai * ai) <= tau2 * fmaf(dr, dr, di * di);
 }
 
 // One orbit over the disk D(c, rc) and over the point c at once (shared
@@ -295,39 +314,49 @@ template <bool TYPE = false>
 __device__ __forceinline__ void disk_orbit2(const PolyDev& P, double cx, double cy, float rc,
                                             double& Vx, double& Vy, float& rv0, float& Wx,
                                             float& Wy, float& rw, float tau2 = 0.f, int* hyp = nullptr) {
+  constexpr float kU53 = 1.1102240834163406e-16f;  // 2^-53 (1 + 2^-20): covers |in_z|'s own rounding
+  constexpr float kU24 = 5.9604644775390625e-08f;  // 2^-24
+  const float kFloor64 = __int_as_float(3), kFloor32 = __int_as_float(2);  // 3 2^-149, 4 2^-150
   double zx = 0.0, zy = 0.0, czx = 0.0, czy = 0.0;
+  float fx = 0.f, fy = 0.f;                      // f32_trunc(Z)
+  float ax = 1.17549435e-38f, ay = 1.17549435e-38f;  // trunc_abs_up(fx), (fy): >= |Re Z|, |Im Z|
   float dx = 0.f, dy = 0.f, cdx = 0.f, cdy = 0.f;
   float rz0 = 0.f, rz = 0.f, rd = 0.f;  // radii: z (point), z (disk), z' (disk)
   float crz0 = 0.f, crd = 0.f;
+  const float cxu = trunc_abs_up(f32_trunc(cx));  // >= |Re c|
   for (int k = 1; k <= P.m; ++k) {
-    const float mz = abs_ub(zx, zy);
-    // z' = 2 z z' + 1 in binary32 around zf = rn32(z)
-    const float fx = f32_trunc(zx), fy = f32_trunc(zy);
-    const float ez = __fadd_ru(trunc_err_ub(fx), trunc_err_ub(fy));
+    const float mz = sqrt_up(__fmaf_ru(ax, ax, __fmul_ru(ay, ay)));  // >= |Z| >= |zf|
+    // z' = 2 z z' + 1 in binary32 around zf; |Z - zf| <= (ax - |fx|) + (ay - |fy|), both exact
+    const float ez = __fadd_ru(ax - fabsf(fx), ay - fabsf(fy));
     const float rzz = __fadd_ru(rz, ez);
-    const float md = abs_ub_f(dx, dy), mzf = abs_ub_f(fx, fy);
+    const float md = sqrt_up(__fmaf_ru(dx, dx, __fmul_ru(dy, dy)));
     const float tfx = fx + fx, tfy = fy + fy;  // exact
     const float in_re = fmaf(-tfy, dy, 1.f);
     const float nd_x = fmaf(tfx, dx, in_re);
     const float p_im = tfy * dx;
     const float nd_y = fmaf(tfx, dy, p_im);
-    const float Rd = hsum_ru(__fadd_ru(ulp32_ub(in_re), ulp32_ub(nd_x)), __fadd_ru(ulp32_ub(p_im), ulp32_ub(nd_y)));
+    const float sd = __fadd_ru(__fadd_ru(fabsf(in_re), fabsf(nd_x)), __fadd_ru(fabsf(p_im), fabsf(nd_y)));
+    const float Rd = __fmaf_ru(kU24, sd, kFloor32);
     // radius of 2 (z z'): 2 (rzz rd + rzz |z'| + rd |zf|)
-    const float prod = __fmaf_ru(rzz, rd, __fmaf_ru(rzz, md, __fmul_ru(rd, mzf)));
+    const float prod = __fmaf_ru(rzz, rd, __fmaf_ru(rzz, md, __fmul_ru(rd, mz)));
     const float nrd = __fmaf_ru(2.f, prod, Rd);
     // z = z^2 + c in binary64: re = fma(zx, zx, fma(-zy, zy, cx)), im = fma(2zx, zy, cy)
     const double tzx = twice_f64(zx);
     const double in_z = fma(-zy, zy, cx);
     const double nz_x = fma(zx, zx, in_z);
     const double nz_y = fma(tzx, zy, cy);
-    const float Rz = __fadd_ru(hsum_ru(ulp_ub(in_z), ulp_ub(nz_x)), __fmul_ru(0.5f, ulp_ub(nz_y)));
+    const float nfx = f32_trunc(nz_x), nfy = f32_trunc(nz_y);
+    const float nax = trunc_abs_up(nfx), nay = trunc_abs_up(nfy);
+    // |in_z| <= (|Re c| + |Im z|^2)(1 + 2^-53), |nz_x| <= nax, |nz_y| <= nay
+    const float inb = __fmaf_ru(ay, ay, cxu);
+    const float Rz = __fmaf_ru(kU53, __fadd_ru(__fadd_ru(inb, nax), nay), kFloor64);
     // radii of z^2 + C: 2 r |z| + r^2 (+ rc for the disk) + Rz
     const float mz2 = __fmul_ru(2.f, mz);
     const float nrz0 = __fmaf_ru(rz0, rz0, __fmaf_ru(mz2, rz0, Rz));
     const float nrz = __fadd_ru(__fmaf_ru(rz, rz, __fmaf_ru(mz2, rz, Rz)), rc);
-    zx = nz_x; zy = nz_y; dx = nd_x; dy = nd_y;
+    zx = nz_x; zy = nz_y; fx = nfx; fy = nfy; ax = nax; ay = nay; dx = nd_x; dy = nd_y;
     rz0 = nrz0; rz = nrz; rd = nrd;
-    if (TYPE && !*hyp && (P.n % k) == 0 && newton_small_f(zx, zy, dx, dy, tau2)) *hyp = k;
+    if (TYPE && !*hyp && (P.n % k) == 0 && newton_small_ff(fx, fy, dx, dy, tau2)) *hyp = k;
     if (k == P.lcap) { czx = zx; czy = zy; cdx = dx; cdy = dy; crz0 = rz0; crd = rd; }
   }
   if (P.lcap >= 0) {  // s_{l,n} = p_m + p_{l-1}, q_{l,n} = p_m - p_l: one disk sum each
@@ -625,6 +654,50 @@ cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint
                                                             rad_cap_of(tol), 0, nullptr, pass, radius, ctr,
                                                             SegView(), type);
   return cudaGetLastError();
+}
+
+// Every normal binary32 x: sqrt_up(x)^2 >= x (exact in binary64), and the
+// largest relative error of the approximation itself.
+__device__ unsigned long long g_sqrt_fail;
+__device__ unsigned g_sqrt_maxrel;
+__global__ void k_check_sqrt_up(unsigned long long count) {
+  unsigned long long nf = 0;
+  unsigned mr = 0;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const float x = __uint_as_float(0x00800000u + (unsigned)i);
+    const float su = sqrt_up(x);
+    nf += !((double)su * (double)su >= (double)x);
+    float s;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(x));
+    const double ex = sqrt((double)x);
+    mr = max(mr, __float_as_uint((float)(fabs((double)s - ex) / ex)));
+  }
+  if (nf) atomicAdd(&g_sqrt_fail, nf);
+  atomicMax(&g_sqrt_maxrel, mr);
+}
+
+cudaError_t check_sqrt_up(unsigned long long* n_fail, double* max_rel, cudaStream_t s) {
+  const unsigned long long zero = 0;
+  const unsigned zu = 0;
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbolAsync(g_sqrt_fail, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyToSymbolAsync(g_sqrt_maxrel, &zu, sizeof zu, 0, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  MT_COUNT_LAUNCH(1);
+  k_check_sqrt_up<<<(unsigned)device_sm_count() * 16, 256, 0, s>>>(0x7f7fffffull - 0x00800000ull + 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  unsigned mr = 0;
+  if ((e = cudaMemcpyFromSymbolAsync(n_fail, g_sqrt_fail, sizeof *n_fail, 0, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyFromSymbolAsync(&mr, g_sqrt_maxrel, sizeof mr, 0, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  float f;
+  std::memcpy(&f, &mr, sizeof f);
+  *max_rel = f;
+  return cudaSuccess;
 }
 
 }  // namespace mt

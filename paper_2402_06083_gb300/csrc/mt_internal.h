@@ -297,6 +297,7 @@ cudaError_t launch_type_q(const PolyDev& P, const double2* roots, int64_t count,
                           uint8_t* per, uint8_t* mult, cudaStream_t s);
 // Standalone certificate of an arbitrary list sorted through 'order'
 // (type: q_{l,n} only, the type codes of the points, or null).
+cudaError_t check_sqrt_up(unsigned long long* n_fail, double* max_rel, cudaStream_t s);
 cudaError_t launch_certify_list(const PolyDev& P, const double2* pts, const uint32_t* order,
                                 int64_t count, double tol, uint8_t* pass, double* radius,
                                 DevCounters* ctr, cudaStream_t s, const uint8_t* type = nullptr);

@@ -89,3 +89,11 @@ extern "C" MT_API mt_status mt_fma_peak(int prec, void* d_work, size_t work_byte
   if (e != cudaSuccess) return peak_fail(MT_ECUDA, cudaGetErrorString(e));
   return MT_OK;
 }
+
+extern "C" MT_API mt_status mt_check_sqrt_up(unsigned long long* n_fail, double* max_rel, void* stream) {
+  mt::set_error_message("");
+  if (!n_fail || !max_rel) return peak_fail(MT_EINVAL, "mt_check_sqrt_up: null output");
+  const cudaError_t e = mt::check_sqrt_up(n_fail, max_rel, (cudaStream_t)stream);
+  if (e != cudaSuccess) return peak_fail(MT_ECUDA, cudaGetErrorString(e));
+  return MT_OK;
+}
