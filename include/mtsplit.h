@@ -93,7 +93,7 @@ typedef struct {
      certificate failed or needed a shrunken radius, the disk of radius
      dd_radius is redone in double-double (level-line chunks, descents,
      root set, types, certificates).  dd_all = 1 redoes every root. */
-  double dd_radius;    /* zone radius (0 -> 1e-9)                                   */
+  double dd_radius;    /* zone radius (0 -> 1e-11 for p_n, n <= 29; else 1e-9)      */
   int dd_all;          /* 1: the whole split in double-double                       */
   /* Streamed split: the level line is walked and descended in this many
      pieces (a power of two), each piece's root set appended to one list

@@ -284,9 +284,13 @@ bool make_plan(int kind, int l, int n, const mt_options* o, int retry, Plan* pl)
     p.dd = 1;
     p.dd_all = o->dd_all ? 1 : 0;
     // a zone must hold the whole cluster binary64 cannot resolve around its
-    // centre.  1e-11 suffices at p_28 and p_29 (a third of the pieces of
-    // 1e-9) but loses roots at p_32, where that cluster by -2 is wider: 1e-9
-    p.dd_R = o->dd_radius > 0 ? o->dd_radius : 1e-9;
+    // centre.  By -2 the roots of p_n lie ~k^2 / 4^n from -2, so the part of
+    // that cluster closer than a fixed binary64 resolution grows like 4^n:
+    // 1e-11 holds it at p_28 and p_29 (a third of the pieces of 1e-9) but
+    // loses roots at p_32, where 1e-9 is needed; the Misiurewicz
+    // polynomials keep 1e-9
+    const double R0 = (kind == 0 && n <= 29) ? 1e-11 : 1e-9;
+    p.dd_R = o->dd_radius > 0 ? o->dd_radius : R0;
     p.dd_margin = std::max(1e-11, 100.0 * p.eps);
     p.eps_dd = std::max(1e-28, raw_eps(kind, l, n));
     p.tol_dd = std::min(o->tol > 0 ? o->tol : 1e-26, 0.05 * p.eps_dd);

@@ -668,14 +668,15 @@ __global__ void k_finish_count(unsigned long long* nlist, const unsigned long lo
 // head[p] = 1 for a sorted position p whose end point starts a group;
 // link[p] = p - q for a follower of the sorted position q (0 otherwise)
 __global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals, const double2* __restrict__ c32,
-                               const float4* __restrict__ pack, const uint8_t* __restrict__ status,
+                               const float4* __restrict__ pack, const unsigned long long* __restrict__ n3,
                                uint32_t* __restrict__ head, uint8_t* __restrict__ link) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  const uint32_t i = vals[p];
   uint32_t h = 0;
   uint8_t lk = 0;
-  if (status[i] == 3) {
+  // the n3 end points to finish (status 3) sort first: their keys lie below TIP_KEY
+  if (p < (int64_t)*n3) {
+    const uint32_t i = vals[p];
     h = 1;
     const double2 a = c32[i];
     const float ha = pack[i].z;
@@ -806,12 +807,14 @@ __global__ void k_finish_followers(int64_t count, const uint32_t* __restrict__ v
                                    const double2* __restrict__ c32, double2* __restrict__ cand,
                                    uint8_t* __restrict__ status, DevCounters* ctr) {
   unsigned long long nconv = 0, ndiv = 0, nto = 0;
+  // sorted positions below n3 hold the end points that were to finish (status 3)
+  const int64_t n3 = (int64_t)ctr->n_c32_fin;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count;
        p += (int64_t)gridDim.x * blockDim.x) {  // grid-stride: few counter atomics
     const uint32_t i = vals[p];
-    uint8_t st = status[i];
     bool finished = head[p] != 0;
-    if (st == 3 && !finished) {
+    uint8_t st = finished ? status[i] : (p < n3 ? 3 : 0);  // a head's outcome of the finish
+    if (p < n3 && !finished) {
       int64_t q = p - link[p];
       for (int g = 0; g < 4096 && !head[q] && link[q]; ++g) q -= link[q];
       if (head[q]) {
@@ -934,7 +937,7 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
       return e;
   }
   MT_COUNT_LAUNCH(1);
-  k_finish_heads<<<nb, bs, 0, s>>>(count, fin.vals, starts, pack, status, fin.head, fin.link);
+  k_finish_heads<<<nb, bs, 0, s>>>(count, fin.vals, starts, pack, &ctr->n_c32_fin, fin.head, fin.link);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_exclusive_scan(fin.head, fin.pos, count, fin.scan_tmp, fin.nheads, s)) != cudaSuccess) return e;
   MT_COUNT_LAUNCH(1);

@@ -167,7 +167,7 @@ def test_dd_complete_and_certified(mt, n):
 
 
 def test_dd_zone_radius_changes_work_not_roots(mt):
-    """A larger zone radius (1e-8 against the default 1e-9) redoes more roots
+    """A larger zone radius (1e-8 against the default 1e-11 of p_26) redoes more roots
     in dd but returns the same certified set (every root within 4e-15, roots
     redone in dd by both runs within TOL_DD)."""
     n = 26
