@@ -10,7 +10,7 @@
 // fold + key -> LSD radix sort of Re keys -> each sorted candidate checks
 // the earlier candidates of its Re window -> exclusive scan -> gather.
 // Every kernel is a coalesced pass over HBM; the radix sort ranks keys
-// stably inside a block with __match_any_sync.
+// stably inside a block (digit peers of a warp by ballots).
 #include "mt_common.cuh"
 
 namespace mt {
@@ -250,6 +250,24 @@ __device__ __forceinline__ int64_t rs_count(int64_t n, const unsigned long long*
   return d < n ? d : n;
 }
 
+// The lanes of the warp whose value d (a digit 0..255, or 256 for no
+// element) equals this lane's.  BAL: nine ballots, one per bit (measured
+// faster on the 64-bit keys of the root sets, whose high bytes repeat
+// along a warp); else one match (faster on the finish keys' uniform
+// digits).
+template <bool BAL>
+__device__ __forceinline__ unsigned rs_peers(unsigned d) {
+  if (!BAL) return __match_any_sync(0xffffffffu, d);
+  unsigned peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned v = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? v : ~v;
+  }
+  return peers;
+}
+
 // block b's tiles [t0, t1) of the ceil(n / RS_TILE) tiles
 __device__ __forceinline__ void rs_range(int64_t n, int64_t& t0, int64_t& t1) {
   const int64_t nt = (n + RS_TILE - 1) / RS_TILE;
@@ -257,6 +275,7 @@ __device__ __forceinline__ void rs_range(int64_t n, int64_t& t0, int64_t& t1) {
   t1 = nt * (blockIdx.x + 1) / gridDim.x;
 }
 
+template <bool BAL>
 __global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                    int shift, uint32_t* __restrict__ hist,
                                                    const unsigned long long* __restrict__ n_dev) {
@@ -278,7 +297,7 @@ __global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ 
     // lanes of a warp that share a digit add once (high digits repeat)
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-      const unsigned peers = __match_any_sync(0xffffffffu, dg[k]);
+      const unsigned peers = rs_peers<BAL>(dg[k]);
       if (dg[k] < 256u && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[dg[k]], (uint32_t)__popc(peers));
     }
   }
@@ -313,6 +332,7 @@ __device__ __forceinline__ void rs_load(const uint64_t* __restrict__ kin, const 
   }
 }
 
+template <bool BAL>
 __global__ void __launch_bounds__(RS_BS, 3) k_rs_scatter(const uint64_t* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin,
                                                          uint64_t* __restrict__ kout,
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(RS_BS, 3) k_rs_scatter(const uint64_t* __restr
     for (int k = 0; k < RS_ITEMS; ++k) {
       const bool valid = base + k * 32 < n;
       dg[k] = valid ? (unsigned)(key[k] >> shift) & 255u : 256u;
-      const unsigned peers = __match_any_sync(0xffffffffu, dg[k]);
+      const unsigned peers = rs_peers<BAL>(dg[k]);
       const unsigned lt = __popc(peers & lanemask_lt());
       const uint32_t before = valid ? wc[w][dg[k]] : 0u;
       __syncwarp();
@@ -427,7 +447,8 @@ static int64_t rs_grid(int64_t n) {
   static int per_sm = 0;
   if (!per_sm) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rs_scatter, RS_BS, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rs_scatter<true>, RS_BS, 0) != cudaSuccess || b < 1)
+      b = 1;
     per_sm = b;
   }
   const int64_t nt = (n + RS_TILE - 1) / RS_TILE;
@@ -442,18 +463,20 @@ size_t radix_temp_bytes(int64_t n) {
 
 // one pass: digit [shift, shift + 8) from (k0, v0) to (k1, v1)
 static cudaError_t rs_pass(const uint64_t* k0, const uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n,
-                           int shift, void* temp, const unsigned long long* n_dev, cudaStream_t s) {
+                           int shift, void* temp, const unsigned long long* n_dev, bool bal, cudaStream_t s) {
   const int64_t G = rs_grid(n);
   const int64_t nh = 256 * G;
   uint32_t* hist = (uint32_t*)temp;
   uint32_t* offs = hist + nh;
   uint32_t* dtot = offs + nh;
   MT_COUNT_LAUNCH(1);
-  k_rs_hist<<<(unsigned)G, RS_BS, 0, s>>>(k0, n, shift, hist, n_dev);
+  if (bal) k_rs_hist<true><<<(unsigned)G, RS_BS, 0, s>>>(k0, n, shift, hist, n_dev);
+  else k_rs_hist<false><<<(unsigned)G, RS_BS, 0, s>>>(k0, n, shift, hist, n_dev);
   MT_COUNT_LAUNCH(1);
   k_rs_offsets<<<256, RS_GRID_MAX / 2, 0, s>>>(hist, offs, dtot, (int)G);
   MT_COUNT_LAUNCH(1);
-  k_rs_scatter<<<(unsigned)G, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, dtot, n_dev);
+  if (bal) k_rs_scatter<true><<<(unsigned)G, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, dtot, n_dev);
+  else k_rs_scatter<false><<<(unsigned)G, RS_BS, 0, s>>>(k0, v0, k1, v1, n, shift, offs, dtot, n_dev);
   return cudaGetLastError();
 }
 
@@ -467,7 +490,7 @@ cudaError_t radix_sort_bits(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, 
   uint64_t* k1 = keys_alt;
   uint32_t* v1 = vals_alt;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
-    cudaError_t e = rs_pass(k0, v0, k1, v1, n, shift, temp, nullptr, s);
+    cudaError_t e = rs_pass(k0, v0, k1, v1, n, shift, temp, nullptr, false, s);
     if (e != cudaSuccess) return e;
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
@@ -485,7 +508,7 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
   uint64_t* k1 = keys_alt;
   uint32_t* v1 = vals_alt;
   for (int shift = 0; shift < 64; shift += 8) {
-    cudaError_t e = rs_pass(k0, v0, k1, v1, n, shift, temp, n_dev, s);
+    cudaError_t e = rs_pass(k0, v0, k1, v1, n, shift, temp, n_dev, true, s);
     if (e != cudaSuccess) return e;
     uint64_t* tk = k0; k0 = k1; k1 = tk;
     uint32_t* tv = v0; v0 = v1; v1 = tv;
