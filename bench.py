@@ -87,6 +87,14 @@ def newton_flops_fp32(m: int) -> int:
     return 19 * (m - 1) + 25  # the first orbit step (from Z_0 = 0) is exact and skipped
 
 
+def anchor_flops_fp32(m: int) -> int:
+    # the float-float reference orbit the binary32 descent computes per start:
+    # per step two TwoProd squares (10 each), a TwoProd product (10), its
+    # doubling (2) and three float-float additions (11 each); then P(c0) (two
+    # additions) and the jump bound (6)
+    return 65 * m + 28
+
+
 def finish_flops_fp64(m: int) -> int:
     return 7 * m + 2  # the orbit's value and z - q; the quotient and the tests run in binary32
 
@@ -116,11 +124,14 @@ def _kernel(name, pipe, flops, ms, launches, peak, peak_nominal, work) -> dict:
 # (profiles/kernels_hyp24_mixed.md: p_24 mixed and p_20 binary64, dram__bytes
 # read + write per launch divided by the units that launch processed), as a
 # function of the orbit length m; a bench launch's traffic is this times its
-# own units.  k_descend (binary64 tier) reads its start (16 B; 16.8 MB per
-# 2^20 starts).  k_finish_f64: 389 + 141 MB per 4.47 M finishes at p_24,
-# 118.5 B each.  A kernel missing here has changed since its last capture
-# (its traffic is reported as null).
+# own units.  k_descend_mixed reads its start and writes (delta, scale) and
+# the status, its anchor slots staying in L2: 135 + 134 MB per 2^23 starts at
+# p_24, 32.1 B a start.  k_descend (binary64 tier) reads its start (16 B;
+# 16.8 MB per 2^20 starts).  k_finish_f64: 389 + 141 MB per 4.47 M finishes
+# at p_24, 118.5 B each.  A kernel missing here has changed since its last
+# capture (its traffic is reported as null).
 TRAFFIC = {
+    "k_descend_mixed": (lambda m: 32.1, "start"),
     "k_descend": (lambda m: 16, "start"),
     "k_finish_f64": (lambda m: 118.5, "finish"),
 }
@@ -154,8 +165,11 @@ def kernel_rooflines(kind: str, l: int, n: int, stats: list, pk: dict, sm_mhz: f
     if s0.get("ms_k_desc32", 0) > 0:
         steps = s0["desc_fp32"]
         launches = -(-s0["n_starts"] // MIX_BATCH)
-        out.append(_kernel("k_descend_mixed", "fp32", steps * newton_flops_fp32(m), mean("ms_k_desc32"), launches,
-                           p32, n32, "binary32 Newton steps %d x %d flops" % (steps, newton_flops_fp32(m))))
+        nst = s0["n_starts"]
+        out.append(_kernel("k_descend_mixed", "fp32", steps * newton_flops_fp32(m) + nst * anchor_flops_fp32(m),
+                           mean("ms_k_desc32"), launches, p32, n32,
+                           "binary32 Newton steps %d x %d flops + float-float anchor orbits %d x %d flops" %
+                           (steps, newton_flops_fp32(m), nst, anchor_flops_fp32(m))))
     if s0.get("ms_k_finish", 0) > 0:
         steps = s0["finish_newton"]
         out.append(_kernel("k_finish_f64", "fp64", steps * finish_flops_fp64(m), mean("ms_k_finish"), 1, p64, n64,
