@@ -183,18 +183,34 @@ __global__ void k_scan_tiles(const uint32_t* in, uint32_t* out, int64_t n,
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
   // each thread owns SCAN_ITEMS consecutive elements (blocked arrangement)
   const int64_t t0 = base + (int64_t)threadIdx.x * SCAN_ITEMS;
+  // a full run of 8 moves as two 16-byte words where both buffers are
+  // 16-byte aligned (t0 is a multiple of 8)
+  const bool full = t0 + SCAN_ITEMS <= n && ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0;
   uint32_t v[SCAN_ITEMS];
   unsigned long long acc = 0;
+  if (full) {
+    const uint4 a = *(const uint4*)(in + t0), b = *(const uint4*)(in + t0 + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    v[k] = (t0 + k < n) ? in[t0 + k] : 0u;
-    acc += v[k];
+    for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = (t0 + k < n) ? in[t0 + k] : 0u;
   }
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) acc += v[k];
   unsigned long long off = block_excl_scan_u64(acc, sh, nullptr) + sums[blockIdx.x];
+  uint32_t o[SCAN_ITEMS];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    if (t0 + k < n) out[t0 + k] = (uint32_t)off;
+    o[k] = (uint32_t)off;
     off += v[k];
+  }
+  if (full) {
+    *(uint4*)(out + t0) = make_uint4(o[0], o[1], o[2], o[3]);
+    *(uint4*)(out + t0 + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+      if (t0 + k < n) out[t0 + k] = o[k];
   }
 }
 

@@ -581,6 +581,16 @@ constexpr int FINISH_KEY_BITS = 40;
 constexpr double FINISH_BUCKET = 7.275957614183426e-12;  // 2^-37
 constexpr uint64_t TIP_KEY = (1ull << FINISH_KEY_BITS) - 2;  // above every finite key, below the rest
 constexpr uint64_t REST_KEY = (1ull << FINISH_KEY_BITS) - 1;
+// The key's bits above FINISH_KEY_BITS carry the descent's squared scale
+// h1 (binary32, its low 8 bits dropped: rounded down, so the grouping test
+// only tightens) through the sort, which orders the low 40 bits only: the
+// group scan reads it from the sorted keys instead of gathering it.
+__device__ __forceinline__ uint64_t with_scale(uint64_t key, float h1) {
+  return key | ((uint64_t)(__float_as_uint(fmaxf(h1, 0.f)) >> 8) << FINISH_KEY_BITS);
+}
+__device__ __forceinline__ float key_scale(uint64_t key) {
+  return __uint_as_float((unsigned)(key >> FINISH_KEY_BITS) << 8);
+}
 __device__ __forceinline__ uint64_t finish_key(double re) {
   // round(re 2^37 + 2.25 2^37) as an integer, by adding 2^52 (exact below 2^52):
   // two binary64 operations, the rest on the integer pipe
@@ -600,29 +610,48 @@ __global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ star
                            uint8_t* __restrict__ status, uint64_t* __restrict__ keys,
                            uint32_t* __restrict__ vals, DevCounters* ctr) {
   // grid-stride over a bounded grid: the counts reach the two counters in a
-  // few thousand atomics, not one per warp of the 2^28 descents
+  // few thousand atomics, not one per warp of the 2^28 descents.  Four
+  // elements a round, all loaded before any is stored (the loads of a round
+  // are in flight together; a load of starts cannot pass an earlier store
+  // to it).
+  constexpr int U = 4;
   unsigned long long n3 = 0, n4 = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 q = pack[i];
-    const double2 c0 = starts[i];
-    double2 c = make_double2(c0.x + (double)q.x, c0.y + (double)q.y);
-    const bool fin = status[i] == 3;
-    if (fin && c.y < 0.0) c.y = -c.y;
-    uint64_t key = REST_KEY;
-    if (fin && c.x < -2.0 + box && c.y < box) {
-      status[i] = 4;  // redone in binary64 from c0
-      key = TIP_KEY;
-      ++n4;
-    } else {
-      starts[i] = c;
-      if (fin) {
-        key = finish_key(c.x);
-        ++n3;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += U * stride) {
+    float4 q[U];
+    double2 c0[U];
+    uint8_t st[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < count) {
+        q[u] = pack[i];
+        c0[u] = starts[i];
+        st[u] = status[i];
       }
     }
-    keys[i] = key;
-    vals[i] = (uint32_t)i;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i >= count) break;
+      double2 c = make_double2(c0[u].x + (double)q[u].x, c0[u].y + (double)q[u].y);
+      const bool fin = st[u] == 3;
+      if (fin && c.y < 0.0) c.y = -c.y;
+      uint64_t key = REST_KEY;
+      if (fin && c.x < -2.0 + box && c.y < box) {
+        status[i] = 4;  // redone in binary64 from c0
+        key = TIP_KEY;
+        ++n4;
+      } else {
+        starts[i] = c;
+        if (fin) {
+          key = with_scale(finish_key(c.x), q[u].z);
+          ++n3;
+        }
+      }
+      keys[i] = key;
+      vals[i] = (uint32_t)i;
+    }
   }
   warp_add_u64(&ctr->n_c32_fin, n3);
   warp_add_u64(&ctr->n_tip64, n4);
@@ -667,9 +696,10 @@ __global__ void k_finish_count(unsigned long long* nlist, const unsigned long lo
 
 // head[p] = 1 for a sorted position p whose end point starts a group;
 // link[p] = p - q for a follower of the sorted position q (0 otherwise)
-__global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals, const double2* __restrict__ c32,
-                               const float4* __restrict__ pack, const unsigned long long* __restrict__ n3,
-                               uint32_t* __restrict__ head, uint8_t* __restrict__ link) {
+__global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals,
+                               const uint64_t* __restrict__ skeys, const double2* __restrict__ c32,
+                               const unsigned long long* __restrict__ n3, uint32_t* __restrict__ head,
+                               uint8_t* __restrict__ link) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
   uint32_t h = 0;
@@ -679,7 +709,7 @@ __global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals,
     const uint32_t i = vals[p];
     h = 1;
     const double2 a = c32[i];
-    const float ha = pack[i].z;
+    const float ha = key_scale(skeys[p]);
     const double reach2 = (double)FINISH_SAME2 * (double)ha;  // min(ha, hb) <= ha
     for (int k = 1; k <= FINISH_SCAN && k <= p; ++k) {
       const uint32_t j = vals[p - k];
@@ -689,7 +719,7 @@ __global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals,
       // b.x + FINISH_BUCKET, so none is within reach once ex - bucket is
       const double eb = ex - FINISH_BUCKET;
       if (eb > 0.0 && eb * eb > reach2) break;
-      const double sc = (double)fminf(ha, pack[j].z);
+      const double sc = (double)fminf(ha, key_scale(skeys[p - k]));
       if (fma(ex, ex, ey * ey) <= (double)FINISH_SAME2 * sc) {
         h = 0;
         lk = (uint8_t)k;
@@ -926,6 +956,7 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
   const unsigned egrid = std::min<unsigned>(nb, (unsigned)device_sm_count() * 16);  // grid-stride kernels
   k_c32_keys<<<egrid, bs, 0, s>>>(count, tip_box(P), starts, pack, status, fin.keys, fin.vals, ctr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const uint64_t* skeys = nullptr;  // the sorted keys
   {
     bool in_alt = false;
     if ((e = radix_sort_bits(fin.keys, fin.vals, fin.keys_alt, fin.vals_alt, count, fin.radix_tmp, 0,
@@ -935,9 +966,10 @@ cudaError_t launch_descend_mixed(const PolyDev& P, double2* starts, int64_t coun
     if (in_alt && (e = cudaMemcpyAsync(fin.vals, fin.vals_alt, (size_t)count * sizeof(uint32_t),
                                        cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return e;
+    skeys = in_alt ? fin.keys_alt : fin.keys;
   }
   MT_COUNT_LAUNCH(1);
-  k_finish_heads<<<nb, bs, 0, s>>>(count, fin.vals, starts, pack, &ctr->n_c32_fin, fin.head, fin.link);
+  k_finish_heads<<<nb, bs, 0, s>>>(count, fin.vals, skeys, starts, &ctr->n_c32_fin, fin.head, fin.link);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_exclusive_scan(fin.head, fin.pos, count, fin.scan_tmp, fin.nheads, s)) != cudaSuccess) return e;
   MT_COUNT_LAUNCH(1);
