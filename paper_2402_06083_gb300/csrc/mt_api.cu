@@ -610,6 +610,22 @@ cudaError_t mark(cudaEvent_t e, cudaStream_t s, bool capturing) {
   return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
 }
 
+// The pass's output list: representatives with their multiplicities, sorted
+// (ties ordered), low parts zero.  An MT_DD pass that is not streamed emits
+// after the host has seen its counters: when the double-double pass runs,
+// it writes the whole list itself, so the binary64 list is only written
+// when that pass does not run.
+bool defer_emit(const Plan& p) { return p.dd && p.stream_P <= 1; }
+mt_status emit_base(const Plan& p, const Buffers& b, double2* out, double2* out_lo, int64_t cap_out,
+                    uint8_t* is_mis, cudaStream_t s) {
+  const int mis_code = p.raw_types ? MIS_CODE_RAW : (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
+  CK(launch_emit(b.reps, &b.ctr->n_reps, p.S, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out,
+                 s));
+  CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s));
+  if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
+  return MT_OK;
+}
+
 // One pass of the whole sequence, enqueued on s (no host synchronisation).
 mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
                        int64_t cap_out, uint8_t* is_mis, cudaStream_t s, EventSet& ev,
@@ -669,11 +685,10 @@ mt_status enqueue_pass(const Plan& p, const Buffers& b, double2* out, double2* o
                       s, SegView(), p.kind == 2 ? b.type : nullptr));
   }
   CK(mark(ev.e[4], s, capturing));
-  const int mis_code = p.raw_types ? MIS_CODE_RAW : (p.kind == 1 && p.P.n < 32) ? p.P.n : -1;
-  CK(launch_emit(b.reps, &b.ctr->n_reps, p.S, b.mult, b.mpos, b.type, mis_code, out, is_mis, cap_out,
-                 s));
-  CK(launch_fix_ties(out, &b.ctr->n_full, cap_out, is_mis, s));
-  if (out_lo) CK(cudaMemsetAsync(out_lo, 0, (size_t)cap_out * sizeof(double2), s));
+  if (!defer_emit(p)) {
+    const mt_status rc = emit_base(p, b, out, out_lo, cap_out, is_mis, s);
+    if (rc != MT_OK) return rc;
+  }
   CK(mark(ev.e[5], s, capturing));
   return MT_OK;
 }
@@ -1093,6 +1108,12 @@ mt_status split_impl(int kind, int l, int n, const mt_options* o, double* d_root
       done = (int64_t)h.n_full == p.degree && h.n_cert_pass == h.n_full;
     } else if (p.dd) {
       done = certified;
+    }
+    if (defer_emit(p) && !dd_ran) {
+      rc = emit_base(p, b, (double2*)d_roots, (double2*)d_roots_lo, cap, d_is_mis, s);
+      if (rc != MT_OK) return rc;
+      const cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return fail(MT_ECUDA, "emit: %s", cudaGetErrorString(e));
     }
     if (retry == 0) {  // kept for the statistics: why a repeat followed
       first.n_roots = (int64_t)h.n_full;

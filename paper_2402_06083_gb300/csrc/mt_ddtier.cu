@@ -43,13 +43,13 @@ __device__ __forceinline__ bool zone_hit(double x, double y, const double2* __re
   // first centre with Re >= x - R, searched on order-preserving integer keys
   // (GB300's binary64 pipe is the scarce one; the comparisons of the search
   // run on the integer pipe)
-  const uint64_t kl = f64_key(x - R);
+  const uint64_t kl = f64_key(x - R), kh = f64_key(x + R);
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (f64_key(bad[mid].x) < kl) lo = mid + 1; else hi = mid;
   }
   const double R2 = R * R;
-  for (int f = lo; f < nbad && bad[f].x <= x + R; ++f) {
+  for (int f = lo; f < nbad && f64_key(bad[f].x) <= kh; ++f) {
     const double dx = x - bad[f].x, dy = y - bad[f].y;
     if (fma(dx, dx, dy * dy) < R2) return true;
   }

@@ -710,8 +710,11 @@ __global__ void k_fix_ties(double2* out, const unsigned long long* __restrict__ 
   if (n > cap_out) n = cap_out;
   if (p + 1 >= n) return;
   // a run: equal Re within one polynomial
+  // Re equal as binary64 values, on the integer pipe: equal bits, or both
+  // zeros of either sign
   auto same = [&](int64_t a, int64_t b) {
-    return out[a].x == out[b].x && (!sv.out_seg || sv.out_seg[a] == sv.out_seg[b]);
+    const long long ba = __double_as_longlong(out[a].x), bb = __double_as_longlong(out[b].x);
+    return (ba == bb || ((ba | bb) << 1) == 0) && (!sv.out_seg || sv.out_seg[a] == sv.out_seg[b]);
   };
   if (p > 0 && same(p - 1, p)) return;  // not the start of a run
   if (!same(p + 1, p)) return;

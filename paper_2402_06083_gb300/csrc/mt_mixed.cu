@@ -575,7 +575,7 @@ inline double tip_box(const PolyDev& P) { return 1e-3 * exp2(2.0 * (P.log2d - 29
 // Sort keys of the binary32 end points: Re in fixed point, 2^-37 per unit
 // over [-2.25, 1.75) (every root of the family lies in Re in [-2, 1/4]),
 // FINISH_KEY_BITS = 40 bits, so that five radix passes order them.  The map
-// c -> round((c + 2.25) 2^37) is monotone (non-decreasing), so the sort
+// c -> floor((c + 2.25) 2^37) is monotone (non-decreasing), so the sort
 // orders the end points by Re up to one bucket, FINISH_BUCKET wide.
 constexpr int FINISH_KEY_BITS = 40;
 constexpr double FINISH_BUCKET = 7.275957614183426e-12;  // 2^-37
@@ -592,11 +592,18 @@ __device__ __forceinline__ float key_scale(uint64_t key) {
   return __uint_as_float((unsigned)(key >> FINISH_KEY_BITS) << 8);
 }
 __device__ __forceinline__ uint64_t finish_key(double re) {
-  // round(re 2^37 + 2.25 2^37) as an integer, by adding 2^52 (exact below 2^52):
-  // two binary64 operations, the rest on the integer pipe
-  const double f = fma(re, 137438953472.0, 309237645312.0);  // (re + 2.25) 2^37
-  const double g = f + 4503599627370496.0;                     // 2^52
-  const long long k = __double_as_longlong(g) - 0x4330000000000000ll;
+  // floor((re + 2.25) 2^37) = floor(re 2^37) + 2.25 2^37, the first term an
+  // arithmetic shift of re's significand (integer pipe only: on GB300 the
+  // binary64 pipe issues at 1/64 of the binary32 rate)
+  const long long b = __double_as_longlong(re);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const long long M = (b & 0x000fffffffffffffll) | (E ? 0x0010000000000000ll : 0ll);
+  const int sh = min(63, 1038 - max(E, 1));  // re 2^37 = M 2^(E' - 1038), E' = max(E, 1)
+  long long k;
+  if (sh <= 0) k = b < 0 ? -0x7fffffffffffll : 0x7fffffffffffll;  // |re| >= 2^14: clamped below
+  else if (b >= 0) k = M >> sh;
+  else k = -(long long)(((unsigned long long)M + ((1ull << sh) - 1ull)) >> sh);
+  k += 309237645312ll;  // 2.25 2^37
   const long long top = (long long)(1ull << (FINISH_KEY_BITS - 1)) - 1;
   return (uint64_t)(k < 0 ? 0 : k > top ? top : k);
 }
@@ -617,6 +624,7 @@ __global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ star
   constexpr int U = 4;
   unsigned long long n3 = 0, n4 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint64_t kx = f64_key(-2.0 + box), ky = f64_key(box);
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += U * stride) {
     float4 q[U];
     double2 c0[U];
@@ -634,11 +642,16 @@ __global__ void k_c32_keys(int64_t count, double box, double2* __restrict__ star
     for (int u = 0; u < U; ++u) {
       const int64_t i = i0 + u * stride;
       if (i >= count) break;
-      double2 c = make_double2(c0[u].x + (double)q[u].x, c0[u].y + (double)q[u].y);
+      // the binary32 deltas widen on the integer pipe (f64_of_f32: a
+      // subnormal delta, far below half an ulp of the start, becomes 0)
+      double2 c = make_double2(c0[u].x + f64_of_f32(q[u].x), c0[u].y + f64_of_f32(q[u].y));
       const bool fin = st[u] == 3;
-      if (fin && c.y < 0.0) c.y = -c.y;
+      // Im c < 0 (sign bit set, not -0): fold into the upper half
+      const long long by = __double_as_longlong(c.y);
+      if (fin && by < 0 && (by << 1) != 0) c.y = __longlong_as_double(by & 0x7fffffffffffffffll);
       uint64_t key = REST_KEY;
-      if (fin && c.x < -2.0 + box && c.y < box) {
+      // the tip box, compared on order-preserving integer keys
+      if (fin && f64_key(c.x) < kx && f64_key(c.y) < ky) {
         status[i] = 4;  // redone in binary64 from c0
         key = TIP_KEY;
         ++n4;
@@ -710,17 +723,20 @@ __global__ void k_finish_heads(int64_t count, const uint32_t* __restrict__ vals,
     h = 1;
     const double2 a = c32[i];
     const float ha = key_scale(skeys[p]);
-    const double reach2 = (double)FINISH_SAME2 * (double)ha;  // min(ha, hb) <= ha
+    const float reach2 = FINISH_SAME2 * ha;  // min(ha, hb) <= ha
     for (int k = 1; k <= FINISH_SCAN && k <= p; ++k) {
       const uint32_t j = vals[p - k];
       const double2 b = c32[j];
-      const double ex = a.x - b.x, ey = a.y - b.y;
+      // the differences in binary64, the tests in binary32 (the differences
+      // truncated on the integer pipe: never larger, so the scan never stops
+      // early)
+      const float ex = f32_trunc(a.x - b.x), ey = f32_trunc(a.y - b.y);
       // sorted by Re up to one bucket: every earlier entry lies below
       // b.x + FINISH_BUCKET, so none is within reach once ex - bucket is
-      const double eb = ex - FINISH_BUCKET;
-      if (eb > 0.0 && eb * eb > reach2) break;
-      const double sc = (double)fminf(ha, key_scale(skeys[p - k]));
-      if (fma(ex, ex, ey * ey) <= (double)FINISH_SAME2 * sc) {
+      const float eb = ex - (float)FINISH_BUCKET;
+      if (eb > 0.f && eb * eb > reach2) break;
+      const float sc = fminf(ha, key_scale(skeys[p - k]));
+      if (fmaf(ex, ex, ey * ey) <= FINISH_SAME2 * sc) {
         h = 0;
         lk = (uint8_t)k;
         break;
