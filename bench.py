@@ -655,12 +655,15 @@ class Bench:
         torch.cuda.synchronize()
         nbytes = self.d * 16 * (1 if self.roots_lo is None else 2)
         t0 = time.perf_counter()
+        self.e2e_step_ms = []
         for i in range(steps):
             k = i % 2
             if copied[k] is not None:
                 main.wait_event(copied[k])  # buffer k is free again
             self.roots, self.roots_lo = outs[k]
+            ts = time.perf_counter()
             self.step()
+            self.e2e_step_ms.append((time.perf_counter() - ts) * 1e3)  # the call's host time
             done = torch.cuda.Event()
             done.record(main)
             with torch.cuda.stream(cs):
@@ -720,9 +723,9 @@ def measure(b: Bench, name: str, steps: int, warmup: int, pk: dict, peak_source:
     ms, stats, wall = b.timed(steps, warmup, barrier=True)
     ms = max_over_ranks(ms, b.dist)
     certified = min(s["n_cert_pass"] for s in stats)
+    clocks = sampler.stop()  # the clocks of the device-timed region
     e2e_s, d2h = b.e2e(steps)
     e2e_s = max_over_ranks(e2e_s, b.dist)
-    clocks = sampler.stop()
     s0 = stats[-1]
     n_units = s0["n_roots"] if kind in ("q", "misbatch") else b.d
     kern = kernel_rooflines(kind if kind != "misbatch" else "mis", l, n if kind != "misbatch" else n - 1, stats, pk,
@@ -733,6 +736,8 @@ def measure(b: Bench, name: str, steps: int, warmup: int, pk: dict, peak_source:
         "steps": steps, "precision": prec,
         "e2e": {"value": whole_job_rate(world, n_units, e2e_s), "unit": "roots/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3,
+                "call_ms": [round(x, 1) for x in getattr(b, "e2e_step_ms", [])],
                 "note": "the input is the integer n (no device input); each step's sorted roots (and low parts) "
                         "are copied to pinned host memory inside the timed loop, on a second stream while the "
                         "next step splits into the other of two output buffers; the time ends when the last "

@@ -48,6 +48,15 @@ mt_status fail(mt_status st, const char* fmt, ...) {
                   __LINE__);                                                             \
   } while (0)
 
+// the device's f64_key0 on the host: -0 as +0, then an order-preserving
+// map of the binary64 bits to unsigned integers
+uint64_t host_key0(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof b);
+  if ((b << 1) == 0) b = 0;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
@@ -325,6 +334,7 @@ struct DdBuffers {
   unsigned long long* cnt;  // [0] centres [1] polish list [2] zone points [3] zone reps
                             // [4] kept main multiplicity [5] zone multiplicity [6] main reps
   double2* bad;
+  uint64_t *bad_klo, *bad_khi;  // the centres' windows of radius dd_R + dd_margin as integer keys
   uint32_t *pflag, *ppos;  // per piece of the level line: redo flag, its scan
   int64_t* pids;           // redone pieces
   void* pscan;
@@ -423,6 +433,8 @@ Buffers carve(const Plan& p, void* ws, size_t cap) {
     const int64_t nst = p.dd_nb * (p.dd_Ls / p.every) + 1;
     d.cnt = c.take<unsigned long long>(8);
     d.bad = c.take<double2>(p.dd_bad_cap);
+    d.bad_klo = c.take<uint64_t>(p.dd_bad_cap);
+    d.bad_khi = c.take<uint64_t>(p.dd_bad_cap);
     d.pflag = c.take<uint32_t>(p.dd_npieces);
     d.ppos = c.take<uint32_t>(p.dd_npieces);
     d.pids = c.take<int64_t>(p.dd_pcap);
@@ -948,7 +960,16 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
     CK(cudaMemcpyAsync(hb.data(), d.bad, sizeof(double2) * nbad, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     std::sort(hb.begin(), hb.end(), [](const double2& a, const double2& c) { return a.x < c.x; });
+    // the windows [x_f - R', x_f + R'] of the bulk zone tests (R' = Rm (1 + 2^-30), rounded outward)
+    const double Rw = (p.dd_R + p.dd_margin) * (1.0 + std::ldexp(1.0, -30));
+    std::vector<uint64_t> klo((size_t)nbad), khi((size_t)nbad);
+    for (int f = 0; f < nbad; ++f) {
+      klo[(size_t)f] = host_key0(std::nextafter(hb[(size_t)f].x - Rw, -INFINITY));
+      khi[(size_t)f] = host_key0(std::nextafter(hb[(size_t)f].x + Rw, INFINITY));
+    }
     CK(cudaMemcpyAsync(d.bad, hb.data(), sizeof(double2) * nbad, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d.bad_klo, klo.data(), sizeof(uint64_t) * nbad, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d.bad_khi, khi.data(), sizeof(uint64_t) * nbad, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
   }
   const double Rm = p.dd_R + p.dd_margin;
@@ -961,7 +982,8 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
     if (b.candq)  // streamed split: from the fixed-point end points of all descents
       CK(dd_mark_pieces_fix(b.candq, b.candq_n, p.every, p.dd_Ls, p.dd_npieces, d.bad, nbad, Rm, d.pflag, s));
     else
-      CK(dd_mark_pieces(b.cand, b.status, p.S, p.every, p.dd_Ls, p.dd_npieces, d.bad, nbad, Rm, d.pflag, s));
+      CK(dd_mark_pieces(b.cand, b.status, p.S, p.every, p.dd_Ls, p.dd_npieces, d.bad, d.bad_klo, d.bad_khi,
+                        nbad, Rm, d.pflag, s));
     CK(launch_exclusive_scan(d.pflag, d.ppos, p.dd_npieces, d.pscan, &d.cnt[7], s));
     CK(dd_piece_ids(d.pflag, d.ppos, p.dd_npieces, d.pids, p.dd_pcap, s));
     unsigned long long np_h = 0;
@@ -977,7 +999,8 @@ mt_status run_dd(const Plan& p, const Buffers& b, double2* out, double2* out_lo,
   // (a streamed split has its own, sized for the final reps)
   uint8_t* drop = b.drop ? b.drop : b.status;
   CK(cudaMemsetAsync(drop, 0, (size_t)p.S, s));
-  CK(dd_near_reps(b.reps, n_main, p.S, d.bad, nbad, Rm, d.near, &d.cnt[1], p.dd_near_cap, s));
+  CK(dd_near_reps(b.reps, n_main, p.S, d.bad, d.bad_klo, d.bad_khi, nbad, Rm, d.near, &d.cnt[1], p.dd_near_cap,
+                  s));
   // dd level line and descents, dd_nb pieces at a time
   const int64_t per_piece = p.dd_Ls / p.every;
   for (int64_t k0 = 0; k0 < npieces; k0 += p.dd_nb) {

@@ -389,5 +389,12 @@ __device__ __forceinline__ uint64_t f64_key(double x) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
+// f64_key with -0 mapped to +0: for non-NaN binary64 values a < b exactly
+// when f64_key0(a) < f64_key0(b)
+__device__ __forceinline__ uint64_t f64_key0(double x) {
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  if ((b << 1) == 0) b = 0;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
 
 }  // namespace mt

@@ -56,6 +56,30 @@ __device__ __forceinline__ bool zone_hit(double x, double y, const double2* __re
   return false;
 }
 
+// zone_hit for the bulk tests (every start, every representative): the
+// centres' windows [x_f - R', x_f + R'] (R' = R (1 + 2^-30), so the windows
+// hold every point the exact test below accepts) as order-preserving integer
+// keys from the host, klo and khi both sorted like the centres.  The first
+// centre whose window reaches x is a binary search on khi, the last one the
+// first klo above x; only the exact test runs in binary64.
+__device__ __forceinline__ bool zone_hit_k(double x, double y, const double2* __restrict__ bad,
+                                           const uint64_t* __restrict__ klo, const uint64_t* __restrict__ khi,
+                                           int nbad, double R) {
+  if (nbad < 0) return true;  // "all" mode
+  const uint64_t kx = f64_key0(x);
+  int lo = 0, hi = nbad;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (khi[mid] < kx) lo = mid + 1; else hi = mid;
+  }
+  const double R2 = R * R;
+  for (int f = lo; f < nbad && klo[f] <= kx; ++f) {
+    const double dx = x - bad[f].x, dy = y - bad[f].y;
+    if (fma(dx, dx, dy * dy) < R2) return true;
+  }
+  return false;
+}
+
 // ulp(x) = 2^(e(x) - 52) for |x| in [2^e, 2^(e+1)); 2^-1074 below 2^-1022
 __device__ __forceinline__ double ulp64(double x) {
   const double a = fabs(x);
@@ -86,12 +110,13 @@ __global__ void k_collect_bad(const double2* __restrict__ reps, const unsigned l
 // zone centre.
 __global__ void k_mark_pieces(const double2* __restrict__ cand, const uint8_t* __restrict__ status,
                               int64_t S, int every, int64_t Ls, int64_t npieces,
-                              const double2* __restrict__ bad, int nbad, double R,
+                              const double2* __restrict__ bad, const uint64_t* __restrict__ klo,
+                              const uint64_t* __restrict__ khi, int nbad, double R,
                               uint32_t* __restrict__ flag) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S || status[i] == 1) return;
   const double2 c = cand[i];
-  if (!finite2(c.x, c.y) || !zone_hit(c.x, fabs(c.y), bad, nbad, R)) return;
+  if (!finite2(c.x, c.y) || !zone_hit_k(c.x, fabs(c.y), bad, klo, khi, nbad, R)) return;
   int64_t G = (i * (int64_t)every) / Ls;
   if (G >= npieces) G = npieces - 1;
   flag[G] = 1;
@@ -131,12 +156,13 @@ __global__ void k_piece_ids(const uint32_t* __restrict__ flag, const uint32_t* _
 
 // Main representatives within R of a centre -> polish list.
 __global__ void k_near_reps(const double2* __restrict__ reps, const unsigned long long* n_reps,
-                            int64_t cap, const double2* __restrict__ bad, int nbad, double R,
+                            int64_t cap, const double2* __restrict__ bad, const uint64_t* __restrict__ klo,
+                            const uint64_t* __restrict__ khi, int nbad, double R,
                             uint32_t* __restrict__ near, unsigned long long* nnear, int64_t near_cap) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= cap || u >= (int64_t)*n_reps) return;
   const double2 c = reps[u];
-  if (!zone_hit(c.x, c.y, bad, nbad, R)) return;
+  if (!zone_hit_k(c.x, c.y, bad, klo, khi, nbad, R)) return;
   const unsigned long long k = atomicAdd(nnear, 1ull);
   if ((int64_t)k < near_cap) near[k] = (uint32_t)u;
 }
@@ -800,10 +826,11 @@ __global__ void k_dd_emit_main(const double2* __restrict__ reps, const unsigned 
   const double2 z = reps[u];
   int64_t nz = (int64_t)*nz_dev;
   if (nz > zcap) nz = zcap;
-  int64_t lo = 0, hi = nz;  // zone reps with hi Re < z.x
+  int64_t lo = 0, hi = nz;  // zone reps with hi Re < z.x (compared as integer keys)
+  const uint64_t kz = f64_key0(z.x);
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if (zrx[mid].hi < z.x) lo = mid + 1; else hi = mid;
+    if (f64_key0(zrx[mid].hi) < kz) lo = mid + 1; else hi = mid;
   }
   const int64_t p = (int64_t)mpos[u] + (lo < nz ? (int64_t)zmpos[lo] : (int64_t)*zt);
   const uint8_t im = !type || mis_code < 0 ? 0
@@ -979,9 +1006,9 @@ cudaError_t dd_collect_bad(const double2* reps, const unsigned long long* n_reps
 }
 
 cudaError_t dd_mark_pieces(const double2* cand, const uint8_t* status, int64_t S, int every,
-                           int64_t Ls, int64_t npieces, const double2* bad, int nbad, double R,
-                           uint32_t* flag, cudaStream_t s) {
-  MT_DD_LAUNCH(k_mark_pieces, S, 256, cand, status, S, every, Ls, npieces, bad, nbad, R, flag);
+                           int64_t Ls, int64_t npieces, const double2* bad, const uint64_t* klo,
+                           const uint64_t* khi, int nbad, double R, uint32_t* flag, cudaStream_t s) {
+  MT_DD_LAUNCH(k_mark_pieces, S, 256, cand, status, S, every, Ls, npieces, bad, klo, khi, nbad, R, flag);
   return cudaGetLastError();
 }
 
@@ -998,9 +1025,9 @@ cudaError_t dd_piece_ids(const uint32_t* flag, const uint32_t* pos, int64_t npie
 }
 
 cudaError_t dd_near_reps(const double2* reps, const unsigned long long* n_reps, int64_t cap,
-                         const double2* bad, int nbad, double R, uint32_t* near,
-                         unsigned long long* nnear, int64_t near_cap, cudaStream_t s) {
-  MT_DD_LAUNCH(k_near_reps, cap, 256, reps, n_reps, cap, bad, nbad, R, near, nnear, near_cap);
+                         const double2* bad, const uint64_t* klo, const uint64_t* khi, int nbad, double R,
+                         uint32_t* near, unsigned long long* nnear, int64_t near_cap, cudaStream_t s) {
+  MT_DD_LAUNCH(k_near_reps, cap, 256, reps, n_reps, cap, bad, klo, khi, nbad, R, near, nnear, near_cap);
   return cudaGetLastError();
 }
 

@@ -309,8 +309,8 @@ cudaError_t dd_collect_bad(const double2* reps, const unsigned long long* n_reps
                            const uint8_t* pass, const double* radius, double thr, double2* bad,
                            unsigned long long* nbad, int max_bad, cudaStream_t s);
 cudaError_t dd_mark_pieces(const double2* cand, const uint8_t* status, int64_t S, int every,
-                           int64_t Ls, int64_t npieces, const double2* bad, int nbad, double R,
-                           uint32_t* flag, cudaStream_t s);
+                           int64_t Ls, int64_t npieces, const double2* bad, const uint64_t* klo,
+                           const uint64_t* khi, int nbad, double R, uint32_t* flag, cudaStream_t s);
 cudaError_t dd_mark_pieces_fix(const int2* candq, int64_t S, int every, int64_t Ls, int64_t npieces,
                                const double2* bad, int nbad, double R, uint32_t* flag, cudaStream_t s);
 // streamed splits: walk of chunks [j0, j0 + nch) (starts from index j0 L / every
@@ -326,8 +326,8 @@ cudaError_t launch_piece_valid(const DevCounters* ctr, unsigned long long* snap,
 cudaError_t dd_piece_ids(const uint32_t* flag, const uint32_t* pos, int64_t npieces, int64_t* ids,
                          int64_t ids_cap, cudaStream_t s);
 cudaError_t dd_near_reps(const double2* reps, const unsigned long long* n_reps, int64_t cap,
-                         const double2* bad, int nbad, double R, uint32_t* near,
-                         unsigned long long* nnear, int64_t near_cap, cudaStream_t s);
+                         const double2* bad, const uint64_t* klo, const uint64_t* khi, int nbad, double R,
+                         uint32_t* near, unsigned long long* nnear, int64_t near_cap, cudaStream_t s);
 cudaError_t dd_seeds(const PolyDev& P, double lambda0, int64_t NQ, int shrink, const int64_t* ids,
                      int64_t nb, uint32_t* cnt, uint32_t* off, void* scan_tmp, dd* sx, dd* sy,
                      DevCounters* ctr, cudaStream_t s);
