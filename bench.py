@@ -654,6 +654,7 @@ class Bench:
         self.step()
         torch.cuda.synchronize()
         nbytes = self.d * 16 * (1 if self.roots_lo is None else 2)
+        cev = []
         t0 = time.perf_counter()
         self.e2e_step_ms = []
         for i in range(steps):
@@ -668,14 +669,18 @@ class Bench:
             done.record(main)
             with torch.cuda.stream(cs):
                 cs.wait_event(done)
+                c0 = torch.cuda.Event(enable_timing=True)
+                c0.record(cs)
                 hosts[k][0].copy_(outs[k][0], non_blocking=True)
                 if hosts[k][1] is not None:
                     hosts[k][1].copy_(outs[k][1], non_blocking=True)
-                copied[k] = torch.cuda.Event()
+                copied[k] = torch.cuda.Event(enable_timing=True)
                 copied[k].record(cs)
+                cev.append((c0, copied[k]))
         cs.synchronize()
         main.synchronize()
         dt = (time.perf_counter() - t0) / steps
+        self.e2e_copy_ms = [a.elapsed_time(c) for a, c in cev]
         self.roots, self.roots_lo = keep
         return dt, nbytes + 1024  # + the counters read by the call
 
@@ -738,6 +743,7 @@ def measure(b: Bench, name: str, steps: int, warmup: int, pk: dict, peak_source:
                 "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3,
                 "call_ms": [round(x, 1) for x in getattr(b, "e2e_step_ms", [])],
+                "copy_ms": [round(x, 1) for x in getattr(b, "e2e_copy_ms", [])],
                 "note": "the input is the integer n (no device input); each step's sorted roots (and low parts) "
                         "are copied to pinned host memory inside the timed loop, on a second stream while the "
                         "next step splits into the other of two output buffers; the time ends when the last "
@@ -801,7 +807,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    stream = torch.cuda.current_stream()
+    # every launch on a created (non-blocking) stream, not the legacy default
+    # stream, which would wait for the e2e copy stream's transfers
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     # FMA rates of this GPU, measured here (the ALU rooflines' denominators)
     pk = {"fp64": mt.fma_peak("fp64"), "fp32": mt.fma_peak("fp32")}
     peak_source = ("measured in this run by mt_fma_peak (independent FMA chains on every SM, CUDA events): "
