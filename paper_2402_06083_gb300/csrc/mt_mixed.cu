@@ -1,5 +1,6 @@
 // mt_mixed.cu -- the mixed-precision tier (MT_MIXED): binary32 level-line
-// tracking and early Newton steps, binary64 anchors and binary64 finish.
+// tracking and early Newton steps around float-float anchors (binary64 ones
+// in the seed lift), and a binary64 finish.
 //
 // Why.  The paper runs everything in FP80 (Sec. 6.1) and notes that GPUs
 // offer little beyond FP64 (Sec. 6.4.5).  On a GB300 the binary64 pipe is
@@ -9,9 +10,10 @@
 //
 // How.  Absolute binary32 coordinates cannot resolve the level line at the
 // periods of interest (sub-step spacings reach 1e-11 near c = -2 at n = 20),
-// so the binary32 work is done in perturbation form around a binary64
-// anchor c0 (the published perturbation technique of deep-zoom Mandelbrot
-// renderers): with Z_k = p_k(c0) in binary64 and c = c0 + delta,
+// so the binary32 work is done in perturbation form around an anchor c0
+// (the published perturbation technique of deep-zoom Mandelbrot
+// renderers): with Z_k = p_k(c0) (float-float, ~1e-14; binary64 in the seed
+// lift) and c = c0 + delta,
 //   e_{k+1} = (2 Z_k + e_k) e_k + delta,   p_k(c) = Z_k + e_k,
 //   p'_{k+1}(c) = 2 (Z_k + e_k) p'_k(c) + 1            (binary32),
 // so binary32 carries only the difference from the anchor and its relative
@@ -20,11 +22,13 @@
 //   - Walk: the anchor is re-taken every K sub-steps (a few turns of the
 //     phase) from the current point, so |delta| stays a few turns' length.
 //   - Descent: the anchor is the start point; binary32 Newton steps run to
-//     the binary32 floor, then binary64 Newton steps (normally two) finish
-//     to the binary64 tolerance (eq. Newton).
-// Every anchor orbit and every finishing step is binary64; the chunk-end
-// check of the walk and the count check catch any tracking failure, and the
-// host then repeats the split in plain binary64.
+//     the binary32 floor, then binary64 Newton steps (1.08 a root at p_28),
+//     once per group of end points on the same root, finish to the binary64
+//     tolerance (eq. Newton).
+// The anchors only steer the binary32 steps; every root's digits come from
+// its binary64 finishing steps.  The chunk-end check of the walk and the
+// count check catch any tracking failure, and the host then repeats the
+// split in plain binary64.
 #include "mt_levelline.cuh"
 #include "mt_pert.cuh"
 
