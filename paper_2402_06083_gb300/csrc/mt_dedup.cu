@@ -310,11 +310,17 @@ __global__ void __launch_bounds__(RS_BS) k_rs_hist(const uint64_t* __restrict__ 
       const int64_t i = base + k * 32;
       dg[k] = i < n ? (unsigned)(keys[i] >> shift) & 255u : 256u;
     }
-    // lanes of a warp that share a digit add once (high digits repeat)
+    // BAL (64-bit keys, whose high digits repeat along a warp): lanes that
+    // share a digit add once; else (the finish keys' uniform digits, where
+    // lanes rarely share one) one shared-memory atomic per element
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-      const unsigned peers = rs_peers<BAL>(dg[k]);
-      if (dg[k] < 256u && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[dg[k]], (uint32_t)__popc(peers));
+      if (BAL) {
+        const unsigned peers = rs_peers<true>(dg[k]);
+        if (dg[k] < 256u && (peers & lanemask_lt()) == 0) atomicAdd(&cnt[dg[k]], (uint32_t)__popc(peers));
+      } else if (dg[k] < 256u) {
+        atomicAdd(&cnt[dg[k]], 1u);
+      }
     }
   }
   __syncthreads();
